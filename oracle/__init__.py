@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the VV10 quadrature sums (arXiv 2208.14639, Sec. II).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and by the
+benchmark's CPU-baseline leg, never by the library.  It shares no code with the CUDA
+path; both sides only share the seeded input generator.
+
+The arithmetic lives in ``vv10_oracle.c`` (plain C, FP64, Neumaier-compensated sums,
+OpenMP over rows); this module compiles it with gcc (``-O2 -fopenmp``, no fast-math,
+no FMA contraction) and wraps it with ctypes.  Every wrapper takes FP64 numpy arrays in
+original point indexing; ``rows`` selects a subset of output rows (full j sums), which
+is how large grids are checked on sampled outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vv10_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, f"liborc_vv10_{platform.machine()}.so")
+_lock = threading.Lock()
+_lib = None
+
+B_DEFAULT = 6.0
+C_DEFAULT = 0.01
+RHO_CUT_DEFAULT = 1e-10
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99",
+               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build()
+    lib = ctypes.CDLL(path)
+    D = ctypes.c_double
+    I64 = ctypes.c_int64
+    I32 = ctypes.c_int32
+    P = ctypes.c_void_p
+    lib.orc_beta.restype = D
+    lib.orc_beta.argtypes = [D]
+    lib.orc_phi.restype = D
+    lib.orc_phi.argtypes = [D, D, D, D, D]
+    lib.orc_point_props.restype = None
+    lib.orc_point_props.argtypes = [I64, P, P, D, D, P]
+    lib.orc_energy.argtypes = [I64, P, P, P, P, D, D, D, P]
+    lib.orc_pair_sums.argtypes = [I64, P, P, P, P, D, D, D, I64, P, P]
+    lib.orc_potential.argtypes = [I64, P, P, P, P, D, D, D, I64, P, P, P, P]
+    lib.orc_hessian_contract.argtypes = [I64, P, P, P, P, D, D, D, I32, P, P, I64, P, P, P]
+    lib.orc_point_grad.argtypes = [I64, P, P, P, P, D, D, D, I64, P, P]
+    lib.orc_atom_grad.argtypes = [I64, P, P, P, P, P, I32, D, D, D, P]
+    lib.orc_atom_resolved.argtypes = [I64, P, P, P, P, P, I32, D, D, D, I64, P, P, P, P]
+    lib.orc_num_threads.restype = ctypes.c_int
+    lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+    for name in ("orc_energy", "orc_pair_sums", "orc_potential", "orc_hessian_contract",
+                 "orc_point_grad", "orc_atom_grad", "orc_atom_resolved"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _rows(rows, n):
+    if rows is None:
+        return None, n
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    if r.size and (r.min() < 0 or r.max() >= n):
+        raise IndexError("row index out of range")
+    return r, int(r.size)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise MemoryError(f"oracle {what} failed (rc={rc})")
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    _load().orc_set_num_threads(int(k))
+
+
+def beta(b: float = B_DEFAULT) -> float:
+    return float(_load().orc_beta(b))
+
+
+def phi(om_i, ka_i, om_j, ka_j, R2) -> float:
+    return float(_load().orc_phi(om_i, ka_i, om_j, ka_j, R2))
+
+
+POINT_FIELDS = ("gamma", "omega", "kappa", "omega_rho", "omega_gamma", "kappa_rho",
+                "omega_rhorho", "omega_rhogamma", "omega_gammagamma", "kappa_rhorho")
+
+
+def point_props(rho, grad_rho, b=B_DEFAULT, C=C_DEFAULT) -> dict:
+    rho = _f64(rho)
+    grad = _f64(grad_rho).reshape(-1, 3)
+    out = np.zeros((rho.size, 11))
+    _load().orc_point_props(rho.size, _ptr(rho), _ptr(grad), b, C, _ptr(out))
+    return {k: out[:, q].copy() for q, k in enumerate(POINT_FIELDS)}
+
+
+def _sys(coords, weights, rho, grad_rho):
+    xyz = _f64(coords).reshape(-1, 3)
+    w = _f64(weights)
+    r = _f64(rho)
+    g = _f64(grad_rho).reshape(-1, 3)
+    n = w.size
+    if not (xyz.shape[0] == n and r.size == n and g.shape[0] == n):
+        raise ValueError("inconsistent point arrays")
+    return n, xyz, w, r, g
+
+
+def energy(coords, weights, rho, grad_rho, b=B_DEFAULT, C=C_DEFAULT,
+           rho_cut=RHO_CUT_DEFAULT) -> float:
+    """E^VV10 from the quadrature definition (double loop)."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    e = np.zeros(1)
+    _check(_load().orc_energy(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), b, C, rho_cut,
+                              _ptr(e)), "energy")
+    return float(e[0])
+
+
+def pair_sums(coords, weights, rho, grad_rho, rows=None, b=B_DEFAULT, C=C_DEFAULT,
+              rho_cut=RHO_CUT_DEFAULT) -> dict:
+    """Row sums E_i, U_i, W_i, A_i, B_i, C_i (j = i included)."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    rr, nr = _rows(rows, n)
+    out = np.zeros((nr, 6))
+    _check(_load().orc_pair_sums(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), b, C, rho_cut, nr,
+                                 _ptr(rr), _ptr(out)), "pair_sums")
+    return {k: out[:, q].copy() for q, k in enumerate("EUWABC")}
+
+
+def potential(coords, weights, rho, grad_rho, rows=None, b=B_DEFAULT, C=C_DEFAULT,
+              rho_cut=RHO_CUT_DEFAULT):
+    """(energy or None, vrho = f^rho, vgamma = f^gamma).  Energy only when rows is None."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    rr, nr = _rows(rows, n)
+    vr = np.zeros(nr)
+    vg = np.zeros(nr)
+    e = np.zeros(1)
+    _check(_load().orc_potential(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), b, C, rho_cut, nr,
+                                 _ptr(rr), _ptr(vr), _ptr(vg),
+                                 _ptr(e) if rr is None else None), "potential")
+    return (float(e[0]) if rr is None else None), vr, vg
+
+
+def hessian_contract(coords, weights, rho, grad_rho, rho_t, grad_rho_t, rows=None,
+                     b=B_DEFAULT, C=C_DEFAULT, rho_cut=RHO_CUT_DEFAULT):
+    """(f^{rho,t}, f^{gamma,t}), each P x n_rows, from the printed pair coefficients."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    rt = _f64(rho_t).reshape(-1, n)
+    P = rt.shape[0]
+    gt = _f64(grad_rho_t).reshape(P, n, 3)
+    rr, nr = _rows(rows, n)
+    fr = np.zeros((P, nr))
+    fg = np.zeros((P, nr))
+    _check(_load().orc_hessian_contract(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), b, C, rho_cut,
+                                        P, _ptr(rt), _ptr(gt), nr, _ptr(rr), _ptr(fr), _ptr(fg)),
+           "hessian_contract")
+    return fr, fg
+
+
+def point_grad(coords, weights, rho, grad_rho, rows=None, b=B_DEFAULT, C=C_DEFAULT,
+               rho_cut=RHO_CUT_DEFAULT) -> np.ndarray:
+    """dE/dr_i for every (selected) grid point, n_rows x 3."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    rr, nr = _rows(rows, n)
+    out = np.zeros((nr, 3))
+    _check(_load().orc_point_grad(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), b, C, rho_cut, nr,
+                                  _ptr(rr), _ptr(out)), "point_grad")
+    return out
+
+
+def atom_grad(coords, weights, rho, grad_rho, atom_of_point, n_atom, b=B_DEFAULT,
+              C=C_DEFAULT, rho_cut=RHO_CUT_DEFAULT) -> np.ndarray:
+    """E^A_gr (first form of Eq. grad_gr), n_atom x 3."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    aop = np.ascontiguousarray(np.asarray(atom_of_point, dtype=np.int32))
+    out = np.zeros((n_atom, 3))
+    _check(_load().orc_atom_grad(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), _ptr(aop), n_atom, b,
+                                 C, rho_cut, _ptr(out)), "atom_grad")
+    return out
+
+
+def atom_resolved(coords, weights, rho, grad_rho, atom_of_point, n_atom, rows=None,
+                  b=B_DEFAULT, C=C_DEFAULT, rho_cut=RHO_CUT_DEFAULT):
+    """(E^{Bgr}, U^{Bgr}, W^{Bgr}), each n_rows x n_atom x 3 (Eq. EiBgr and after)."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    aop = np.ascontiguousarray(np.asarray(atom_of_point, dtype=np.int32))
+    rr, nr = _rows(rows, n)
+    oE = np.zeros((nr, n_atom, 3))
+    oU = np.zeros((nr, n_atom, 3))
+    oW = np.zeros((nr, n_atom, 3))
+    _check(_load().orc_atom_resolved(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), _ptr(aop), n_atom,
+                                     b, C, rho_cut, nr, _ptr(rr), _ptr(oE), _ptr(oU), _ptr(oW)),
+           "atom_resolved")
+    return oE, oU, oW

@@ -1,0 +1,368 @@
+"""Seeded synthetic molecule-shaped quadrature grids, densities and trial densities.
+
+This module produces the *inputs* of the VV10 double grid sum.  It stands in for what a
+quantum-chemistry code hands the nonlocal kernel: an atom-centred quadrature grid
+(Sec. II.A: Becke-style atom-centred quadrature, points r_i and weights w_i), the
+ground-state density rho_i and its gradient on that grid (Eq. for omega/kappa need
+rho and gamma = |grad rho|^2), and the trial densities (rho^t_i, grad rho^t_i) of the
+contracted orbital Hessian (Eq. frhot and the definition of rho^t, gamma^t that follows
+it).  The paper's own data sets and Q-Chem grids are not available; every molecule,
+grid and density here is synthetic and seeded.
+
+It contains none of the VV10 arithmetic (no omega, kappa, Phi or pair sum): both the
+CUDA path and the CPU oracle consume its arrays, and neither imports the other.
+
+Recipe (all lengths in bohr, FP64):
+* radial grid: Euler-Maclaurin with the Murray-Handy-Laming map,
+  r_k = R_A k^2/(n+1-k)^2, w_k = 2 R_A^3 (n+1) k^5/(n+1-k)^7 (r^2 dr included);
+* angular grid: Fibonacci sphere, z_m = 1-(2m+1)/n, phi_m = m*pi*(3-sqrt 5), w = 4 pi/n;
+* Becke fuzzy-cell partition (three smoothing iterations, no size adjustment) evaluated
+  over the owning atom plus its 8 nearest other atoms (exact Becke for <= 9 atoms);
+  weights are then fixed inputs;
+* density: per atom three normalised s-Gaussians, exponents 0.3, sqrt(0.3*20), 20,
+  each holding Z/3 electrons; analytic gradient;
+* trial densities: analytic nuclear-displacement derivatives d rho/d R_{A,c}
+  and their spatial gradients, P = 3 N_atom, ordered t = 3A + c.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+BOHR_PER_ANGSTROM = 1.8897261246
+Z_OF = {"H": 1, "C": 6, "N": 7, "O": 8}
+# Radial scale R_A of the Murray-Handy-Laming map (bohr); a free choice of this recipe.
+RADIAL_SCALE = {"H": 1.0, "C": 1.5, "N": 1.4, "O": 1.3}
+GAUSS_EXPONENTS = (0.3, math.sqrt(0.3 * 20.0), 20.0)
+BECKE_NEIGHBOURS = 8
+
+
+@dataclasses.dataclass
+class Molecule:
+    symbols: List[str]
+    coords: np.ndarray  # (n_atom, 3) bohr
+
+    @property
+    def n_atom(self) -> int:
+        return len(self.symbols)
+
+    @property
+    def charges(self) -> np.ndarray:
+        return np.array([Z_OF[s] for s in self.symbols], dtype=np.float64)
+
+
+@dataclasses.dataclass
+class GridDensity:
+    """Grid points with the density on them (all FP64, C-contiguous)."""
+
+    coords: np.ndarray         # (N, 3)
+    weights: np.ndarray        # (N,)
+    rho: np.ndarray            # (N,)
+    grad_rho: np.ndarray       # (N, 3)
+    atom_of_point: np.ndarray  # (N,) int32, points are contiguous per atom
+    molecule: Molecule
+
+    @property
+    def n(self) -> int:
+        return int(self.weights.shape[0])
+
+
+# ----------------------------------------------------------------------------- molecules
+
+def _random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform random SO(3) matrix from a normalised Gaussian quaternion."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def _random_unit(rng: np.random.Generator) -> np.ndarray:
+    v = rng.normal(size=3)
+    return v / np.linalg.norm(v)
+
+
+def water() -> Molecule:
+    """O at the origin, two H at 0.96 A with a 104.5 degree angle, in the xy plane."""
+    d = 0.96 * BOHR_PER_ANGSTROM
+    half = math.radians(104.5) / 2
+    coords = np.array([[0.0, 0.0, 0.0],
+                       [d * math.sin(half), d * math.cos(half), 0.0],
+                       [-d * math.sin(half), d * math.cos(half), 0.0]])
+    return Molecule(["O", "H", "H"], coords)
+
+
+def water_cluster(rng: np.random.Generator, n_water: int = 6) -> Molecule:
+    """Rigid waters with O on a puckered ring, neighbouring O-O = 2.8 +- 0.2 A.
+
+    Each water is rotated by a uniform random rotation about its O; a rotation is
+    redrawn while any intermolecular H-H or O-H distance is below 1.5 A.
+    """
+    w = water()
+    # Ring radius giving a 2.8 A side for a regular n-gon, perturbed per vertex.
+    side = 2.8 * BOHR_PER_ANGSTROM
+    radius = side / (2 * math.sin(math.pi / n_water))
+    o_pos = []
+    for k in range(n_water):
+        r = radius + rng.uniform(-0.2, 0.2) * BOHR_PER_ANGSTROM
+        ang = 2 * math.pi * k / n_water
+        z = (0.25 if k % 2 == 0 else -0.25) * BOHR_PER_ANGSTROM
+        o_pos.append(np.array([r * math.cos(ang), r * math.sin(ang), z]))
+    symbols: List[str] = []
+    coords: List[np.ndarray] = []
+    min_d = 1.5 * BOHR_PER_ANGSTROM
+    for k in range(n_water):
+        for _ in range(1000):
+            rot = _random_rotation(rng)
+            cand = (w.coords @ rot.T) + o_pos[k]
+            ok = True
+            for s_new, c_new in zip(w.symbols, cand):
+                for s_old, c_old in zip(symbols, coords):
+                    if s_new == "O" and s_old == "O":
+                        continue
+                    if np.linalg.norm(c_new - c_old) < min_d:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if ok:
+                break
+        symbols.extend(w.symbols)
+        coords.extend(list(cand))
+    return Molecule(symbols, np.array(coords))
+
+
+def random_chon(rng: np.random.Generator, n_atom: int) -> Molecule:
+    """Random tree-grown C/H/N/O molecule (element odds 0.4/0.4/0.1/0.1).
+
+    Each new atom is bonded to a random existing atom at U(1.0, 1.5) A in a random
+    direction; a placement closer than 1.0 A to any other atom is redrawn.
+    """
+    elems = ["C", "H", "N", "O"]
+    probs = [0.4, 0.4, 0.1, 0.1]
+    symbols = [str(rng.choice(elems, p=probs))]
+    coords = [np.zeros(3)]
+    lo, hi, dmin = (x * BOHR_PER_ANGSTROM for x in (1.0, 1.5, 1.0))
+    while len(symbols) < n_atom:
+        parent = coords[int(rng.integers(len(coords)))]
+        cand = parent + rng.uniform(lo, hi) * _random_unit(rng)
+        if min(np.linalg.norm(cand - c) for c in coords) < dmin * 0.999:
+            continue
+        symbols.append(str(rng.choice(elems, p=probs)))
+        coords.append(cand)
+    c = np.array(coords)
+    return Molecule(symbols, c - c.mean(axis=0))
+
+
+def fragment_cluster(rng: np.random.Generator, n_frag: int = 4, frag_atoms: int = 6) -> Molecule:
+    """n_frag random CHON fragments whose closest inter-fragment atoms are 3-4 A apart."""
+    frags = [random_chon(rng, frag_atoms) for _ in range(n_frag)]
+    symbols = list(frags[0].symbols)
+    coords = frags[0].coords.copy()
+    for f in frags[1:]:
+        target = rng.uniform(3.0, 4.0) * BOHR_PER_ANGSTROM
+        direction = _random_unit(rng)
+        rot = _random_rotation(rng)
+        fc = f.coords @ rot.T
+
+        def gap(t: float) -> float:
+            moved = fc + t * direction
+            d = np.linalg.norm(moved[:, None, :] - coords[None, :, :], axis=-1)
+            return float(d.min())
+
+        t_lo, t_hi = 0.0, 10.0
+        while gap(t_hi) < target:
+            t_hi *= 2
+        for _ in range(60):  # bisection on the translation length
+            mid = 0.5 * (t_lo + t_hi)
+            if gap(mid) < target:
+                t_lo = mid
+            else:
+                t_hi = mid
+        symbols.extend(f.symbols)
+        coords = np.vstack([coords, fc + t_hi * direction])
+    return Molecule(symbols, coords - coords.mean(axis=0))
+
+
+# ----------------------------------------------------------------------------- grids
+
+def radial_grid(n: int, scale: float):
+    k = np.arange(1, n + 1, dtype=np.float64)
+    r = scale * k ** 2 / (n + 1 - k) ** 2
+    w = 2.0 * scale ** 3 * (n + 1) * k ** 5 / (n + 1 - k) ** 7
+    return r, w
+
+
+def fibonacci_sphere(n: int):
+    m = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * m + 1.0) / n
+    phi = m * math.pi * (3.0 - math.sqrt(5.0))
+    rxy = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    u = np.stack([rxy * np.cos(phi), rxy * np.sin(phi), z], axis=1)
+    return u, np.full(n, 4.0 * math.pi / n)
+
+
+def _becke_s(mu: np.ndarray) -> np.ndarray:
+    p = mu
+    for _ in range(3):
+        p = 1.5 * p - 0.5 * p ** 3
+    return 0.5 * (1.0 - p)
+
+
+def _becke_fraction(points: np.ndarray, owner: int, atoms: np.ndarray) -> np.ndarray:
+    """Becke cell weight of atom `owner` at each point, over owner + nearest others."""
+    n_atom = atoms.shape[0]
+    d = np.linalg.norm(points[:, None, :] - atoms[None, :, :], axis=-1)  # (n, n_atom)
+    if n_atom == 1:
+        return np.ones(points.shape[0])
+    k = min(BECKE_NEIGHBOURS, n_atom - 1)
+    d_other = d.copy()
+    d_other[:, owner] = np.inf
+    nbr = np.argpartition(d_other, k - 1, axis=1)[:, :k]                # (n, k)
+    idx = np.concatenate([np.full((points.shape[0], 1), owner), nbr], axis=1)  # (n, m)
+    dm = np.take_along_axis(d, idx, axis=1)                              # (n, m)
+    r_atoms = np.linalg.norm(atoms[:, None, :] - atoms[None, :, :], axis=-1)
+    rab = r_atoms[idx[:, :, None], idx[:, None, :]]                      # (n, m, m)
+    m = idx.shape[1]
+    eye = np.eye(m, dtype=bool)[None]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mu = (dm[:, :, None] - dm[:, None, :]) / rab
+    s = np.where(eye, 1.0, _becke_s(np.clip(np.nan_to_num(mu), -1.0, 1.0)))
+    cell = np.prod(s, axis=2)                                            # (n, m)
+    return cell[:, 0] / cell.sum(axis=1)
+
+
+def molecular_grid(mol: Molecule, n_rad: int, n_ang: int, chunk: int = 100_000):
+    """Atom-centred grid: (coords (N,3), weights (N,), atom_of_point (N,) int32)."""
+    u, wa = fibonacci_sphere(n_ang)
+    pts, wts, own = [], [], []
+    for a, (sym, centre) in enumerate(zip(mol.symbols, mol.coords)):
+        r, wr = radial_grid(n_rad, RADIAL_SCALE[sym])
+        p = (r[:, None, None] * u[None, :, :]).reshape(-1, 3) + centre
+        w = (wr[:, None] * wa[None, :]).reshape(-1)
+        frac = np.empty(p.shape[0])
+        for s0 in range(0, p.shape[0], chunk):
+            frac[s0:s0 + chunk] = _becke_fraction(p[s0:s0 + chunk], a, mol.coords)
+        pts.append(p)
+        wts.append(w * frac)
+        own.append(np.full(p.shape[0], a, dtype=np.int32))
+    return np.concatenate(pts), np.concatenate(wts), np.concatenate(own)
+
+
+# ----------------------------------------------------------------------------- densities
+
+def _gauss_coeffs(z: float) -> np.ndarray:
+    a = np.array(GAUSS_EXPONENTS)
+    return (z / 3.0) * (a / math.pi) ** 1.5
+
+
+def density(mol: Molecule, points: np.ndarray):
+    """rho (N,) and grad rho (N,3) of the sum of atomic s-Gaussians."""
+    rho = np.zeros(points.shape[0])
+    grad = np.zeros_like(points)
+    alphas = np.array(GAUSS_EXPONENTS)
+    for z, centre in zip(mol.charges, mol.coords):
+        d = points - centre
+        r2 = np.einsum("ij,ij->i", d, d)
+        for c, a in zip(_gauss_coeffs(z), alphas):
+            e = c * np.exp(-a * r2)
+            rho += e
+            grad += (-2.0 * a * e)[:, None] * d
+    return rho, grad
+
+
+def trial_densities(mol: Molecule, points: np.ndarray, atoms: Optional[Sequence[int]] = None,
+                    dtype=np.float64):
+    """Nuclear-displacement trial densities.
+
+    rho^{A,c}(r) = d rho / d R_{A,c} = sum_k c_k 2 a_k (r_c - R_{A,c}) exp(-a_k |r-R_A|^2),
+    d_d rho^{A,c} = sum_k c_k 2 a_k exp(...) [delta_cd - 2 a_k (r_c-R_{A,c})(r_d-R_{A,d})].
+    Returns rho_t (P, N) and grad_rho_t (P, N, 3) with t = 3*A + c.
+    """
+    atoms = list(range(mol.n_atom)) if atoms is None else list(atoms)
+    n = points.shape[0]
+    P = 3 * len(atoms)
+    rho_t = np.zeros((P, n), dtype=dtype)
+    grad_t = np.zeros((P, n, 3), dtype=dtype)
+    alphas = np.array(GAUSS_EXPONENTS)
+    eye = np.eye(3)
+    for ia, a_idx in enumerate(atoms):
+        z, centre = mol.charges[a_idx], mol.coords[a_idx]
+        d = points - centre
+        r2 = np.einsum("ij,ij->i", d, d)
+        rt = np.zeros((n, 3))
+        gt = np.zeros((n, 3, 3))
+        for c, a in zip(_gauss_coeffs(z), alphas):
+            e = 2.0 * a * c * np.exp(-a * r2)
+            rt += e[:, None] * d
+            gt += e[:, None, None] * (eye[None] - 2.0 * a * d[:, :, None] * d[:, None, :])
+        for cc in range(3):
+            rho_t[3 * ia + cc] = rt[:, cc]
+            grad_t[3 * ia + cc] = gt[:, cc, :]
+    return rho_t, grad_t
+
+
+# ----------------------------------------------------------------------------- configs
+
+def make_system(mol: Molecule, n_rad: int, n_ang: int) -> GridDensity:
+    coords, weights, own = molecular_grid(mol, n_rad, n_ang)
+    rho, grad = density(mol, coords)
+    return GridDensity(np.ascontiguousarray(coords), np.ascontiguousarray(weights),
+                       np.ascontiguousarray(rho), np.ascontiguousarray(grad),
+                       np.ascontiguousarray(own), mol)
+
+
+SEED_BASE = 20220830
+
+
+def config_water(n_rad: int = 30, n_ang: int = 110) -> GridDensity:
+    """Water, 30 x 110 points per atom = 9,900 points."""
+    return make_system(water(), n_rad, n_ang)
+
+
+def config_water_hexamer(n_rad: int = 50, n_ang: int = 194, seed: int = SEED_BASE + 1) -> GridDensity:
+    """Six rigid waters, 50 x 194 points per atom = 174,600 points (P = 54)."""
+    return make_system(water_cluster(np.random.default_rng(seed)), n_rad, n_ang)
+
+
+def config_chon60(n_rad: int = 75, n_ang: int = 302, seed: int = SEED_BASE + 2,
+                  n_atom: int = 60) -> GridDensity:
+    """60-atom random CHON molecule, 75 x 302 points per atom = 1,359,000 points (P = 180)."""
+    return make_system(random_chon(np.random.default_rng(seed), n_atom), n_rad, n_ang)
+
+
+def config_batch(n_mol: int = 64, n_rad: int = 50, n_ang: int = 194, seed: int = SEED_BASE + 3,
+                 atom_range=(3, 30)) -> List[GridDensity]:
+    """Batch of random CHON molecules with U{3..30} atoms, 50 x 194 points per atom."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(atom_range[0], atom_range[1] + 1, size=n_mol)
+    return [make_system(random_chon(rng, int(s)), n_rad, n_ang) for s in sizes]
+
+
+def config_cluster24(n_rad: int = 30, n_ang: int = 139, seed: int = SEED_BASE + 4) -> GridDensity:
+    """Four 6-atom CHON fragments 3-4 A apart, 30 x 139 points per atom = 100,080 points."""
+    return make_system(fragment_cluster(np.random.default_rng(seed)), n_rad, n_ang)
+
+
+def random_points(n: int, seed: int, spread: float = 2.0, n_atom: int = 2) -> GridDensity:
+    """Tiny random system for brute-force tests: a few atoms, n scattered points.
+
+    Points are drawn around the atoms with positive random weights, so every pair
+    quantity is generic (no symmetry, no coincident points).
+    """
+    rng = np.random.default_rng(seed)
+    atoms = rng.normal(scale=1.5, size=(n_atom, 3))
+    syms = [["O", "C", "N", "H"][k % 4] for k in range(n_atom)]
+    mol = Molecule(syms, atoms)
+    own = np.sort(rng.integers(0, n_atom, size=n)).astype(np.int32)
+    coords = atoms[own] + rng.normal(scale=spread, size=(n, 3)) * 0.5
+    weights = rng.uniform(0.05, 0.5, size=n)
+    rho, grad = density(mol, coords)
+    return GridDensity(coords, weights, rho, grad, own, mol)

@@ -1,0 +1,31 @@
+"""The oracle reproduces its stored water values (written by tests/golden/make_golden.py,
+which calls only oracle/); this catches a change in the oracle's arithmetic or a
+machine-dependent build (x86 here, aarch64 on the GPU host)."""
+import json
+import os
+
+import numpy as np
+
+from paper_2208_14639_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_water_golden(oracle_mod):
+    with open(os.path.join(HERE, "golden", "water_9900.json")) as f:
+        gold = json.load(f)
+    g = synth.config_water()
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    assert int((g.rho >= 1e-10).sum()) == gold["n_kept"]
+    e, _, _ = oracle_mod.potential(*args)
+    assert abs(e - gold["energy"]) <= 1e-12 * abs(gold["energy"])
+    rows = gold["rows"]
+    _, vr, vg = oracle_mod.potential(*args, rows=rows)
+    np.testing.assert_allclose(vr, gold["vrho"], rtol=1e-11)
+    np.testing.assert_allclose(vg, gold["vgamma"], rtol=1e-11)
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt, rows=rows)
+    np.testing.assert_allclose(fr, gold["f_rho_t"], rtol=1e-10, atol=1e-13 * np.abs(fr).max())
+    np.testing.assert_allclose(fg, gold["f_gamma_t"], rtol=1e-10, atol=1e-13 * np.abs(fg).max())
+    pg = oracle_mod.point_grad(*args, rows=rows)
+    np.testing.assert_allclose(pg, gold["point_grad"], rtol=1e-10, atol=1e-14)

@@ -1,0 +1,328 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks it against a value fixed
+independently (a physical limit the paper states, an equivalent published definition,
+a closed form, a finite difference of the oracle's own *energy*, an exact invariant).
+A dropped term, a wrong sign or index, or a swapped g/g' in any oracle routine fails at
+least one of them.  The paper prints no VV10 numbers for any system, so no test pins
+against printed values.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2208_14639_gb300 import synth
+
+B, C = 6.0, 0.01
+
+
+def _sys(seed=3, n=9, n_atom=2):
+    g = synth.random_points(n, seed=seed, n_atom=n_atom)
+    return g, (g.coords, g.weights, g.rho, g.grad_rho)
+
+
+# --------------------------------------------------------------------- point quantities
+
+@pytest.mark.parametrize("rho", [1e-6, 1e-3, 0.1, 3.0, 200.0])
+def test_beta_from_uniform_gas_limit(oracle_mod, rho):
+    """Sec. II.A: beta makes E^VV10 vanish for a uniform density.
+
+    For constant rho (gamma = 0) the energy per volume is rho*beta + 1/2 rho^2 * int Phi d^3R,
+    so beta = -1/2 rho * int_0^inf Phi(R) 4 pi R^2 dR, independent of rho.  The integral is
+    done by quadrature over the oracle's own omega, kappa and Phi; this pins beta, kappa,
+    the gamma = 0 part of omega and the form of Phi at once.
+    """
+    p = oracle_mod.point_props([rho], [[0.0, 0.0, 0.0]], b=B, C=C)
+    om, ka = p["omega"][0], p["kappa"][0]
+    f = lambda R: oracle_mod.phi(om, ka, om, ka, R * R) * 4.0 * math.pi * R * R
+    scale = math.sqrt(ka / om)
+    val = integrate.quad(f, 0, scale, epsabs=0, epsrel=1e-13, limit=400)[0]
+    val += integrate.quad(f, scale, np.inf, epsabs=0, epsrel=1e-13, limit=400)[0]
+    beta_uniform = -0.5 * rho * val
+    assert beta_uniform == pytest.approx(oracle_mod.beta(B), rel=1e-9)
+
+
+def test_kappa_is_b_vF2_over_wp(oracle_mod):
+    """kappa = b (3 pi/2)(rho/9pi)^(1/6) equals b v_F^2 / omega_p with v_F = (3 pi^2 rho)^(1/3)
+    and omega_p = (4 pi rho)^(1/2), the original VV10 definition of kappa."""
+    rho = np.logspace(-10, 3, 27)
+    p = oracle_mod.point_props(rho, np.zeros((rho.size, 3)), b=B, C=C)
+    vf = (3.0 * math.pi ** 2 * rho) ** (1.0 / 3.0)
+    wp = np.sqrt(4.0 * math.pi * rho)
+    np.testing.assert_allclose(p["kappa"], B * vf ** 2 / wp, rtol=1e-13)
+
+
+def test_omega_is_sqrt_wg2_plus_wp2_over_3(oracle_mod):
+    """omega = sqrt(omega_g^2 + omega_p^2/3) with omega_g^2 = C |grad rho / rho|^4 and
+    omega_p^2 = 4 pi rho; gamma^2/rho^4 is |grad rho/rho|^4 when gamma = |grad rho|^2."""
+    rng = np.random.default_rng(5)
+    rho = 10.0 ** rng.uniform(-9, 2, 40)
+    grad = rng.normal(size=(40, 3)) * rho[:, None] * 10.0 ** rng.uniform(-1, 1.3, (40, 1))
+    p = oracle_mod.point_props(rho, grad, b=B, C=C)
+    s = np.linalg.norm(grad, axis=1) / rho
+    np.testing.assert_allclose(p["omega"], np.sqrt(C * s ** 4 + 4.0 * math.pi * rho / 3.0), rtol=1e-13)
+    np.testing.assert_allclose(p["gamma"], np.linalg.norm(grad, axis=1) ** 2, rtol=1e-14)
+
+
+def test_point_derivatives_by_finite_differences(oracle_mod):
+    """d omega/d rho, d omega/d gamma, d kappa/d rho and the second derivatives used by the
+    potential and the Hessian terms, against central differences of omega and kappa."""
+    rng = np.random.default_rng(11)
+    for _ in range(12):
+        rho = 10.0 ** rng.uniform(-6, 1.5)
+        gam = (rho * 10.0 ** rng.uniform(-0.5, 1.2)) ** 2
+
+        def ok(r, gm):
+            p = oracle_mod.point_props([r], [[math.sqrt(gm), 0.0, 0.0]], b=B, C=C)
+            return np.array([p["omega"][0], p["kappa"][0], p["omega_rho"][0],
+                             p["omega_gamma"][0], p["kappa_rho"][0]])
+
+        base = oracle_mod.point_props([rho], [[math.sqrt(gam), 0.0, 0.0]], b=B, C=C)
+        hr, hg = 1e-5 * rho, 1e-5 * gam
+        dr = (ok(rho + hr, gam) - ok(rho - hr, gam)) / (2 * hr)
+        dg = (ok(rho, gam + hg) - ok(rho, gam - hg)) / (2 * hg)
+        assert dr[0] == pytest.approx(base["omega_rho"][0], rel=1e-7)
+        assert dg[0] == pytest.approx(base["omega_gamma"][0], rel=1e-7)
+        assert dr[1] == pytest.approx(base["kappa_rho"][0], rel=1e-7)
+        # second derivatives: tolerance on the natural scale (first derivative / variable)
+        s_rr = abs(base["omega_rho"][0]) / rho + abs(base["omega_rhorho"][0])
+        s_rg = abs(base["omega_gamma"][0]) / rho + abs(base["omega_rhogamma"][0])
+        s_gg = abs(base["omega_gamma"][0]) / gam + abs(base["omega_gammagamma"][0])
+        assert abs(dr[2] - base["omega_rhorho"][0]) < 1e-6 * s_rr
+        assert abs(dg[2] - base["omega_rhogamma"][0]) < 1e-6 * s_rg
+        assert abs(dr[3] - base["omega_rhogamma"][0]) < 1e-6 * s_rg
+        assert abs(dg[3] - base["omega_gammagamma"][0]) < 1e-6 * s_gg
+        assert dr[4] == pytest.approx(base["kappa_rhorho"][0], rel=1e-7)
+
+
+# --------------------------------------------------------------------- kernel Phi
+
+def test_phi_symmetry_and_closed_forms(oracle_mod):
+    """Phi_ij = Phi_ji (g'_ij = g_ji); Phi_ii = -3/(4 kappa^3) at R = 0; and the
+    large-R limit -3 / (2 omega_i omega_j (omega_i + omega_j) R^6)."""
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        oi, oj = rng.uniform(0.1, 50, 2)
+        ki, kj = rng.uniform(0.3, 20, 2)
+        R2 = rng.uniform(0, 30)
+        assert oracle_mod.phi(oi, ki, oj, kj, R2) == pytest.approx(oracle_mod.phi(oj, kj, oi, ki, R2), rel=1e-15)
+        assert oracle_mod.phi(oi, ki, oj, ki, 0.0) == pytest.approx(-3.0 / (4.0 * ki ** 3), rel=1e-15)
+        R2 = 1e8
+        asym = -3.0 / (2.0 * oi * oj * (oi + oj) * R2 ** 3)
+        assert oracle_mod.phi(oi, ki, oj, kj, R2) == pytest.approx(asym, rel=1e-5)
+
+
+def test_one_and_two_point_energies(oracle_mod):
+    """E = sum_i w_i rho_i (beta + 1/2 sum_j w_j rho_j Phi_ij) with j = i included,
+    written out for one and for two points."""
+    g, _ = _sys(seed=8, n=2)
+    p = oracle_mod.point_props(g.rho, g.grad_rho)
+    beta = oracle_mod.beta()
+    c = g.weights * g.rho
+    e1 = oracle_mod.energy(g.coords[:1], g.weights[:1], g.rho[:1], g.grad_rho[:1])
+    assert e1 == pytest.approx(c[0] * beta + 0.5 * c[0] ** 2 * (-3.0 / (4.0 * p["kappa"][0] ** 3)), rel=1e-14)
+    R2 = float(np.sum((g.coords[0] - g.coords[1]) ** 2))
+    phi = lambda a, b_, r2: oracle_mod.phi(p["omega"][a], p["kappa"][a], p["omega"][b_], p["kappa"][b_], r2)
+    expect = beta * c.sum() + 0.5 * (c[0] ** 2 * phi(0, 0, 0.0) + c[1] ** 2 * phi(1, 1, 0.0)
+                                     + 2.0 * c[0] * c[1] * phi(0, 1, R2))
+    assert oracle_mod.energy(*_sys(seed=8, n=2)[1]) == pytest.approx(expect, rel=1e-14)
+
+
+def test_rotation_and_translation_invariance(oracle_mod):
+    g, args = _sys(seed=4, n=12)
+    e0 = oracle_mod.energy(*args)
+    th = 0.7
+    rot = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1.0]])
+    rot = rot @ np.array([[1, 0, 0], [0, math.cos(0.3), -math.sin(0.3)], [0, math.sin(0.3), math.cos(0.3)]])
+    e1 = oracle_mod.energy(g.coords @ rot.T + 1.7, g.weights, g.rho, g.grad_rho @ rot.T)
+    assert e1 == pytest.approx(e0, rel=1e-13)
+
+
+def test_cutoff_drops_points(oracle_mod):
+    """Points below rho_cut take part in no sum and get zero outputs."""
+    g, args = _sys(seed=9, n=10)
+    rho = g.rho.copy()
+    rho[3] = 1e-12
+    full = oracle_mod.energy(g.coords, g.weights, rho, g.grad_rho)
+    keep = np.arange(10) != 3
+    sub = oracle_mod.energy(g.coords[keep], g.weights[keep], rho[keep], g.grad_rho[keep])
+    assert full == pytest.approx(sub, rel=1e-15)
+    _, vr, vg = oracle_mod.potential(g.coords, g.weights, rho, g.grad_rho)
+    assert vr[3] == 0.0 and vg[3] == 0.0
+
+
+# --------------------------------------------------------------------- first derivatives
+
+def test_potential_is_energy_derivative(oracle_mod):
+    """w_k f^rho_k = dE/d rho_k and 2 w_k f^gamma_k grad rho_k = dE/d grad rho_k
+    (Sec. II.A), checked at every point by central differences of the energy."""
+    g, args = _sys(seed=3, n=9)
+    _, vr, vg = oracle_mod.potential(*args)
+    for k in range(g.n):
+        h = 1e-5 * g.rho[k]
+        rp, rm = g.rho.copy(), g.rho.copy()
+        rp[k] += h
+        rm[k] -= h
+        fd = (oracle_mod.energy(g.coords, g.weights, rp, g.grad_rho)
+              - oracle_mod.energy(g.coords, g.weights, rm, g.grad_rho)) / (2 * h)
+        assert fd == pytest.approx(g.weights[k] * vr[k], rel=1e-7)
+        for d in range(3):
+            hh = 1e-4 * np.linalg.norm(g.grad_rho[k])
+            gp, gm = g.grad_rho.copy(), g.grad_rho.copy()
+            gp[k, d] += hh
+            gm[k, d] -= hh
+            fd = (oracle_mod.energy(g.coords, g.weights, g.rho, gp)
+                  - oracle_mod.energy(g.coords, g.weights, g.rho, gm)) / (2 * hh)
+            an = 2 * g.weights[k] * vg[k] * g.grad_rho[k, d]
+            assert fd == pytest.approx(an, rel=1e-5, abs=1e-9 * abs(g.weights[k] * vr[k]))
+
+
+def test_weight_derivative(oracle_mod):
+    """dE/dw_k = rho_k (beta + E_k) (the E^A_w term of Sec. II.A)."""
+    g, args = _sys(seed=6, n=9)
+    Ek = oracle_mod.pair_sums(*args)["E"]
+    for k in range(g.n):
+        h = 1e-6 * g.weights[k]
+        wp, wm = g.weights.copy(), g.weights.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd = (oracle_mod.energy(g.coords, wp, g.rho, g.grad_rho)
+              - oracle_mod.energy(g.coords, wm, g.rho, g.grad_rho)) / (2 * h)
+        assert fd == pytest.approx(g.rho[k] * (oracle_mod.beta() + Ek[k]), rel=1e-8)
+
+
+def test_point_gradient_is_energy_derivative(oracle_mod):
+    g, args = _sys(seed=12, n=10)
+    pg = oracle_mod.point_grad(*args)
+    scale = np.abs(pg).max()
+    for k in range(g.n):
+        for d in range(3):
+            h = 1e-5
+            cp, cm = g.coords.copy(), g.coords.copy()
+            cp[k, d] += h
+            cm[k, d] -= h
+            fd = (oracle_mod.energy(cp, g.weights, g.rho, g.grad_rho)
+                  - oracle_mod.energy(cm, g.weights, g.rho, g.grad_rho)) / (2 * h)
+            assert fd == pytest.approx(pg[k, d], rel=1e-6, abs=1e-8 * scale)
+    np.testing.assert_allclose(pg.sum(axis=0), 0.0, atol=1e-15 * np.abs(pg).sum())
+
+
+def test_atom_gradient_first_form(oracle_mod):
+    """E^A_gr from the first form of Eq. grad_gr equals the derivative of E when all points
+    of atom A move rigidly, equals the sum of the point gradients over i in A, and the
+    atom terms sum to zero (translational invariance)."""
+    g, args = _sys(seed=14, n=16, n_atom=3)
+    ag = oracle_mod.atom_grad(*args, g.atom_of_point, 3)
+    pg = oracle_mod.point_grad(*args)
+    for A in range(3):
+        np.testing.assert_allclose(ag[A], pg[g.atom_of_point == A].sum(axis=0), rtol=1e-11,
+                                   atol=1e-14 * np.abs(ag).max())
+        for d in range(3):
+            h = 1e-5
+            cp, cm = g.coords.copy(), g.coords.copy()
+            cp[g.atom_of_point == A, d] += h
+            cm[g.atom_of_point == A, d] -= h
+            fd = (oracle_mod.energy(cp, g.weights, g.rho, g.grad_rho)
+                  - oracle_mod.energy(cm, g.weights, g.rho, g.grad_rho)) / (2 * h)
+            assert fd == pytest.approx(ag[A, d], rel=1e-6, abs=1e-8 * np.abs(ag).max())
+    np.testing.assert_allclose(ag.sum(axis=0), 0.0, atol=1e-13 * np.abs(ag).max())
+
+
+def test_simplified_gradient_form_disagrees(oracle_mod):
+    """Reading of Eq. grad_gr: its second, 'simplified' form (keeping only the omega_i
+    terms, times 2) is not the derivative of E; the oracle uses the first form."""
+    g, args = _sys(seed=14, n=16, n_atom=3)
+    p = oracle_mod.point_props(g.rho, g.grad_rho)
+    c = g.weights * g.rho
+    A = 0
+    inA = g.atom_of_point == A
+    simp = np.zeros(3)
+    for i in range(g.n):
+        for j in range(g.n):
+            if inA[i] == inA[j]:
+                continue
+            R2 = float(np.sum((g.coords[i] - g.coords[j]) ** 2))
+            gi = p["omega"][i] * R2 + p["kappa"][i]
+            gj = p["omega"][j] * R2 + p["kappa"][j]
+            phi = oracle_mod.phi(p["omega"][i], p["kappa"][i], p["omega"][j], p["kappa"][j], R2)
+            if inA[i]:
+                simp += -2 * c[i] * c[j] * phi * (p["omega"][i] / gi + p["omega"][i] / (gi + gj)) * (g.coords[i] - g.coords[j])
+            else:
+                simp += -2 * c[i] * c[j] * phi * (p["omega"][j] / gj + p["omega"][j] / (gi + gj)) * (g.coords[j] - g.coords[i])
+    ag = oracle_mod.atom_grad(*args, g.atom_of_point, 3)
+    assert np.abs(simp - ag[A]).max() > 1e-3 * np.abs(ag[A]).max()
+
+
+def test_atom_resolved_terms_are_derivatives(oracle_mod):
+    """E_i^{Bgr}, U_i^{Bgr}, W_i^{Bgr} are the derivatives of E_i, U_i, W_i when atom B's
+    points move rigidly, for i not in B (the sums of Eq. EiBgr) and i in B (minus the
+    other atoms' terms)."""
+    g, args = _sys(seed=21, n=14, n_atom=3)
+    oE, oU, oW = oracle_mod.atom_resolved(*args, g.atom_of_point, 3)
+    h = 1e-5
+    for B_ in range(3):
+        for d in range(3):
+            cp, cm = g.coords.copy(), g.coords.copy()
+            cp[g.atom_of_point == B_, d] += h
+            cm[g.atom_of_point == B_, d] -= h
+            sp = oracle_mod.pair_sums(cp, g.weights, g.rho, g.grad_rho)
+            sm = oracle_mod.pair_sums(cm, g.weights, g.rho, g.grad_rho)
+            for key, arr in (("E", oE), ("U", oU), ("W", oW)):
+                fd = (sp[key] - sm[key]) / (2 * h)
+                scale = np.abs(arr[:, :, d]).max()
+                np.testing.assert_allclose(arr[:, B_, d], fd, rtol=1e-5, atol=1e-8 * scale)
+
+
+# --------------------------------------------------------------------- Hessian contraction
+
+def _trials(g, P=None):
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    return rt, gt
+
+
+def test_hessian_contraction_is_potential_derivative(oracle_mod):
+    """f^{rho,t}, f^{gamma,t} (Eq. frhot with the printed f^{rho rho} ... f^{gamma gamma},
+    including their delta_ij/w_i parts) are the directional derivatives of f^rho, f^gamma
+    along (rho^t, grad rho^t)."""
+    g, args = _sys(seed=3, n=11, n_atom=2)
+    rt, gt = _trials(g)
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    eps = 1e-5
+    for t in range(rt.shape[0]):
+        _, vrp, vgp = oracle_mod.potential(g.coords, g.weights, g.rho + eps * rt[t], g.grad_rho + eps * gt[t])
+        _, vrm, vgm = oracle_mod.potential(g.coords, g.weights, g.rho - eps * rt[t], g.grad_rho - eps * gt[t])
+        np.testing.assert_allclose(fr[t], (vrp - vrm) / (2 * eps), rtol=1e-6, atol=1e-7 * np.abs(fr[t]).max())
+        np.testing.assert_allclose(fg[t], (vgp - vgm) / (2 * eps), rtol=1e-6, atol=1e-7 * np.abs(fg[t]).max())
+
+
+def test_hessian_symmetry_and_linearity(oracle_mod):
+    """<t1, H t2> = <t2, H t1> with <t, v> = sum_i w_i (rho^t_i v^rho_i + 2 gamma^t_i v^gamma_i),
+    and the contraction is linear in the trial."""
+    g, args = _sys(seed=5, n=15, n_atom=3)
+    rng = np.random.default_rng(0)
+    rt = rng.normal(size=(3, g.n)) * g.rho
+    gt = rng.normal(size=(3, g.n, 3)) * np.linalg.norm(g.grad_rho, axis=1)[None, :, None]
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    gam_t = np.einsum("nd,tnd->tn", g.grad_rho, gt)
+    ip = lambda a, b_: float(np.sum(g.weights * (rt[a] * fr[b_] + 2 * gam_t[a] * fg[b_])))
+    for a, b_ in ((0, 1), (0, 2), (1, 2)):
+        assert ip(a, b_) == pytest.approx(ip(b_, a), rel=1e-11)
+    fr2, fg2 = oracle_mod.hessian_contract(*args, 2.0 * rt[:1] - 3.0 * rt[1:2], 2.0 * gt[:1] - 3.0 * gt[1:2])
+    np.testing.assert_allclose(fr2[0], 2 * fr[0] - 3 * fr[1], rtol=1e-11, atol=1e-14 * np.abs(fr).max())
+    np.testing.assert_allclose(fg2[0], 2 * fg[0] - 3 * fg[1], rtol=1e-11, atol=1e-14 * np.abs(fg).max())
+
+
+def test_row_sampling_matches_full(oracle_mod):
+    g, args = _sys(seed=7, n=20, n_atom=2)
+    rows = np.array([17, 2, 9])
+    full = oracle_mod.pair_sums(*args)
+    part = oracle_mod.pair_sums(*args, rows=rows)
+    for k in "EUWABC":
+        np.testing.assert_array_equal(part[k], full[k][rows])
+    rt, gt = _trials(g)
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    fr2, fg2 = oracle_mod.hessian_contract(*args, rt, gt, rows=rows)
+    np.testing.assert_array_equal(fr2, fr[:, rows])
+    np.testing.assert_array_equal(fg2, fg[:, rows])

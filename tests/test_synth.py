@@ -1,0 +1,54 @@
+"""Self-checks of the seeded synthetic input generator (no VV10 arithmetic here)."""
+import numpy as np
+import pytest
+
+from paper_2208_14639_gb300 import synth
+
+
+def test_water_grid_integrates_density():
+    g = synth.config_water()
+    assert g.n == 9900
+    assert float(g.weights @ g.rho) == pytest.approx(10.0, rel=1e-3)
+    assert np.all(g.weights >= 0)
+    assert np.all(np.diff(g.atom_of_point) >= 0)
+
+
+def test_radial_and_angular_rules():
+    r, w = synth.radial_grid(60, 1.3)
+    # int_0^inf r^2 exp(-r^2) dr = sqrt(pi)/4
+    assert float(w @ np.exp(-r ** 2)) == pytest.approx(np.sqrt(np.pi) / 4, rel=1e-8)
+    u, wa = synth.fibonacci_sphere(302)
+    np.testing.assert_allclose(np.linalg.norm(u, axis=1), 1.0, rtol=1e-14)
+    assert wa.sum() == pytest.approx(4 * np.pi)
+
+
+def test_density_gradient_and_trials_by_finite_differences():
+    g = synth.random_points(6, seed=1, n_atom=2)
+    mol = g.molecule
+    h = 1e-6
+    rho0, grad0 = synth.density(mol, g.coords)
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        fd = (synth.density(mol, g.coords + e)[0] - synth.density(mol, g.coords - e)[0]) / (2 * h)
+        np.testing.assert_allclose(grad0[:, d], fd, rtol=1e-6, atol=1e-12)
+    rt, gt = synth.trial_densities(mol, g.coords)
+    for A in range(mol.n_atom):
+        for c in range(3):
+            m_p = synth.Molecule(mol.symbols, mol.coords.copy())
+            m_m = synth.Molecule(mol.symbols, mol.coords.copy())
+            m_p.coords[A, c] += h
+            m_m.coords[A, c] -= h
+            rp, gp = synth.density(m_p, g.coords)
+            rm, gm = synth.density(m_m, g.coords)
+            np.testing.assert_allclose(rt[3 * A + c], (rp - rm) / (2 * h), rtol=1e-6, atol=1e-12)
+            np.testing.assert_allclose(gt[3 * A + c], (gp - gm) / (2 * h), rtol=1e-6, atol=1e-11)
+
+
+def test_configs_are_seeded():
+    a = synth.config_cluster24(n_rad=6, n_ang=14)
+    b = synth.config_cluster24(n_rad=6, n_ang=14)
+    np.testing.assert_array_equal(a.coords, b.coords)
+    assert a.molecule.n_atom == 24
+    batch = synth.config_batch(n_mol=3, n_rad=4, n_ang=6)
+    assert all(3 <= m.molecule.n_atom <= 30 for m in batch)
