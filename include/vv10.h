@@ -1,0 +1,180 @@
+/*
+ * vv10.h -- C ABI of a single-GPU (sm_103a) library for the VV10 nonlocal-correlation
+ * double grid sum and its analytic derivatives (Liang, Feng, Liu, Head-Gordon,
+ * "Analytic second derivatives of VV10-containing functionals", arXiv 2208.14639).
+ *
+ * Notation follows the paper (Sec. II): for a grid point i, rho_i, grad rho_i,
+ * gamma_i = |grad rho_i|^2, weight w_i, position r_i; for a pair, R^2 = |r_i - r_j|^2,
+ * g = omega_i R^2 + kappa_i, g' = omega_j R^2 + kappa_j, Phi_ij = -3/(2 g g' (g + g')).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments are caller-owned DEVICE pointers (e.g. torch CUDA tensors' data_ptr),
+ *    C-contiguous, FP64 unless noted; the library never frees or keeps them after the
+ *    call returns (it copies what it needs into handle-owned device memory).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    All work is enqueued on it; a call returns once its work is enqueued, except where
+ *    it says it synchronises.
+ *  - Outputs are written in the caller's original point indexing; points dropped by the
+ *    density cutoff (rho_i < rho_cut) get zeros.
+ *  - All inner sums over j include j = i (Phi_ii = -3/(4 kappa_i^3)); with that reading
+ *    the delta_ij/w_i terms of Sec. II.B are exactly the Hessian of the quadrature energy.
+ *  - Errors are reported by return code only; the library never aborts or prints.  A
+ *    device-side condition detected asynchronously (a bounded wait that gave up, an
+ *    invalid atom index, a non-finite output) is reported by the next call that
+ *    synchronises (vv10_energy_potential, vv10_prepare_points, vv10_sync).
+ *  - A handle is not thread-safe; use one handle per host thread / stream.
+ */
+#ifndef VV10_H
+#define VV10_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VV10_OK = 0,
+    VV10_ERR_INVALID_ARG = 1,  /* bad pointer, size, parameter, or call order            */
+    VV10_ERR_CUDA = 2,         /* a CUDA runtime/driver call failed (see vv10_last_error) */
+    VV10_ERR_OOM = 3,          /* device allocation failed                                */
+    VV10_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                      */
+    VV10_ERR_NONFINITE = 5,    /* a NaN/Inf was produced in an output                     */
+    VV10_ERR_UNSUPPORTED = 6   /* valid request outside this build's limits               */
+} vv10_status;
+
+typedef enum {
+    VV10_FP64 = 0,          /* all pair arithmetic and sums in FP64                          */
+    VV10_MIXED_TF32X3 = 1,  /* FP32 pair tiles; Hessian contraction on tensor cores as split
+                               TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate; FP64 point
+                               precompute and FP64 cross-tile / final reductions            */
+    VV10_MIXED_BF16X3 = 2   /* as above with split BF16 operands for the contraction         */
+} vv10_precision;
+
+/* VV10 parameters b and C (Sec. II.A) and the density cutoff below which a point is
+ * dropped from every sum (the paper does not state one; 1e-10 is used throughout). */
+typedef struct {
+    double b;
+    double C;
+    double rho_cut;
+} vv10_params;
+
+typedef struct vv10_ctx* vv10_handle;
+
+/* Limits of this build. */
+#define VV10_MAX_ATOMS 4096
+#define VV10_MAX_TRIALS 4096
+
+/* Create a handle bound to CUDA device `device`.  Allocates no large buffers yet.
+ * Errors: INVALID_ARG (h NULL, bad device), CUDA. */
+vv10_status vv10_create(vv10_handle* h, int device);
+
+/* Release the handle and every device buffer it owns (synchronises the device's work
+ * on those buffers first).  NULL is accepted. */
+vv10_status vv10_destroy(vv10_handle h);
+
+/* Static English description of a status code. */
+const char* vv10_status_string(vv10_status s);
+
+/* Description of the last error seen on this handle ("" if none). */
+const char* vv10_last_error(vv10_handle h);
+
+/* Per-point precompute (Sec. II.A definitions of gamma, omega, kappa and beta, and the
+ * derivatives of omega and kappa used by f^rho, f^gamma (Sec. II.A) and by f^{rho rho},
+ * f^{gamma rho}, f^{rho gamma}, f^{gamma gamma} (Sec. II.B)), in FP64.
+ *   n              number of grid points (>= 1)
+ *   xyz            n x 3 point coordinates r_i (bohr)
+ *   w              n quadrature weights w_i
+ *   rho            n densities rho_i
+ *   grad_rho       n x 3 density gradients
+ *   atom_of_point  n int32 atom index of each point ("i in A" of Eqs. grad_gr, EiBgr),
+ *                  values in [0, n_atom); may be NULL (then n_atom must be 0 and the
+ *                  atom outputs of vv10_coord_grad are unavailable)
+ *   n_atom         number of atoms, 0 <= n_atom <= VV10_MAX_ATOMS
+ *   prm            b > 0, C >= 0, rho_cut > 0
+ *   n_kept         host out: number of points with rho >= rho_cut
+ * Replaces any previously prepared point set (and invalidates cached sums).  Synchronises
+ * `stream` once (to return n_kept).  Errors: INVALID_ARG (null pointer, n < 1, bad
+ * params, atom index out of range, non-finite input), UNSUPPORTED (n_atom too large),
+ * OOM, CUDA. */
+vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, const double* w,
+                                const double* rho, const double* grad_rho,
+                                const int32_t* atom_of_point, int32_t n_atom, vv10_params prm,
+                                int64_t* n_kept, void* stream);
+
+/* Energy and potential (Sec. II.A):
+ *   E^VV10 = sum_i w_i rho_i (beta + E_i / 2),       E_i = sum_j w_j rho_j Phi_ij
+ *   f^rho_i = beta + E_i + rho_i (kappa'_i U_i + omega_rho,i W_i),
+ *   f^gamma_i = rho_i omega_gamma,i W_i,
+ * with U_i, W_i the pair sums defined there.  f^rho and f^gamma are per unit weight:
+ * dE/d rho_i = w_i f^rho_i and dE/d(grad rho_i) = 2 w_i f^gamma_i grad rho_i.
+ *   prec      VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ *   energy    HOST pointer, receives E (may be NULL: then the call does not synchronise)
+ *   vrho      n device out, f^rho (may be NULL)
+ *   vgamma    n device out, f^gamma (may be NULL)
+ * Caches E_i, U_i, W_i in the handle for vv10_hessian_contract / vv10_weight_grad.
+ * Errors: INVALID_ARG (no prepared points), OOM, CUDA, TIMEOUT, NONFINITE. */
+vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* energy,
+                                  double* vrho, double* vgamma, void* stream);
+
+/* Nonlocal response contracted with P trial densities (Sec. II.B, Eq. frhot):
+ *   f^{rho,t}_i   = sum_j w_j (f^{rho rho}_ij rho^t_j + 2 f^{rho gamma}_ij gamma^t_j)
+ *   f^{gamma,t}_i = sum_j w_j (f^{gamma rho}_ij rho^t_j + 2 f^{gamma gamma}_ij gamma^t_j)
+ * with gamma^t_j = grad rho_j . grad rho^t_j (formed here), including the delta_ij/w_i
+ * terms built from U_i, W_i, A_i, B_i, C_i.  These are the directional derivatives of
+ * f^rho, f^gamma along (rho^t, grad rho^t).
+ *   P            number of trials, 1 <= P <= VV10_MAX_TRIALS
+ *   rho_t        P x n trial densities (row t contiguous over points)
+ *   grad_rho_t   P x n x 3 trial density gradients
+ *   f_rho_t      P x n device out
+ *   f_gamma_t    P x n device out
+ * vv10_energy_potential must have been called on the current point set first (it
+ * provides U_i, W_i); otherwise INVALID_ARG.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
+ * CUDA, TIMEOUT. */
+vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P,
+                                  const double* rho_t, const double* grad_rho_t,
+                                  double* f_rho_t, double* f_gamma_t, void* stream);
+
+/* Grid-position derivative terms (Sec. II.A Eq. grad_gr, first form; Sec. II.B Eq. EiBgr):
+ *   grad_points  n x 3 out (may be NULL): dE/dr_i with rho, grad rho and w held fixed,
+ *                = -2 w_i rho_i sum_j w_j rho_j Phi_ij D_ij (r_i - r_j),
+ *                D_ij = omega_i/g + omega_j/g' + (omega_i + omega_j)/(g + g')
+ *   grad_atoms   n_atom x 3 out (may be NULL): E^A_gr = sum_{i in A} dE/dr_i
+ *   EUW_Bgr      3 x n x n_atom x 3 out (may be NULL): E_i^{Bgr}, U_i^{Bgr}, W_i^{Bgr};
+ *                for i not in B the sums over j in B of Eq. EiBgr and the two that
+ *                follow it, for i in B minus the sum over the other atoms
+ * Atom outputs need atom_of_point at prepare time (else INVALID_ARG).  Needs no earlier
+ * call other than vv10_prepare_points.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_points,
+                            double* grad_atoms, double* EUW_Bgr, void* stream);
+
+/* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
+ * by the last vv10_energy_potential call.  dEdw: n device out. */
+vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
+
+/* Synchronise `stream` and report any deferred device-side error on this handle. */
+vv10_status vv10_sync(vv10_handle h, void* stream);
+
+/* Tile-shape override for the pair-sum kernels (used by the autotuner; the paper has no
+ * counterpart).  what = mode + 3 * fp64 with mode 0 = energy/potential sums, 1 = the
+ * A/B/C sums of the Hessian diagonal, 2 = coordinate gradient; rows_per_thread in
+ * {1, 2, 4} (FP64: {1, 2}), 0 = back to the default; n_split = number of j-splits,
+ * 0 = derived from the SM count.  Errors: INVALID_ARG. */
+vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split);
+
+/* Failure-injection hooks for tests (the paper has no counterpart).
+ *   VV10_DEBUG_FAIL_ALLOC  value k > 0: the k-th device allocation from now fails (OOM)
+ *   VV10_DEBUG_STALL_COPY  value 1: in the next pair-sum launch one CTA never issues its
+ *                          tile copies, so its bounded wait gives up after about one
+ *                          second and the call that synchronises returns TIMEOUT.
+ * Errors: INVALID_ARG. */
+#define VV10_DEBUG_FAIL_ALLOC 1
+#define VV10_DEBUG_STALL_COPY 2
+vv10_status vv10_debug_inject(vv10_handle h, int what, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VV10_H */

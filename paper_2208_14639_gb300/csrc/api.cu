@@ -1,0 +1,567 @@
+// C ABI of the VV10 library: handle, argument validation, buffer management and the
+// orchestration of the kernels of each entry point (declared in include/vv10.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.hpp"
+#include "vv10.h"
+#include "vv10_internal.hpp"
+
+using namespace vv10;
+
+// ---------------------------------------------------------------- helpers
+
+void vv10_ctx::set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(last_error, sizeof(last_error), fmt, ap);
+    va_end(ap);
+}
+
+vv10_status vv10_ctx::cuda_fail(cudaError_t e, const char* where) {
+    set_error("%s: %s", where, cudaGetErrorString(e));
+    cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+    return e == cudaErrorMemoryAllocation ? VV10_ERR_OOM : VV10_ERR_CUDA;
+}
+
+vv10_status vv10_ctx::ensure(DevBuf& b, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return VV10_OK;
+    if (debug_fail_alloc > 0 && --debug_fail_alloc == 0) {
+        set_error("allocation of %zu bytes for %s failed (injected)", bytes, what);
+        return VV10_ERR_OOM;
+    }
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
+        return VV10_ERR_OOM;
+    }
+    b.bytes = bytes;
+    return VV10_OK;
+}
+
+void vv10_ctx::release_all() {
+    DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
+                      &soa, &r64a, &r64b, &r32a, &r32b, &sumE, &sumU, &sumW, &sumA, &sumB,
+                      &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &dev_err};
+    for (DevBuf* b : bufs) {
+        if (b->p) cudaFree(b->p);
+        b->p = nullptr;
+        b->bytes = 0;
+    }
+    if (h_pinned) cudaFreeHost(h_pinned);
+    h_pinned = nullptr;
+}
+
+// Pointer must be device-accessible memory of this handle's device (device or managed).
+static bool device_ptr_ok(const void* p, int device) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+static bool aligned(const void* p, size_t a) {
+    return (reinterpret_cast<uintptr_t>(p) % a) == 0;
+}
+
+#define VV10_CHECK_HANDLE(h)                          \
+    do {                                              \
+        if (!(h)) return VV10_ERR_INVALID_ARG;        \
+    } while (0)
+
+#define VV10_CUDA(h, expr, where)                        \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return (h)->cuda_fail(e_, where); \
+    } while (0)
+
+#define VV10_TRY(expr)                        \
+    do {                                      \
+        vv10_status s_ = (expr);              \
+        if (s_ != VV10_OK) return s_;         \
+    } while (0)
+
+vv10_status vv10_ctx::bind() {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return VV10_OK;
+}
+
+// Read and clear the device error word (synchronises the stream).
+vv10_status vv10_ctx::check_device_errors(cudaStream_t st) {
+    int* herr = reinterpret_cast<int*>(h_pinned) + 8;
+    VV10_CUDA(this, cudaMemcpyAsync(herr, dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st),
+              "read error word");
+    VV10_CUDA(this, cudaMemsetAsync(dev_err.p, 0, sizeof(int), st), "clear error word");
+    VV10_CUDA(this, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    const int v = *herr;
+    if (v & DEVERR_TIMEOUT) {
+        set_error("a bounded device-side wait gave up");
+        return VV10_ERR_TIMEOUT;
+    }
+    if (v & DEVERR_BAD_ATOM) {
+        set_error("atom_of_point holds an index outside [0, n_atom)");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (v & DEVERR_BAD_INPUT) {
+        set_error("non-finite coordinate, weight, density or gradient in the input");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (v & DEVERR_NONFINITE) {
+        set_error("a non-finite value was produced in an output");
+        return VV10_ERR_NONFINITE;
+    }
+    return VV10_OK;
+}
+
+PointsDev vv10_ctx::points() const { return P; }
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char* vv10_status_string(vv10_status s) {
+    switch (s) {
+        case VV10_OK: return "ok";
+        case VV10_ERR_INVALID_ARG: return "invalid argument";
+        case VV10_ERR_CUDA: return "CUDA error";
+        case VV10_ERR_OOM: return "out of device memory";
+        case VV10_ERR_TIMEOUT: return "device-side wait timed out";
+        case VV10_ERR_NONFINITE: return "non-finite output";
+        case VV10_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* vv10_last_error(vv10_handle h) { return h ? h->last_error : "null handle"; }
+
+vv10_status vv10_create(vv10_handle* out, int device) {
+    if (!out) return VV10_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VV10_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return VV10_ERR_INVALID_ARG;
+    vv10_ctx* h = new (std::nothrow) vv10_ctx();
+    if (!h) return VV10_ERR_OOM;
+    h->device = device;
+    vv10_status s = h->bind();
+    if (s != VV10_OK) {
+        delete h;
+        return s;
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return VV10_ERR_CUDA;
+    }
+    h->n_sm = prop.multiProcessorCount;
+    h->cc_major = prop.major;
+    h->cc_minor = prop.minor;
+    e = cudaMallocHost(&h->h_pinned, 256);
+    if (e != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return VV10_ERR_OOM;
+    }
+    s = h->ensure(h->dev_err, 64, "error word");
+    if (s == VV10_OK) {
+        e = cudaMemset(h->dev_err.p, 0, 64);
+        if (e != cudaSuccess) s = h->cuda_fail(e, "cudaMemset");
+    }
+    if (s != VV10_OK) {
+        h->release_all();
+        delete h;
+        return s;
+    }
+    *out = h;
+    return VV10_OK;
+}
+
+vv10_status vv10_destroy(vv10_handle h) {
+    if (!h) return VV10_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    h->release_all();
+    delete h;
+    return VV10_OK;
+}
+
+vv10_status vv10_sync(vv10_handle h, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    VV10_TRY(h->bind());
+    return h->check_device_errors(static_cast<cudaStream_t>(stream));
+}
+
+vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, const double* w,
+                                const double* rho, const double* grad_rho,
+                                const int32_t* atom_of_point, int32_t n_atom, vv10_params prm,
+                                int64_t* n_kept, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    if (n < 1 || !n_kept) {
+        h->set_error("n must be >= 1 and n_kept non-NULL");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (!(prm.b > 0.0) || !(prm.C >= 0.0) || !(prm.rho_cut > 0.0) || !std::isfinite(prm.b) ||
+        !std::isfinite(prm.C) || !std::isfinite(prm.rho_cut)) {
+        h->set_error("parameters need b > 0, C >= 0, rho_cut > 0 (finite)");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (n_atom < 0 || (atom_of_point == nullptr) != (n_atom == 0)) {
+        h->set_error("atom_of_point and n_atom must be given together");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (n_atom > VV10_MAX_ATOMS) {
+        h->set_error("n_atom %d exceeds VV10_MAX_ATOMS", n_atom);
+        return VV10_ERR_UNSUPPORTED;
+    }
+    VV10_TRY(h->bind());
+    const void* ptrs[] = {xyz, w, rho, grad_rho};
+    for (const void* q : ptrs)
+        if (!device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+            h->set_error("input arrays must be 8-byte aligned device pointers on device %d",
+                         h->device);
+            return VV10_ERR_INVALID_ARG;
+        }
+    if (atom_of_point && (!device_ptr_ok(atom_of_point, h->device) || !aligned(atom_of_point, 4))) {
+        h->set_error("atom_of_point must be a device pointer");
+        return VV10_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->prepared = false;
+    h->have_euw = false;
+    h->have_abc = false;
+
+    const int nblk = prepare_nblk(n);
+    const int n_keys = (n_atom > 0 ? n_atom : 1) + 1;
+    const int64_t M = static_cast<int64_t>(n_keys) * nblk;
+    VV10_TRY(h->ensure(h->prep_hist, sizeof(int32_t) * M, "prepare histogram"));
+    VV10_TRY(h->ensure(h->prep_offs, sizeof(int64_t) * (M + n_keys + 1), "prepare offsets"));
+    VV10_TRY(h->ensure(h->prep_bbox, sizeof(double) * 6 * nblk, "prepare bbox"));
+    VV10_TRY(h->ensure(h->prep_small, 64, "prepare scalars"));
+    PrepareScratch ps;
+    ps.hist = static_cast<int32_t*>(h->prep_hist.p);
+    ps.offs = static_cast<int64_t*>(h->prep_offs.p);
+    ps.bbox_part = static_cast<double*>(h->prep_bbox.p);
+    ps.center = static_cast<double*>(h->prep_small.p);
+    ps.nk_dev = reinterpret_cast<int64_t*>(static_cast<double*>(h->prep_small.p) + 4);
+    int* err = static_cast<int*>(h->dev_err.p);
+    VV10_CUDA(h, launch_prepare_count(n, xyz, w, rho, grad_rho, atom_of_point, n_atom, prm.rho_cut,
+                                      ps, err, st),
+              "prepare count");
+    int64_t* hnk = reinterpret_cast<int64_t*>(h->h_pinned);
+    VV10_CUDA(h, cudaMemcpyAsync(hnk, ps.nk_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+              "read n_kept");
+    VV10_TRY(h->check_device_errors(st));  // synchronises
+    const int64_t nk = *hnk;
+    const int64_t nk_pad = ((nk + kJTile - 1) / kJTile) * kJTile;
+    const int64_t cap = nk_pad > 0 ? nk_pad : kJTile;
+    const int n_seg = (n_atom > 0 ? n_atom : 1) + 1;
+    VV10_TRY(h->ensure(h->orig, sizeof(int64_t) * cap, "kept index map"));
+    VV10_TRY(h->ensure(h->seg, sizeof(int64_t) * n_seg, "atom segments"));
+    VV10_TRY(h->ensure(h->atom_k, sizeof(int32_t) * cap, "kept atoms"));
+    VV10_TRY(h->ensure(h->soa, sizeof(double) * F_COUNT * cap, "point arrays"));
+    VV10_TRY(h->ensure(h->r64a, sizeof(double4) * cap, "FP64 records"));
+    VV10_TRY(h->ensure(h->r64b, sizeof(double4) * cap, "FP64 records"));
+    VV10_TRY(h->ensure(h->r32a, sizeof(float4) * cap, "FP32 records"));
+    VV10_TRY(h->ensure(h->r32b, sizeof(float4) * cap, "FP32 records"));
+    VV10_CUDA(h, launch_prepare_scatter(n, xyz, w, rho, grad_rho, atom_of_point, n_atom,
+                                        prm.rho_cut, prm.b, prm.C, ps, nk, nk_pad,
+                                        static_cast<int64_t*>(h->orig.p),
+                                        static_cast<int64_t*>(h->seg.p),
+                                        static_cast<int32_t*>(h->atom_k.p),
+                                        static_cast<double*>(h->soa.p),
+                                        static_cast<double4*>(h->r64a.p),
+                                        static_cast<double4*>(h->r64b.p),
+                                        static_cast<float4*>(h->r32a.p),
+                                        static_cast<float4*>(h->r32b.p), st),
+              "prepare scatter");
+    PointsDev& P = h->P;
+    P.n = n;
+    P.nk = nk;
+    P.nk_pad = nk_pad;
+    P.n_atom = n_atom;
+    P.beta = std::pow(3.0 / (prm.b * prm.b), 0.75) / 32.0;  // beta of Sec. II.A
+    P.orig = static_cast<const int64_t*>(h->orig.p);
+    P.seg = static_cast<const int64_t*>(h->seg.p);
+    P.atom = static_cast<const int32_t*>(h->atom_k.p);
+    const double* f = static_cast<const double*>(h->soa.p);
+    P.w = f + F_W * cap;
+    P.rho = f + F_RHO * cap;
+    P.gx = f + F_GX * cap;
+    P.gy = f + F_GY * cap;
+    P.gz = f + F_GZ * cap;
+    P.om = f + F_OM * cap;
+    P.ka = f + F_KA * cap;
+    P.om_r = f + F_OMR * cap;
+    P.om_g = f + F_OMG * cap;
+    P.ka_r = f + F_KAR * cap;
+    P.om_rr = f + F_OMRR * cap;
+    P.om_rg = f + F_OMRG * cap;
+    P.om_gg = f + F_OMGG * cap;
+    P.ka_rr = f + F_KARR * cap;
+    P.r64a = static_cast<const double4*>(h->r64a.p);
+    P.r64b = static_cast<const double4*>(h->r64b.p);
+    P.r32a = static_cast<const float4*>(h->r32a.p);
+    P.r32b = static_cast<const float4*>(h->r32b.p);
+    h->soa_ld = cap;
+    h->prm = prm;
+    h->prepared = true;
+    *n_kept = nk;
+    return VV10_OK;
+}
+
+}  // extern "C"
+
+// SoA arrays are laid out with leading dimension soa_ld (= nk_pad, or kJTile when empty);
+// kernels index them with nk_pad, so keep the two equal.
+static_assert(kJTile > 0, "tile");
+
+vv10_status vv10_ctx::require_prepared() {
+    if (!prepared) {
+        set_error("vv10_prepare_points has not been called on this handle");
+        return VV10_ERR_INVALID_ARG;
+    }
+    return VV10_OK;
+}
+
+vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_split_out) {
+    PairLaunch cfg;
+    const TileChoice tc = tiles_for(mode, fp64);
+    cfg.rows_per_thread = tc.rows_per_thread;
+    cfg.n_split = tc.n_split > 0 ? tc.n_split : pairsum_default_split(P, fp64, cfg.rows_per_thread, n_sm);
+    if (debug_stall) {
+        cfg.stall = 1;
+        debug_stall = 0;
+    }
+    // normalise the split count the same way the launcher does
+    const int64_t ntile = P.nk_pad / kJTile;
+    int req = cfg.n_split < 1 ? 1 : cfg.n_split;
+    if (req > ntile) req = static_cast<int>(ntile > 0 ? ntile : 1);
+    const int64_t tps = ntile > 0 ? (ntile + req - 1) / req : 1;
+    const int ns = static_cast<int>(ntile > 0 ? (ntile + tps - 1) / tps : 1);
+    cfg.n_split = req;
+    VV10_TRY(ensure(part, sizeof(double) * 3 * static_cast<size_t>(ns) * (P.nk_pad > 0 ? P.nk_pad : 1),
+                    "pair-sum partials"));
+    VV10_CUDA(this, launch_pairsum(P, mode, fp64, cfg, static_cast<double*>(part.p),
+                                   static_cast<int*>(dev_err.p), st),
+              "pair-sum kernel");
+    *n_split_out = ns;
+    return VV10_OK;
+}
+
+TileChoice vv10_ctx::tiles_for(int mode, bool fp64) const {
+    TileChoice t;
+    t.rows_per_thread = fp64 ? 1 : 2;
+    t.n_split = 0;
+    for (const TileOverride& o : overrides)
+        if (o.active && o.mode == mode && o.fp64 == fp64) {
+            t.rows_per_thread = o.rows_per_thread;
+            t.n_split = o.n_split;
+        }
+    return t;
+}
+
+extern "C" {
+
+vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* energy,
+                                  double* vrho, double* vgamma, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    if ((vrho && (!device_ptr_ok(vrho, h->device) || !aligned(vrho, 8))) ||
+        (vgamma && (!device_ptr_ok(vgamma, h->device) || !aligned(vgamma, 8)))) {
+        h->set_error("vrho / vgamma must be 8-byte aligned device pointers");
+        return VV10_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool fp64 = (prec == VV10_FP64);
+    PointsDev& P = h->P;
+    const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
+    VV10_TRY(h->ensure(h->sumE, nkb, "E_i"));
+    VV10_TRY(h->ensure(h->sumU, nkb, "U_i"));
+    VV10_TRY(h->ensure(h->sumW, nkb, "W_i"));
+    const int nblk = ep_epilogue_blocks(P.nk);
+    VV10_TRY(h->ensure(h->eblk, sizeof(double) * nblk, "energy partials"));
+    VV10_TRY(h->ensure(h->scal, 64, "energy"));
+    if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
+    if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
+    double* escal = static_cast<double*>(h->scal.p);
+    if (P.nk > 0) {
+        int ns = 1;
+        VV10_TRY(h->run_pairsum(MODE_EUW, fp64, st, &ns));
+        VV10_CUDA(h, launch_ep_epilogue(P, static_cast<double*>(h->part.p), ns,
+                                        static_cast<double*>(h->sumE.p),
+                                        static_cast<double*>(h->sumU.p),
+                                        static_cast<double*>(h->sumW.p), vrho, vgamma,
+                                        static_cast<double*>(h->eblk.p),
+                                        static_cast<int*>(h->dev_err.p), st),
+                  "energy epilogue");
+        VV10_CUDA(h, launch_sum_blocks(static_cast<double*>(h->eblk.p), nblk, escal, st),
+                  "energy sum");
+    } else {
+        VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
+    }
+    h->have_euw = true;
+    h->have_abc = false;
+    h->euw_fp64 = fp64;
+    if (energy) {
+        double* he = reinterpret_cast<double*>(h->h_pinned) + 2;
+        VV10_CUDA(h, cudaMemcpyAsync(he, escal, sizeof(double), cudaMemcpyDeviceToHost, st),
+                  "read energy");
+        VV10_TRY(h->check_device_errors(st));  // synchronises
+        *energy = *he;
+    }
+    return VV10_OK;
+}
+
+vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (!h->have_euw) {
+        h->set_error("vv10_energy_potential must be called first");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    if (!device_ptr_ok(dEdw, h->device) || !aligned(dEdw, 8)) {
+        h->set_error("dEdw must be an 8-byte aligned device pointer");
+        return VV10_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    VV10_CUDA(h, cudaMemsetAsync(dEdw, 0, sizeof(double) * h->P.n, st), "memset dEdw");
+    VV10_CUDA(h, launch_weight_grad(h->P, static_cast<double*>(h->sumE.p), dEdw, st),
+              "weight gradient");
+    return VV10_OK;
+}
+
+vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P_trials,
+                                  const double* rho_t, const double* grad_rho_t,
+                                  double* f_rho_t, double* f_gamma_t, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (!h->have_euw) {
+        h->set_error("vv10_energy_potential must be called first (it provides U_i, W_i)");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (P_trials < 1 || P_trials > VV10_MAX_TRIALS) {
+        h->set_error("P must be in [1, VV10_MAX_TRIALS]");
+        return P_trials < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    const void* ptrs[] = {rho_t, grad_rho_t, f_rho_t, f_gamma_t};
+    for (const void* q : ptrs)
+        if (!device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+            h->set_error("trial and output arrays must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st);
+}
+
+vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_points,
+                            double* grad_atoms, double* EUW_Bgr, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    if ((grad_atoms || EUW_Bgr) && h->P.n_atom == 0) {
+        h->set_error("atom outputs need atom_of_point at prepare time");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    void* outs[] = {grad_points, grad_atoms, EUW_Bgr};
+    for (void* q : outs)
+        if (q && (!device_ptr_ok(q, h->device) || !aligned(q, 8))) {
+            h->set_error("outputs must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool fp64 = (prec == VV10_FP64);
+    PointsDev& P = h->P;
+    if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
+    if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
+    if (EUW_Bgr)
+        VV10_CUDA(h, cudaMemsetAsync(EUW_Bgr, 0, sizeof(double) * 9 * P.n * P.n_atom, st), "memset");
+    if (P.nk == 0) return VV10_OK;
+    if (grad_points || grad_atoms) {
+        int ns = 1;
+        VV10_TRY(h->run_pairsum(MODE_GRAD, fp64, st, &ns));
+        VV10_TRY(h->ensure(h->gk, sizeof(double) * 3 * h->soa_ld, "kept gradient"));
+        VV10_CUDA(h, launch_grad_epilogue(P, static_cast<double*>(h->part.p), ns,
+                                          static_cast<double*>(h->gk.p), grad_points, st),
+                  "gradient epilogue");
+        if (grad_atoms)
+            VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
+                      "atom sums");
+    }
+    if (EUW_Bgr)
+        VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr, static_cast<int*>(h->dev_err.p), st),
+                  "atom-resolved terms");
+    return VV10_OK;
+}
+
+vv10_status vv10_debug_inject(vv10_handle h, int what, int64_t value) {
+    VV10_CHECK_HANDLE(h);
+    switch (what) {
+        case VV10_DEBUG_FAIL_ALLOC:
+            h->debug_fail_alloc = static_cast<int>(value);
+            return VV10_OK;
+        case VV10_DEBUG_STALL_COPY:
+            h->debug_stall = static_cast<int>(value);
+            return VV10_OK;
+        default:
+            return VV10_ERR_INVALID_ARG;
+    }
+}
+
+vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split) {
+    VV10_CHECK_HANDLE(h);
+    if (what < 0 || what >= 6 || rows_per_thread < 0 || n_split < 0) return VV10_ERR_INVALID_ARG;
+    TileOverride& o = h->overrides[what];
+    o.mode = what % 3;
+    o.fp64 = what >= 3;
+    o.active = rows_per_thread > 0;
+    o.rows_per_thread = rows_per_thread;
+    o.n_split = n_split;
+    return VV10_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// K4: grid-coordinate derivative terms (Sec. II.A Eq. grad_gr, Sec. II.B Eq. EiBgr).
+//
+// Point gradient: the MODE_GRAD pair sums G_i = sum_j w_j rho_j Phi_ij D_ij (r_i - r_j) give
+// dE/dr_i = -2 w_i rho_i G_i.  Atom terms E^A_gr = sum_{i in A} dE/dr_i: one CTA per atom
+// over its contiguous segment (fixed reduction order).
+//
+// Atom-resolved terms: for every kept row i and atom B != atom(i), sums over j in B of
+//   E_i^{Bgr} = -2 sum w_j rho_j Phi D (r_j - r_i)
+//   U_i^{Bgr} =  2 sum w_j rho_j Phi [D (1/s + 1/g) + omega_i/g^2 + (omega_i+omega_j)/s^2] (r_j - r_i)
+//   W_i^{Bgr} =  2 sum w_j rho_j Phi [R^2 D (1/s + 1/g) + R^2 (omega_i/g^2 + (omega_i+omega_j)/s^2)
+//                                     - (1/s + 1/g)] (r_j - r_i)
+// and for B = atom(i) minus the sum over the other atoms (translational invariance).
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace vv10 {
+
+static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__global__ void k_grad_epilogue(PointsDev P, const double* __restrict__ part, int n_split,
+                                double* __restrict__ gk, double* __restrict__ grad_points) {
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= P.nk) return;
+    const double c = -2.0 * P.w[p] * P.rho[p];
+    const int64_t i = P.orig[p];
+    for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int k = 0; k < n_split; ++k) s += part[(static_cast<int64_t>(d) * n_split + k) * P.nk_pad + p];
+        const double g = c * s;
+        gk[3 * p + d] = g;
+        if (grad_points) grad_points[3 * i + d] = g;
+    }
+}
+
+cudaError_t launch_grad_epilogue(const PointsDev& p, const double* part, int n_split, double* gk,
+                                 double* grad_points, cudaStream_t st) {
+    if (p.nk == 0) return cudaSuccess;
+    k_grad_epilogue<<<static_cast<unsigned>(cdiv64(p.nk, 256)), 256, 0, st>>>(p, part, n_split, gk,
+                                                                            grad_points);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256)
+k_atom_sums(PointsDev P, const double* __restrict__ gk, double* __restrict__ out) {
+    __shared__ double sh[8];
+    const int a = blockIdx.x;
+    const int64_t s0 = P.seg[a], s1 = P.seg[a + 1];
+    for (int d = 0; d < 3; ++d) {
+        double v = 0.0;
+        for (int64_t p = s0 + threadIdx.x; p < s1; p += blockDim.x) v += gk[3 * p + d];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) out[3 * a + d] = v;
+    }
+}
+
+cudaError_t launch_atom_sums(const PointsDev& p, const double* gk, double* grad_atoms,
+                             cudaStream_t st) {
+    if (p.n_atom <= 0) return cudaSuccess;
+    k_atom_sums<<<p.n_atom, 256, 0, st>>>(p, gk, grad_atoms);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ atom-resolved
+template <class T> struct RecsAR;
+template <> struct RecsAR<float> { using A = float4; using B = float4; };
+template <> struct RecsAR<double> { using A = double4; using B = double4; };
+
+constexpr int kArThreads = 128;
+constexpr int kArJT = 128;
+
+template <class T>
+__global__ void __launch_bounds__(kArThreads)
+k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
+                const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ out) {
+    using RA = typename RecsAR<T>::A;
+    using RB = typename RecsAR<T>::B;
+    __shared__ RA sa[kArJT];
+    __shared__ RB sb[kArJT];
+    const int tid = threadIdx.x;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * kArThreads + tid;
+    const bool valid = i < P.nk;
+    T xi = 0, yi = 0, zi = 0, oi = 1, ki = 1;
+    int ai = -1;
+    if (valid) {
+        const RA a = ra[i];
+        const RB b = rb[i];
+        xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y;
+        ai = P.atom[i];
+    }
+    const int64_t n = P.n, na = P.n_atom;
+    const int64_t oi_idx = valid ? P.orig[i] : 0;
+    double rest[9];  // running sum over atoms B != atom(i)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) rest[q] = 0.0;
+
+    for (int B = 0; B < P.n_atom; ++B) {
+        const int64_t s0 = P.seg[B], s1 = P.seg[B + 1];
+        double tot[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) tot[q] = 0.0;
+        for (int64_t j0 = s0; j0 < s1; j0 += kArJT) {
+            __syncthreads();
+            if (j0 + tid < s1) {
+                sa[tid] = ra[j0 + tid];
+                sb[tid] = rb[j0 + tid];
+            }
+            __syncthreads();
+            const int cnt = static_cast<int>(s1 - j0 < kArJT ? s1 - j0 : kArJT);
+            T acc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[q] = T(0);
+            for (int jj = 0; jj < cnt; ++jj) {
+                const RA a = sa[jj];
+                const RB b = sb[jj];
+                const T dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                const T g = oi * r2 + ki;
+                const T gp = b.x * r2 + b.y;
+                const T s = g + gp;
+                const T ggp = g * gp;
+                const T inv = recip(ggp * s);
+                const T ph = a.w * inv;          // w_j rho_j Phi_ij
+                const T L = ggp * inv;           // 1/s
+                const T Gi = (gp * s) * inv;     // 1/g
+                const T D = (oi * gp * (s + g) + b.x * g * (s + gp)) * inv;
+                const T t1 = L + Gi;
+                const T t3 = oi * Gi * Gi + (oi + b.x) * L * L;
+                const T cE = ph * D;
+                const T cU = ph * (D * t1 + t3);
+                const T cW = ph * (r2 * (D * t1 + t3) - t1);
+                acc[0] += cE * dx; acc[1] += cE * dy; acc[2] += cE * dz;
+                acc[3] += cU * dx; acc[4] += cU * dy; acc[5] += cU * dz;
+                acc[6] += cW * dx; acc[7] += cW * dy; acc[8] += cW * dz;
+            }
+#pragma unroll
+            for (int q = 0; q < 9; ++q) tot[q] += static_cast<double>(acc[q]);
+        }
+        // (r_i - r_j) was accumulated: E = +2 acc, U = -2 acc, W = -2 acc
+        if (valid && B != ai) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const double v = (q < 3 ? 2.0 : -2.0) * tot[q];
+                rest[q] += v;
+                out[((static_cast<int64_t>(q / 3) * n + oi_idx) * na + B) * 3 + (q % 3)] = v;
+            }
+        }
+    }
+    if (valid && ai >= 0 && ai < P.n_atom) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            out[((static_cast<int64_t>(q / 3) * n + oi_idx) * na + ai) * 3 + (q % 3)] = -rest[q];
+    }
+}
+
+cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, int* err,
+                                 cudaStream_t st) {
+    (void)err;
+    if (p.nk == 0 || p.n_atom <= 0) return cudaSuccess;
+    const unsigned g = static_cast<unsigned>(cdiv64(p.nk, kArThreads));
+    if (fp64) k_atom_resolved<double><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out);
+    else k_atom_resolved<float><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out);
+    return cudaGetLastError();
+}
+
+}  // namespace vv10

@@ -1,0 +1,92 @@
+// Orchestration of vv10_hessian_contract (Sec. II.B, Eq. frhot): A/B/C row sums for the
+// delta_ij/w_i terms, trial preparation, the pair-part contraction and the epilogue.
+#include "kernels.hpp"
+#include "vv10_internal.hpp"
+
+using namespace vv10;
+
+#define H_CUDA(expr, where)                                  \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);  \
+    } while (0)
+#define H_TRY(expr)                   \
+    do {                              \
+        vv10_status s_ = (expr);      \
+        if (s_ != VV10_OK) return s_; \
+    } while (0)
+
+// Trials per CTA of the FP64 SIMT contraction: minimise chunks * (pair-generation cost +
+// 4 FMAs per trial), the FP64 operation count per pair.
+static int pick_trials_per_cta(int32_t P) {
+    int best = 8;
+    long best_cost = -1;
+    for (int pc : {8, 16, 32}) {
+        const long chunks = (P + pc - 1) / pc;
+        const long cost = chunks * (45 + 4L * pc);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = pc;
+        }
+    }
+    return best;
+}
+
+vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho_t,
+                              const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
+                              cudaStream_t st) {
+    const bool fp64 = (prec == VV10_FP64);
+    const size_t out_bytes = sizeof(double) * static_cast<size_t>(Pn) * P.n;
+    H_CUDA(cudaMemsetAsync(f_rho_t, 0, out_bytes, st), "memset f_rho_t");
+    H_CUDA(cudaMemsetAsync(f_gamma_t, 0, out_bytes, st), "memset f_gamma_t");
+    if (P.nk == 0) return VV10_OK;
+    if (!fp64) {
+        set_error("mixed-precision Hessian contraction is not available in this build");
+        return VV10_ERR_UNSUPPORTED;
+    }
+
+    // A_i, B_i, C_i (pair sums of the diagonal terms), in the requested precision
+    const size_t nkb = sizeof(double) * static_cast<size_t>(soa_ld);
+    if (!have_abc || (fp64 && !abc_fp64)) {
+        H_TRY(ensure(sumA, nkb, "A_i"));
+        H_TRY(ensure(sumB, nkb, "B_i"));
+        H_TRY(ensure(sumC, nkb, "C_i"));
+        int ns = 1;
+        H_TRY(run_pairsum(MODE_ABC, fp64, st, &ns));
+        H_CUDA(launch_abc_epilogue(P, static_cast<double*>(part.p), ns,
+                                   static_cast<double*>(sumA.p), static_cast<double*>(sumB.p),
+                                   static_cast<double*>(sumC.p), st),
+               "A/B/C epilogue");
+        have_abc = true;
+        abc_fp64 = fp64;
+    }
+
+    // trial inputs at kept points
+    const size_t tpad = sizeof(double) * static_cast<size_t>(Pn) * P.nk_pad;
+    const size_t tk = sizeof(double) * static_cast<size_t>(Pn) * (P.nk > 0 ? P.nk : 1);
+    H_TRY(ensure(tu, tpad, "trial u"));
+    H_TRY(ensure(ty, tpad, "trial y"));
+    H_TRY(ensure(trt, tk, "trial rho at kept points"));
+    H_TRY(ensure(tgt, tk, "trial gamma at kept points"));
+    H_CUDA(launch_trial_prep(P, Pn, rho_t, grad_rho_t, static_cast<double*>(tu.p),
+                             static_cast<double*>(ty.p), static_cast<double*>(trt.p),
+                             static_cast<double*>(tgt.p), st),
+           "trial prep");
+
+    HessLaunch cfg;
+    cfg.trials_per_cta = pick_trials_per_cta(Pn);
+    cfg.n_split = hess_f64_default_split(P, Pn, cfg.trials_per_cta, n_sm);
+    H_TRY(ensure(hacc, sizeof(double) * 2 * static_cast<size_t>(cfg.n_split) * Pn * P.nk_pad,
+                 "contraction partials"));
+    H_CUDA(launch_hess_f64(P, Pn, static_cast<double*>(tu.p), static_cast<double*>(ty.p), cfg,
+                           static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
+           "FP64 contraction");
+    H_CUDA(launch_hess_epilogue(P, Pn, static_cast<double*>(hacc.p), cfg.n_split, P.nk_pad,
+                                static_cast<double*>(sumU.p), static_cast<double*>(sumW.p),
+                                static_cast<double*>(sumA.p), static_cast<double*>(sumB.p),
+                                static_cast<double*>(sumC.p), static_cast<double*>(trt.p),
+                                static_cast<double*>(tgt.p), f_rho_t, f_gamma_t,
+                                static_cast<int*>(dev_err.p), st),
+           "Hessian epilogue");
+    return VV10_OK;
+}

@@ -1,0 +1,118 @@
+// Host-side launch interface between the VV10 translation units (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vv10 {
+
+constexpr int kJTile = 256;  // j records are padded to a multiple of this
+
+// Prepared point block (device memory owned by the handle), kept points only, sorted
+// by atom (stable), so that each atom's points form one contiguous segment.
+struct PointsDev {
+    int64_t n = 0;       // caller's points
+    int64_t nk = 0;      // kept points
+    int64_t nk_pad = 0;  // nk rounded up to kJTile (padding records have c = 0)
+    int32_t n_atom = 0;
+    double beta = 0.0;
+    const int64_t* orig = nullptr;  // nk: kept -> caller index
+    const int64_t* seg = nullptr;   // n_atom + 1 segment starts (kept indexing)
+    const int32_t* atom = nullptr;  // nk atom of each kept point (0 if none given)
+    // FP64 per kept point
+    const double *w, *rho, *gx, *gy, *gz;
+    const double *om, *ka, *om_r, *om_g, *ka_r, *om_rr, *om_rg, *om_gg, *ka_rr;
+    // packed pair records, nk_pad each
+    const double4* r64a;  // x, y, z, -1.5 w rho
+    const double4* r64b;  // omega, kappa, rho kappa', rho omega_rho
+    const float4* r32a;   // x-cx, y-cy, z-cz, -1.5 w rho   (recentred, FP32)
+    const float4* r32b;   // omega, kappa, rho kappa', rho omega_rho
+};
+
+// SoA field order inside the FP64 per-point arena (each field nk_pad long).
+enum SoaField : int {
+    F_W = 0, F_RHO, F_GX, F_GY, F_GZ, F_OM, F_KA, F_OMR, F_OMG, F_KAR, F_OMRR, F_OMRG, F_OMGG,
+    F_KARR, F_COUNT
+};
+
+// ---------------------------------------------------------------- prepare (prepare.cu)
+struct PrepareScratch {
+    int32_t* hist;      // n_keys * nblk
+    int64_t* offs;      // n_keys * nblk
+    double* bbox_part;  // nblk * 6
+    double* center;     // 3
+    int64_t* nk_dev;    // 1
+};
+int prepare_nblk(int64_t n);
+cudaError_t launch_prepare_count(int64_t n, const double* xyz, const double* w, const double* rho,
+                                 const double* grad, const int32_t* atom, int32_t n_atom,
+                                 double rho_cut, const PrepareScratch& s, int* err,
+                                 cudaStream_t st);
+cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w,
+                                   const double* rho, const double* grad, const int32_t* atom,
+                                   int32_t n_atom, double rho_cut, double b, double C,
+                                   const PrepareScratch& s, int64_t nk, int64_t nk_pad,
+                                   int64_t* orig, int64_t* seg, int32_t* atom_k, double* soa,
+                                   double4* r64a, double4* r64b, float4* r32a, float4* r32b,
+                                   cudaStream_t st);
+
+// ---------------------------------------------------------------- pair sums (pairsum.cu)
+enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2 };
+
+struct PairLaunch {
+    int rows_per_thread = 2;  // FP32: 1, 2, 4; FP64: 1, 2
+    int n_split = 1;          // j-splits (partials reduced by the epilogue)
+    int stall = 0;            // test hook: CTA (0,0) issues no copies, so its waits time out
+};
+// part: [3][n_split][nk_pad] FP64 partial sums (quantity-major).
+cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLaunch& cfg,
+                           double* part, int* err, cudaStream_t st);
+int pairsum_default_split(const PointsDev& p, bool fp64, int rows_per_thread, int n_sm);
+
+// Energy / potential epilogue: reduces the partials, writes E,U,W (kept indexing),
+// f^rho, f^gamma (caller indexing) and per-block energy partials.
+int ep_epilogue_blocks(int64_t nk);
+cudaError_t launch_ep_epilogue(const PointsDev& p, const double* part, int n_split, double* E,
+                               double* U, double* W, double* vrho, double* vgamma,
+                               double* eblk, int* err, cudaStream_t st);
+cudaError_t launch_sum_blocks(const double* eblk, int nblk, double* out, cudaStream_t st);
+cudaError_t launch_abc_epilogue(const PointsDev& p, const double* part, int n_split, double* A,
+                                double* B, double* C, cudaStream_t st);
+cudaError_t launch_weight_grad(const PointsDev& p, const double* E, double* dEdw,
+                               cudaStream_t st);
+
+// ---------------------------------------------------------------- Hessian (hess.cu)
+// Trial inputs at kept points: u = w rho^t, y = 2 w sigma gamma^t (sigma = rho omega_gamma)
+// as FP64 [P][nk_pad] (j contiguous), and rho^t, gamma^t (FP64 [P][nk]) for the diagonal.
+cudaError_t launch_trial_prep(const PointsDev& p, int32_t P, const double* rho_t,
+                              const double* grad_rho_t, double* u, double* y, double* rt_k,
+                              double* gt_k, cudaStream_t st);
+// FP32 split variant: u/y hi/lo as FP32 [Ppad][nk_pad] rows (tf32 or bf16-rounded hi).
+cudaError_t launch_trial_split(const double* u, const double* y, int32_t P, int32_t Ppad,
+                               int64_t nk_pad, bool bf16, float* uh, float* ul, float* yh,
+                               float* yl, cudaStream_t st);
+
+struct HessLaunch {
+    int trials_per_cta = 16;  // FP64 SIMT: 8, 16, 32
+    int n_split = 1;
+};
+int hess_f64_default_split(const PointsDev& p, int32_t P, int pc, int n_sm);
+// acc: [2][n_split][P][nk_pad] partial sums of the pair part (rho row, gamma row).
+cudaError_t launch_hess_f64(const PointsDev& p, int32_t P, const double* u, const double* y,
+                            const HessLaunch& cfg, double* acc, int* err, cudaStream_t st);
+cudaError_t launch_hess_epilogue(const PointsDev& p, int32_t P, const double* acc, int n_split,
+                                 int64_t acc_ld, const double* U, const double* W,
+                                 const double* A, const double* B, const double* C,
+                                 const double* rt_k, const double* gt_k, double* f_rho_t,
+                                 double* f_gamma_t, int* err, cudaStream_t st);
+
+// ---------------------------------------------------------------- coordinates (coord.cu)
+cudaError_t launch_grad_epilogue(const PointsDev& p, const double* part, int n_split,
+                                 double* gk /* nk x 3 kept */, double* grad_points,
+                                 cudaStream_t st);
+cudaError_t launch_atom_sums(const PointsDev& p, const double* gk, double* grad_atoms,
+                             cudaStream_t st);
+cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, int* err,
+                                 cudaStream_t st);
+
+}  // namespace vv10

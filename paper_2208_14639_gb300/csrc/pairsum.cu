@@ -1,0 +1,347 @@
+// K2 / K4: flash-style double grid sums over kept points i (rows) and j (columns).
+//
+// One CTA owns NT*RPT rows i held in registers and streams a contiguous range of
+// j-records through shared memory in tiles of kJTile, double-buffered, each tile fetched
+// by two 1-D bulk asynchronous copies (TMA engine) completing on an mbarrier.  Every
+// thread evaluates the closed-form pair kernel for its rows against every j of the tile
+// (shared-memory broadcast reads).  The j range may be split over gridDim.y CTAs; each
+// split writes FP64 partial sums that an epilogue reduces in a fixed order.
+//
+// Modes (the three quantities each mode accumulates per row i):
+//   MODE_EUW  E_i = sum_j w_j rho_j Phi_ij, and sum_j w_j rho_j Phi_ij (1/s + 1/g) {1, R^2}
+//             (U_i and W_i of Sec. II.A up to their sign)
+//   MODE_ABC  sum_j w_j rho_j Phi_ij (1/s^2 + 1/(s g) + 1/g^2) {1, R^2, R^4}
+//             (A_i, B_i, C_i of Sec. II.B up to the factor 2)
+//   MODE_GRAD sum_j w_j rho_j Phi_ij D_ij (r_i - r_j), D_ij the bracket of Eq. grad_gr
+// with g = omega_i R^2 + kappa_i, g' = omega_j R^2 + kappa_j, s = g + g' and all of
+// 1/g, 1/g', 1/s, Phi obtained from the single reciprocal inv = 1/(g g' s).
+//
+// FP32 variant: recentred FP32 coordinates, FP32 pair arithmetic, FP32 sums within a
+// tile, promoted to FP64 once per tile.  FP64 variant: everything in FP64.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace vv10 {
+
+template <class T> struct Recs;
+template <> struct Recs<float> { using A = float4; using B = float4; };
+template <> struct Recs<double> { using A = double4; using B = double4; };
+
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <class T>
+struct Row {
+    T x, y, z, om, ka;
+};
+
+// Accumulate one (i, j) pair into acc[0..2] for the given mode.
+template <class T, int MODE, class RA, class RB>
+__device__ __forceinline__ void pair_accumulate(const Row<T>& r, const RA& a, const RB& b,
+                                                T (&acc)[3]) {
+    const T dx = r.x - a.x, dy = r.y - a.y, dz = r.z - a.z;
+    T r2 = dx * dx;
+    r2 = fmadd(dy, dy, r2);
+    r2 = fmadd(dz, dz, r2);
+    const T g = fmadd(r.om, r2, r.ka);
+    const T gp = fmadd(b.x, r2, b.y);
+    const T s = g + gp;
+    const T ggp = g * gp;
+    const T inv = recip(ggp * s);
+    const T ph = a.w * inv;  // w_j rho_j Phi_ij  (a.w = -3/2 w_j rho_j)
+    if constexpr (MODE == MODE_EUW) {
+        const T t = ((g + s) * gp) * inv;  // 1/s + 1/g
+        const T pt = ph * t;
+        acc[0] += ph;
+        acc[1] += pt;
+        acc[2] = fmadd(pt, r2, acc[2]);
+    } else if constexpr (MODE == MODE_ABC) {
+        const T L = ggp * inv;         // 1/s
+        const T Gi = (gp * s) * inv;   // 1/g
+        const T m = fmadd(L, L + Gi, Gi * Gi);
+        const T v = ph * m;
+        acc[0] += v;
+        const T v2 = v * r2;
+        acc[1] += v2;
+        acc[2] = fmadd(v2, r2, acc[2]);
+    } else {
+        // D g g' s = omega_i g' (s + g) + omega_j g (s + g')
+        const T num = fmadd(r.om * gp, s + g, (b.x * g) * (s + gp));
+        const T f = (ph * inv) * num;
+        acc[0] = fmadd(f, dx, acc[0]);
+        acc[1] = fmadd(f, dy, acc[1]);
+        acc[2] = fmadd(f, dz, acc[2]);
+    }
+}
+
+template <class T, int MODE, int RPT, int NT>
+__global__ void __launch_bounds__(NT)
+k_pairsum(const typename Recs<T>::A* __restrict__ ra, const typename Recs<T>::B* __restrict__ rb,
+          int64_t nk, int64_t nk_pad, int64_t j_per_split, double* __restrict__ part,
+          int* __restrict__ err, int stall) {
+    using RA = typename Recs<T>::A;
+    using RB = typename Recs<T>::B;
+    __shared__ __align__(128) RA sa[2][kJTile];
+    __shared__ __align__(128) RB sb[2][kJTile];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int tid = threadIdx.x;
+    const int n_split = gridDim.y;
+    const int split = blockIdx.y;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * (NT * RPT);
+    const int64_t jb = static_cast<int64_t>(split) * j_per_split;
+    const int64_t je = min(nk_pad, jb + j_per_split);
+    const int ntile = je > jb ? static_cast<int>((je - jb) / kJTile) : 0;
+
+    Row<T> row[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int64_t i = i0 + r * NT + tid;
+        if (i < nk) {
+            const RA a = ra[i];
+            const RB b = rb[i];
+            row[r] = Row<T>{a.x, a.y, a.z, b.x, b.y};
+        } else {
+            row[r] = Row<T>{T(0), T(0), T(0), T(1), T(1)};
+        }
+    }
+    T acc[RPT][3];
+    double dacc[RPT][3];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { acc[r][q] = T(0); dacc[r][q] = 0.0; }
+
+    constexpr uint32_t kBytesA = sizeof(RA) * kJTile, kBytesB = sizeof(RB) * kJTile;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // Test hook: a stalled CTA never issues its copies, so its first wait runs out.
+    const bool stalled = stall && blockIdx.x == 0 && blockIdx.y == 0;
+    int issued = 0;
+    if (tid == 0 && !stalled) {
+        for (; issued < 2 && issued < ntile; ++issued) {
+            const int64_t j0 = jb + static_cast<int64_t>(issued) * kJTile;
+            mbar_expect_tx(&bar[issued], kBytesA + kBytesB);
+            bulk_g2s(sa[issued], ra + j0, kBytesA, &bar[issued]);
+            bulk_g2s(sb[issued], rb + j0, kBytesB, &bar[issued]);
+        }
+    }
+    int consumed = 0;
+    for (int t = 0; t < ntile; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait(&bar[buf], (t >> 1) & 1, err);
+        const RA* A = sa[buf];
+        const RB* B = sb[buf];
+#pragma unroll 2
+        for (int jj = 0; jj < kJTile; ++jj) {
+            const RA a = A[jj];
+            const RB b = B[jj];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) pair_accumulate<T, MODE>(row[r], a, b, acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                dacc[r][q] += static_cast<double>(acc[r][q]);
+                acc[r][q] = T(0);
+            }
+        consumed = t + 1;
+        if (__syncthreads_or(!ok)) break;  // every thread leaves together
+        if (tid == 0 && !stalled && issued < ntile) {
+            const int64_t j0 = jb + static_cast<int64_t>(issued) * kJTile;
+            mbar_expect_tx(&bar[buf], kBytesA + kBytesB);
+            bulk_g2s(sa[buf], ra + j0, kBytesA, &bar[buf]);
+            bulk_g2s(sb[buf], rb + j0, kBytesB, &bar[buf]);
+            ++issued;
+        }
+    }
+    // After a timeout, wait (bounded) for copies still in flight before the CTA exits.
+    if (tid == 0)
+        for (int t = consumed; t < issued; ++t) mbar_wait(&bar[t & 1], (t >> 1) & 1, err);
+
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int64_t i = i0 + r * NT + tid;
+        if (i < nk) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                part[(static_cast<int64_t>(q) * n_split + split) * nk_pad + i] = dacc[r][q];
+        }
+    }
+}
+
+static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Normalise a requested split count so that every split holds whole tiles.
+static inline void split_geometry(int64_t nk_pad, int req, int64_t& j_per_split, int& n_split) {
+    const int64_t ntile = nk_pad / kJTile;
+    if (req < 1) req = 1;
+    if (req > ntile) req = static_cast<int>(ntile > 0 ? ntile : 1);
+    const int64_t tps = cdiv(ntile, req);
+    j_per_split = tps * kJTile;
+    n_split = static_cast<int>(ntile > 0 ? cdiv(ntile, tps) : 1);
+}
+
+int pairsum_default_split(const PointsDev& p, bool fp64, int rpt, int n_sm) {
+    const int NT = fp64 ? 128 : 256;
+    const int64_t n_itile = cdiv(p.nk, static_cast<int64_t>(NT) * rpt);
+    const int64_t target = static_cast<int64_t>(n_sm) * (fp64 ? 8 : 4);
+    int req = static_cast<int>(cdiv(target, n_itile > 0 ? n_itile : 1));
+    int64_t jps;
+    int ns;
+    split_geometry(p.nk_pad, req, jps, ns);
+    return ns;
+}
+
+template <class T, int MODE, int RPT, int NT>
+static cudaError_t launch_t(const PointsDev& p, const typename Recs<T>::A* ra,
+                            const typename Recs<T>::B* rb, int req_split, int stall,
+                            double* part, int* err, cudaStream_t st) {
+    int64_t jps;
+    int ns;
+    split_geometry(p.nk_pad, req_split, jps, ns);
+    dim3 grid(static_cast<unsigned>(cdiv(p.nk, static_cast<int64_t>(NT) * RPT)),
+              static_cast<unsigned>(ns));
+    k_pairsum<T, MODE, RPT, NT><<<grid, NT, 0, st>>>(ra, rb, p.nk, p.nk_pad, jps, part, err,
+                                                     stall);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_mode(const PointsDev& p, bool fp64, const PairLaunch& cfg, double* part,
+                               int* err, cudaStream_t st) {
+    if (fp64) {
+        if (cfg.rows_per_thread >= 2)
+            return launch_t<double, MODE, 2, 128>(p, p.r64a, p.r64b, cfg.n_split, cfg.stall, part, err, st);
+        return launch_t<double, MODE, 1, 128>(p, p.r64a, p.r64b, cfg.n_split, cfg.stall, part, err, st);
+    }
+    if (cfg.rows_per_thread >= 4)
+        return launch_t<float, MODE, 4, 256>(p, p.r32a, p.r32b, cfg.n_split, cfg.stall, part, err, st);
+    if (cfg.rows_per_thread == 2)
+        return launch_t<float, MODE, 2, 256>(p, p.r32a, p.r32b, cfg.n_split, cfg.stall, part, err, st);
+    return launch_t<float, MODE, 1, 256>(p, p.r32a, p.r32b, cfg.n_split, cfg.stall, part, err, st);
+}
+
+cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLaunch& cfg,
+                           double* part, int* err, cudaStream_t st) {
+    if (p.nk == 0) return cudaSuccess;
+    switch (mode) {
+        case MODE_EUW: return launch_mode<MODE_EUW>(p, fp64, cfg, part, err, st);
+        case MODE_ABC: return launch_mode<MODE_ABC>(p, fp64, cfg, part, err, st);
+        default: return launch_mode<MODE_GRAD>(p, fp64, cfg, part, err, st);
+    }
+}
+
+// ------------------------------------------------------------------ epilogues
+constexpr int kEpThreads = 256;
+int ep_epilogue_blocks(int64_t nk) { return static_cast<int>(cdiv(nk > 0 ? nk : 1, kEpThreads)); }
+
+__device__ __forceinline__ double sum_splits(const double* part, int q, int n_split,
+                                             int64_t nk_pad, int64_t p) {
+    double s = 0.0;
+    for (int k = 0; k < n_split; ++k) s += part[(static_cast<int64_t>(q) * n_split + k) * nk_pad + p];
+    return s;
+}
+
+__global__ void __launch_bounds__(kEpThreads)
+k_ep_epilogue(PointsDev P, const double* __restrict__ part, int n_split, double* __restrict__ E,
+              double* __restrict__ U, double* __restrict__ W, double* __restrict__ vrho,
+              double* __restrict__ vgamma, double* __restrict__ eblk, int* err) {
+    __shared__ double sh[kEpThreads / 32];
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    double ei = 0.0;
+    if (p < P.nk) {
+        const double e = sum_splits(part, 0, n_split, P.nk_pad, p);
+        const double u = -sum_splits(part, 1, n_split, P.nk_pad, p);
+        const double wv = -sum_splits(part, 2, n_split, P.nk_pad, p);
+        E[p] = e;
+        U[p] = u;
+        W[p] = wv;
+        const double r = P.rho[p];
+        const double fr = P.beta + e + r * (P.ka_r[p] * u + P.om_r[p] * wv);  // f^rho
+        const double fg = r * P.om_g[p] * wv;                                  // f^gamma
+        const int64_t i = P.orig[p];
+        if (vrho) vrho[i] = fr;
+        if (vgamma) vgamma[i] = fg;
+        if (!isfinite(fr) || !isfinite(fg)) atomicOr(err, DEVERR_NONFINITE);
+        ei = P.w[p] * r * (P.beta + 0.5 * e);
+    }
+    const double s = block_sum(ei, sh);
+    if (threadIdx.x == 0) eblk[blockIdx.x] = s;
+}
+
+cudaError_t launch_ep_epilogue(const PointsDev& p, const double* part, int n_split, double* E,
+                               double* U, double* W, double* vrho, double* vgamma,
+                               double* eblk, int* err, cudaStream_t st) {
+    k_ep_epilogue<<<ep_epilogue_blocks(p.nk), kEpThreads, 0, st>>>(p, part, n_split, E, U, W,
+                                                                    vrho, vgamma, eblk, err);
+    return cudaGetLastError();
+}
+
+// Compensated (Neumaier per thread, TwoSum tree across threads) sum of block partials.
+__global__ void __launch_bounds__(256) k_sum_blocks(const double* __restrict__ v, int n,
+                                                    double* __restrict__ out) {
+    __shared__ double ss[256], sc[256];
+    double s = 0.0, c = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) {
+        const double x = v[k];
+        const double t = s + x;
+        c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            double hi, lo;
+            two_sum(ss[threadIdx.x], ss[threadIdx.x + o], hi, lo);
+            ss[threadIdx.x] = hi;
+            sc[threadIdx.x] += sc[threadIdx.x + o] + lo;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = ss[0] + sc[0];
+}
+
+cudaError_t launch_sum_blocks(const double* eblk, int nblk, double* out, cudaStream_t st) {
+    k_sum_blocks<<<1, 256, 0, st>>>(eblk, nblk, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_abc_epilogue(PointsDev P, const double* __restrict__ part, int n_split,
+                               double* __restrict__ A, double* __restrict__ B,
+                               double* __restrict__ C) {
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= P.nk) return;
+    A[p] = 2.0 * sum_splits(part, 0, n_split, P.nk_pad, p);
+    B[p] = 2.0 * sum_splits(part, 1, n_split, P.nk_pad, p);
+    C[p] = 2.0 * sum_splits(part, 2, n_split, P.nk_pad, p);
+}
+
+cudaError_t launch_abc_epilogue(const PointsDev& p, const double* part, int n_split, double* A,
+                                double* B, double* C, cudaStream_t st) {
+    if (p.nk == 0) return cudaSuccess;
+    k_abc_epilogue<<<ep_epilogue_blocks(p.nk), kEpThreads, 0, st>>>(p, part, n_split, A, B, C);
+    return cudaGetLastError();
+}
+
+__global__ void k_weight_grad(PointsDev P, const double* __restrict__ E, double* __restrict__ out) {
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= P.nk) return;
+    out[P.orig[p]] = P.rho[p] * (P.beta + E[p]);  // dE/dw_i = rho_i (beta + E_i)
+}
+
+cudaError_t launch_weight_grad(const PointsDev& p, const double* E, double* dEdw,
+                               cudaStream_t st) {
+    if (p.nk == 0) return cudaSuccess;
+    k_weight_grad<<<ep_epilogue_blocks(p.nk), kEpThreads, 0, st>>>(p, E, dEdw);
+    return cudaGetLastError();
+}
+
+}  // namespace vv10

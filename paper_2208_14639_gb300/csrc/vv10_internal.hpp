@@ -1,0 +1,88 @@
+// Definition of the opaque handle behind vv10_handle (host side, not part of the ABI).
+#pragma once
+
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.hpp"
+#include "vv10.h"
+
+namespace vv10 {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct TileChoice {
+    int rows_per_thread = 2;
+    int n_split = 0;  // 0 = derive from the SM count
+};
+
+struct TileOverride {
+    bool active = false;
+    int mode = 0;
+    bool fp64 = false;
+    int rows_per_thread = 0;
+    int n_split = 0;
+};
+
+}  // namespace vv10
+
+struct vv10_ctx {
+    int device = 0;
+    int n_sm = 0;
+    int cc_major = 0, cc_minor = 0;
+    char last_error[512] = {0};
+    void* h_pinned = nullptr;  // small pinned host scratch for scalar read-backs
+
+    // device error word (DEVERR_* bits)
+    vv10::DevBuf dev_err;
+
+    // prepare scratch
+    vv10::DevBuf prep_hist, prep_offs, prep_bbox, prep_small;
+    // prepared point block
+    vv10::DevBuf orig, seg, atom_k, soa, r64a, r64b, r32a, r32b;
+    vv10::PointsDev P;
+    int64_t soa_ld = 0;
+    vv10_params prm{6.0, 0.01, 1e-10};
+    bool prepared = false;
+
+    // cached row sums (kept indexing)
+    vv10::DevBuf sumE, sumU, sumW, sumA, sumB, sumC;
+    bool have_euw = false, euw_fp64 = false;
+    bool have_abc = false, abc_fp64 = false;
+
+    // pair-sum partials and energy reduction scratch
+    vv10::DevBuf part, eblk, scal;
+
+    // Hessian scratch
+    vv10::DevBuf tu, ty, trt, tgt, hacc;
+    vv10::DevBuf tc_uh, tc_ul, tc_yh, tc_yl;
+
+    // coordinate scratch
+    vv10::DevBuf gk;
+
+    // tile overrides (index = mode + 3 * fp64), set by vv10_set_tiles / the autotuner
+    vv10::TileOverride overrides[6];
+
+    // test hooks
+    int debug_fail_alloc = 0;
+    int debug_stall = 0;
+
+    void set_error(const char* fmt, ...);
+    vv10_status cuda_fail(cudaError_t e, const char* where);
+    vv10_status ensure(vv10::DevBuf& b, size_t bytes, const char* what);
+    void release_all();
+    vv10_status bind();
+    vv10_status check_device_errors(cudaStream_t st);
+    vv10_status require_prepared();
+    vv10::PointsDev points() const;
+    vv10::TileChoice tiles_for(int mode, bool fp64) const;
+    vv10_status run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_split_out);
+    vv10_status hessian(vv10_precision prec, int32_t P, const double* rho_t,
+                        const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
+                        cudaStream_t st);
+};

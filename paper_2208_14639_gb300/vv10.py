@@ -1,0 +1,262 @@
+"""ctypes binding of libvv10 (include/vv10.h), one Python function per C entry point.
+
+Argument marshalling only: tensors are checked for device, dtype, shape and contiguity
+and passed as raw device pointers together with the current torch CUDA stream; every
+step of the computation runs in the library's CUDA kernels.  There is no CPU fallback:
+if the library is missing or the device is not a CUDA GPU the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+VV10_OK = 0
+VV10_ERR_INVALID_ARG = 1
+VV10_ERR_CUDA = 2
+VV10_ERR_OOM = 3
+VV10_ERR_TIMEOUT = 4
+VV10_ERR_NONFINITE = 5
+VV10_ERR_UNSUPPORTED = 6
+
+VV10_FP64 = 0
+VV10_MIXED_TF32X3 = 1
+VV10_MIXED_BF16X3 = 2
+PRECISIONS = {"fp64": VV10_FP64, "tf32x3": VV10_MIXED_TF32X3, "bf16x3": VV10_MIXED_BF16X3,
+              "mixed": VV10_MIXED_TF32X3}
+
+VV10_DEBUG_FAIL_ALLOC = 1
+VV10_DEBUG_STALL_COPY = 2
+
+# Function names declared in include/vv10.h (checked against the header by the tests).
+EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error",
+           "vv10_prepare_points", "vv10_energy_potential", "vv10_hessian_contract",
+           "vv10_coord_grad", "vv10_weight_grad", "vv10_sync", "vv10_set_tiles",
+           "vv10_debug_inject")
+
+
+class VV10Params(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_double), ("C", ctypes.c_double), ("rho_cut", ctypes.c_double)]
+
+
+class VV10Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libvv10 (optionally compiling it first).  Raises if it is not available."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libvv10 is not built ({_build.LIB} missing); run "
+                           "paper_2208_14639_gb300.build.build() or __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    I32, I64, D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "vv10_create": (st, [ctypes.POINTER(P), ctypes.c_int]),
+        "vv10_destroy": (st, [P]),
+        "vv10_status_string": (ctypes.c_char_p, [st]),
+        "vv10_last_error": (ctypes.c_char_p, [P]),
+        "vv10_prepare_points": (st, [P, I64, P, P, P, P, P, I32, VV10Params,
+                                     ctypes.POINTER(I64), P]),
+        "vv10_energy_potential": (st, [P, st, ctypes.POINTER(D), P, P, P]),
+        "vv10_hessian_contract": (st, [P, st, I32, P, P, P, P, P]),
+        "vv10_coord_grad": (st, [P, st, P, P, P, P]),
+        "vv10_weight_grad": (st, [P, P, P]),
+        "vv10_sync": (st, [P, P]),
+        "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "vv10_debug_inject": (st, [P, ctypes.c_int, I64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(h, status: int, what: str):
+    if status != VV10_OK:
+        lib = load()
+        msg = lib.vv10_status_string(status).decode()
+        detail = lib.vv10_last_error(h).decode() if h else ""
+        raise VV10Error(status, f"{what}: {msg}" + (f" ({detail})" if detail else ""))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t: Optional[torch.Tensor], name: str, dtype=torch.float64, shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- one wrapper per entry point
+
+def vv10_create(device: int = 0) -> ctypes.c_void_p:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(None, lib.vv10_create(ctypes.byref(h), int(device)), "vv10_create")
+    return h
+
+
+def vv10_destroy(h) -> None:
+    _check(None, load().vv10_destroy(h), "vv10_destroy")
+
+
+def vv10_status_string(status: int) -> str:
+    return load().vv10_status_string(int(status)).decode()
+
+
+def vv10_last_error(h) -> str:
+    return load().vv10_last_error(h).decode()
+
+
+def vv10_prepare_points(h, xyz, w, rho, grad_rho, atom_of_point=None, n_atom: int = 0,
+                        b: float = 6.0, C: float = 0.01, rho_cut: float = 1e-10,
+                        stream=None) -> int:
+    n = int(w.shape[0])
+    nk = ctypes.c_int64()
+    st = load().vv10_prepare_points(
+        h, n, _dptr(xyz, "xyz", shape=(n, 3)), _dptr(w, "w", shape=(n,)),
+        _dptr(rho, "rho", shape=(n,)), _dptr(grad_rho, "grad_rho", shape=(n, 3)),
+        _dptr(atom_of_point, "atom_of_point", torch.int32, (n,)), int(n_atom),
+        VV10Params(b, C, rho_cut), ctypes.byref(nk), _stream(stream))
+    _check(h, st, "vv10_prepare_points")
+    return int(nk.value)
+
+
+def vv10_energy_potential(h, prec: int, vrho=None, vgamma=None, stream=None,
+                          want_energy: bool = True) -> Optional[float]:
+    e = ctypes.c_double()
+    st = load().vv10_energy_potential(h, int(prec), ctypes.byref(e) if want_energy else None,
+                                      _dptr(vrho, "vrho"), _dptr(vgamma, "vgamma"),
+                                      _stream(stream))
+    _check(h, st, "vv10_energy_potential")
+    return float(e.value) if want_energy else None
+
+
+def vv10_hessian_contract(h, prec: int, rho_t, grad_rho_t, f_rho_t, f_gamma_t,
+                          stream=None) -> None:
+    P, n = int(rho_t.shape[0]), int(rho_t.shape[1])
+    st = load().vv10_hessian_contract(
+        h, int(prec), P, _dptr(rho_t, "rho_t", shape=(P, n)),
+        _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)),
+        _dptr(f_rho_t, "f_rho_t", shape=(P, n)), _dptr(f_gamma_t, "f_gamma_t", shape=(P, n)),
+        _stream(stream))
+    _check(h, st, "vv10_hessian_contract")
+
+
+def vv10_coord_grad(h, prec: int, grad_points=None, grad_atoms=None, EUW_Bgr=None,
+                    stream=None) -> None:
+    st = load().vv10_coord_grad(h, int(prec), _dptr(grad_points, "grad_points"),
+                                _dptr(grad_atoms, "grad_atoms"), _dptr(EUW_Bgr, "EUW_Bgr"),
+                                _stream(stream))
+    _check(h, st, "vv10_coord_grad")
+
+
+def vv10_weight_grad(h, dEdw, stream=None) -> None:
+    _check(h, load().vv10_weight_grad(h, _dptr(dEdw, "dEdw"), _stream(stream)),
+           "vv10_weight_grad")
+
+
+def vv10_sync(h, stream=None) -> None:
+    _check(h, load().vv10_sync(h, _stream(stream)), "vv10_sync")
+
+
+def vv10_set_tiles(h, what: int, rows_per_thread: int, n_split: int) -> None:
+    _check(h, load().vv10_set_tiles(h, int(what), int(rows_per_thread), int(n_split)),
+           "vv10_set_tiles")
+
+
+def vv10_debug_inject(h, what: int, value: int) -> None:
+    _check(h, load().vv10_debug_inject(h, int(what), int(value)), "vv10_debug_inject")
+
+
+# ---------------------------------------------------------------- convenience owner
+
+class VV10:
+    """Owns a handle and allocates outputs; every computation is a library call."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        self.h = vv10_create(self.device)
+        self.n = 0
+        self.n_atom = 0
+        self.n_kept = 0
+
+    def close(self):
+        if self.h is not None:
+            vv10_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare(self, xyz, w, rho, grad_rho, atom_of_point=None, n_atom=0, b=6.0, C=0.01,
+                rho_cut=1e-10, stream=None) -> int:
+        self.n = int(w.shape[0])
+        self.n_atom = int(n_atom)
+        self.n_kept = vv10_prepare_points(self.h, xyz, w, rho, grad_rho, atom_of_point, n_atom,
+                                          b, C, rho_cut, stream)
+        return self.n_kept
+
+    def energy_potential(self, prec=VV10_FP64, stream=None, want_energy=True):
+        dev = torch.device("cuda", self.device)
+        vrho = torch.empty(self.n, dtype=torch.float64, device=dev)
+        vgamma = torch.empty(self.n, dtype=torch.float64, device=dev)
+        e = vv10_energy_potential(self.h, prec, vrho, vgamma, stream, want_energy)
+        return e, vrho, vgamma
+
+    def hessian_contract(self, rho_t, grad_rho_t, prec=VV10_FP64, stream=None):
+        fr = torch.empty_like(rho_t)
+        fg = torch.empty_like(rho_t)
+        vv10_hessian_contract(self.h, prec, rho_t, grad_rho_t, fr, fg, stream)
+        return fr, fg
+
+    def coord_grad(self, prec=VV10_FP64, atoms=True, resolved=False, stream=None):
+        dev = torch.device("cuda", self.device)
+        gp = torch.empty(self.n, 3, dtype=torch.float64, device=dev)
+        ga = torch.empty(self.n_atom, 3, dtype=torch.float64, device=dev) if atoms and self.n_atom else None
+        euw = (torch.empty(3, self.n, self.n_atom, 3, dtype=torch.float64, device=dev)
+               if resolved and self.n_atom else None)
+        vv10_coord_grad(self.h, prec, gp, ga, euw, stream)
+        return gp, ga, euw
+
+    def weight_grad(self, stream=None):
+        out = torch.empty(self.n, dtype=torch.float64, device=torch.device("cuda", self.device))
+        vv10_weight_grad(self.h, out, stream)
+        return out

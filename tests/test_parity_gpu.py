@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (each error against the FP64 oracle):
+  FP64 path:  |dE|/|E| <= 1e-11; potential, Hessian contraction and coordinate terms
+              <= 1e-10 relative (L2 / Frobenius over the whole output);
+  mixed path: |dE| <= 1e-7 Eh; potential <= 1e-6 relative L2 (vrho and vgamma separately);
+              coordinate gradient <= 1e-6 relative.
+Small cases compare every output element; the full-size water-hexamer grid (174,600
+points) compares the energy in full and sampled output rows (full j sums) otherwise.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2208_14639_gb300 import synth, vv10
+
+pytestmark = pytest.mark.gpu
+
+FP64 = vv10.VV10_FP64
+MIXED = vv10.VV10_MIXED_TF32X3
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    vv10.load(build_if_missing=True)
+    return torch.device("cuda", 0)
+
+
+def T(a, dev, dt=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+
+def make_engine(g, dev):
+    eng = vv10.VV10(0)
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                T(g.atom_of_point, dev, torch.int32), g.molecule.n_atom)
+    return eng
+
+
+def small_systems():
+    out = [("water", synth.config_water())]
+    for n, seed, na in ((1, 1, 1), (2, 2, 2), (37, 3, 2), (255, 4, 3), (256, 5, 3), (257, 6, 3),
+                        (700, 7, 4)):
+        out.append((f"rand{n}", synth.random_points(n, seed=seed, n_atom=na)))
+    return out
+
+
+SMALL = small_systems()
+
+
+@pytest.mark.parametrize("name,g", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_energy_potential(dev, oracle_mod, name, g, prec):
+    e_ref, vr_ref, vg_ref = oracle_mod.potential(g.coords, g.weights, g.rho, g.grad_rho)
+    eng = make_engine(g, dev)
+    e, vr, vg = eng.energy_potential(prec)
+    vr, vg = vr.cpu().numpy(), vg.cpu().numpy()
+    if prec == FP64:
+        assert abs(e - e_ref) <= 1e-11 * abs(e_ref)
+        assert rel(vr, vr_ref) <= 1e-10
+        assert rel(vg, vg_ref) <= 1e-10
+    else:
+        assert abs(e - e_ref) <= 1e-7
+        assert rel(vr, vr_ref) <= 1e-6
+        assert rel(vg, vg_ref) <= 1e-6
+    kept = g.rho >= 1e-10
+    assert np.all(vr[~kept] == 0.0) and np.all(vg[~kept] == 0.0)
+    eng.close()
+
+
+@pytest.mark.parametrize("name,g", SMALL[:1] + SMALL[3:], ids=[s[0] for s in SMALL[:1] + SMALL[3:]])
+def test_hessian_contraction_fp64(dev, oracle_mod, name, g):
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+    eng = make_engine(g, dev)
+    eng.energy_potential(FP64)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
+    assert rel(fr.cpu().numpy(), fr_ref) <= 1e-10
+    assert rel(fg.cpu().numpy(), fg_ref) <= 1e-10
+    eng.close()
+
+
+def test_hessian_single_trial_and_odd_P(dev, oracle_mod):
+    g = synth.random_points(300, seed=11, n_atom=3)
+    rng = np.random.default_rng(1)
+    for P in (1, 5, 33):
+        rt = rng.normal(size=(P, g.n)) * g.rho
+        gt = rng.normal(size=(P, g.n, 3)) * np.abs(g.grad_rho)[None]
+        fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+        eng = make_engine(g, dev)
+        eng.energy_potential(FP64)
+        fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
+        assert rel(fr.cpu().numpy(), fr_ref) <= 1e-10
+        assert rel(fg.cpu().numpy(), fg_ref) <= 1e-10
+        eng.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_coordinate_terms(dev, oracle_mod, prec):
+    g = synth.config_water()
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    pg_ref = oracle_mod.point_grad(*args)
+    rows = np.arange(0, g.n, 97)
+    oE, oU, oW = oracle_mod.atom_resolved(*args, g.atom_of_point, 3, rows=rows)
+    eng = make_engine(g, dev)
+    gp, ga, euw = eng.coord_grad(prec, atoms=True, resolved=True)
+    gp, ga, euw = gp.cpu().numpy(), ga.cpu().numpy(), euw.cpu().numpy()
+    tol = 1e-10 if prec == FP64 else 1e-6
+    assert rel(gp, pg_ref) <= tol
+    seg = np.array([pg_ref[g.atom_of_point == a].sum(axis=0) for a in range(3)])
+    assert rel(ga, seg) <= (1e-9 if prec == FP64 else 1e-5)
+    # translational invariance: the atom terms sum to zero up to rounding
+    assert np.abs(ga.sum(axis=0)).max() <= (1e-9 if prec == FP64 else 1e-6) * np.abs(ga).max()
+    for q, ref in enumerate((oE, oU, oW)):
+        assert rel(euw[q][rows], ref) <= (1e-10 if prec == FP64 else 1e-5)
+    eng.close()
+
+
+def test_atom_resolved_and_gradient_with_interleaved_atoms(dev, oracle_mod):
+    """Points given in a random order (atoms interleaved) are grouped by the library."""
+    g = synth.random_points(400, seed=13, n_atom=4)
+    perm = np.random.default_rng(0).permutation(g.n)
+    h = synth.GridDensity(g.coords[perm], g.weights[perm], g.rho[perm], g.grad_rho[perm],
+                          g.atom_of_point[perm], g.molecule)
+    args = (h.coords, h.weights, h.rho, h.grad_rho)
+    pg_ref = oracle_mod.point_grad(*args)
+    ag_ref = oracle_mod.atom_grad(*args, h.atom_of_point, 4)
+    oE, oU, oW = oracle_mod.atom_resolved(*args, h.atom_of_point, 4)
+    eng = make_engine(h, dev)
+    gp, ga, euw = eng.coord_grad(FP64, atoms=True, resolved=True)
+    assert rel(gp.cpu().numpy(), pg_ref) <= 1e-10
+    assert rel(ga.cpu().numpy(), ag_ref) <= 1e-10
+    euw = euw.cpu().numpy()
+    for q, ref in enumerate((oE, oU, oW)):
+        assert rel(euw[q], ref) <= 1e-10
+    eng.close()
+
+
+def test_permutation_and_determinism(dev):
+    g = synth.random_points(333, seed=21, n_atom=3)
+    perm = np.random.default_rng(5).permutation(g.n)
+    eng = make_engine(g, dev)
+    e1, vr1, _ = eng.energy_potential(MIXED)
+    e1b, vr1b, _ = eng.energy_potential(MIXED)
+    assert e1 == e1b and torch.equal(vr1, vr1b)  # bitwise repeatable
+    h = synth.GridDensity(g.coords[perm], g.weights[perm], g.rho[perm], g.grad_rho[perm],
+                          g.atom_of_point[perm], g.molecule)
+    eng2 = make_engine(h, dev)
+    e2, vr2, _ = eng2.energy_potential(FP64)
+    e3, vr3, _ = eng.energy_potential(FP64)
+    assert abs(e2 - e3) <= 1e-13 * abs(e3)
+    assert rel(vr2.cpu().numpy(), vr3.cpu().numpy()[perm]) <= 1e-12
+    eng.close()
+    eng2.close()
+
+
+def test_weight_gradient(dev, oracle_mod):
+    g = synth.random_points(500, seed=8, n_atom=3)
+    E = oracle_mod.pair_sums(g.coords, g.weights, g.rho, g.grad_rho)["E"]
+    ref = g.rho * (oracle_mod.beta() + E)
+    eng = make_engine(g, dev)
+    eng.energy_potential(FP64)
+    assert rel(eng.weight_grad().cpu().numpy(), ref) <= 1e-10
+    eng.close()
+
+
+# ----------------------------------------------------------------- full-size grid
+
+@pytest.fixture(scope="module")
+def hexamer():
+    return synth.config_water_hexamer()
+
+
+def test_full_size_hexamer_energy_potential(dev, oracle_mod, hexamer):
+    g = hexamer
+    e_ref = oracle_mod.energy(g.coords, g.weights, g.rho, g.grad_rho)
+    rows = np.linspace(0, g.n - 1, 400).astype(np.int64)
+    _, vr_ref, vg_ref = oracle_mod.potential(g.coords, g.weights, g.rho, g.grad_rho, rows=rows)
+    eng = make_engine(g, dev)
+    for prec in (FP64, MIXED):
+        e, vr, vg = eng.energy_potential(prec)
+        vr, vg = vr.cpu().numpy()[rows], vg.cpu().numpy()[rows]
+        if prec == FP64:
+            assert abs(e - e_ref) <= 1e-11 * abs(e_ref)
+            assert rel(vr, vr_ref) <= 1e-10 and rel(vg, vg_ref) <= 1e-10
+        else:
+            assert abs(e - e_ref) <= 1e-7
+            assert rel(vr, vr_ref) <= 1e-6 and rel(vg, vg_ref) <= 1e-6
+    eng.close()
+
+
+def test_full_size_hexamer_hessian_fp64_sampled(dev, oracle_mod, hexamer):
+    g = hexamer
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    rows = np.linspace(0, g.n - 1, 96).astype(np.int64)
+    fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt,
+                                                 rows=rows)
+    eng = make_engine(g, dev)
+    eng.energy_potential(FP64)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
+    assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-10
+    assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-10
+    eng.close()
+
+
+# ----------------------------------------------------------------- error paths
+
+def test_error_paths(dev):
+    g = synth.random_points(64, seed=3)
+    eng = vv10.VV10(0)
+    lib = vv10.load()
+    # call order: nothing prepared
+    assert lib.vv10_energy_potential(eng.h, FP64, None, None, None, None) == vv10.VV10_ERR_INVALID_ARG
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                T(g.atom_of_point, dev, torch.int32), 2)
+    rt = T(np.ones((2, g.n)), dev)
+    gt = T(np.ones((2, g.n, 3)), dev)
+    fr = torch.empty_like(rt)
+    with pytest.raises(vv10.VV10Error) as ei:  # Hessian before energy/potential
+        vv10.vv10_hessian_contract(eng.h, FP64, rt, gt, fr, fr.clone())
+    assert ei.value.status == vv10.VV10_ERR_INVALID_ARG
+    # a host pointer where a device pointer is required
+    host = np.zeros(g.n)
+    st = lib.vv10_energy_potential(eng.h, FP64, None, ctypes.c_void_p(host.ctypes.data), None, None)
+    assert st == vv10.VV10_ERR_INVALID_ARG
+    # bad precision, P out of range
+    assert lib.vv10_energy_potential(eng.h, 7, None, None, None, None) == vv10.VV10_ERR_INVALID_ARG
+    # injected allocation failure, then recovery
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev))
+    vv10.vv10_debug_inject(eng.h, vv10.VV10_DEBUG_FAIL_ALLOC, 1)
+    with pytest.raises(vv10.VV10Error) as ei:
+        eng.energy_potential(FP64)
+    assert ei.value.status == vv10.VV10_ERR_OOM
+    e_ok, _, _ = eng.energy_potential(FP64)
+    # bounded wait that runs out: TIMEOUT reported, the context stays usable
+    vv10.vv10_debug_inject(eng.h, vv10.VV10_DEBUG_STALL_COPY, 1)
+    with pytest.raises(vv10.VV10Error) as ei:
+        eng.energy_potential(FP64)
+    assert ei.value.status == vv10.VV10_ERR_TIMEOUT
+    e_again, _, _ = eng.energy_potential(FP64)
+    assert e_again == e_ok
+    # non-finite input is rejected
+    bad = g.weights.copy()
+    bad[5] = np.nan
+    with pytest.raises(vv10.VV10Error) as ei:
+        eng.prepare(T(g.coords, dev), T(bad, dev), T(g.rho, dev), T(g.grad_rho, dev))
+    assert ei.value.status == vv10.VV10_ERR_INVALID_ARG
+    # atom index out of range is rejected
+    atoms = g.atom_of_point.copy()
+    atoms[3] = 9
+    with pytest.raises(vv10.VV10Error) as ei:
+        eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                    T(atoms, dev, torch.int32), 2)
+    assert ei.value.status == vv10.VV10_ERR_INVALID_ARG
+    eng.close()
