@@ -1,0 +1,469 @@
+#!/usr/bin/env python
+"""VV10 pair-evaluation throughput on GB300 (and the FP64 CPU oracle as the reference arm).
+
+One step = one pass of the whole hot path over the workload's synthetic grid, through the
+C ABI: vv10_prepare_points -> vv10_energy_potential -> vv10_hessian_contract (P trials) ->
+vv10_coord_grad (point gradient, atom sums, atom-resolved E/U/W^Bgr).  Each of the three
+pair-sum entry points evaluates N_kept^2 ordered pairs per call, so
+    value = 3 * N_kept^2 * steps / (time of the timed steps)         [pair evals/s]
+with inputs resident in HBM when the timed region starts.  The same step in FP64 and
+per-call rates are reported beside it.  N > 1 (torchrun): every rank runs its own copy of
+the workload (independent problems, no data-path collective); value sums over ranks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload hexamer|water|cluster24|chon60] [--precision mixed|fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "VV10 pair evals/s: E+potential & Hessian contraction, mixed vs FP64 GPU"
+UNIT = "pair evals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+# FP32 operations per pair counted from the formulas each kernel evaluates:
+#   tensor-core contraction: kernel tiles T1..T4 with their TF32 hi/lo splits, both kinds
+ALU_OPS_PER_PAIR_TC = 80
+
+
+def workloads():
+    from paper_2208_14639_gb300 import synth
+    return {
+        "water": ("water, 3 atoms, 30x110 points per atom (9,900 points), P=9", synth.config_water),
+        "hexamer": ("water-hexamer-like cluster, 18 atoms, 50x194 points per atom (174,600 points), P=54",
+                    synth.config_water_hexamer),
+        "cluster24": ("24-atom fragment cluster, 30x139 points per atom (100,080 points), P=72",
+                      synth.config_cluster24),
+        "chon60": ("60-atom CHON molecule, 75x302 points per atom (1,359,000 points), P=180",
+                   synth.config_chon60),
+    }
+
+
+# ------------------------------------------------------------------ host-side rank logic
+
+def rank_info():
+    """(rank, world_size, local_rank) from the torchrun environment (defaults 0, 1, 0)."""
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Maximum of a per-rank scalar (a host-side reduction of the timing, not of data)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "-i", str(self.index),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, active = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.REASONS, parts[2:6]):
+                if v.lower().startswith("active"):
+                    active.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(active),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+class Problem:
+    """A workload's inputs resident on the device plus preallocated outputs."""
+
+    def __init__(self, g, dev):
+        import torch
+        from paper_2208_14639_gb300 import synth
+        T = lambda a, dt=torch.float64: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+        rt, gt = synth.trial_densities(g.molecule, g.coords)
+        self.g = g
+        self.n = g.n
+        self.n_atom = g.molecule.n_atom
+        self.P = rt.shape[0]
+        self.host = {"xyz": g.coords, "w": g.weights, "rho": g.rho, "grad": g.grad_rho,
+                     "atom": g.atom_of_point.astype(np.int32), "rt": rt, "gt": gt}
+        self.d = {k: T(v, torch.int32 if k == "atom" else torch.float64) for k, v in self.host.items()}
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.out = {
+            "vrho": torch.empty(self.n, **f64), "vgamma": torch.empty(self.n, **f64),
+            "frt": torch.empty(self.P, self.n, **f64), "fgt": torch.empty(self.P, self.n, **f64),
+            "gp": torch.empty(self.n, 3, **f64), "ga": torch.empty(self.n_atom, 3, **f64),
+            "euw": torch.empty(3, self.n, self.n_atom, 3, **f64),
+        }
+
+    def input_bytes(self):
+        return int(sum(v.nbytes for v in self.host.values()))
+
+
+def run_step(vv, h, pb, prec):
+    """One pass of the whole path through the C ABI; returns (n_kept, energy)."""
+    d, o = pb.d, pb.out
+    nk = vv.vv10_prepare_points(h, d["xyz"], d["w"], d["rho"], d["grad"], d["atom"], pb.n_atom)
+    e = vv.vv10_energy_potential(h, prec, o["vrho"], o["vgamma"])
+    vv.vv10_hessian_contract(h, prec, d["rt"], d["gt"], o["frt"], o["fgt"])
+    vv.vv10_coord_grad(h, prec, o["gp"], o["ga"], o["euw"])
+    return nk, e
+
+
+def time_steps(vv, h, pb, prec, steps, warmup, world):
+    import torch
+    for _ in range(warmup):
+        run_step(vv, h, pb, prec)
+    vv.vv10_sync(h)
+    vv.vv10_profile_enable(h, True)
+    vv.vv10_profile_read(h)  # reset counters
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    nk = e = None
+    for _ in range(steps):
+        nk, e = run_step(vv, h, pb, prec)
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = a.elapsed_time(b)
+    prof = vv.vv10_profile_read(h)
+    vv.vv10_profile_enable(h, False)
+    return ms, nk, e, prof
+
+
+def time_e2e(vv, h, pb, prec, steps, warmup):
+    """Same step with host inputs: pinned H2D of every input and D2H of every output inside
+    the timed region."""
+    import torch
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).to(
+        torch.int32 if k == "atom" else torch.float64).pin_memory() for k, v in pb.host.items()}
+    pout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in pb.out.items()}
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = sum(t.numel() * t.element_size() for t in pout.values()) + 8  # + the energy scalar
+
+    def one():
+        for k, t in pin.items():
+            pb.d[k].copy_(t, non_blocking=True)
+        nk, e = run_step(vv, h, pb, prec)
+        for k, t in pout.items():
+            t.copy_(pb.out[k], non_blocking=True)
+        return nk
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nk = 0
+    for _ in range(steps):
+        nk = one()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    return sec, nk, h2d, d2h
+
+
+def cpu_baseline(pb, budget_s: float):
+    """The FP64 oracle, as it stands, on a bounded row sample of the same workload."""
+    import oracle
+    g = pb.g
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    kept = np.flatnonzero(g.rho >= 1e-10)
+    nk = kept.size
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(cores)
+    # calibrate on a small sample, then size the sample to the budget
+    rows = kept[np.linspace(0, nk - 1, 64).astype(np.int64)]
+    t0 = time.perf_counter()
+    oracle.potential(*args, rows=rows)
+    oracle.hessian_contract(*args, pb.host["rt"], pb.host["gt"], rows=rows[:16])
+    oracle.point_grad(*args, rows=rows)
+    cal = time.perf_counter() - t0
+    scale = max(1.0, budget_s / max(cal, 1e-3))
+    n_rows = int(min(nk, 64 * scale))
+    n_hrows = int(min(nk, 16 * scale))
+    rows = kept[np.linspace(0, nk - 1, n_rows).astype(np.int64)]
+    hrows = kept[np.linspace(0, nk - 1, n_hrows).astype(np.int64)]
+    t0 = time.perf_counter()
+    oracle.potential(*args, rows=rows)
+    oracle.hessian_contract(*args, pb.host["rt"], pb.host["gt"], rows=hrows)
+    oracle.point_grad(*args, rows=rows)
+    sec = time.perf_counter() - t0
+    pairs = (2 * n_rows + n_hrows) * nk
+    return {"value": pairs / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "seconds": sec,
+            "sample": f"{n_rows} rows (energy/potential and point gradient) and {n_hrows} rows "
+                      f"(Hessian contraction, P={pb.P}) of {nk} kept points, full j sums"}
+
+
+def gpu_arm(args):
+    import torch
+    from paper_2208_14639_gb300 import vv10 as vv
+
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vv.load(build_if_missing=True)
+    label, make = workloads()[args.workload]
+    g = make()
+    pb = Problem(g, dev)
+    h = vv.vv10_create(local)
+    prec = vv.PRECISIONS[args.precision]
+    peaks, peak_src = load_peaks()
+
+    with ClockSampler(local) as clk:
+        ms, nk, e_mixed, prof = time_steps(vv, h, pb, prec, args.steps, args.warmup, world)
+    clocks = clk.summary()
+    ms_max = max_over_ranks(ms, world)
+    pairs_call = float(nk) * float(nk)
+    value = 3.0 * pairs_call * args.steps * world / (ms_max / 1e3)
+
+    K = args.steps
+    per = {k: v[0] / K for k, v in prof.items()}
+    launches = sum(v[1] for v in prof.values())
+    t_ep = per["pair_sums_EUW"] + per["energy_epilogue"]
+    t_hess = (per["pair_sums_ABC"] + per["trial_prep"] + per["contraction_fp64"] +
+              per["contraction_tensor_core"] + per["hessian_epilogue"])
+    t_coord = per["pair_sums_grad"] + per["grad_epilogue"] + per["atom_resolved"]
+    hess_flops = 8.0 * pairs_call * pb.P
+    breakdown = {
+        "energy_potential_pairs_per_s": pairs_call / (t_ep / 1e3) if t_ep else None,
+        "hessian_pairs_per_s": pairs_call / (t_hess / 1e3) if t_hess else None,
+        "hessian_P_pairs_per_s": pb.P * pairs_call / (t_hess / 1e3) if t_hess else None,
+        "hessian_alg_tflops": hess_flops / (t_hess / 1e3) / 1e12 if t_hess else None,
+        "coord_grad_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
+        "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
+    }
+
+    # roofline of the dominant kernel
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    dom = max(per, key=per.get)
+    roof = None
+    if dom == "contraction_tensor_core":
+        t = per[dom] / 1e3
+        ppad = ((pb.P + 31) // 32) * 32
+        tf32_peak = peaks["bf16_tflops"] * 0.5 * 1e12  # nominal tf32 : bf16 = 1 : 2
+        t_tensor = 3 * 8.0 * pairs_call * ppad / tf32_peak
+        alu_peak = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
+        t_alu = ALU_OPS_PER_PAIR_TC * pairs_call / alu_peak
+        if t_alu >= t_tensor:
+            roof = {"bound": "alu", "achieved": ALU_OPS_PER_PAIR_TC * pairs_call / t / 1e12,
+                    "peak": alu_peak / 1e12, "unit": "TFLOP/s (FP32 ops)",
+                    "frac": t_alu / t, "traffic": None, "kernel": "k_hess_tc",
+                    "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median under load)",
+                    "tensor_alt": {"achieved_alg_tflops": hess_flops / t / 1e12,
+                                   "tf32_peak_tflops": tf32_peak / 1e12,
+                                   "frac_of_split_peak": t_tensor / t}}
+        else:
+            roof = {"bound": "tensor", "achieved": hess_flops / t / 1e12, "peak": tf32_peak / 1e12,
+                    "unit": "TFLOP/s", "frac": hess_flops / t / tf32_peak, "traffic": None,
+                    "kernel": "k_hess_tc",
+                    "peak_source": f"{peak_src} bf16 {peaks['bf16_tflops']} x 0.5 (tf32)"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "kernel": dom}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions"
+                 if prec != vv.VV10_FP64 else "f64",
+        "data": "synthetic (seeded molecule-shaped grids, Gaussian densities, analytic trials)",
+        "config": {"workload": label, "n_points": pb.n, "n_kept": nk, "P": pb.P,
+                   "precision": args.precision, "pairs_per_call": pairs_call,
+                   "l2": f"inputs larger than L2 ({pb.input_bytes() / 1e6:.0f} MB resident)",
+                   "parallelism": f"replica x{world}"},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "breakdown": breakdown,
+        "energy": e_mixed,
+    }
+
+    if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
+        ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
+        per64 = {k: v[0] for k, v in prof64.items()}
+        t_h64 = (per64["pair_sums_ABC"] + per64["trial_prep"] + per64["contraction_fp64"] +
+                 per64["hessian_epilogue"])
+        result["fp64"] = {
+            "value": 3.0 * pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
+            "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
+            "energy_potential_pairs_per_s": pairs_call / ((per64["pair_sums_EUW"] + per64["energy_epilogue"]) / 1e3),
+            "hessian_pairs_per_s": pairs_call / (t_h64 / 1e3),
+            "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
+        }
+        result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
+
+    sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, max(1, min(K, 3)), 1)
+    result["e2e"] = {"value": 3.0 * pairs_call * max(1, min(K, 3)) / sec, "unit": UNIT,
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(pb, args.cpu_seconds)
+
+    vv.vv10_destroy(h)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+
+def reference_arm(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    import oracle
+    label, make = workloads()[args.workload]
+    g = make()
+    from paper_2208_14639_gb300 import synth
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    argsg = (g.coords, g.weights, g.rho, g.grad_rho)
+    kept = np.flatnonzero(g.rho >= 1e-10)
+    nk = kept.size
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(cores)
+    # each step: a bounded row sample of the same three calls (about 20 s per step)
+    rows = kept[np.linspace(0, nk - 1, 64).astype(np.int64)]
+    t0 = time.perf_counter()
+    oracle.potential(*argsg, rows=rows)
+    oracle.hessian_contract(*argsg, rt, gt, rows=rows[:16])
+    oracle.point_grad(*argsg, rows=rows)
+    scale = max(1.0, min(20.0, 120.0 / (args.steps + args.warmup)) / max(time.perf_counter() - t0, 1e-3))
+    n_rows, n_hrows = int(min(nk, 64 * scale)), int(min(nk, 16 * scale))
+    rows = kept[np.linspace(0, nk - 1, n_rows).astype(np.int64)]
+    hrows = kept[np.linspace(0, nk - 1, n_hrows).astype(np.int64)]
+
+    def step():
+        oracle.potential(*argsg, rows=rows)
+        oracle.hessian_contract(*argsg, rt, gt, rows=hrows)
+        oracle.point_grad(*argsg, rows=rows)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sec = time.perf_counter() - t0
+    pairs = (2 * n_rows + n_hrows) * nk * args.steps
+    value = pairs / sec
+    sample = (f"{n_rows} rows (energy/potential, point gradient) and {n_hrows} rows (Hessian, "
+              f"P={rt.shape[0]}) of {nk} kept points per step, full j sums")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": label, "n_points": g.n, "n_kept": int(nk),
+                                        "P": int(rt.shape[0])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("hexamer", "water", "cluster24", "chon60"), default="hexamer")
+    ap.add_argument("--precision", choices=("mixed", "tf32x3", "fp64"), default="mixed")
+    ap.add_argument("--no-fp64-arm", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

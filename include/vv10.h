@@ -163,6 +163,17 @@ vv10_status vv10_sync(vv10_handle h, void* stream);
  * 0 = derived from the SM count.  Errors: INVALID_ARG. */
 vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split);
 
+/* Launch accounting and per-phase GPU timing (the paper has no counterpart).
+ * vv10_profile_enable(h, 1): from now on every kernel launch of this handle is bracketed
+ * by CUDA events recorded on the call's stream; launches are always counted.
+ * vv10_profile_read synchronises the device, writes for phases 0..n-1 (n <= VV10_N_PHASES)
+ * the accumulated milliseconds (ms, may be NULL; 0 when timing was off) and launch counts
+ * (launches, may be NULL), then resets both.  Phase names: vv10_profile_phase_name. */
+#define VV10_N_PHASES 11
+vv10_status vv10_profile_enable(vv10_handle h, int on);
+vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches);
+const char* vv10_profile_phase_name(int phase);
+
 /* Failure-injection hooks for tests (the paper has no counterpart).
  *   VV10_DEBUG_FAIL_ALLOC  value k > 0: the k-th device allocation from now fails (OOM)
  *   VV10_DEBUG_STALL_COPY  value 1: in the next pair-sum launch one CTA never issues its

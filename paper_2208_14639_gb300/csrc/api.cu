@@ -62,6 +62,13 @@ void vv10_ctx::release_all() {
     }
     if (h_pinned) cudaFreeHost(h_pinned);
     h_pinned = nullptr;
+    for (ProfRec& r : prof) {
+        event_pool.push_back(r.a);
+        event_pool.push_back(r.b);
+    }
+    prof.clear();
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+    event_pool.clear();
 }
 
 // Pointer must be device-accessible memory of this handle's device (device or managed).
@@ -132,6 +139,40 @@ vv10_status vv10_ctx::check_device_errors(cudaStream_t st) {
 }
 
 PointsDev vv10_ctx::points() const { return P; }
+
+cudaEvent_t vv10_ctx::take_event() {
+    if (!event_pool.empty()) {
+        cudaEvent_t e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void vv10_ctx::phase_begin(int phase, cudaStream_t st, ProfRec* rec) {
+    rec->phase = phase;
+    rec->a = rec->b = nullptr;
+    if (!prof_on) return;
+    rec->a = take_event();
+    if (rec->a) cudaEventRecord(rec->a, st);
+}
+
+void vv10_ctx::phase_end(ProfRec* rec, cudaStream_t st, int n_launch) {
+    launches[rec->phase] += n_launch;
+    if (!prof_on || !rec->a) return;
+    rec->b = take_event();
+    if (!rec->b) {
+        event_pool.push_back(rec->a);
+        return;
+    }
+    cudaEventRecord(rec->b, st);
+    prof.push_back(*rec);
+}
 
 // ---------------------------------------------------------------- ABI
 
@@ -270,9 +311,12 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
     ps.center = static_cast<double*>(h->prep_small.p);
     ps.nk_dev = reinterpret_cast<int64_t*>(static_cast<double*>(h->prep_small.p) + 4);
     int* err = static_cast<int*>(h->dev_err.p);
-    VV10_CUDA(h, launch_prepare_count(n, xyz, w, rho, grad_rho, atom_of_point, n_atom, prm.rho_cut,
-                                      ps, err, st),
-              "prepare count");
+    {
+        PhaseScope ph(h, PH_PREPARE, st, 2);
+        VV10_CUDA(h, launch_prepare_count(n, xyz, w, rho, grad_rho, atom_of_point, n_atom,
+                                          prm.rho_cut, ps, err, st),
+                  "prepare count");
+    }
     int64_t* hnk = reinterpret_cast<int64_t*>(h->h_pinned);
     VV10_CUDA(h, cudaMemcpyAsync(hnk, ps.nk_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
               "read n_kept");
@@ -289,6 +333,7 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
     VV10_TRY(h->ensure(h->r64b, sizeof(double4) * cap, "FP64 records"));
     VV10_TRY(h->ensure(h->r32a, sizeof(float4) * cap, "FP32 records"));
     VV10_TRY(h->ensure(h->r32b, sizeof(float4) * cap, "FP32 records"));
+    PhaseScope ph_scatter(h, PH_PREPARE, st, nk_pad > 0 ? 2 : 1);
     VV10_CUDA(h, launch_prepare_scatter(n, xyz, w, rho, grad_rho, atom_of_point, n_atom,
                                         prm.rho_cut, prm.b, prm.C, ps, nk, nk_pad,
                                         static_cast<int64_t*>(h->orig.p),
@@ -367,9 +412,13 @@ vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_s
     cfg.n_split = req;
     VV10_TRY(ensure(part, sizeof(double) * 3 * static_cast<size_t>(ns) * (P.nk_pad > 0 ? P.nk_pad : 1),
                     "pair-sum partials"));
-    VV10_CUDA(this, launch_pairsum(P, mode, fp64, cfg, static_cast<double*>(part.p),
-                                   static_cast<int*>(dev_err.p), st),
-              "pair-sum kernel");
+    {
+        PhaseScope ph(this, mode == MODE_EUW ? PH_PAIR_EUW : (mode == MODE_ABC ? PH_PAIR_ABC : PH_PAIR_GRAD),
+                      st, 1);
+        VV10_CUDA(this, launch_pairsum(P, mode, fp64, cfg, static_cast<double*>(part.p),
+                                       static_cast<int*>(dev_err.p), st),
+                  "pair-sum kernel");
+    }
     *n_split_out = ns;
     return VV10_OK;
 }
@@ -419,6 +468,7 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
     if (P.nk > 0) {
         int ns = 1;
         VV10_TRY(h->run_pairsum(MODE_EUW, fp64, st, &ns));
+        PhaseScope ph(h, PH_EP_EPILOGUE, st, 2);
         VV10_CUDA(h, launch_ep_epilogue(P, static_cast<double*>(h->part.p), ns,
                                         static_cast<double*>(h->sumE.p),
                                         static_cast<double*>(h->sumU.p),
@@ -525,6 +575,7 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
         int ns = 1;
         VV10_TRY(h->run_pairsum(MODE_GRAD, fp64, st, &ns));
         VV10_TRY(h->ensure(h->gk, sizeof(double) * 3 * h->soa_ld, "kept gradient"));
+        PhaseScope ph(h, PH_GRAD_EPILOGUE, st, grad_atoms ? 2 : 1);
         VV10_CUDA(h, launch_grad_epilogue(P, static_cast<double*>(h->part.p), ns,
                                           static_cast<double*>(h->gk.p), grad_points, st),
                   "gradient epilogue");
@@ -532,10 +583,48 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
             VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
                       "atom sums");
     }
-    if (EUW_Bgr)
+    if (EUW_Bgr) {
+        PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
         VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr, static_cast<int*>(h->dev_err.p), st),
                   "atom-resolved terms");
+    }
     return VV10_OK;
+}
+
+vv10_status vv10_profile_enable(vv10_handle h, int on) {
+    VV10_CHECK_HANDLE(h);
+    h->prof_on = (on != 0);
+    return VV10_OK;
+}
+
+vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches) {
+    VV10_CHECK_HANDLE(h);
+    if (n < 0 || n > VV10_N_PHASES) return VV10_ERR_INVALID_ARG;
+    VV10_TRY(h->bind());
+    VV10_CUDA(h, cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    double acc[PH_COUNT] = {0};
+    for (ProfRec& r : h->prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) acc[r.phase] += t;
+        else cudaGetLastError();
+        h->event_pool.push_back(r.a);
+        h->event_pool.push_back(r.b);
+    }
+    h->prof.clear();
+    for (int k = 0; k < n; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = h->launches[k];
+    }
+    for (int k = 0; k < PH_COUNT; ++k) h->launches[k] = 0;
+    return VV10_OK;
+}
+
+const char* vv10_profile_phase_name(int phase) {
+    static const char* names[PH_COUNT] = {
+        "prepare", "pair_sums_EUW", "energy_epilogue", "pair_sums_ABC", "trial_prep",
+        "contraction_fp64", "contraction_tensor_core", "hessian_epilogue", "pair_sums_grad",
+        "grad_epilogue", "atom_resolved"};
+    return (phase >= 0 && phase < PH_COUNT) ? names[phase] : "unknown";
 }
 
 vv10_status vv10_debug_inject(vv10_handle h, int what, int64_t value) {

@@ -40,8 +40,8 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
     H_CUDA(cudaMemsetAsync(f_rho_t, 0, out_bytes, st), "memset f_rho_t");
     H_CUDA(cudaMemsetAsync(f_gamma_t, 0, out_bytes, st), "memset f_gamma_t");
     if (P.nk == 0) return VV10_OK;
-    if (!fp64) {
-        set_error("mixed-precision Hessian contraction is not available in this build");
+    if (prec == VV10_MIXED_BF16X3) {
+        set_error("the BF16x3 Hessian contraction is not available in this build");
         return VV10_ERR_UNSUPPORTED;
     }
 
@@ -53,6 +53,7 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
         H_TRY(ensure(sumC, nkb, "C_i"));
         int ns = 1;
         H_TRY(run_pairsum(MODE_ABC, fp64, st, &ns));
+        PhaseScope ph(this, PH_PAIR_ABC, st, 1);
         H_CUDA(launch_abc_epilogue(P, static_cast<double*>(part.p), ns,
                                    static_cast<double*>(sumA.p), static_cast<double*>(sumB.p),
                                    static_cast<double*>(sumC.p), st),
@@ -68,19 +69,71 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
     H_TRY(ensure(ty, tpad, "trial y"));
     H_TRY(ensure(trt, tk, "trial rho at kept points"));
     H_TRY(ensure(tgt, tk, "trial gamma at kept points"));
+    {
+    PhaseScope ph(this, PH_TRIAL_PREP, st, 1);
     H_CUDA(launch_trial_prep(P, Pn, rho_t, grad_rho_t, static_cast<double*>(tu.p),
                              static_cast<double*>(ty.p), static_cast<double*>(trt.p),
                              static_cast<double*>(tgt.p), st),
            "trial prep");
+    }
+
+    if (!fp64) {
+        // tensor-core path: trials in groups of at most 192 (the MMA N of one launch)
+        const int ng = (Pn + 191) / 192;
+        const int pg = (Pn + ng - 1) / ng;
+        const int ppad = hess_tc_ppad(pg);
+        const int64_t rows = static_cast<int64_t>(ng - 1) * pg + ppad;
+        const size_t sb = sizeof(float) * static_cast<size_t>(rows) * P.nk_pad;
+        H_TRY(ensure(tc_uh, sb, "trial u hi"));
+        H_TRY(ensure(tc_ul, sb, "trial u lo"));
+        H_TRY(ensure(tc_yh, sb, "trial y hi"));
+        H_TRY(ensure(tc_yl, sb, "trial y lo"));
+        {
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 1);
+        H_CUDA(launch_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), Pn,
+                                  static_cast<int32_t>(rows), P.nk_pad, false,
+                                  static_cast<float*>(tc_uh.p), static_cast<float*>(tc_ul.p),
+                                  static_cast<float*>(tc_yh.p), static_cast<float*>(tc_yl.p), st),
+               "trial split");
+        }
+        const size_t ab = sizeof(double) * 2 * static_cast<size_t>(Pn) * P.nk_pad;
+        H_TRY(ensure(hacc, ab, "contraction partials"));
+        H_CUDA(cudaMemsetAsync(hacc.p, 0, ab, st), "zero contraction partials");
+        {
+        PhaseScope ph(this, PH_CONTRACT_TC, st, ng);
+        for (int g = 0; g < ng; ++g) {
+            const int t0 = g * pg;
+            const int pn = (Pn - t0 < pg) ? Pn - t0 : pg;
+            H_CUDA(launch_hess_tc(P, pn, t0, Pn, static_cast<float*>(tc_uh.p),
+                                  static_cast<float*>(tc_ul.p), static_cast<float*>(tc_yh.p),
+                                  static_cast<float*>(tc_yl.p), rows, n_sm, tc_flush,
+                                  static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
+                   "tensor-core contraction");
+        }
+        }
+        PhaseScope ph2(this, PH_HESS_EPILOGUE, st, 1);
+        H_CUDA(launch_hess_epilogue(P, Pn, static_cast<double*>(hacc.p), 1, P.nk_pad,
+                                    static_cast<double*>(sumU.p), static_cast<double*>(sumW.p),
+                                    static_cast<double*>(sumA.p), static_cast<double*>(sumB.p),
+                                    static_cast<double*>(sumC.p), static_cast<double*>(trt.p),
+                                    static_cast<double*>(tgt.p), f_rho_t, f_gamma_t,
+                                    static_cast<int*>(dev_err.p), st),
+               "Hessian epilogue");
+        return VV10_OK;
+    }
 
     HessLaunch cfg;
     cfg.trials_per_cta = pick_trials_per_cta(Pn);
     cfg.n_split = hess_f64_default_split(P, Pn, cfg.trials_per_cta, n_sm);
     H_TRY(ensure(hacc, sizeof(double) * 2 * static_cast<size_t>(cfg.n_split) * Pn * P.nk_pad,
                  "contraction partials"));
-    H_CUDA(launch_hess_f64(P, Pn, static_cast<double*>(tu.p), static_cast<double*>(ty.p), cfg,
-                           static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
-           "FP64 contraction");
+    {
+        PhaseScope ph(this, PH_CONTRACT_F64, st, 1);
+        H_CUDA(launch_hess_f64(P, Pn, static_cast<double*>(tu.p), static_cast<double*>(ty.p), cfg,
+                               static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
+               "FP64 contraction");
+    }
+    PhaseScope ph2(this, PH_HESS_EPILOGUE, st, 1);
     H_CUDA(launch_hess_epilogue(P, Pn, static_cast<double*>(hacc.p), cfg.n_split, P.nk_pad,
                                 static_cast<double*>(sumU.p), static_cast<double*>(sumW.p),
                                 static_cast<double*>(sumA.p), static_cast<double*>(sumB.p),

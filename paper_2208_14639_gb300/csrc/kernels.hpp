@@ -87,10 +87,20 @@ cudaError_t launch_weight_grad(const PointsDev& p, const double* E, double* dEdw
 cudaError_t launch_trial_prep(const PointsDev& p, int32_t P, const double* rho_t,
                               const double* grad_rho_t, double* u, double* y, double* rt_k,
                               double* gt_k, cudaStream_t st);
-// FP32 split variant: u/y hi/lo as FP32 [Ppad][nk_pad] rows (tf32 or bf16-rounded hi).
-cudaError_t launch_trial_split(const double* u, const double* y, int32_t P, int32_t Ppad,
+// Split u, y (FP64 [P][nk_pad]) into TF32 hi and FP32 lo parts, FP32 [Prows][nk_pad];
+// rows t >= P are zero.
+cudaError_t launch_trial_split(const double* u, const double* y, int32_t P, int32_t Prows,
                                int64_t nk_pad, bool bf16, float* uh, float* ul, float* yh,
                                float* yl, cudaStream_t st);
+
+// Tensor-core (split-TF32) contraction of trials [t0, t0 + Pn), Pn <= 192, into the FP64
+// partial output acc [2][acc_P][nk_pad] (zeroed by the caller).  uh/ul/yh/yl: FP32
+// [rows][nk_pad] hi/lo parts of u and y; `flush` = stages between FP64 flushes.
+int hess_tc_ppad(int32_t P);
+cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
+                           const float* uh, const float* ul, const float* yh, const float* yl,
+                           int64_t rows, int n_sm, int flush, double* acc, int* err,
+                           cudaStream_t st);
 
 struct HessLaunch {
     int trials_per_cta = 16;  // FP64 SIMT: 8, 16, 32

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "kernels.hpp"
 #include "vv10.h"
@@ -27,6 +28,17 @@ struct TileOverride {
     bool fp64 = false;
     int rows_per_thread = 0;
     int n_split = 0;
+};
+
+enum Phase : int {
+    PH_PREPARE = 0, PH_PAIR_EUW, PH_EP_EPILOGUE, PH_PAIR_ABC, PH_TRIAL_PREP, PH_CONTRACT_F64,
+    PH_CONTRACT_TC, PH_HESS_EPILOGUE, PH_PAIR_GRAD, PH_GRAD_EPILOGUE, PH_ATOM_RESOLVED,
+    PH_COUNT
+};
+
+struct ProfRec {
+    int phase;
+    cudaEvent_t a, b;
 };
 
 }  // namespace vv10
@@ -68,6 +80,18 @@ struct vv10_ctx {
     // tile overrides (index = mode + 3 * fp64), set by vv10_set_tiles / the autotuner
     vv10::TileOverride overrides[6];
 
+    // stages between FP64 flushes of the tensor-core contraction's register accumulators
+    int tc_flush = 128;
+
+    // launch accounting / profiling
+    bool prof_on = false;
+    int64_t launches[vv10::PH_COUNT] = {0};
+    std::vector<vv10::ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event();
+    void phase_begin(int phase, cudaStream_t st, vv10::ProfRec* rec);
+    void phase_end(vv10::ProfRec* rec, cudaStream_t st, int n_launch);
+
     // test hooks
     int debug_fail_alloc = 0;
     int debug_stall = 0;
@@ -86,3 +110,18 @@ struct vv10_ctx {
                         const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
                         cudaStream_t st);
 };
+
+namespace vv10 {
+// Brackets the kernel launches of one phase: counts them and, when profiling is on,
+// records CUDA events around them on the call's stream.
+struct PhaseScope {
+    vv10_ctx* h;
+    cudaStream_t st;
+    ProfRec rec;
+    int n;
+    PhaseScope(vv10_ctx* h_, int phase, cudaStream_t s, int n_launch) : h(h_), st(s), n(n_launch) {
+        h->phase_begin(phase, st, &rec);
+    }
+    ~PhaseScope() { h->phase_end(&rec, st, n); }
+};
+}  // namespace vv10

@@ -36,7 +36,9 @@ VV10_DEBUG_STALL_COPY = 2
 EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error",
            "vv10_prepare_points", "vv10_energy_potential", "vv10_hessian_contract",
            "vv10_coord_grad", "vv10_weight_grad", "vv10_sync", "vv10_set_tiles",
-           "vv10_debug_inject")
+           "vv10_debug_inject", "vv10_profile_enable", "vv10_profile_read",
+           "vv10_profile_phase_name")
+VV10_N_PHASES = 11
 
 
 class VV10Params(ctypes.Structure):
@@ -84,6 +86,9 @@ def load(build_if_missing: bool = False):
         "vv10_sync": (st, [P, P]),
         "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "vv10_debug_inject": (st, [P, ctypes.c_int, I64]),
+        "vv10_profile_enable": (st, [P, ctypes.c_int]),
+        "vv10_profile_read": (st, [P, ctypes.c_int, P, P]),
+        "vv10_profile_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -197,6 +202,24 @@ def vv10_sync(h, stream=None) -> None:
 def vv10_set_tiles(h, what: int, rows_per_thread: int, n_split: int) -> None:
     _check(h, load().vv10_set_tiles(h, int(what), int(rows_per_thread), int(n_split)),
            "vv10_set_tiles")
+
+
+def vv10_profile_enable(h, on: bool) -> None:
+    _check(h, load().vv10_profile_enable(h, 1 if on else 0), "vv10_profile_enable")
+
+
+def vv10_profile_phase_name(phase: int) -> str:
+    return load().vv10_profile_phase_name(int(phase)).decode()
+
+
+def vv10_profile_read(h) -> dict:
+    """{phase name: (milliseconds, launches)}; synchronises and resets the counters."""
+    import numpy as np
+    ms = np.zeros(VV10_N_PHASES)
+    n = np.zeros(VV10_N_PHASES, dtype=np.int64)
+    _check(h, load().vv10_profile_read(h, VV10_N_PHASES, ms.ctypes.data_as(ctypes.c_void_p),
+                                       n.ctypes.data_as(ctypes.c_void_p)), "vv10_profile_read")
+    return {vv10_profile_phase_name(k): (float(ms[k]), int(n[k])) for k in range(VV10_N_PHASES)}
 
 
 def vv10_debug_inject(h, what: int, value: int) -> None:

@@ -106,6 +106,41 @@ def test_hessian_single_trial_and_odd_P(dev, oracle_mod):
         eng.close()
 
 
+MIXED_HESS = [("water", synth.config_water()), ("rand255", synth.random_points(255, seed=4, n_atom=3)),
+              ("rand700", synth.random_points(700, seed=7, n_atom=4))]
+
+
+@pytest.mark.parametrize("name,g", MIXED_HESS, ids=[s[0] for s in MIXED_HESS])
+def test_hessian_contraction_mixed(dev, oracle_mod, name, g):
+    """Split-TF32 tensor-core contraction: <= 1e-6 relative Frobenius per output."""
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+    eng = make_engine(g, dev)
+    eng.energy_potential(MIXED)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), MIXED)
+    vv10.vv10_sync(eng.h)
+    assert rel(fr.cpu().numpy(), fr_ref) <= 1e-6
+    assert rel(fg.cpu().numpy(), fg_ref) <= 1e-6
+    eng.close()
+
+
+@pytest.mark.parametrize("P", [1, 33, 200])
+def test_hessian_mixed_trial_counts(dev, oracle_mod, P):
+    """Trial counts below one MMA tile, ragged, and above one launch's 192 (two groups)."""
+    g = synth.random_points(300, seed=17, n_atom=3)
+    rng = np.random.default_rng(P)
+    rt = rng.normal(size=(P, g.n)) * g.rho
+    gt = rng.normal(size=(P, g.n, 3)) * np.abs(g.grad_rho)[None]
+    fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+    eng = make_engine(g, dev)
+    eng.energy_potential(MIXED)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), MIXED)
+    vv10.vv10_sync(eng.h)
+    assert rel(fr.cpu().numpy(), fr_ref) <= 1e-6
+    assert rel(fg.cpu().numpy(), fg_ref) <= 1e-6
+    eng.close()
+
+
 @pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
 def test_coordinate_terms(dev, oracle_mod, prec):
     g = synth.config_water()
@@ -200,15 +235,21 @@ def test_full_size_hexamer_energy_potential(dev, oracle_mod, hexamer):
     eng.close()
 
 
-def test_full_size_hexamer_hessian_fp64_sampled(dev, oracle_mod, hexamer):
+def test_full_size_hexamer_hessian_sampled(dev, oracle_mod, hexamer):
     g = hexamer
     rt, gt = synth.trial_densities(g.molecule, g.coords)
     rows = np.linspace(0, g.n - 1, 96).astype(np.int64)
     fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt,
                                                  rows=rows)
     eng = make_engine(g, dev)
+    rtd, gtd = T(rt, dev), T(gt, dev)
+    eng.energy_potential(MIXED)
+    fr, fg = eng.hessian_contract(rtd, gtd, MIXED)
+    vv10.vv10_sync(eng.h)
+    assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-6
+    assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-6
     eng.energy_potential(FP64)
-    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
+    fr, fg = eng.hessian_contract(rtd, gtd, FP64)
     assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-10
     assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-10
     eng.close()
