@@ -5,7 +5,7 @@
 // kernel tiles T1 | T2, 1: f^{gamma,t} / sigma_i with T3 | T4) x all P trials (N of the
 // MMA, padded to a multiple of 32, <= 192) x every j.  A persistent CTA walks its tiles;
 // per stage of 16 j:
-//   * 8 generator warps (2 per TMEM lane quadrant, 8 j each) evaluate the two kernel
+//   * 16 generator warps (4 per TMEM lane quadrant, 4 j each) evaluate the two kernel
 //     tiles for their row in FP32, split them into TF32 hi/lo and store the four 128x16
 //     operand tiles into tensor memory (tcgen05.st);
 //   * the producer warp fetches the stage's j-records (1-D bulk copy) and the four
@@ -27,7 +27,7 @@
 namespace vv10 {
 
 constexpr int kTcKj = 16;                        // j per stage
-constexpr int kTcGenWarps = 8;                   // generator / drain warps
+constexpr int kTcGenWarps = 16;                  // generator / drain warps (4 per lane quadrant)
 constexpr int kTcProducerWarp = kTcGenWarps;     // TMA producer
 constexpr int kTcMmaWarp = kTcGenWarps + 1;      // MMA issuer + TMEM owner
 constexpr int kTcThreads = (kTcGenWarps + 2) * 32;
@@ -82,10 +82,14 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, in
     return true;
 }
 
-// Kernel tiles of one pair: kind 0 -> (T1, T2), kind 1 -> (T3, T4); FP32.
+// Kernel tiles of one pair, FP32, without the -3/2 of Phi (the trial split carries it),
+// i.e. T1..T4 scaled by -2/3.  The hardware reciprocal (relative error below 2^-22) is
+// accurate enough for operands carried to ~22 bits.  NK = 2: all four tiles; NK = 1: the
+// two tiles of output kind `kind` (0 -> T1, T2; 1 -> T3, T4) in t[0], t[1].
+template <int NK>
 __device__ __forceinline__ void pair_tiles(int kind, float xi, float yi, float zi, float oi,
                                            float ki, float pi_, float qi, const float4& a,
-                                           const float4& b, float& ta, float& tb) {
+                                           const float4& b, float (&t)[2 * NK]) {
     const float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
     float r2 = dx * dx;
     r2 = __fmaf_rn(dy, dy, r2);
@@ -94,34 +98,54 @@ __device__ __forceinline__ void pair_tiles(int kind, float xi, float yi, float z
     const float gp = __fmaf_rn(b.x, r2, b.y);
     const float s = g + gp;
     const float ggp = g * gp;
-    const float inv = rcp_refined(ggp * s);
-    const float phi = -1.5f * inv;
-    const float L = ggp * inv;
-    const float Gi = (gp * s) * inv;
-    const float Gj = (g * s) * inv;
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(ggp * s));
+    const float L = ggp * inv;          // 1/s
+    const float Gi = (gp * s) * inv;    // 1/g
+    const float Gj = (g * s) * inv;     // 1/g'
     const float M = 2.0f * __fmaf_rn(L, L, Gi * Gj);
     const float Ai = __fmaf_rn(qi, r2, pi_);   // rho_i a_i
     const float Aj = __fmaf_rn(b.w, r2, b.z);  // rho_j a_j
-    const float rp = r2 * phi;
-    if (kind == 0) {
-        const float LGi = L + Gi, LGj = L + Gj;
+    const float rp = r2 * inv;
+    const float LGi = L + Gi, LGj = L + Gj;
+    if (NK == 2 || kind == 0) {
         float br = __fmaf_rn(-Ai, LGi, 1.0f);
         br = __fmaf_rn(-Aj, LGj, br);
         br = __fmaf_rn(Ai * Aj, M, br);
-        ta = phi * br;                            // T1
-        tb = rp * __fmaf_rn(Ai, M, -LGj);         // T2
-    } else {
-        ta = rp * __fmaf_rn(Aj, M, -(L + Gi));    // T3
-        tb = (rp * r2) * M;                       // T4
+        t[0] = inv * br;                          // T1
+        t[1] = rp * __fmaf_rn(Ai, M, -LGj);       // T2
+    }
+    if (NK == 2 || kind == 1) {
+        t[2 * NK - 2] = rp * __fmaf_rn(Aj, M, -LGi);  // T3
+        t[2 * NK - 1] = (rp * r2) * M;                // T4
     }
 }
 
-template <int PH>  // accumulator columns per generator thread (= Ppad / 2)
+// FP32 -> TF32 with round-to-nearest, ties away from zero, on the bit pattern (finite x):
+// add half a TF32 ulp to the magnitude and clear the 13 low mantissa bits.
+__device__ __forceinline__ uint32_t tf32_rna_bits(float x) {
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+
+// TMEM column map.  NK = 1 (Ppad <= 192): accumulator buffer b at 192 b, operand buffer
+// b (4 tiles x 16 columns) at 384 + 64 b.  NK = 2 (Ppad <= 64): accumulator (kind k,
+// buffer b) at 64 (2k + b), operand buffer b (8 tiles x 16 columns) at 256 + 128 b.
+template <int NK>
+__device__ __forceinline__ uint32_t d_col(int kind, int b) {
+    return NK == 1 ? 192u * b : 64u * (2 * kind + b);
+}
+template <int NK>
+__device__ __forceinline__ uint32_t a_col(int b) {
+    return NK == 1 ? 384u + 64u * b : 256u + 128u * b;
+}
+
+template <int PQ, int NK>  // PQ accumulator columns per generator thread (= Ppad / 4)
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUtensorMap tm_ul,
           const __grid_constant__ CUtensorMap tm_yh, const __grid_constant__ CUtensorMap tm_yl,
           TcArgs args) {
-    constexpr int PPAD = 2 * PH;
+    constexpr int PPAD = 4 * PQ;
+    static_assert(NK == 1 || PPAD <= 64, "two kinds per tile need Ppad <= 64");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-B aligned base (the 64-B swizzle pattern repeats every 512 B)
     uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -138,8 +162,9 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const PointsDev& P = args.P;
-    const int64_t n_stage = P.nk_pad / kTcKj;
-    const int64_t n_tiles = 2 * args.n_row_tiles;
+    const int n_stage = static_cast<int>(P.nk_pad / kTcKj);
+    // a tile = 128 rows x (both kinds if NK == 2, else one kind)
+    const int64_t n_tiles = (NK == 2 ? 1 : 2) * args.n_row_tiles;
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < kTcRing; ++b) {
@@ -167,19 +192,19 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
             tc::prefetch_tmap(&tm_ul);
             tc::prefetch_tmap(&tm_yh);
             tc::prefetch_tmap(&tm_yl);
-            int64_t gs = 0;
+            int slot = 0;
+            uint32_t ph = 0;   // phase bit of the ring slot's current use
+            int64_t issued = 0;
             bool ok = true;
             for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
-                for (int64_t s = 0; s < n_stage && ok; ++s, ++gs) {
-                    const int slot = static_cast<int>(gs % kTcRing);
-                    const uint32_t ph = static_cast<uint32_t>((gs / kTcRing) & 1);
+                for (int s = 0; s < n_stage; ++s) {
                     if (!wait_or_abort(&b_empty[slot], ph ^ 1u, args.err, abort_flag)) {
                         ok = false;
                         break;
                     }
                     uint8_t* base = smem + slot * L.ring_bytes;
                     uint8_t* rec = smem + L.rec_off + slot * 512;
-                    const int j0 = static_cast<int>(s * kTcKj);
+                    const int j0 = s * kTcKj;
                     mbar_expect_tx(&b_full[slot], L.ring_bytes + 512u);
                     bulk_g2s(rec, P.r32a + j0, 256u, &b_full[slot]);
                     bulk_g2s(rec + 256, P.r32b + j0, 256u, &b_full[slot]);
@@ -187,50 +212,65 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     tc::tma_load_2d(base + 1 * L.tile_bytes, &tm_ul, j0, args.t0, &b_full[slot]);
                     tc::tma_load_2d(base + 2 * L.tile_bytes, &tm_yh, j0, args.t0, &b_full[slot]);
                     tc::tma_load_2d(base + 3 * L.tile_bytes, &tm_yl, j0, args.t0, &b_full[slot]);
+                    ++issued;
+                    if (++slot == kTcRing) {
+                        slot = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             // copies in flight must land before the CTA exits
-            for (int64_t k = (gs > kTcRing ? gs - kTcRing : 0); k < gs; ++k)
+            for (int64_t k = (issued > kTcRing ? issued - kTcRing : 0); k < issued; ++k)
                 mbar_wait(&b_full[k % kTcRing], static_cast<uint32_t>((k / kTcRing) & 1), args.err);
         }
     } else if (warp == kTcMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_tf32(128, PPAD);
-            int64_t gs = 0;
+            int slot = 0, ab = 0;
+            uint32_t ph = 0, aph = 0;
             bool ok = true, issued_any = false;
             for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
-                for (int64_t s = 0; s < n_stage; ++s, ++gs) {
-                    const int slot = static_cast<int>(gs % kTcRing);
-                    const int ab = static_cast<int>(gs & 1);
-                    if (!wait_or_abort(&a_full[ab], static_cast<uint32_t>((gs >> 1) & 1), args.err, abort_flag) ||
-                        !wait_or_abort(&b_full[slot], static_cast<uint32_t>((gs / kTcRing) & 1), args.err, abort_flag)) {
+                const int kind0 = NK == 2 ? 0 : static_cast<int>(q & 1);
+                for (int s = 0; s < n_stage; ++s) {
+                    if (!wait_or_abort(&a_full[ab], aph, args.err, abort_flag) ||
+                        !wait_or_abort(&b_full[slot], ph, args.err, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
                     const uint32_t base = smem_u32(smem + slot * L.ring_bytes);
-                    const uint32_t d = tmem + kDCol * ab;
-                    const uint32_t a = tmem + kACol0 + 64u * ab;
+                    const uint32_t a = tmem + a_col<NK>(ab);
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t ko = 32u * kk;  // 8 tf32 along K inside the 64-B row
-                        const uint64_t duh = tc::sdesc_kmajor_sw64(base + 0 * L.tile_bytes + ko);
-                        const uint64_t dul = tc::sdesc_kmajor_sw64(base + 1 * L.tile_bytes + ko);
-                        const uint64_t dyh = tc::sdesc_kmajor_sw64(base + 2 * L.tile_bytes + ko);
-                        const uint64_t dyl = tc::sdesc_kmajor_sw64(base + 3 * L.tile_bytes + ko);
-                        const uint32_t ah = a + 0 + 8 * kk, al = a + 16 + 8 * kk;
-                        const uint32_t bh = a + 32 + 8 * kk, bl = a + 48 + 8 * kk;
-                        tc::mma_tf32_ts(d, ah, duh, idesc, kk);  // first MMA of the stage overwrites
-                        tc::mma_tf32_ts(d, ah, dul, idesc, 1);
-                        tc::mma_tf32_ts(d, al, duh, idesc, 1);
-                        tc::mma_tf32_ts(d, bh, dyh, idesc, 1);
-                        tc::mma_tf32_ts(d, bh, dyl, idesc, 1);
-                        tc::mma_tf32_ts(d, bl, dyh, idesc, 1);
+                    for (int k = 0; k < NK; ++k) {
+                        const uint32_t d = tmem + d_col<NK>(NK == 2 ? k : kind0, ab);
+                        const uint32_t at = a + 64u * k;  // this kind's 4 operand tiles
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t ko = 32u * kk;  // 8 tf32 along K inside the 64-B row
+                            const uint64_t duh = tc::sdesc_kmajor_sw64(base + 0 * L.tile_bytes + ko);
+                            const uint64_t dul = tc::sdesc_kmajor_sw64(base + 1 * L.tile_bytes + ko);
+                            const uint64_t dyh = tc::sdesc_kmajor_sw64(base + 2 * L.tile_bytes + ko);
+                            const uint64_t dyl = tc::sdesc_kmajor_sw64(base + 3 * L.tile_bytes + ko);
+                            const uint32_t ah = at + 0 + 8 * kk, al = at + 16 + 8 * kk;
+                            const uint32_t bh = at + 32 + 8 * kk, bl = at + 48 + 8 * kk;
+                            tc::mma_tf32_ts(d, ah, duh, idesc, kk);  // the stage's first MMA overwrites
+                            tc::mma_tf32_ts(d, ah, dul, idesc, 1);
+                            tc::mma_tf32_ts(d, al, duh, idesc, 1);
+                            tc::mma_tf32_ts(d, bh, dyh, idesc, 1);
+                            tc::mma_tf32_ts(d, bh, dyl, idesc, 1);
+                            tc::mma_tf32_ts(d, bl, dyh, idesc, 1);
+                        }
                     }
                     issued_any = true;
                     tc::commit(&mma_done[ab]);
                     tc::commit(&b_empty[slot]);
+                    if (++slot == kTcRing) {
+                        slot = 0;
+                        ph ^= 1u;
+                    }
+                    ab ^= 1;
+                    if (ab == 0) aph ^= 1u;
                 }
             }
             if (issued_any) {  // every MMA finished before TMEM is released
@@ -240,61 +280,68 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
         }
     } else {
         // ------------------------------------------------------------ generators
-        const int quad = warp & 3, half = warp >> 2;
+        const int quad = warp & 3, part = warp >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
-        float acc[PH];
+        float acc[NK][PQ];
 #pragma unroll
-        for (int k = 0; k < PH; ++k) acc[k] = 0.0f;
-        int64_t gs = 0;
+        for (int k = 0; k < NK; ++k)
+#pragma unroll
+            for (int c = 0; c < PQ; ++c) acc[k][c] = 0.0f;
         bool ok = true;
 
-        auto drain = [&](int64_t st) -> bool {
-            const int db = static_cast<int>(st & 1);
-            const bool got = wait_or_abort(&mma_done[db], static_cast<uint32_t>((st >> 1) & 1), args.err, abort_flag);
+        // issue the TMEM loads of a finished accumulator (all kinds of this tile)
+        auto drain_issue = [&](int db, uint32_t dphase, int kind0, uint32_t (&r)[NK][PQ]) -> bool {
+            const bool got = wait_or_abort(&mma_done[db], dphase, args.err, abort_flag);
             if (!__all_sync(0xffffffffu, got)) return false;  // warp-uniform exit
             tc::fence_after();
 #pragma unroll
-            for (int c = 0; c < PH / 16; ++c) {
-                uint32_t r[16];
-                tc::ld_x16(tmem + lane_off + kDCol * db + half * PH + 16 * c, r);
-                tc::wait_ld();
+            for (int k = 0; k < NK; ++k)
 #pragma unroll
-                for (int k = 0; k < 16; ++k) acc[16 * c + k] += __uint_as_float(r[k]);
-            }
-            tc::fence_before();
+                for (int c = 0; c < PQ / 8; ++c) {
+                    uint32_t (&rc)[8] = *reinterpret_cast<uint32_t(*)[8]>(&r[k][8 * c]);
+                    tc::ld_x8(tmem + lane_off + d_col<NK>(NK == 2 ? k : kind0, db) + part * PQ + 8 * c, rc);
+                }
             return true;
         };
-        auto flush = [&](int kind, int64_t i) {
-            if (i < P.nk) {
+        auto drain_add = [&](uint32_t (&r)[NK][PQ]) {
 #pragma unroll
-                for (int k = 0; k < PH; ++k) {
-                    const int t = half * PH + k;
-                    if (t < args.Pn) {
+            for (int k = 0; k < NK; ++k)
+#pragma unroll
+                for (int c = 0; c < PQ; ++c) acc[k][c] += __uint_as_float(r[k][c]);
+        };
+        auto flush = [&](int kind0, int64_t i) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int kind = NK == 2 ? k : kind0;
+#pragma unroll
+                for (int c = 0; c < PQ; ++c) {
+                    const int t = part * PQ + c;
+                    if (i < P.nk && t < args.Pn) {
                         double* o = args.acc + ((static_cast<int64_t>(kind) * args.acc_P + args.t0 + t) * P.nk_pad + i);
-                        *o += static_cast<double>(acc[k]);
+                        *o += static_cast<double>(acc[k][c]);
                     }
-                    acc[k] = 0.0f;
+                    acc[k][c] = 0.0f;
                 }
-            } else {
-#pragma unroll
-                for (int k = 0; k < PH; ++k) acc[k] = 0.0f;
             }
         };
 
+        int slot = 0, ab = 0;
+        uint32_t ph = 0, aph = 0;
+        int dbuf = 0;          // accumulator buffer of the previous stage
+        uint32_t dph = 0;      // and its phase bit
         for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
-            const int kind = static_cast<int>(q & 1);
-            const int64_t i = (q >> 1) * 128 + quad * 32 + lane;
+            const int kind0 = NK == 2 ? 0 : static_cast<int>(q & 1);
+            const int64_t i = (NK == 2 ? q : (q >> 1)) * 128 + quad * 32 + lane;
             float xi = 0.f, yi = 0.f, zi = 0.f, oi = 1.f, ki = 1.f, pi_ = 0.f, qi = 0.f;
             if (i < P.nk) {
                 const float4 a = P.r32a[i], b = P.r32b[i];
                 xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y; pi_ = b.z; qi = b.w;
             }
-            for (int64_t s = 0; s < n_stage; ++s, ++gs) {
-                const int slot = static_cast<int>(gs % kTcRing);
-                const int ab = static_cast<int>(gs & 1);
-                // operand buffer ab is free once the MMAs of stage gs-2 are done
-                bool got = wait_or_abort(&b_full[slot], static_cast<uint32_t>((gs / kTcRing) & 1), args.err, abort_flag);
-                got = got && wait_or_abort(&mma_done[ab], static_cast<uint32_t>(((gs >> 1) & 1) ^ 1), args.err, abort_flag);
+            int until_flush = args.flush;
+            for (int s = 0; s < n_stage; ++s) {
+                // operand buffer ab is free once the MMAs of the stage two back are done
+                bool got = wait_or_abort(&b_full[slot], ph, args.err, abort_flag);
+                got = got && wait_or_abort(&mma_done[ab], aph ^ 1u, args.err, abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {  // warp-uniform exit
                     ok = false;
                     break;
@@ -302,22 +349,43 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                 tc::fence_after();  // the MMAs that read this operand buffer are complete
                 const float4* recA = reinterpret_cast<const float4*>(smem + L.rec_off + slot * 512);
                 const float4* recB = recA + 16;
-                uint32_t ah[8], al[8], bh[8], bl[8];
+                {
+                    uint32_t hi[2 * NK][4], lo[2 * NK][4];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int jj = half * 8 + k;
-                    float ta, tb;
-                    pair_tiles(kind, xi, yi, zi, oi, ki, pi_, qi, recA[jj], recB[jj], ta, tb);
-                    ah[k] = tc::to_tf32(ta);
-                    al[k] = __float_as_uint(ta - __uint_as_float(ah[k]));
-                    bh[k] = tc::to_tf32(tb);
-                    bl[k] = __float_as_uint(tb - __uint_as_float(bh[k]));
+                    for (int k = 0; k < 4; ++k) {
+                        const int jj = part * 4 + k;
+                        float t[2 * NK];
+                        pair_tiles<NK>(kind0, xi, yi, zi, oi, ki, pi_, qi, recA[jj], recB[jj], t);
+#pragma unroll
+                        for (int m = 0; m < 2 * NK; ++m) {
+                            hi[m][k] = tf32_rna_bits(t[m]);
+                            lo[m][k] = __float_as_uint(t[m] - __uint_as_float(hi[m][k]));
+                        }
+                    }
+                    // operand tiles of kind k: [hi(Ta), lo(Ta), hi(Tb), lo(Tb)], 16 columns each
+                    const uint32_t a = tmem + lane_off + a_col<NK>(ab) + part * 4;
+#pragma unroll
+                    for (int k = 0; k < NK; ++k) {
+                        tc::st_x4(a + 64u * k + 0, hi[2 * k]);
+                        tc::st_x4(a + 64u * k + 16, lo[2 * k]);
+                        tc::st_x4(a + 64u * k + 32, hi[2 * k + 1]);
+                        tc::st_x4(a + 64u * k + 48, lo[2 * k + 1]);
+                    }
                 }
-                const uint32_t a = tmem + lane_off + kACol0 + 64u * ab + half * 8;
-                tc::st_x8(a + 0, ah);
-                tc::st_x8(a + 16, al);
-                tc::st_x8(a + 32, bh);
-                tc::st_x8(a + 48, bl);
+                // drain the previous stage while the stores land
+                if (s > 0) {
+                    uint32_t r[NK][PQ];
+                    if (!drain_issue(dbuf, dph, kind0, r)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::wait_ld();
+                    drain_add(r);
+                    if (--until_flush == 0) {
+                        flush(kind0, i);
+                        until_flush = args.flush;
+                    }
+                }
                 tc::wait_st();
                 tc::fence_before();
                 __syncwarp();
@@ -325,21 +393,28 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     mbar_arrive(&a_full[ab]);
                     mbar_arrive(&b_empty[slot]);
                 }
-                if (s > 0) {
-                    if (!drain(gs - 1)) {
-                        ok = false;
-                        break;
-                    }
-                    if (s % args.flush == 0) flush(kind, i);
+                dbuf = ab;
+                dph = aph;
+                if (++slot == kTcRing) {
+                    slot = 0;
+                    ph ^= 1u;
                 }
+                ab ^= 1;
+                if (ab == 0) aph ^= 1u;
             }
             if (!ok) break;
-            if (!drain(gs - 1)) {
+            uint32_t r[NK][PQ];
+            if (!drain_issue(dbuf, dph, kind0, r)) {
                 ok = false;
                 break;
             }
-            flush(kind, i);
+            tc::wait_ld();
+            drain_add(r);
+            tc::fence_before();
+            flush(kind0, i);
         }
+        tc::wait_st();  // nothing of ours is in flight to TMEM on any exit path
+        tc::wait_ld();
     }
 
     tc::fence_before();
@@ -361,9 +436,9 @@ __global__ void k_trial_split(const double* __restrict__ u, const double* __rest
     if (p >= nk_pad) return;
     const int64_t o = static_cast<int64_t>(t) * nk_pad + p;
     float a = 0.f, b = 0.f;
-    if (t < P) {
-        a = static_cast<float>(u[o]);
-        b = static_cast<float>(y[o]);
+    if (t < P) {  // the -3/2 of Phi rides on the trial side (the tiles omit it)
+        a = static_cast<float>(-1.5 * u[o]);
+        b = static_cast<float>(-1.5 * y[o]);
     }
     const float ah = __uint_as_float(tc::to_tf32(a)), bh = __uint_as_float(tc::to_tf32(b));
     uh[o] = ah;
@@ -415,13 +490,15 @@ int hess_tc_ppad(int32_t P) {
     return p < 32 ? 32 : p;
 }
 
-template <int PH>
-static cudaError_t launch_tc_t(const CUtensorMap* maps, const TcArgs& a, int grid, cudaStream_t st) {
-    const TcSmemLayout L = tc_layout(2 * PH);
-    cudaError_t e = cudaFuncSetAttribute(k_hess_tc<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int PQ, int NK>
+static cudaError_t launch_tc_t(const CUtensorMap* maps, const TcArgs& a, int n_sm, cudaStream_t st) {
+    const TcSmemLayout L = tc_layout(4 * PQ);
+    cudaError_t e = cudaFuncSetAttribute(k_hess_tc<PQ, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L.total));
     if (e != cudaSuccess) return e;
-    k_hess_tc<PH><<<grid, kTcThreads, L.total, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    const int64_t n_tiles = (NK == 2 ? 1 : 2) * a.n_row_tiles;
+    const int grid = static_cast<int>(n_tiles < n_sm ? n_tiles : n_sm);
+    k_hess_tc<PQ, NK><<<grid, kTcThreads, L.total, st>>>(maps[0], maps[1], maps[2], maps[3], a);
     return cudaGetLastError();
 }
 
@@ -446,15 +523,13 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
     a.flush = flush > 0 ? flush : 128;
     a.acc = acc;
     a.err = err;
-    const int64_t n_tiles = 2 * a.n_row_tiles;
-    const int grid = static_cast<int>(n_tiles < n_sm ? n_tiles : n_sm);
-    switch (ppad / 2) {
-        case 16: return launch_tc_t<16>(maps, a, grid, st);
-        case 32: return launch_tc_t<32>(maps, a, grid, st);
-        case 48: return launch_tc_t<48>(maps, a, grid, st);
-        case 64: return launch_tc_t<64>(maps, a, grid, st);
-        case 80: return launch_tc_t<80>(maps, a, grid, st);
-        default: return launch_tc_t<96>(maps, a, grid, st);
+    switch (ppad / 4) {  // two kinds per tile whenever both accumulators fit in TMEM
+        case 8: return launch_tc_t<8, 2>(maps, a, n_sm, st);
+        case 16: return launch_tc_t<16, 2>(maps, a, n_sm, st);
+        case 24: return launch_tc_t<24, 1>(maps, a, n_sm, st);
+        case 32: return launch_tc_t<32, 1>(maps, a, n_sm, st);
+        case 40: return launch_tc_t<40, 1>(maps, a, n_sm, st);
+        default: return launch_tc_t<48, 1>(maps, a, n_sm, st);
     }
 }
 

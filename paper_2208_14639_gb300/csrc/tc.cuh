@@ -39,6 +39,20 @@ __device__ __forceinline__ void st_x8(uint32_t taddr, const uint32_t (&r)[8]) {
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
         : "memory");
 }
+// 4 consecutive 32-bit columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void st_x4(uint32_t taddr, const uint32_t (&r)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+// 8 consecutive 32-bit columns of this warp's 32 lanes.
+__device__ __forceinline__ void ld_x8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
 // 16 consecutive 32-bit columns of this warp's 32 lanes.
 __device__ __forceinline__ void ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
