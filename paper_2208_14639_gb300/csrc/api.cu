@@ -52,7 +52,7 @@ vv10_status vv10_ctx::ensure(DevBuf& b, size_t bytes, const char* what) {
 
 void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
-                      &soa, &r64a, &r64b, &r32a, &r32b, &sumE, &sumU, &sumW, &sumA, &sumB,
+                      &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
                       &tc_uh, &tc_ul, &tc_yh, &tc_yl, &dev_err};
     for (DevBuf* b : bufs) {
@@ -333,6 +333,7 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
     VV10_TRY(h->ensure(h->r64b, sizeof(double4) * cap, "FP64 records"));
     VV10_TRY(h->ensure(h->r32a, sizeof(float4) * cap, "FP32 records"));
     VV10_TRY(h->ensure(h->r32b, sizeof(float4) * cap, "FP32 records"));
+    VV10_TRY(h->ensure(h->r32p, sizeof(float4) * 2 * cap, "pair-packed FP32 records"));
     PhaseScope ph_scatter(h, PH_PREPARE, st, nk_pad > 0 ? 2 : 1);
     VV10_CUDA(h, launch_prepare_scatter(n, xyz, w, rho, grad_rho, atom_of_point, n_atom,
                                         prm.rho_cut, prm.b, prm.C, ps, nk, nk_pad,
@@ -343,7 +344,8 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
                                         static_cast<double4*>(h->r64a.p),
                                         static_cast<double4*>(h->r64b.p),
                                         static_cast<float4*>(h->r32a.p),
-                                        static_cast<float4*>(h->r32b.p), st),
+                                        static_cast<float4*>(h->r32b.p),
+                                        static_cast<float4*>(h->r32p.p), st),
               "prepare scatter");
     PointsDev& P = h->P;
     P.n = n;
@@ -373,6 +375,7 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
     P.r64b = static_cast<const double4*>(h->r64b.p);
     P.r32a = static_cast<const float4*>(h->r32a.p);
     P.r32b = static_cast<const float4*>(h->r32b.p);
+    P.r32p = static_cast<const float4*>(h->r32p.p);
     h->soa_ld = cap;
     h->prm = prm;
     h->prepared = true;

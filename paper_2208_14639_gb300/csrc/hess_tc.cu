@@ -82,42 +82,61 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, in
     return true;
 }
 
-// Kernel tiles of one pair, FP32, without the -3/2 of Phi (the trial split carries it),
-// i.e. T1..T4 scaled by -2/3.  The hardware reciprocal (relative error below 2^-22) is
-// accurate enough for operands carried to ~22 bits.  NK = 2: all four tiles; NK = 1: the
-// two tiles of output kind `kind` (0 -> T1, T2; 1 -> T3, T4) in t[0], t[1].
+// Kernel tiles for two j at once (packed FP32x2 arithmetic) from a pair-packed record
+// v0..v3 = {-x,-y}, {-z,om}, {ka,-p}, {-q,c} (two lanes each), against row i.
+// With inv = 1/(g g' s), L = 1/s, G_i = 1/g, G_j = 1/g', M = 2/s^2 + 2/(g g'),
+// nA_i = -rho_i a_i, nA_j = -rho_j a_j and rp = R^2 inv, the values produced are
+//   T1c = inv (1 + nA_i (L+G_i) + nA_j (L+G_j) + nA_i nA_j M)   = T1 / (-3/2)
+//   T2c = rp (nA_i M + L + G_j)                                   = T2 / (+3/2)
+//   T3c = rp (nA_j M + L + G_i)                                   = T3 / (+3/2)
+//   T4c = rp R^2 M                                                = T4 / (-3/2)
+// The trial split carries u -> -3/2 u and y -> +3/2 y, so the rho accumulator receives
+// sum T1 u + T2 y and the gamma accumulator receives -(sum T3 u + T4 y) (its flush
+// negates).  The hardware reciprocal (relative error below 2^-22) suffices for operands
+// carried to ~22 bits.  NK = 2: all four tiles; NK = 1: the two of output `kind`.
+struct RowC {
+    float2 x, y, z, om, ka, np, nq;  // row i values, both lanes equal; np = -p_i, nq = -q_i
+};
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
 template <int NK>
-__device__ __forceinline__ void pair_tiles(int kind, float xi, float yi, float zi, float oi,
-                                           float ki, float pi_, float qi, const float4& a,
-                                           const float4& b, float (&t)[2 * NK]) {
-    const float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
-    float r2 = dx * dx;
-    r2 = __fmaf_rn(dy, dy, r2);
-    r2 = __fmaf_rn(dz, dz, r2);
-    const float g = __fmaf_rn(oi, r2, ki);
-    const float gp = __fmaf_rn(b.x, r2, b.y);
-    const float s = g + gp;
-    const float ggp = g * gp;
-    float inv;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(ggp * s));
-    const float L = ggp * inv;          // 1/s
-    const float Gi = (gp * s) * inv;    // 1/g
-    const float Gj = (g * s) * inv;     // 1/g'
-    const float M = 2.0f * __fmaf_rn(L, L, Gi * Gj);
-    const float Ai = __fmaf_rn(qi, r2, pi_);   // rho_i a_i
-    const float Aj = __fmaf_rn(b.w, r2, b.z);  // rho_j a_j
-    const float rp = r2 * inv;
-    const float LGi = L + Gi, LGj = L + Gj;
+__device__ __forceinline__ void pair_tiles2(int kind, const RowC& r, const float4 v0,
+                                            const float4 v1, const float4 v2, const float4 v3,
+                                            float2 (&t)[2 * NK]) {
+    const float2 one = make_float2(1.0f, 1.0f), two = make_float2(2.0f, 2.0f);
+    const float2 dx = __fadd2_rn(r.x, lo2(v0));
+    const float2 dy = __fadd2_rn(r.y, hi2(v0));
+    const float2 dz = __fadd2_rn(r.z, lo2(v1));
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float2 g = __ffma2_rn(r.om, r2, r.ka);
+    const float2 gp = __ffma2_rn(hi2(v1), r2, lo2(v2));
+    const float2 s = __fadd2_rn(g, gp);
+    const float2 ggp = __fmul2_rn(g, gp);
+    const float2 den = __fmul2_rn(ggp, s);
+    float2 inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.x) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.y) : "f"(den.y));
+    const float2 L = __fmul2_rn(ggp, inv);
+    const float2 Gi = __fmul2_rn(__fmul2_rn(gp, s), inv);
+    const float2 Gj = __fmul2_rn(__fmul2_rn(g, s), inv);
+    const float2 M = __fmul2_rn(two, __ffma2_rn(L, L, __fmul2_rn(Gi, Gj)));
+    const float2 nAi = __ffma2_rn(r.nq, r2, r.np);
+    const float2 nAj = __ffma2_rn(lo2(v3), r2, hi2(v2));
+    const float2 rp = __fmul2_rn(r2, inv);
+    const float2 LGi = __fadd2_rn(L, Gi), LGj = __fadd2_rn(L, Gj);
     if (NK == 2 || kind == 0) {
-        float br = __fmaf_rn(-Ai, LGi, 1.0f);
-        br = __fmaf_rn(-Aj, LGj, br);
-        br = __fmaf_rn(Ai * Aj, M, br);
-        t[0] = inv * br;                          // T1
-        t[1] = rp * __fmaf_rn(Ai, M, -LGj);       // T2
+        float2 br = __ffma2_rn(nAi, LGi, one);
+        br = __ffma2_rn(nAj, LGj, br);
+        br = __ffma2_rn(__fmul2_rn(nAi, nAj), M, br);
+        t[0] = __fmul2_rn(inv, br);                       // T1c
+        t[1] = __fmul2_rn(rp, __ffma2_rn(nAi, M, LGj));   // T2c
     }
     if (NK == 2 || kind == 1) {
-        t[2 * NK - 2] = rp * __fmaf_rn(Aj, M, -LGi);  // T3
-        t[2 * NK - 1] = (rp * r2) * M;                // T4
+        t[2 * NK - 2] = __fmul2_rn(rp, __ffma2_rn(nAj, M, LGi));  // T3c
+        t[2 * NK - 1] = __fmul2_rn(__fmul2_rn(rp, r2), M);        // T4c
     }
 }
 
@@ -206,8 +225,7 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     uint8_t* rec = smem + L.rec_off + slot * 512;
                     const int j0 = s * kTcKj;
                     mbar_expect_tx(&b_full[slot], L.ring_bytes + 512u);
-                    bulk_g2s(rec, P.r32a + j0, 256u, &b_full[slot]);
-                    bulk_g2s(rec + 256, P.r32b + j0, 256u, &b_full[slot]);
+                    bulk_g2s(rec, P.r32p + 2 * j0, 512u, &b_full[slot]);
                     tc::tma_load_2d(base + 0 * L.tile_bytes, &tm_uh, j0, args.t0, &b_full[slot]);
                     tc::tma_load_2d(base + 1 * L.tile_bytes, &tm_ul, j0, args.t0, &b_full[slot]);
                     tc::tma_load_2d(base + 2 * L.tile_bytes, &tm_yh, j0, args.t0, &b_full[slot]);
@@ -307,7 +325,13 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
 #pragma unroll
             for (int k = 0; k < NK; ++k)
 #pragma unroll
-                for (int c = 0; c < PQ; ++c) acc[k][c] += __uint_as_float(r[k][c]);
+                for (int c = 0; c < PQ; c += 2) {
+                    const float2 v = __fadd2_rn(make_float2(acc[k][c], acc[k][c + 1]),
+                                                make_float2(__uint_as_float(r[k][c]),
+                                                            __uint_as_float(r[k][c + 1])));
+                    acc[k][c] = v.x;
+                    acc[k][c + 1] = v.y;
+                }
         };
         auto flush = [&](int kind0, int64_t i) {
 #pragma unroll
@@ -318,7 +342,8 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     const int t = part * PQ + c;
                     if (i < P.nk && t < args.Pn) {
                         double* o = args.acc + ((static_cast<int64_t>(kind) * args.acc_P + args.t0 + t) * P.nk_pad + i);
-                        *o += static_cast<double>(acc[k][c]);
+                        const double v = static_cast<double>(acc[k][c]);
+                        *o += (kind == 0) ? v : -v;  // the gamma accumulator holds -(T3 u + T4 y)
                     }
                     acc[k][c] = 0.0f;
                 }
@@ -337,6 +362,9 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                 const float4 a = P.r32a[i], b = P.r32b[i];
                 xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y; pi_ = b.z; qi = b.w;
             }
+            const RowC rc{make_float2(xi, xi), make_float2(yi, yi), make_float2(zi, zi),
+                          make_float2(oi, oi), make_float2(ki, ki), make_float2(-pi_, -pi_),
+                          make_float2(-qi, -qi)};
             int until_flush = args.flush;
             for (int s = 0; s < n_stage; ++s) {
                 // operand buffer ab is free once the MMAs of the stage two back are done
@@ -347,19 +375,24 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     break;
                 }
                 tc::fence_after();  // the MMAs that read this operand buffer are complete
-                const float4* recA = reinterpret_cast<const float4*>(smem + L.rec_off + slot * 512);
-                const float4* recB = recA + 16;
+                const float4* rec = reinterpret_cast<const float4*>(smem + L.rec_off + slot * 512);
                 {
+                    // this warp's 4 j = pair-packed records 2 part and 2 part + 1
                     uint32_t hi[2 * NK][4], lo[2 * NK][4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int jj = part * 4 + k;
-                        float t[2 * NK];
-                        pair_tiles<NK>(kind0, xi, yi, zi, oi, ki, pi_, qi, recA[jj], recB[jj], t);
+                    for (int h = 0; h < 2; ++h) {
+                        const float4* v = rec + 4 * (2 * part + h);
+                        float2 t[2 * NK];
+                        pair_tiles2<NK>(kind0, rc, v[0], v[1], v[2], v[3], t);
 #pragma unroll
                         for (int m = 0; m < 2 * NK; ++m) {
-                            hi[m][k] = tf32_rna_bits(t[m]);
-                            lo[m][k] = __float_as_uint(t[m] - __uint_as_float(hi[m][k]));
+                            const uint32_t h0 = tf32_rna_bits(t[m].x), h1 = tf32_rna_bits(t[m].y);
+                            const float2 l = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)),
+                                                        make_float2(-1.0f, -1.0f), t[m]);
+                            hi[m][2 * h] = h0;
+                            hi[m][2 * h + 1] = h1;
+                            lo[m][2 * h] = __float_as_uint(l.x);
+                            lo[m][2 * h + 1] = __float_as_uint(l.y);
                         }
                     }
                     // operand tiles of kind k: [hi(Ta), lo(Ta), hi(Tb), lo(Tb)], 16 columns each
@@ -372,7 +405,14 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                         tc::st_x4(a + 64u * k + 48, lo[2 * k + 1]);
                     }
                 }
-                // drain the previous stage while the stores land
+                tc::wait_st();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) {  // hand the operands to the MMA issuer before draining
+                    mbar_arrive(&a_full[ab]);
+                    mbar_arrive(&b_empty[slot]);
+                }
+                // drain the previous stage while this stage's MMAs run
                 if (s > 0) {
                     uint32_t r[NK][PQ];
                     if (!drain_issue(dbuf, dph, kind0, r)) {
@@ -381,17 +421,11 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     }
                     tc::wait_ld();
                     drain_add(r);
+                    tc::fence_before();
                     if (--until_flush == 0) {
                         flush(kind0, i);
                         until_flush = args.flush;
                     }
-                }
-                tc::wait_st();
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&a_full[ab]);
-                    mbar_arrive(&b_empty[slot]);
                 }
                 dbuf = ab;
                 dph = aph;
@@ -436,9 +470,9 @@ __global__ void k_trial_split(const double* __restrict__ u, const double* __rest
     if (p >= nk_pad) return;
     const int64_t o = static_cast<int64_t>(t) * nk_pad + p;
     float a = 0.f, b = 0.f;
-    if (t < P) {  // the -3/2 of Phi rides on the trial side (the tiles omit it)
+    if (t < P) {  // the kernel tiles omit the -3/2 of Phi and the sign of T2: see pair_tiles2
         a = static_cast<float>(-1.5 * u[o]);
-        b = static_cast<float>(-1.5 * y[o]);
+        b = static_cast<float>(1.5 * y[o]);
     }
     const float ah = __uint_as_float(tc::to_tf32(a)), bh = __uint_as_float(tc::to_tf32(b));
     uh[o] = ah;
@@ -520,7 +554,7 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
     a.t0 = t0;
     a.acc_P = acc_P;
     a.n_row_tiles = (p.nk + 127) / 128;
-    a.flush = flush > 0 ? flush : 128;
+    a.flush = flush > 0 ? flush : 512;
     a.acc = acc;
     a.err = err;
     switch (ppad / 4) {  // two kinds per tile whenever both accumulators fit in TMEM

@@ -27,6 +27,10 @@ struct PointsDev {
     const double4* r64b;  // omega, kappa, rho kappa', rho omega_rho
     const float4* r32a;   // x-cx, y-cy, z-cz, -1.5 w rho   (recentred, FP32)
     const float4* r32b;   // omega, kappa, rho kappa', rho omega_rho
+    // Pair-packed FP32 records for two consecutive j (2m, 2m+1), 4 float4 per pair:
+    //   {-x0,-x1,-y0,-y1}, {-z0,-z1,om0,om1}, {ka0,ka1,-p0,-p1}, {-q0,-q1,c0,c1}
+    // (recentred coordinates; p = rho kappa', q = rho omega_rho, c = -1.5 w rho), nk_pad/2 pairs.
+    const float4* r32p;
 };
 
 // SoA field order inside the FP64 per-point arena (each field nk_pad long).
@@ -54,7 +58,7 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
                                    const PrepareScratch& s, int64_t nk, int64_t nk_pad,
                                    int64_t* orig, int64_t* seg, int32_t* atom_k, double* soa,
                                    double4* r64a, double4* r64b, float4* r32a, float4* r32b,
-                                   cudaStream_t st);
+                                   float4* r32p, cudaStream_t st);
 
 // ---------------------------------------------------------------- pair sums (pairsum.cu)
 enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2 };

@@ -161,14 +161,18 @@ k_prep_points(int64_t nk, int64_t nk_pad, const int64_t* __restrict__ orig,
               const int32_t* __restrict__ atom, double b, double C,
               const double* __restrict__ center, int32_t* __restrict__ atom_k,
               double* __restrict__ soa, double4* __restrict__ r64a, double4* __restrict__ r64b,
-              float4* __restrict__ r32a, float4* __restrict__ r32b) {
+              float4* __restrict__ r32a, float4* __restrict__ r32b, float4* __restrict__ r32p) {
     const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (p >= nk_pad) return;
+    // pair-packed record slots of this point: pair m = p / 2, component h = p % 2
+    float* pk = reinterpret_cast<float*>(r32p) + (p >> 1) * 16 + (p & 1);
     if (p >= nk) {  // padding record: contributes exactly zero to every pair sum
         r64a[p] = make_double4(0.0, 0.0, 0.0, 0.0);
         r64b[p] = make_double4(1.0, 1.0, 0.0, 0.0);
         r32a[p] = make_float4(0.f, 0.f, 0.f, 0.f);
         r32b[p] = make_float4(1.f, 1.f, 0.f, 0.f);
+        const float pad[8] = {0.f, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 8; ++k) pk[2 * k] = pad[k];
         return;
     }
     const int64_t i = orig[p];
@@ -216,6 +220,11 @@ k_prep_points(int64_t nk, int64_t nk_pad, const int64_t* __restrict__ orig,
                           static_cast<float>(z - center[2]), static_cast<float>(cj));
     r32b[p] = make_float4(static_cast<float>(om), static_cast<float>(ka),
                           static_cast<float>(r * ka_r), static_cast<float>(r * om_r));
+    const float4 a = r32a[p];
+    const float vals[8] = {-a.x, -a.y, -a.z, static_cast<float>(om), static_cast<float>(ka),
+                           -static_cast<float>(r * ka_r), -static_cast<float>(r * om_r),
+                           static_cast<float>(cj)};
+    for (int k = 0; k < 8; ++k) pk[2 * k] = vals[k];
     atom_k[p] = atom ? atom[i] : 0;
 }
 
@@ -242,7 +251,7 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
                                    const PrepareScratch& s, int64_t nk, int64_t nk_pad,
                                    int64_t* orig, int64_t* seg, int32_t* atom_k, double* soa,
                                    double4* r64a, double4* r64b, float4* r32a, float4* r32b,
-                                   cudaStream_t st) {
+                                   float4* r32p, cudaStream_t st) {
     const int nblk = prepare_nblk(n);
     const int n_keys = (n_atom > 0 ? n_atom : 1) + 1;
     const int64_t M = static_cast<int64_t>(n_keys) * nblk;
@@ -257,7 +266,7 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
     if (nk_pad > 0) {
         const int g = static_cast<int>((nk_pad + 255) / 256);
         k_prep_points<<<g, 256, 0, st>>>(nk, nk_pad, orig, xyz, w, rho, grad, atom, b, C,
-                                         s.center, atom_k, soa, r64a, r64b, r32a, r32b);
+                                         s.center, atom_k, soa, r64a, r64b, r32a, r32b, r32p);
         e = cudaGetLastError();
     }
     return e;

@@ -56,7 +56,7 @@ struct vv10_ctx {
     // prepare scratch
     vv10::DevBuf prep_hist, prep_offs, prep_bbox, prep_small;
     // prepared point block
-    vv10::DevBuf orig, seg, atom_k, soa, r64a, r64b, r32a, r32b;
+    vv10::DevBuf orig, seg, atom_k, soa, r64a, r64b, r32a, r32b, r32p;
     vv10::PointsDev P;
     int64_t soa_ld = 0;
     vv10_params prm{6.0, 0.01, 1e-10};
@@ -81,7 +81,7 @@ struct vv10_ctx {
     vv10::TileOverride overrides[6];
 
     // stages between FP64 flushes of the tensor-core contraction's register accumulators
-    int tc_flush = 128;
+    int tc_flush = 512;
 
     // launch accounting / profiling
     bool prof_on = false;
