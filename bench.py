@@ -38,8 +38,9 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 N_SM = 152
 FP32_LANES_PER_SM = 128
 # FP32 operations per pair counted from the formulas each kernel evaluates:
-#   tensor-core contraction: kernel tiles T1..T4 with their TF32 hi/lo splits, both kinds
-ALU_OPS_PER_PAIR_TC = 80
+#   tensor-core contraction: kernel tiles T1..T4 (36, the reciprocal counted once) and
+#   their four hi - lo subtractions
+ALU_OPS_PER_PAIR_TC = 40
 
 
 def workloads():
@@ -339,7 +340,9 @@ def gpu_arm(args):
             roof = {"bound": "tensor", "achieved": hess_flops / t / 1e12, "peak": tf32_peak / 1e12,
                     "unit": "TFLOP/s", "frac": hess_flops / t / tf32_peak, "traffic": None,
                     "kernel": "k_hess_tc",
-                    "peak_source": f"{peak_src} bf16 {peaks['bf16_tflops']} x 0.5 (tf32)"}
+                    "peak_source": f"{peak_src} bf16 {peaks['bf16_tflops']} x 0.5 (tf32 dense)",
+                    "issued_mma_frac": t_tensor / t,
+                    "alu_alt": {"frac": t_alu / t, "ops_per_pair": ALU_OPS_PER_PAIR_TC}}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None, "kernel": dom}
