@@ -153,6 +153,33 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
  * by the last vv10_energy_potential call.  dEdw: n device out. */
 vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
 
+/* Energy and potential for callers that cannot allocate device memory (the paper has no
+ * counterpart).  Some callers are not allowed to call cudaMalloc at all: code recorded
+ * into a CUDA graph, runtimes that grab (nearly) all device memory up front for their own
+ * allocator, or plug-ins that are only ever handed buffers.  This entry point gives them
+ * the same E, f^rho and f^gamma as vv10_energy_potential (same pair-sum kernel) without a
+ * handle and without allocating: its scratch is one static device array of about 11 MB
+ * that every GPU which loads this library holds until the process exits.
+ *   n                  number of points, 1 <= n <= VV10_NOALLOC_MAX_POINTS
+ *   xyz, w, rho, grad_rho   as for vv10_prepare_points (device pointers, FP64)
+ *   prm, prec          as for vv10_prepare_points / vv10_energy_potential
+ *   energy             DEVICE pointer to one double (out)
+ *   vrho, vgamma       n device out, f^rho and f^gamma (may be NULL)
+ * It runs on the calling thread's current device and does not synchronise.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current): make that first call before any stream capture.  Every call shares
+ * the one array and leaves its contents behind; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller.  Points
+ * below rho_cut take part in no sum and get zero outputs, as elsewhere.
+ * Errors: INVALID_ARG (n < 1, bad pointer or parameter), UNSUPPORTED (n above the
+ * maximum), CUDA.  Device-side conditions (non-finite values, a wait that gave up) are
+ * not reported by this entry point. */
+#define VV10_NOALLOC_MAX_POINTS 32768
+vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xyz, const double* w,
+                                          const double* rho, const double* grad_rho,
+                                          vv10_params prm, vv10_precision prec, double* energy,
+                                          double* vrho, double* vgamma, void* stream);
+
 /* Synchronise `stream` and report any deferred device-side error on this handle. */
 vv10_status vv10_sync(vv10_handle h, void* stream);
 

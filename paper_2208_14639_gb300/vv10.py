@@ -37,7 +37,8 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_prepare_points", "vv10_energy_potential", "vv10_hessian_contract",
            "vv10_coord_grad", "vv10_weight_grad", "vv10_sync", "vv10_set_tiles",
            "vv10_debug_inject", "vv10_profile_enable", "vv10_profile_read",
-           "vv10_profile_phase_name")
+           "vv10_profile_phase_name", "vv10_energy_potential_noalloc")
+VV10_NOALLOC_MAX_POINTS = 32768
 VV10_N_PHASES = 11
 
 
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = False):
         "vv10_profile_enable": (st, [P, ctypes.c_int]),
         "vv10_profile_read": (st, [P, ctypes.c_int, P, P]),
         "vv10_profile_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
+        "vv10_energy_potential_noalloc": (st, [I64, P, P, P, P, VV10Params, st, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -220,6 +222,20 @@ def vv10_profile_read(h) -> dict:
     _check(h, load().vv10_profile_read(h, VV10_N_PHASES, ms.ctypes.data_as(ctypes.c_void_p),
                                        n.ctypes.data_as(ctypes.c_void_p)), "vv10_profile_read")
     return {vv10_profile_phase_name(k): (float(ms[k]), int(n[k])) for k in range(VV10_N_PHASES)}
+
+
+def vv10_energy_potential_noalloc(xyz, w, rho, grad_rho, prec: int, energy, vrho=None,
+                                  vgamma=None, b: float = 6.0, C: float = 0.01,
+                                  rho_cut: float = 1e-10, stream=None) -> None:
+    """Energy (into the 1-element device tensor `energy`) and potential without any device
+    allocation; for callers that may not allocate (see include/vv10.h)."""
+    n = int(w.shape[0])
+    st = load().vv10_energy_potential_noalloc(
+        n, _dptr(xyz, "xyz", shape=(n, 3)), _dptr(w, "w", shape=(n,)),
+        _dptr(rho, "rho", shape=(n,)), _dptr(grad_rho, "grad_rho", shape=(n, 3)),
+        VV10Params(b, C, rho_cut), int(prec), _dptr(energy, "energy", shape=(1,)),
+        _dptr(vrho, "vrho", shape=(n,)), _dptr(vgamma, "vgamma", shape=(n,)), _stream(stream))
+    _check(None, st, "vv10_energy_potential_noalloc")
 
 
 def vv10_debug_inject(h, what: int, value: int) -> None:
