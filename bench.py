@@ -41,6 +41,9 @@ FP32_LANES_PER_SM = 128
 #   tensor-core contraction: kernel tiles T1..T4 (36, the reciprocal counted once) and
 #   their four hi - lo subtractions
 ALU_OPS_PER_PAIR_TC = 40
+# DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
+# (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
+PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.228e9}
 
 
 def workloads():
@@ -338,7 +341,8 @@ def gpu_arm(args):
                                    "frac_of_split_peak": t_tensor / t}}
         else:
             roof = {"bound": "tensor", "achieved": hess_flops / t / 1e12, "peak": tf32_peak / 1e12,
-                    "unit": "TFLOP/s", "frac": hess_flops / t / tf32_peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": hess_flops / t / tf32_peak,
+                    "traffic": PROFILED_TRAFFIC.get(("k_hess_tc", args.workload)),
                     "kernel": "k_hess_tc",
                     "peak_source": f"{peak_src} bf16 {peaks['bf16_tflops']} x 0.5 (tf32 dense)",
                     "issued_mma_frac": t_tensor / t,
