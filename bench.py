@@ -11,7 +11,9 @@ per-call rates are reported beside it.  N > 1 (torchrun): every rank runs its ow
 the workload (independent problems, no data-path collective); value sums over ranks.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload hexamer|water|cluster24|chon60] [--precision mixed|fp64]
+                       [--workload hexamer|water|cluster24|chon60|batch] [--precision mixed|fp64]
+--workload batch runs the 64-molecule batch through vv10_batch_prepare + vv10_batch_run
+(energy, potential and Hessian contraction; 2 sum_m N_kept,m^2 pairs per step).
 """
 from __future__ import annotations
 
@@ -41,6 +43,8 @@ FP32_LANES_PER_SM = 128
 #   tensor-core contraction: kernel tiles T1..T4 (36, the reciprocal counted once) and
 #   their four hi - lo subtractions
 ALU_OPS_PER_PAIR_TC = 40
+# the same when each output kind has its own tile generation (Ppad > 64): 2 x (25 + 5.5 + 2)
+ALU_OPS_PER_PAIR_TC_SPLIT = 65
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
 # (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
 PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.228e9}
@@ -398,12 +402,318 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched workload
+
+BATCH_LABEL = ("64 CHON molecules, 3-30 atoms (uniform), 50x194 points per atom (9,700-291,000 "
+               "points each), P = 3 N_atom per molecule")
+
+
+def tc_alu_ops_per_pair(ppad: int) -> int:
+    """FP32 operations per pair of the tensor-core contraction: both outputs share one tile
+    generation when Ppad <= 64; above that each output kind generates its own two tiles and
+    repeats the common part (25 shared + 7 or 4 tile + 2 split operations per kind)."""
+    return ALU_OPS_PER_PAIR_TC if ppad <= 64 else ALU_OPS_PER_PAIR_TC_SPLIT
+
+
+class BatchProblem:
+    """The batch of molecules on the device: concatenated grids, trial densities generated
+    on the device (torch), preallocated outputs."""
+
+    def __init__(self, dev, workers: int, systems=None):
+        import torch
+        from paper_2208_14639_gb300 import synth
+        self.sys = systems if systems is not None else synth.config_batch(workers=workers)
+        self.P = [3 * g.molecule.n_atom for g in self.sys]
+        self.n = [g.n for g in self.sys]
+        self.off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.toff = np.concatenate([[0], np.cumsum([P * k for P, k in zip(self.P, self.n)])]).astype(np.int64)
+        cat = lambda f: np.ascontiguousarray(np.concatenate([getattr(g, f) for g in self.sys]))
+        self.host = {"xyz": cat("coords"), "w": cat("weights"), "rho": cat("rho"),
+                     "grad": cat("grad_rho"), "atom": cat("atom_of_point").astype(np.int32)}
+        T = lambda a: torch.from_numpy(a).to(dev)
+        self.d = {k: T(v) for k, v in self.host.items()}
+        tot = int(self.toff[-1])
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.d["rt"] = torch.empty(tot, **f64)
+        self.d["gt"] = torch.empty(tot, 3, **f64)
+        for m, g in enumerate(self.sys):
+            s, e = int(self.toff[m]), int(self.toff[m + 1])
+            synth.trial_densities_torch(g.molecule, self.d["xyz"][int(self.off[m]):int(self.off[m + 1])],
+                                        out_rho=self.d["rt"][s:e].view(self.P[m], self.n[m]),
+                                        out_grad=self.d["gt"][s:e].view(self.P[m], self.n[m], 3))
+        N = int(self.off[-1])
+        self.out = {"E": torch.empty(len(self.sys), **f64), "vrho": torch.empty(N, **f64),
+                    "vgamma": torch.empty(N, **f64), "frt": torch.empty(tot, **f64),
+                    "fgt": torch.empty(tot, **f64)}
+        self.n_atom = [g.molecule.n_atom for g in self.sys]
+
+    def input_bytes(self):
+        return int(sum(t.numel() * t.element_size() for t in self.d.values()))
+
+
+def run_batch_step(vv, h, bp, prec):
+    """One pass over the whole batch through the C ABI: prepare every molecule, then energy,
+    potential and Hessian contraction of all of them (one recorded graph after the first)."""
+    d, o = bp.d, bp.out
+    nk = vv.vv10_batch_prepare(h, bp.off, d["xyz"], d["w"], d["rho"], d["grad"], d["atom"], bp.n_atom)
+    vv.vv10_batch_run(h, prec, bp.P, d["rt"], d["gt"], o["E"], o["vrho"], o["vgamma"], o["frt"], o["fgt"])
+    return nk
+
+
+def time_batch(vv, h, bp, prec, steps, warmup, world):
+    import torch
+    for _ in range(warmup):
+        run_batch_step(vv, h, bp, prec)
+    vv.vv10_sync(h)
+    vv.vv10_profile_enable(h, True)
+    vv.vv10_profile_read(h)
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    nk = None
+    for _ in range(steps):
+        nk = run_batch_step(vv, h, bp, prec)
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof = vv.vv10_profile_read(h)
+    vv.vv10_profile_enable(h, False)
+    return a.elapsed_time(b), nk, prof
+
+
+def time_batch_e2e(vv, h, bp, prec, steps, warmup):
+    """The batched step with host inputs: pinned H2D of every input (grids and trial
+    densities) and D2H of every output inside the timed region."""
+    import torch
+    pin = {k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in bp.d.items()}
+    for k, t in pin.items():
+        t.copy_(bp.d[k])
+    pout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in bp.out.items()}
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = sum(t.numel() * t.element_size() for t in pout.values())
+
+    def one():
+        for k, t in pin.items():
+            bp.d[k].copy_(t, non_blocking=True)
+        nk = run_batch_step(vv, h, bp, prec)
+        for k, t in pout.items():
+            t.copy_(bp.out[k], non_blocking=True)
+        return nk
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, h2d, d2h
+
+
+def batch_cpu_sample(bp, budget_s: float):
+    """The FP64 oracle on a bounded row sample of the batch: rows of the smallest, a middle
+    and the largest molecule (energy/potential and Hessian contraction, full j sums)."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(cores)
+    order = np.argsort(bp.n, kind="stable")
+    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    data = []
+    for m in picks:
+        g = bp.sys[m]
+        s, e = int(bp.toff[m]), int(bp.toff[m + 1])
+        rt = bp.d["rt"][s:e].view(bp.P[m], bp.n[m]).cpu().numpy()
+        gt = bp.d["gt"][s:e].view(bp.P[m], bp.n[m], 3).cpu().numpy()
+        kept = np.flatnonzero(g.rho >= 1e-10)
+        data.append(((g.coords, g.weights, g.rho, g.grad_rho), rt, gt, kept))
+
+    def run(n_rows):
+        pairs = 0
+        for args, rt, gt, kept in data:
+            rows = kept[np.linspace(0, kept.size - 1, n_rows).astype(np.int64)]
+            oracle.potential(*args, rows=rows)
+            oracle.hessian_contract(*args, rt, gt, rows=rows)
+            pairs += 2 * n_rows * kept.size
+        return pairs
+
+    t0 = time.perf_counter()
+    run(4)
+    cal = time.perf_counter() - t0
+    n_rows = int(max(4, min(4096, 4 * budget_s / max(cal, 1e-3))))
+    t0 = time.perf_counter()
+    pairs = run(n_rows)
+    sec = time.perf_counter() - t0
+    return {"value": pairs / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": sec,
+            "sample": f"{n_rows} rows each (energy/potential and Hessian contraction, full j sums) "
+                      f"of molecules {picks} ({[bp.n[m] for m in picks]} points, "
+                      f"P={[bp.P[m] for m in picks]})"}
+
+
+def gpu_batch_arm(args):
+    import torch
+    from paper_2208_14639_gb300 import vv10 as vv
+
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vv.load(build_if_missing=True)
+    bp = BatchProblem(dev, workers=max(1, len(os.sched_getaffinity(0))))
+    h = vv.vv10_create(local)
+    prec = vv.PRECISIONS[args.precision]
+    peaks, peak_src = load_peaks()
+
+    with ClockSampler(local) as clk:
+        ms, nk, prof = time_batch(vv, h, bp, prec, args.steps, args.warmup, world)
+    clocks = clk.summary()
+    ms_max = max_over_ranks(ms, world)
+    nk = np.asarray(nk, dtype=np.float64)
+    pairs_step = float((nk * nk).sum())
+    K = args.steps
+    value = 2.0 * pairs_step * K * world / (ms_max / 1e3)
+    per = {k: v[0] / K for k, v in prof.items()}
+    launches = sum(v[1] for v in prof.values())
+
+    # tensor-core groups (<= 192 trials each) and padded group width per molecule
+    groups = [-(-p // 192) for p in bp.P]
+    ppad = np.array([max(32, 32 * -(-(-(-p // g)) // 32)) for p, g in zip(bp.P, groups)])
+    nk2 = nk * nk
+    hess_flops = 8.0 * float((nk2 * np.array(bp.P)).sum())
+    dom = max(per, key=per.get)
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "kernel": dom}
+    if dom == "contraction_tensor_core":
+        t = per[dom] / 1e3
+        tf32_peak = peaks["bf16_tflops"] * 0.5 * 1e12
+        t_tensor = 3 * 8.0 * float((nk2 * ppad * np.array(groups)).sum()) / tf32_peak
+        alu_peak = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
+        alu_ops = float(sum(nk2[m] * groups[m] * tc_alu_ops_per_pair(int(ppad[m])) for m in range(len(nk))))
+        roof = {"bound": "alu", "achieved": alu_ops / t / 1e12, "peak": alu_peak / 1e12,
+                "unit": "TFLOP/s (FP32 ops)", "frac": alu_ops / t / alu_peak, "traffic": None,
+                "kernel": "k_hess_tc (batched)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median under load)",
+                "tensor_alt": {"achieved_alg_tflops": hess_flops / t / 1e12,
+                               "tf32_peak_tflops": tf32_peak / 1e12,
+                               "frac_of_split_peak": t_tensor / t}}
+    t_ep = per["pair_sums_EUW"] + per["energy_epilogue"]
+    t_hess = (per["pair_sums_ABC"] + per["trial_prep"] + per["contraction_tensor_core"] +
+              per["contraction_fp64"] + per["hessian_epilogue"])
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions"
+                 if prec != vv.VV10_FP64 else "f64",
+        "data": "synthetic (seeded CHON molecules, Gaussian densities, analytic trials)",
+        "config": {"workload": BATCH_LABEL, "n_molecules": len(bp.sys), "n_points": int(bp.off[-1]),
+                   "n_kept": int(nk.sum()), "pairs_per_step": 2.0 * pairs_step,
+                   "trials_total": int(sum(bp.P)), "precision": args.precision,
+                   "l2": f"inputs larger than L2 ({bp.input_bytes() / 1e9:.1f} GB resident)",
+                   "parallelism": f"replica x{world}",
+                   "pair_count": "2 sum_m N_kept,m^2 (energy/potential + Hessian contraction)"},
+        "roofline": roof, "gpu_launches": launches, "clocks": clocks,
+        "breakdown": {"energy_potential_pairs_per_s": pairs_step / (t_ep / 1e3) if t_ep else None,
+                      "hessian_pairs_per_s": pairs_step / (t_hess / 1e3) if t_hess else None,
+                      "hessian_alg_tflops": hess_flops / (t_hess / 1e3) / 1e12 if t_hess else None,
+                      "phase_ms_per_step": {k: round(v, 3) for k, v in per.items() if v}},
+        "energies_first4": [float(x) for x in bp.out["E"][:4].cpu()],
+    }
+    if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
+        # FP64 baseline on the eight smallest molecules (the whole batch would take minutes)
+        order = np.argsort(bp.n, kind="stable")[:8]
+        sub = BatchProblem(dev, 1, systems=[bp.sys[m] for m in sorted(order)])
+        for k in ("rt", "gt"):  # same trial values as the mixed run
+            parts = [bp.d[k][int(bp.toff[m]):int(bp.toff[m + 1])] for m in sorted(order)]
+            sub.d[k].copy_(torch.cat(parts))
+        ms64, nk64, _ = time_batch(vv, h, sub, vv.VV10_FP64, 1, 1, 1)
+        e64 = sub.out["E"].cpu().numpy()
+        msm, _, _ = time_batch(vv, h, sub, prec, 1, 1, 1)
+        em = sub.out["E"].cpu().numpy()
+        nk64 = np.asarray(nk64, dtype=np.float64)
+        result["fp64_subset"] = {
+            "molecules": [int(m) for m in sorted(order)],
+            "value": 2.0 * float((nk64 * nk64).sum()) / (ms64 / 1e3),
+            "mixed_value_same_subset": 2.0 * float((nk64 * nk64).sum()) / (msm / 1e3),
+            "max_abs_energy_diff_mixed_vs_fp64": float(np.abs(em - e64).max()),
+        }
+        del sub
+        run_batch_step(vv, h, bp, prec)  # back to the full batch (the handle holds one batch)
+    sec, h2d, d2h = time_batch_e2e(vv, h, bp, prec, max(1, min(K, 2)), 1)
+    result["e2e"] = {"value": 2.0 * pairs_step * max(1, min(K, 2)) / sec, "unit": UNIT,
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = batch_cpu_sample(bp, args.cpu_seconds)
+    vv.vv10_destroy(h)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------ reference arm (oracle)
+
+def reference_batch_arm(args):
+    """The oracle on the batch workload: each step a bounded row sample of three molecules."""
+    import oracle
+    from paper_2208_14639_gb300 import synth
+    systems = synth.config_batch(workers=max(1, len(os.sched_getaffinity(0))))
+    n = [g.n for g in systems]
+    order = np.argsort(n, kind="stable")
+    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(cores)
+    data = []
+    for m in picks:
+        g = systems[m]
+        rt, gt = synth.trial_densities(g.molecule, g.coords)
+        data.append(((g.coords, g.weights, g.rho, g.grad_rho), rt, gt,
+                     np.flatnonzero(g.rho >= 1e-10)))
+
+    def step(n_rows):
+        pairs = 0
+        for a, rt, gt, kept in data:
+            rows = kept[np.linspace(0, kept.size - 1, n_rows).astype(np.int64)]
+            oracle.potential(*a, rows=rows)
+            oracle.hessian_contract(*a, rt, gt, rows=rows)
+            pairs += 2 * n_rows * kept.size
+        return pairs
+
+    t0 = time.perf_counter()
+    step(4)
+    per_step = min(20.0, 120.0 / (args.steps + args.warmup))
+    n_rows = int(max(4, min(4096, 4 * per_step / max(time.perf_counter() - t0, 1e-3))))
+    for _ in range(args.warmup):
+        step(n_rows)
+    t0 = time.perf_counter()
+    pairs = sum(step(n_rows) for _ in range(args.steps))
+    sec = time.perf_counter() - t0
+    value = pairs / sec
+    sample = (f"{n_rows} rows each (energy/potential and Hessian contraction, full j sums) of "
+              f"molecules {picks} ({[n[m] for m in picks]} points) per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": BATCH_LABEL, "n_molecules": len(systems)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
 
 def reference_arm(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return
+    if args.workload == "batch":
+        return reference_batch_arm(args)
     import oracle
     label, make = workloads()[args.workload]
     g = make()
@@ -458,7 +768,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hexamer", "water", "cluster24", "chon60"), default="hexamer")
+    ap.add_argument("--workload", choices=("hexamer", "water", "cluster24", "chon60", "batch"),
+                    default="hexamer")
     ap.add_argument("--precision", choices=("mixed", "tf32x3", "fp64"), default="mixed")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -468,6 +779,8 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batch":
+        gpu_batch_arm(args)
     else:
         gpu_arm(args)
 

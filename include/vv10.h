@@ -180,6 +180,62 @@ vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xyz, const do
                                           vv10_params prm, vv10_precision prec, double* energy,
                                           double* vrho, double* vgamma, void* stream);
 
+/* ---------------------------------------------------------------- batched molecules
+ * Many independent molecules in one call (the paper has no counterpart: it evaluates one
+ * system at a time; every quantity below is, per molecule, exactly the one defined for a
+ * single system in Sec. II.A and Sec. II.B, and molecules never interact).  The pair sums
+ * of all molecules run as one persistent launch over a table of (molecule, row tile,
+ * j-split) tasks; the tensor-core contraction as one launch per padded trial width.
+ * Molecule m owns the points offsets[m] .. offsets[m+1]-1 of the concatenated arrays.
+ *
+ * vv10_batch_prepare: like vv10_prepare_points, for n_mol >= 1 molecules.
+ *   offsets       HOST int64[n_mol + 1], offsets[0] = 0, strictly increasing (each
+ *                 molecule has at least one point); offsets[n_mol] = n_total
+ *   xyz, w, rho, grad_rho   device FP64, n_total rows, layouts as for vv10_prepare_points
+ *   atom_of_point device int32[n_total] with per-molecule atom indices, or NULL
+ *   n_atom        HOST int32[n_mol] (each in [1, VV10_MAX_ATOMS]) or NULL (with
+ *                 atom_of_point NULL)
+ *   n_kept        HOST int64[n_mol] out: points kept per molecule (rho >= rho_cut)
+ * The prepared blocks are owned by the handle and replace any earlier batch; the
+ * single-system state of the handle is not touched.  Synchronises `stream` once.
+ * Errors: INVALID_ARG, OOM, CUDA, NONFINITE.
+ *
+ * vv10_batch_energy_potential: E per molecule (energies: DEVICE double[n_mol] out, written
+ * on `stream`, not synchronised) and f^rho, f^gamma (device n_total out, caller indexing,
+ * may be NULL).  prec as for vv10_energy_potential.  Errors: INVALID_ARG, OOM, CUDA;
+ * device-side conditions are reported by the next vv10_sync.
+ *
+ * vv10_batch_hessian_contract: f^{rho,t}, f^{gamma,t} (Eq. frhot) for P[m] trial densities
+ * of molecule m (P: HOST int32[n_mol], each in [1, VV10_MAX_TRIALS]).  rho_t, grad_rho_t,
+ * f_rho_t, f_gamma_t are the concatenation over molecules of each molecule's [P[m]][n_m]
+ * (and [P[m]][n_m][3]) row-major blocks, molecule 0 first.  prec: VV10_FP64 or
+ * VV10_MIXED_TF32X3 (VV10_MIXED_BF16X3: UNSUPPORTED).  Needs a preceding
+ * vv10_batch_energy_potential.  Not synchronised.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
+ * CUDA.
+ *
+ * vv10_batch_run: vv10_batch_energy_potential followed by vv10_batch_hessian_contract.
+ * The first call for a given (prec, P, pointer set) runs eagerly and then records the
+ * same launches into a CUDA graph owned by the handle; later calls with the same
+ * arguments replay that graph on `stream` (one graph launch, no host work per kernel).
+ * The graph reads the argument pointers given at recording time: their contents may
+ * change between calls, their addresses may not (other addresses record a new graph).
+ * It stays valid until the next vv10_batch_prepare, vv10_set_tiles or vv10_destroy.  Do
+ * not call it while `stream` is being captured by the caller.  Errors: as above. */
+vv10_status vv10_batch_prepare(vv10_handle h, int32_t n_mol, const int64_t* offsets,
+                               const double* xyz, const double* w, const double* rho,
+                               const double* grad_rho, const int32_t* atom_of_point,
+                               const int32_t* n_atom, vv10_params prm, int64_t* n_kept,
+                               void* stream);
+vv10_status vv10_batch_energy_potential(vv10_handle h, vv10_precision prec, double* energies,
+                                        double* vrho, double* vgamma, void* stream);
+vv10_status vv10_batch_hessian_contract(vv10_handle h, vv10_precision prec, const int32_t* P,
+                                        const double* rho_t, const double* grad_rho_t,
+                                        double* f_rho_t, double* f_gamma_t, void* stream);
+vv10_status vv10_batch_run(vv10_handle h, vv10_precision prec, const int32_t* P,
+                           const double* rho_t, const double* grad_rho_t, double* energies,
+                           double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
+                           void* stream);
+
 /* Synchronise `stream` and report any deferred device-side error on this handle. */
 vv10_status vv10_sync(vv10_handle h, void* stream);
 

@@ -51,6 +51,7 @@ vv10_status vv10_ctx::ensure(DevBuf& b, size_t bytes, const char* what) {
 }
 
 void vv10_ctx::release_all() {
+    batch_release();
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
@@ -653,6 +654,7 @@ vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_s
     o.active = rows_per_thread > 0;
     o.rows_per_thread = rows_per_thread;
     o.n_split = n_split;
+    h->batch_drop_graph();  // a recorded batch graph holds the old tiles
     return VV10_OK;
 }
 

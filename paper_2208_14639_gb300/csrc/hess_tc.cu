@@ -17,6 +17,7 @@
 //     output in global memory (each tile's rows are owned by one CTA: no atomics).
 // The tensor core accumulates with truncation, so each TMEM accumulation run is kept to
 // one stage (12 adds); the register and FP64 levels bound the rest of the rounding.
+#include <cstring>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -56,16 +57,45 @@ __host__ __device__ inline TcSmemLayout tc_layout(int ppad) {
     return L;
 }
 
+// One system (molecule) of a tensor-core launch.
+struct TcMol {
+    const float4* r32a;     // row records (x, y, z, c) and (omega, kappa, p, q)
+    const float4* r32b;
+    const float4* r32p;     // pair-packed column records
+    const CUtensorMap* maps;  // u_hi, u_lo, y_hi, y_lo maps in global memory (batch), or null
+    double* acc;            // [2][acc_P][nk_pad] FP64 partial output, zero on entry
+    int64_t nk, nk_pad, acc_P;
+    int32_t Pn, t0;         // trials of this launch and the first one's row in the split arrays
+};
+// One work unit: 128 rows of molecule `mol`, output kind (ignored when both kinds share a tile).
+struct TcTask {
+    int32_t mol, row_tile, kind, pad;
+};
 struct TcArgs {
-    PointsDev P;
-    int32_t Pn;       // trials in this launch
-    int32_t t0;       // first trial of this launch (row offset into the split arrays)
-    int64_t acc_P;    // trial count of the FP64 accumulator layout
-    int64_t n_row_tiles;
-    int flush;        // stages per FP64 flush
-    double* acc;      // [2][acc_P][nk_pad], zero on entry
+    TcMol single;           // the system of a single-system launch
+    const TcMol* mols;      // batch: molecule table (null for a single system)
+    const TcTask* tasks;    // batch: task table, largest molecules first (null: implicit)
+    int64_t n_tasks;
+    int flush;              // stages per FP64 flush
     int* err;
 };
+
+template <int NK>
+__device__ __forceinline__ TcTask tc_task(const TcArgs& a, int64_t q) {
+    if (a.tasks) return a.tasks[q];
+    TcTask t;
+    t.mol = 0;
+    t.row_tile = static_cast<int32_t>(NK == 2 ? q : (q >> 1));
+    t.kind = NK == 2 ? 0 : static_cast<int32_t>(q & 1);
+    t.pad = 0;
+    return t;
+}
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(m))
+                 : "memory");
+}
 
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, int* err,
                                               volatile int* abort_flag) {
@@ -180,10 +210,8 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kTcRing + 6);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const PointsDev& P = args.P;
-    const int n_stage = static_cast<int>(P.nk_pad / kTcKj);
-    // a tile = 128 rows x (both kinds if NK == 2, else one kind)
-    const int64_t n_tiles = (NK == 2 ? 1 : 2) * args.n_row_tiles;
+    // a task = 128 rows of one molecule x (both kinds if NK == 2, else one kind)
+    const int64_t n_tiles = args.n_tasks;
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < kTcRing; ++b) {
@@ -207,15 +235,26 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
     if (warp == kTcProducerWarp) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            tc::prefetch_tmap(&tm_uh);
-            tc::prefetch_tmap(&tm_ul);
-            tc::prefetch_tmap(&tm_yh);
-            tc::prefetch_tmap(&tm_yl);
             int slot = 0;
             uint32_t ph = 0;   // phase bit of the ring slot's current use
             int64_t issued = 0;
             bool ok = true;
+            int cur_mol = -1;
+            const CUtensorMap* mp[4] = {&tm_uh, &tm_ul, &tm_yh, &tm_yl};
             for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
+                const TcTask tk = tc_task<NK>(args, q);
+                const TcMol M = args.mols ? args.mols[tk.mol] : args.single;
+                if (tk.mol != cur_mol) {  // a new molecule's tensor maps
+                    cur_mol = tk.mol;
+                    for (int k = 0; k < 4; ++k) {
+                        if (M.maps) {
+                            mp[k] = M.maps + k;
+                            tmap_acquire(mp[k]);
+                        }
+                        tc::prefetch_tmap(mp[k]);
+                    }
+                }
+                const int n_stage = static_cast<int>(M.nk_pad / kTcKj);
                 for (int s = 0; s < n_stage; ++s) {
                     if (!wait_or_abort(&b_empty[slot], ph ^ 1u, args.err, abort_flag)) {
                         ok = false;
@@ -225,11 +264,11 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     uint8_t* rec = smem + L.rec_off + slot * 512;
                     const int j0 = s * kTcKj;
                     mbar_expect_tx(&b_full[slot], L.ring_bytes + 512u);
-                    bulk_g2s(rec, P.r32p + 2 * j0, 512u, &b_full[slot]);
-                    tc::tma_load_2d(base + 0 * L.tile_bytes, &tm_uh, j0, args.t0, &b_full[slot]);
-                    tc::tma_load_2d(base + 1 * L.tile_bytes, &tm_ul, j0, args.t0, &b_full[slot]);
-                    tc::tma_load_2d(base + 2 * L.tile_bytes, &tm_yh, j0, args.t0, &b_full[slot]);
-                    tc::tma_load_2d(base + 3 * L.tile_bytes, &tm_yl, j0, args.t0, &b_full[slot]);
+                    bulk_g2s(rec, M.r32p + 2 * j0, 512u, &b_full[slot]);
+                    tc::tma_load_2d(base + 0 * L.tile_bytes, mp[0], j0, M.t0, &b_full[slot]);
+                    tc::tma_load_2d(base + 1 * L.tile_bytes, mp[1], j0, M.t0, &b_full[slot]);
+                    tc::tma_load_2d(base + 2 * L.tile_bytes, mp[2], j0, M.t0, &b_full[slot]);
+                    tc::tma_load_2d(base + 3 * L.tile_bytes, mp[3], j0, M.t0, &b_full[slot]);
                     ++issued;
                     if (++slot == kTcRing) {
                         slot = 0;
@@ -249,7 +288,10 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
             uint32_t ph = 0, aph = 0;
             bool ok = true, issued_any = false;
             for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
-                const int kind0 = NK == 2 ? 0 : static_cast<int>(q & 1);
+                const TcTask tk = tc_task<NK>(args, q);
+                const int kind0 = tk.kind;
+                const int64_t nkp = args.mols ? args.mols[tk.mol].nk_pad : args.single.nk_pad;
+                const int n_stage = static_cast<int>(nkp / kTcKj);
                 for (int s = 0; s < n_stage; ++s) {
                     if (!wait_or_abort(&a_full[ab], aph, args.err, abort_flag) ||
                         !wait_or_abort(&b_full[slot], ph, args.err, abort_flag)) {
@@ -333,15 +375,23 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     acc[k][c + 1] = v.y;
                 }
         };
-        auto flush = [&](int kind0, int64_t i) {
+        // descriptor fields are read where they are used (not held across the stage loop)
+        auto flush = [&](int mol, int kind0, int64_t i) {
+            const TcMol* mp = args.mols ? args.mols + mol : nullptr;
+            const int64_t nk = mp ? mp->nk : args.single.nk;
+            const int64_t nk_pad = mp ? mp->nk_pad : args.single.nk_pad;
+            const int64_t acc_P = mp ? mp->acc_P : args.single.acc_P;
+            const int32_t Pn = mp ? mp->Pn : args.single.Pn;
+            const int32_t t0 = mp ? mp->t0 : args.single.t0;
+            double* acc_base = mp ? mp->acc : args.single.acc;
 #pragma unroll
             for (int k = 0; k < NK; ++k) {
                 const int kind = NK == 2 ? k : kind0;
 #pragma unroll
                 for (int c = 0; c < PQ; ++c) {
                     const int t = part * PQ + c;
-                    if (i < P.nk && t < args.Pn) {
-                        double* o = args.acc + ((static_cast<int64_t>(kind) * args.acc_P + args.t0 + t) * P.nk_pad + i);
+                    if (i < nk && t < Pn) {
+                        double* o = acc_base + ((static_cast<int64_t>(kind) * acc_P + t0 + t) * nk_pad + i);
                         const double v = static_cast<double>(acc[k][c]);
                         *o += (kind == 0) ? v : -v;  // the gamma accumulator holds -(T3 u + T4 y)
                     }
@@ -355,11 +405,15 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
         int dbuf = 0;          // accumulator buffer of the previous stage
         uint32_t dph = 0;      // and its phase bit
         for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
-            const int kind0 = NK == 2 ? 0 : static_cast<int>(q & 1);
-            const int64_t i = (NK == 2 ? q : (q >> 1)) * 128 + quad * 32 + lane;
+            const TcTask tk = tc_task<NK>(args, q);
+            const TcMol* mp = args.mols ? args.mols + tk.mol : nullptr;
+            const int n_stage = static_cast<int>((mp ? mp->nk_pad : args.single.nk_pad) / kTcKj);
+            const int kind0 = tk.kind;
+            const int64_t i = static_cast<int64_t>(tk.row_tile) * 128 + quad * 32 + lane;
             float xi = 0.f, yi = 0.f, zi = 0.f, oi = 1.f, ki = 1.f, pi_ = 0.f, qi = 0.f;
-            if (i < P.nk) {
-                const float4 a = P.r32a[i], b = P.r32b[i];
+            if (i < (mp ? mp->nk : args.single.nk)) {
+                const float4 a = (mp ? mp->r32a : args.single.r32a)[i];
+                const float4 b = (mp ? mp->r32b : args.single.r32b)[i];
                 xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y; pi_ = b.z; qi = b.w;
             }
             const RowC rc{make_float2(xi, xi), make_float2(yi, yi), make_float2(zi, zi),
@@ -423,7 +477,7 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     drain_add(r);
                     tc::fence_before();
                     if (--until_flush == 0) {
-                        flush(kind0, i);
+                        flush(tk.mol, kind0, i);
                         until_flush = args.flush;
                     }
                 }
@@ -445,7 +499,7 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
             tc::wait_ld();
             drain_add(r);
             tc::fence_before();
-            flush(kind0, i);
+            flush(tk.mol, kind0, i);
         }
         tc::wait_st();  // nothing of ours is in flight to TMEM on any exit path
         tc::wait_ld();
@@ -530,13 +584,29 @@ static cudaError_t launch_tc_t(const CUtensorMap* maps, const TcArgs& a, int n_s
     cudaError_t e = cudaFuncSetAttribute(k_hess_tc<PQ, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L.total));
     if (e != cudaSuccess) return e;
-    const int64_t n_tiles = (NK == 2 ? 1 : 2) * a.n_row_tiles;
-    const int grid = static_cast<int>(n_tiles < n_sm ? n_tiles : n_sm);
+    const int grid = static_cast<int>(a.n_tasks < n_sm ? a.n_tasks : n_sm);
+    if (grid <= 0) return cudaSuccess;
     k_hess_tc<PQ, NK><<<grid, kTcThreads, L.total, st>>>(maps[0], maps[1], maps[2], maps[3], a);
     return cudaGetLastError();
 }
 
-// Contract the trials [t0, t0 + Pn) (Pn <= 192); split arrays have `rows` rows.
+// Both kinds share a tile whenever both accumulators fit in TMEM (Ppad <= 64).
+int hess_tc_kinds_per_tile(int ppad) { return ppad <= 64 ? 2 : 1; }
+
+static cudaError_t launch_tc_dispatch(int ppad, const CUtensorMap* maps, const TcArgs& a, int n_sm,
+                                      cudaStream_t st) {
+    switch (ppad / 4) {
+        case 8: return launch_tc_t<8, 2>(maps, a, n_sm, st);
+        case 16: return launch_tc_t<16, 2>(maps, a, n_sm, st);
+        case 24: return launch_tc_t<24, 1>(maps, a, n_sm, st);
+        case 32: return launch_tc_t<32, 1>(maps, a, n_sm, st);
+        case 40: return launch_tc_t<40, 1>(maps, a, n_sm, st);
+        case 48: return launch_tc_t<48, 1>(maps, a, n_sm, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Contract the trials [t0, t0 + Pn) (Pn <= 192) of one system; split arrays have `rows` rows.
 cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
                            const float* uh, const float* ul, const float* yh, const float* yl,
                            int64_t rows, int n_sm, int flush, double* acc, int* err,
@@ -549,22 +619,55 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
     for (int k = 0; k < 4; ++k)
         if (!make_map(&maps[k], src[k], p.nk_pad, rows, ppad)) return cudaErrorInvalidValue;
     TcArgs a;
-    a.P = p;
-    a.Pn = Pn;
-    a.t0 = t0;
-    a.acc_P = acc_P;
-    a.n_row_tiles = (p.nk + 127) / 128;
+    a.single = TcMol{p.r32a, p.r32b, p.r32p, nullptr, acc, p.nk, p.nk_pad, acc_P, Pn, t0};
+    a.mols = nullptr;
+    a.tasks = nullptr;
+    a.n_tasks = (hess_tc_kinds_per_tile(ppad) == 2 ? 1 : 2) * ((p.nk + 127) / 128);
     a.flush = flush > 0 ? flush : 512;
-    a.acc = acc;
     a.err = err;
-    switch (ppad / 4) {  // two kinds per tile whenever both accumulators fit in TMEM
-        case 8: return launch_tc_t<8, 2>(maps, a, n_sm, st);
-        case 16: return launch_tc_t<16, 2>(maps, a, n_sm, st);
-        case 24: return launch_tc_t<24, 1>(maps, a, n_sm, st);
-        case 32: return launch_tc_t<32, 1>(maps, a, n_sm, st);
-        case 40: return launch_tc_t<40, 1>(maps, a, n_sm, st);
-        default: return launch_tc_t<48, 1>(maps, a, n_sm, st);
-    }
+    return launch_tc_dispatch(ppad, maps, a, n_sm, st);
+}
+
+// Tensor maps of one molecule of a batched contraction (4 consecutive CUtensorMap).
+bool hess_tc_make_maps(void* out4, const float* uh, const float* ul, const float* yh,
+                       const float* yl, int64_t nk_pad, int64_t rows, int ppad) {
+    CUtensorMap* m = static_cast<CUtensorMap*>(out4);
+    const float* src[4] = {uh, ul, yh, yl};
+    for (int k = 0; k < 4; ++k)
+        if (!make_map(&m[k], src[k], nk_pad, rows, ppad)) return false;
+    return true;
+}
+
+// Batched contraction: every task of the table shares `ppad`; molecules and tensor maps
+// live in device memory (written before the launch).
+cudaError_t launch_hess_tc_batch(const void* mols, const void* tasks, int64_t n_tasks, int ppad,
+                                 int n_sm, int flush, int* err, cudaStream_t st) {
+    if (n_tasks <= 0) return cudaSuccess;
+    CUtensorMap unused[4];
+    memset(unused, 0, sizeof(unused));
+    TcArgs a;
+    memset(&a.single, 0, sizeof(a.single));
+    a.mols = static_cast<const TcMol*>(mols);
+    a.tasks = static_cast<const TcTask*>(tasks);
+    a.n_tasks = n_tasks;
+    a.flush = flush > 0 ? flush : 512;
+    a.err = err;
+    return launch_tc_dispatch(ppad, unused, a, n_sm, st);
+}
+
+size_t hess_tc_mol_bytes() { return sizeof(TcMol); }
+size_t hess_tc_task_bytes() { return sizeof(TcTask); }
+
+void hess_tc_fill_mol(void* dst, const float4* r32a, const float4* r32b, const float4* r32p,
+                      const void* maps_dev, double* acc, int64_t nk, int64_t nk_pad, int64_t acc_P,
+                      int32_t Pn, int32_t t0) {
+    TcMol m{r32a, r32b, r32p, static_cast<const CUtensorMap*>(maps_dev), acc, nk, nk_pad, acc_P, Pn, t0};
+    memcpy(dst, &m, sizeof(m));
+}
+
+void hess_tc_fill_task(void* dst, int32_t mol, int32_t row_tile, int32_t kind) {
+    TcTask t{mol, row_tile, kind, 0};
+    memcpy(dst, &t, sizeof(t));
 }
 
 }  // namespace vv10

@@ -18,7 +18,7 @@ using namespace vv10;
 
 // Trials per CTA of the FP64 SIMT contraction: minimise chunks * (pair-generation cost +
 // 4 FMAs per trial), the FP64 operation count per pair.
-static int pick_trials_per_cta(int32_t P) {
+int vv10::hess_f64_trials_per_cta(int32_t P) {
     int best = 8;
     long best_cost = -1;
     for (int pc : {8, 16, 32}) {
@@ -123,7 +123,7 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
     }
 
     HessLaunch cfg;
-    cfg.trials_per_cta = pick_trials_per_cta(Pn);
+    cfg.trials_per_cta = hess_f64_trials_per_cta(Pn);
     cfg.n_split = hess_f64_default_split(P, Pn, cfg.trials_per_cta, n_sm);
     H_TRY(ensure(hacc, sizeof(double) * 2 * static_cast<size_t>(cfg.n_split) * Pn * P.nk_pad,
                  "contraction partials"));

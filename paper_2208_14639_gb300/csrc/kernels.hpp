@@ -73,6 +73,26 @@ cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLa
                            double* part, int* err, cudaStream_t st);
 int pairsum_default_split(const PointsDev& p, bool fp64, int rows_per_thread, int n_sm);
 
+// Batched pair sums (batch.cu): one persistent launch over a task table with an atomic
+// work counter.  PairMol describes one molecule's records and partial buffer
+// part[3][n_split][nk_pad]; PairTask one (molecule, row tile, j-split) unit.
+struct PairMol {
+    const void* ra32;
+    const void* rb32;
+    const void* ra64;
+    const void* rb64;
+    int64_t nk, nk_pad, j_per_split;
+    int32_t n_split, pad;
+    double* part;
+};
+struct PairTask {
+    int32_t mol, row_tile, split, pad;
+};
+cudaError_t launch_pairsum_batch(const PairMol* mols, const PairTask* tasks, int n_tasks,
+                                 int* counter, int mode, bool fp64, int rows_per_thread, int n_sm,
+                                 int* err, cudaStream_t st);
+int pairsum_rows_per_cta(bool fp64, int rows_per_thread);
+
 // Energy / potential epilogue: reduces the partials, writes E,U,W (kept indexing),
 // f^rho, f^gamma (caller indexing) and per-block energy partials.
 int ep_epilogue_blocks(int64_t nk);
@@ -106,11 +126,26 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
                            int64_t rows, int n_sm, int flush, double* acc, int* err,
                            cudaStream_t st);
 
+// Batched tensor-core contraction (molecule and task tables in device memory; see
+// hess_tc.cu for the record layouts the fill helpers write).
+int hess_tc_kinds_per_tile(int ppad);
+bool hess_tc_make_maps(void* out4 /* 4 CUtensorMap */, const float* uh, const float* ul,
+                       const float* yh, const float* yl, int64_t nk_pad, int64_t rows, int ppad);
+cudaError_t launch_hess_tc_batch(const void* mols, const void* tasks, int64_t n_tasks, int ppad,
+                                 int n_sm, int flush, int* err, cudaStream_t st);
+size_t hess_tc_mol_bytes();
+size_t hess_tc_task_bytes();
+void hess_tc_fill_mol(void* dst, const float4* r32a, const float4* r32b, const float4* r32p,
+                      const void* maps_dev, double* acc, int64_t nk, int64_t nk_pad, int64_t acc_P,
+                      int32_t Pn, int32_t t0);
+void hess_tc_fill_task(void* dst, int32_t mol, int32_t row_tile, int32_t kind);
+
 struct HessLaunch {
     int trials_per_cta = 16;  // FP64 SIMT: 8, 16, 32
     int n_split = 1;
 };
 int hess_f64_default_split(const PointsDev& p, int32_t P, int pc, int n_sm);
+int hess_f64_trials_per_cta(int32_t P);
 // acc: [2][n_split][P][nk_pad] partial sums of the pair part (rho row, gamma row).
 cudaError_t launch_hess_f64(const PointsDev& p, int32_t P, const double* u, const double* y,
                             const HessLaunch& cfg, double* acc, int* err, cudaStream_t st);

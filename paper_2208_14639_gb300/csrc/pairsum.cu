@@ -20,59 +20,9 @@
 // tile, promoted to FP64 once per tile.  FP64 variant: everything in FP64.
 #include "common.cuh"
 #include "kernels.hpp"
+#include "pairsum.cuh"
 
 namespace vv10 {
-
-template <class T> struct Recs;
-template <> struct Recs<float> { using A = float4; using B = float4; };
-template <> struct Recs<double> { using A = double4; using B = double4; };
-
-__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
-
-template <class T>
-struct Row {
-    T x, y, z, om, ka;
-};
-
-// Accumulate one (i, j) pair into acc[0..2] for the given mode.
-template <class T, int MODE, class RA, class RB>
-__device__ __forceinline__ void pair_accumulate(const Row<T>& r, const RA& a, const RB& b,
-                                                T (&acc)[3]) {
-    const T dx = r.x - a.x, dy = r.y - a.y, dz = r.z - a.z;
-    T r2 = dx * dx;
-    r2 = fmadd(dy, dy, r2);
-    r2 = fmadd(dz, dz, r2);
-    const T g = fmadd(r.om, r2, r.ka);
-    const T gp = fmadd(b.x, r2, b.y);
-    const T s = g + gp;
-    const T ggp = g * gp;
-    const T inv = recip(ggp * s);
-    const T ph = a.w * inv;  // w_j rho_j Phi_ij  (a.w = -3/2 w_j rho_j)
-    if constexpr (MODE == MODE_EUW) {
-        const T t = ((g + s) * gp) * inv;  // 1/s + 1/g
-        const T pt = ph * t;
-        acc[0] += ph;
-        acc[1] += pt;
-        acc[2] = fmadd(pt, r2, acc[2]);
-    } else if constexpr (MODE == MODE_ABC) {
-        const T L = ggp * inv;         // 1/s
-        const T Gi = (gp * s) * inv;   // 1/g
-        const T m = fmadd(L, L + Gi, Gi * Gi);
-        const T v = ph * m;
-        acc[0] += v;
-        const T v2 = v * r2;
-        acc[1] += v2;
-        acc[2] = fmadd(v2, r2, acc[2]);
-    } else {
-        // D g g' s = omega_i g' (s + g) + omega_j g (s + g')
-        const T num = fmadd(r.om * gp, s + g, (b.x * g) * (s + gp));
-        const T f = (ph * inv) * num;
-        acc[0] = fmadd(f, dx, acc[0]);
-        acc[1] = fmadd(f, dy, acc[1]);
-        acc[2] = fmadd(f, dz, acc[2]);
-    }
-}
 
 template <class T, int MODE, int RPT, int NT>
 __global__ void __launch_bounds__(NT)
@@ -91,28 +41,6 @@ k_pairsum(const typename Recs<T>::A* __restrict__ ra, const typename Recs<T>::B*
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * (NT * RPT);
     const int64_t jb = static_cast<int64_t>(split) * j_per_split;
     const int64_t je = min(nk_pad, jb + j_per_split);
-    const int ntile = je > jb ? static_cast<int>((je - jb) / kJTile) : 0;
-
-    Row<T> row[RPT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int64_t i = i0 + r * NT + tid;
-        if (i < nk) {
-            const RA a = ra[i];
-            const RB b = rb[i];
-            row[r] = Row<T>{a.x, a.y, a.z, b.x, b.y};
-        } else {
-            row[r] = Row<T>{T(0), T(0), T(0), T(1), T(1)};
-        }
-    }
-    T acc[RPT][3];
-    double dacc[RPT][3];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) { acc[r][q] = T(0); dacc[r][q] = 0.0; }
-
-    constexpr uint32_t kBytesA = sizeof(RA) * kJTile, kBytesB = sizeof(RB) * kJTile;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -121,49 +49,9 @@ k_pairsum(const typename Recs<T>::A* __restrict__ ra, const typename Recs<T>::B*
     __syncthreads();
     // Test hook: a stalled CTA never issues its copies, so its first wait runs out.
     const bool stalled = stall && blockIdx.x == 0 && blockIdx.y == 0;
-    int issued = 0;
-    if (tid == 0 && !stalled) {
-        for (; issued < 2 && issued < ntile; ++issued) {
-            const int64_t j0 = jb + static_cast<int64_t>(issued) * kJTile;
-            mbar_expect_tx(&bar[issued], kBytesA + kBytesB);
-            bulk_g2s(sa[issued], ra + j0, kBytesA, &bar[issued]);
-            bulk_g2s(sb[issued], rb + j0, kBytesB, &bar[issued]);
-        }
-    }
-    int consumed = 0;
-    for (int t = 0; t < ntile; ++t) {
-        const int buf = t & 1;
-        const bool ok = mbar_wait(&bar[buf], (t >> 1) & 1, err);
-        const RA* A = sa[buf];
-        const RB* B = sb[buf];
-#pragma unroll 2
-        for (int jj = 0; jj < kJTile; ++jj) {
-            const RA a = A[jj];
-            const RB b = B[jj];
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) pair_accumulate<T, MODE>(row[r], a, b, acc[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < RPT; ++r)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                dacc[r][q] += static_cast<double>(acc[r][q]);
-                acc[r][q] = T(0);
-            }
-        consumed = t + 1;
-        if (__syncthreads_or(!ok)) break;  // every thread leaves together
-        if (tid == 0 && !stalled && issued < ntile) {
-            const int64_t j0 = jb + static_cast<int64_t>(issued) * kJTile;
-            mbar_expect_tx(&bar[buf], kBytesA + kBytesB);
-            bulk_g2s(sa[buf], ra + j0, kBytesA, &bar[buf]);
-            bulk_g2s(sb[buf], rb + j0, kBytesB, &bar[buf]);
-            ++issued;
-        }
-    }
-    // After a timeout, wait (bounded) for copies still in flight before the CTA exits.
-    if (tid == 0)
-        for (int t = consumed; t < issued; ++t) mbar_wait(&bar[t & 1], (t >> 1) & 1, err);
-
+    uint32_t gtile = 0;
+    double dacc[RPT][3];
+    pairsum_range<T, MODE, RPT, NT>(sa, sb, bar, gtile, ra, rb, nk, i0, jb, je, dacc, err, stalled);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int64_t i = i0 + r * NT + tid;

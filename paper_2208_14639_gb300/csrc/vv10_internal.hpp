@@ -41,6 +41,54 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
+// One molecule of a batch (byte offsets into the batch's device arenas).
+struct BatchMol {
+    int64_t off = 0, n = 0, nk = 0, nk_pad = 0, cap = 0;
+    int32_t n_atom = 0;
+    PointsDev P;
+    size_t sums = 0;             // E, U, W, A, B, C (6 x cap doubles)
+    int n_split = 1;             // pair-sum j-splits of the current task table
+    int64_t j_per_split = 0;
+    size_t part = 0;             // pair-sum partials [3][n_split][nk_pad]
+    size_t eblk = 0;             // energy block partials
+    int nblk = 0;
+    int32_t n_t = 0;             // trials of the current Hessian layout
+    int64_t toff = 0;            // first trial value in the caller's concatenated arrays
+    int ng = 1, pg = 0, ppad = 0;  // tensor-core groups of <= 192 trials, padded group width
+    int64_t rows = 0;            // rows of each trial split ((ng - 1) pg + ppad)
+    size_t rt = 0, gt = 0;       // rho^t, gamma^t at kept points (n_t x nk doubles each)
+    size_t split = 0;            // four FP32 [rows][nk_pad] trial splits
+    size_t acc = 0;              // FP64 [2][n_t][nk_pad] contraction partials
+};
+
+struct TcClass {
+    int ppad = 0;
+    int64_t n_tasks = 0;
+    size_t mols = 0, tasks = 0;  // byte offsets in tc_tab
+};
+
+struct BatchState {
+    std::vector<BatchMol> mol;
+    std::vector<int> order;      // molecules, largest first
+    int64_t n_total = 0;
+    bool prepared = false, have_euw = false, have_abc = false, abc_fp64 = false;
+    DevBuf scratch, small, arena, sums, part, eblk, pair_tab, counter;
+    void* h_small = nullptr;
+    size_t h_small_bytes = 0;
+    int pair_tab_fp64 = -1, pair_tab_rpt = 0, n_pair_tasks = 0;
+    size_t pair_mols = 0, pair_tasks = 0;
+    // Hessian layout (valid for hess_P)
+    std::vector<int32_t> hess_P;
+    DevBuf rtgt, splits, acc, maps, tc_tab;
+    std::vector<TcClass> tc_classes;
+    // graph of a whole batched pass, and what it was captured for
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> graph_key;
+    int graph_prec = -1;
+    std::vector<int32_t> graph_P;
+    int64_t graph_launches[PH_COUNT] = {0};  // kernel launches (by phase) in one replay
+};
+
 }  // namespace vv10
 
 struct vv10_ctx {
@@ -91,6 +139,17 @@ struct vv10_ctx {
     cudaEvent_t take_event();
     void phase_begin(int phase, cudaStream_t st, vv10::ProfRec* rec);
     void phase_end(vv10::ProfRec* rec, cudaStream_t st, int n_launch);
+
+    // batched molecules (vv10_batch_*)
+    vv10::BatchState batch;
+    vv10_status batch_pair_tables(bool fp64, int rpt);
+    vv10_status batch_ep(vv10_precision prec, double* energies, double* vrho, double* vgamma,
+                         cudaStream_t st);
+    vv10_status batch_hess(vv10_precision prec, const int32_t* P, const double* rho_t,
+                           const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
+                           cudaStream_t st);
+    void batch_release();
+    void batch_drop_graph();
 
     // test hooks
     int debug_fail_alloc = 0;

@@ -309,6 +309,34 @@ def trial_densities(mol: Molecule, points: np.ndarray, atoms: Optional[Sequence[
     return rho_t, grad_t
 
 
+def trial_densities_torch(mol: Molecule, points, atoms: Optional[Sequence[int]] = None,
+                          out_rho=None, out_grad=None):
+    """trial_densities evaluated with torch on the device of `points` (an (N, 3) float64
+    tensor), for inputs too large to build on the host.  Writes into out_rho (P, N) and
+    out_grad (P, N, 3) when given (any float64 views), else allocates them."""
+    import torch
+    atoms = list(range(mol.n_atom)) if atoms is None else list(atoms)
+    n = points.shape[0]
+    P = 3 * len(atoms)
+    kw = dict(dtype=torch.float64, device=points.device)
+    rho_t = torch.empty(P, n, **kw) if out_rho is None else out_rho
+    grad_t = torch.empty(P, n, 3, **kw) if out_grad is None else out_grad
+    eye = torch.eye(3, **kw)
+    for ia, a_idx in enumerate(atoms):
+        z = float(mol.charges[a_idx])
+        d = points - torch.as_tensor(mol.coords[a_idx], **kw)
+        r2 = (d * d).sum(dim=1)
+        rt = torch.zeros(n, 3, **kw)
+        gt = torch.zeros(n, 3, 3, **kw)
+        for c, a in zip(_gauss_coeffs(z), GAUSS_EXPONENTS):
+            e = 2.0 * a * float(c) * torch.exp(-a * r2)
+            rt += e[:, None] * d
+            gt += e[:, None, None] * (eye[None] - 2.0 * a * d[:, :, None] * d[:, None, :])
+        rho_t[3 * ia:3 * ia + 3] = rt.T
+        grad_t[3 * ia:3 * ia + 3] = gt.permute(1, 0, 2)
+    return rho_t, grad_t
+
+
 # ----------------------------------------------------------------------------- configs
 
 def make_system(mol: Molecule, n_rad: int, n_ang: int) -> GridDensity:
@@ -339,11 +367,18 @@ def config_chon60(n_rad: int = 75, n_ang: int = 302, seed: int = SEED_BASE + 2,
 
 
 def config_batch(n_mol: int = 64, n_rad: int = 50, n_ang: int = 194, seed: int = SEED_BASE + 3,
-                 atom_range=(3, 30)) -> List[GridDensity]:
-    """Batch of random CHON molecules with U{3..30} atoms, 50 x 194 points per atom."""
+                 atom_range=(3, 30), workers: int = 1) -> List[GridDensity]:
+    """Batch of random CHON molecules with U{3..30} atoms, 50 x 194 points per atom.
+
+    workers > 1 builds the molecules' grids in that many spawned processes (same result)."""
     rng = np.random.default_rng(seed)
     sizes = rng.integers(atom_range[0], atom_range[1] + 1, size=n_mol)
-    return [make_system(random_chon(rng, int(s)), n_rad, n_ang) for s in sizes]
+    mols = [random_chon(rng, int(s)) for s in sizes]
+    if workers <= 1:
+        return [make_system(m, n_rad, n_ang) for m in mols]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(workers, n_mol)) as pool:
+        return pool.starmap(make_system, [(m, n_rad, n_ang) for m in mols], chunksize=1)
 
 
 def config_cluster24(n_rad: int = 30, n_ang: int = 139, seed: int = SEED_BASE + 4) -> GridDensity:

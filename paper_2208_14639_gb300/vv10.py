@@ -37,7 +37,9 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_prepare_points", "vv10_energy_potential", "vv10_hessian_contract",
            "vv10_coord_grad", "vv10_weight_grad", "vv10_sync", "vv10_set_tiles",
            "vv10_debug_inject", "vv10_profile_enable", "vv10_profile_read",
-           "vv10_profile_phase_name", "vv10_energy_potential_noalloc")
+           "vv10_profile_phase_name", "vv10_energy_potential_noalloc",
+           "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
+           "vv10_batch_run")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_N_PHASES = 11
 
@@ -91,6 +93,10 @@ def load(build_if_missing: bool = False):
         "vv10_profile_read": (st, [P, ctypes.c_int, P, P]),
         "vv10_profile_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
         "vv10_energy_potential_noalloc": (st, [I64, P, P, P, P, VV10Params, st, P, P, P, P]),
+        "vv10_batch_prepare": (st, [P, I32, P, P, P, P, P, P, P, VV10Params, P, P]),
+        "vv10_batch_energy_potential": (st, [P, st, P, P, P, P]),
+        "vv10_batch_hessian_contract": (st, [P, st, P, P, P, P, P, P]),
+        "vv10_batch_run": (st, [P, st, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -236,6 +242,73 @@ def vv10_energy_potential_noalloc(xyz, w, rho, grad_rho, prec: int, energy, vrho
         VV10Params(b, C, rho_cut), int(prec), _dptr(energy, "energy", shape=(1,)),
         _dptr(vrho, "vrho", shape=(n,)), _dptr(vgamma, "vgamma", shape=(n,)), _stream(stream))
     _check(None, st, "vv10_energy_potential_noalloc")
+
+
+def _host(a, dtype):
+    """Contiguous host copy (numpy) of a sequence of integers, and its address."""
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    return arr, ctypes.c_void_p(arr.ctypes.data)
+
+
+def vv10_batch_prepare(h, offsets, xyz, w, rho, grad_rho, atom_of_point=None, n_atom=None,
+                       b: float = 6.0, C: float = 0.01, rho_cut: float = 1e-10,
+                       stream=None) -> list:
+    """Prepare n_mol molecules; molecule m owns rows offsets[m]:offsets[m+1] of the
+    concatenated arrays.  Returns the kept points per molecule."""
+    import numpy as np
+    off, off_p = _host(offsets, np.int64)
+    n_mol = int(off.shape[0]) - 1
+    n = int(w.shape[0])
+    if n_mol < 1 or int(off[-1]) != n:
+        raise ValueError("offsets must have n_mol + 1 entries ending at the number of points")
+    na, na_p = _host(n_atom, np.int32) if n_atom is not None else (None, None)
+    nk = np.zeros(n_mol, dtype=np.int64)
+    st = load().vv10_batch_prepare(
+        h, n_mol, off_p, _dptr(xyz, "xyz", shape=(n, 3)), _dptr(w, "w", shape=(n,)),
+        _dptr(rho, "rho", shape=(n,)), _dptr(grad_rho, "grad_rho", shape=(n, 3)),
+        _dptr(atom_of_point, "atom_of_point", torch.int32, (n,)), na_p,
+        VV10Params(b, C, rho_cut), ctypes.c_void_p(nk.ctypes.data), _stream(stream))
+    _check(h, st, "vv10_batch_prepare")
+    return [int(x) for x in nk]
+
+
+def vv10_batch_energy_potential(h, prec: int, energies, vrho=None, vgamma=None,
+                                stream=None) -> None:
+    """Energies (device tensor, one per molecule) and the concatenated potential."""
+    st = load().vv10_batch_energy_potential(h, int(prec), _dptr(energies, "energies"),
+                                            _dptr(vrho, "vrho"), _dptr(vgamma, "vgamma"),
+                                            _stream(stream))
+    _check(h, st, "vv10_batch_energy_potential")
+
+
+def vv10_batch_hessian_contract(h, prec: int, P, rho_t, grad_rho_t, f_rho_t, f_gamma_t,
+                                stream=None) -> None:
+    """P[m] trials per molecule; rho_t, f_rho_t, f_gamma_t: 1-D concatenations of the
+    molecules' [P[m], n_m] blocks, grad_rho_t of their [P[m], n_m, 3] blocks."""
+    import numpy as np
+    Pa, P_p = _host(P, np.int32)
+    tot = int(rho_t.numel())
+    st = load().vv10_batch_hessian_contract(
+        h, int(prec), P_p, _dptr(rho_t, "rho_t", shape=(tot,)),
+        _dptr(grad_rho_t, "grad_rho_t", shape=(tot, 3)), _dptr(f_rho_t, "f_rho_t", shape=(tot,)),
+        _dptr(f_gamma_t, "f_gamma_t", shape=(tot,)), _stream(stream))
+    _check(h, st, "vv10_batch_hessian_contract")
+
+
+def vv10_batch_run(h, prec: int, P, rho_t, grad_rho_t, energies, vrho, vgamma, f_rho_t,
+                   f_gamma_t, stream=None) -> None:
+    """Energy, potential and Hessian contraction of the prepared batch; repeated calls with
+    the same tensors replay one recorded CUDA graph."""
+    import numpy as np
+    Pa, P_p = _host(P, np.int32)
+    tot = int(rho_t.numel())
+    st = load().vv10_batch_run(
+        h, int(prec), P_p, _dptr(rho_t, "rho_t", shape=(tot,)),
+        _dptr(grad_rho_t, "grad_rho_t", shape=(tot, 3)), _dptr(energies, "energies"),
+        _dptr(vrho, "vrho"), _dptr(vgamma, "vgamma"), _dptr(f_rho_t, "f_rho_t", shape=(tot,)),
+        _dptr(f_gamma_t, "f_gamma_t", shape=(tot,)), _stream(stream))
+    _check(h, st, "vv10_batch_run")
 
 
 def vv10_debug_inject(h, what: int, value: int) -> None:

@@ -52,3 +52,27 @@ def test_configs_are_seeded():
     assert a.molecule.n_atom == 24
     batch = synth.config_batch(n_mol=3, n_rad=4, n_ang=6)
     assert all(3 <= m.molecule.n_atom <= 30 for m in batch)
+
+
+def test_trial_densities_torch_matches_numpy():
+    import torch
+    g = synth.random_points(500, seed=71, n_atom=3)
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    rt2, gt2 = synth.trial_densities_torch(g.molecule, torch.from_numpy(g.coords))
+    assert np.allclose(rt2.numpy(), rt, rtol=1e-13, atol=1e-13 * np.abs(rt).max())
+    assert np.allclose(gt2.numpy(), gt, rtol=1e-13, atol=1e-13 * np.abs(gt).max())
+    # into preallocated views of a larger buffer
+    buf = torch.zeros(rt.size + 4, dtype=torch.float64)
+    gbuf = torch.zeros(gt.size + 12, dtype=torch.float64)
+    synth.trial_densities_torch(g.molecule, torch.from_numpy(g.coords),
+                                out_rho=buf[4:].view(rt.shape), out_grad=gbuf[12:].view(gt.shape))
+    assert np.array_equal(buf[4:].view(rt.shape).numpy(), rt2.numpy())
+    assert np.array_equal(gbuf[12:].view(gt.shape).numpy(), gt2.numpy())
+
+
+def test_config_batch_parallel_is_identical():
+    a = synth.config_batch(n_mol=3, n_rad=4, n_ang=6, atom_range=(2, 4))
+    b = synth.config_batch(n_mol=3, n_rad=4, n_ang=6, atom_range=(2, 4), workers=2)
+    for x, y in zip(a, b):
+        for f in ("coords", "weights", "rho", "grad_rho", "atom_of_point"):
+            assert np.array_equal(getattr(x, f), getattr(y, f))
