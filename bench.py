@@ -299,9 +299,13 @@ def gpu_arm(args):
     h = vv.vv10_create(local)
     prec = vv.PRECISIONS[args.precision]
     peaks, peak_src = load_peaks()
+    if prec != vv.VV10_FP64:  # tile shapes tuned on first use, i.e. inside the warm-up steps
+        vv.vv10_set_autotune(h, vv.VV10_TUNE_PAIRSUMS | vv.VV10_TUNE_CONTRACTION)
 
     with ClockSampler(local) as clk:
         ms, nk, e_mixed, prof = time_steps(vv, h, pb, prec, args.steps, args.warmup, world)
+    tiles = {"pair_sums_rows_per_thread_splits": [vv.vv10_get_tiles(h, m) for m in range(3)],
+             "contraction_group_width": vv.vv10_get_tiles(h, vv.TILES_CONTRACTION)[0]}
     clocks = clk.summary()
     ms_max = max_over_ranks(ms, world)
     pairs_call = float(nk) * float(nk)
@@ -370,10 +374,12 @@ def gpu_arm(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "breakdown": breakdown,
+        "tiles": tiles,
         "energy": e_mixed,
     }
 
     if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
+        vv.vv10_set_autotune(h, 0)  # FP64 baseline at its default shapes
         ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
         per64 = {k: v[0] for k, v in prof64.items()}
         t_h64 = (per64["pair_sums_ABC"] + per64["trial_prep"] + per64["contraction_fp64"] +
@@ -567,6 +573,8 @@ def gpu_batch_arm(args):
     h = vv.vv10_create(local)
     prec = vv.PRECISIONS[args.precision]
     peaks, peak_src = load_peaks()
+    if prec != vv.VV10_FP64:  # batched pair-sum tiles tuned on first use (warm-up)
+        vv.vv10_set_autotune(h, vv.VV10_TUNE_BATCH)
 
     with ClockSampler(local) as clk:
         ms, nk, prof = time_batch(vv, h, bp, prec, args.steps, args.warmup, world)
@@ -618,6 +626,7 @@ def gpu_batch_arm(args):
                    "parallelism": f"replica x{world}",
                    "pair_count": "2 sum_m N_kept,m^2 (energy/potential + Hessian contraction)"},
         "roofline": roof, "gpu_launches": launches, "clocks": clocks,
+        "tiles": {"batch_rows_per_thread_tiles_per_split": vv.vv10_get_tiles(h, vv.TILES_BATCH)},
         "breakdown": {"energy_potential_pairs_per_s": pairs_step / (t_ep / 1e3) if t_ep else None,
                       "hessian_pairs_per_s": pairs_step / (t_hess / 1e3) if t_hess else None,
                       "hessian_alg_tflops": hess_flops / (t_hess / 1e3) / 1e12 if t_hess else None,
@@ -626,6 +635,7 @@ def gpu_batch_arm(args):
     }
     if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
         # FP64 baseline on the eight smallest molecules (the whole batch would take minutes)
+        vv.vv10_set_autotune(h, 0)
         order = np.argsort(bp.n, kind="stable")[:8]
         sub = BatchProblem(dev, 1, systems=[bp.sys[m] for m in sorted(order)])
         for k in ("rt", "gt"):  # same trial values as the mixed run

@@ -239,12 +239,46 @@ vv10_status vv10_batch_run(vv10_handle h, vv10_precision prec, const int32_t* P,
 /* Synchronise `stream` and report any deferred device-side error on this handle. */
 vv10_status vv10_sync(vv10_handle h, void* stream);
 
-/* Tile-shape override for the pair-sum kernels (used by the autotuner; the paper has no
- * counterpart).  what = mode + 3 * fp64 with mode 0 = energy/potential sums, 1 = the
- * A/B/C sums of the Hessian diagonal, 2 = coordinate gradient; rows_per_thread in
- * {1, 2, 4} (FP64: {1, 2}), 0 = back to the default; n_split = number of j-splits,
- * 0 = derived from the SM count.  Errors: INVALID_ARG. */
+/* Tile shapes (the paper has no counterpart).  `what` selects a kernel:
+ *   0..5  single-system pair sums, mode + 3 * fp64 (mode 0 = energy/potential sums, 1 = the
+ *         A/B/C sums of the Hessian diagonal, 2 = coordinate gradient): rows_per_thread in
+ *         {1, 2, 4} (FP64: {1, 2}), n_split = number of j-splits (0 = from the SM count);
+ *   6, 7  batched pair sums, 6 + fp64: rows_per_thread as above, n_split = j tiles (of 256
+ *         points) per split (0 = 32);
+ *   8     tensor-core contraction: rows_per_thread = the widest trial group, in [32, 192]
+ *         (n_split unused).  Groups of at most 64 trials produce both outputs from one tile
+ *         generation; wider groups issue fewer MMAs per trial.
+ * vv10_set_tiles fixes a shape (rows_per_thread = 0: back to automatic, i.e. the autotuner's
+ * choice when tuning is enabled, else the default); the autotuner never replaces a fixed
+ * shape.  vv10_get_tiles reads the shape in effect (for 8: the width fixed, else the one the
+ * last mixed vv10_hessian_contract used; 0 before any).  Errors: INVALID_ARG. */
 vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split);
+vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n_split);
+
+/* Autotuner (the paper has no counterpart).  Times every candidate shape of a kernel (see
+ * vv10_set_tiles) on the handle's prepared data, on `stream`, and applies the fastest:
+ *   VV10_TUNE_PAIRSUMS     the three pair-sum modes of the prepared single system (for prec:
+ *                          rows per thread x {default, half, twice} the j-splits);
+ *   VV10_TUNE_BATCH        the batched pair sums of the prepared batch (for prec: rows per
+ *                          thread x {16, 32, 64} j tiles per split);
+ *   VV10_TUNE_CONTRACTION  the widest trial group of the mixed contraction (64, 96, 128,
+ *                          192; only for P > 64), timed on the real trials.
+ * Choices are cached for the process, keyed by kernel, mode, precision, N bucket
+ * (ceil(log2 N_kept); for a batch that of its largest molecule and of its total), trial
+ * count (contraction) and SM count, so a later handle with a same-keyed workload reuses them
+ * without timing.  vv10_autotune(h, prec, what, stream) tunes VV10_TUNE_PAIRSUMS and / or
+ * VV10_TUNE_BATCH now (synchronises the stream; INVALID_ARG while the stream is captured).
+ * vv10_set_autotune(h, flags) makes the handle tune on first use of each key instead: the
+ * pair sums on the first call that runs them, the batched pair sums on the first
+ * vv10_batch_energy_potential / vv10_batch_run, the contraction width on the first mixed
+ * vv10_hessian_contract for a trial count (the batched contraction uses the cached width
+ * of each molecule's key, else 192).  Nothing is timed while a stream is being captured.
+ * Tuning runs are not counted by vv10_profile_read.  Errors: INVALID_ARG, OOM, CUDA. */
+#define VV10_TUNE_PAIRSUMS 1
+#define VV10_TUNE_BATCH 2
+#define VV10_TUNE_CONTRACTION 4
+vv10_status vv10_autotune(vv10_handle h, vv10_precision prec, int what, void* stream);
+vv10_status vv10_set_autotune(vv10_handle h, int flags);
 
 /* Launch accounting and per-phase GPU timing (the paper has no counterpart).
  * vv10_profile_enable(h, 1): from now on every kernel launch of this handle is bracketed

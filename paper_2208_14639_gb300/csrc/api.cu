@@ -399,6 +399,7 @@ vv10_status vv10_ctx::require_prepared() {
 }
 
 vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_split_out) {
+    if (autotune & VV10_TUNE_PAIRSUMS) VV10_TRY(tune_pairsum(mode, fp64, st, false));
     PairLaunch cfg;
     const TileChoice tc = tiles_for(mode, fp64);
     cfg.rows_per_thread = tc.rows_per_thread;
@@ -647,15 +648,89 @@ vv10_status vv10_debug_inject(vv10_handle h, int what, int64_t value) {
 
 vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split) {
     VV10_CHECK_HANDLE(h);
-    if (what < 0 || what >= 6 || rows_per_thread < 0 || n_split < 0) return VV10_ERR_INVALID_ARG;
-    TileOverride& o = h->overrides[what];
-    o.mode = what % 3;
-    o.fp64 = what >= 3;
+    if (what < 0 || what > 8 || rows_per_thread < 0 || n_split < 0) return VV10_ERR_INVALID_ARG;
+    if (what == 8) {  // widest trial group of the tensor-core contraction
+        if (rows_per_thread != 0 && (rows_per_thread < 32 || rows_per_thread > 192)) {
+            h->set_error("the trial-group width must be 0 or in [32, 192]");
+            return VV10_ERR_INVALID_ARG;
+        }
+        h->tc_cap_manual = rows_per_thread;
+        h->batch.tc_classes.clear();  // rebuild the batch layout with the new width
+        h->batch_drop_graph();
+        return VV10_OK;
+    }
+    const bool fp64 = what >= 6 ? what == 7 : what >= 3;
+    const int max_rpt = fp64 ? 2 : 4;
+    if (rows_per_thread != 0 && rows_per_thread != 1 && rows_per_thread != 2 &&
+        rows_per_thread != max_rpt) {
+        h->set_error("rows_per_thread must be 0, 1, 2 or %d", max_rpt);
+        return VV10_ERR_INVALID_ARG;
+    }
+    TileOverride& o = what >= 6 ? h->batch_over[what - 6] : h->overrides[what];
+    o = TileOverride{};
+    o.mode = what >= 6 ? 0 : what % 3;
+    o.fp64 = what >= 6 ? what == 7 : what >= 3;
     o.active = rows_per_thread > 0;
+    o.manual = o.active;
     o.rows_per_thread = rows_per_thread;
     o.n_split = n_split;
     h->batch_drop_graph();  // a recorded batch graph holds the old tiles
     return VV10_OK;
+}
+
+vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n_split) {
+    VV10_CHECK_HANDLE(h);
+    if (what < 0 || what > 8 || !rows_per_thread || !n_split) return VV10_ERR_INVALID_ARG;
+    if (what == 8) {
+        *rows_per_thread = h->tc_cap_manual > 0 ? h->tc_cap_manual : h->tc_cap_last;
+        *n_split = 0;
+    } else if (what >= 6) {
+        h->batch_tiles(what == 7, rows_per_thread, n_split);
+    } else {
+        const TileChoice t = h->tiles_for(what % 3, what >= 3);
+        *rows_per_thread = t.rows_per_thread;
+        *n_split = t.n_split;
+    }
+    return VV10_OK;
+}
+
+vv10_status vv10_set_autotune(vv10_handle h, int flags) {
+    VV10_CHECK_HANDLE(h);
+    if (flags & ~(VV10_TUNE_PAIRSUMS | VV10_TUNE_BATCH | VV10_TUNE_CONTRACTION))
+        return VV10_ERR_INVALID_ARG;
+    h->autotune = flags;
+    return VV10_OK;
+}
+
+vv10_status vv10_autotune(vv10_handle h, vv10_precision prec, int what, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3)
+        return VV10_ERR_INVALID_ARG;
+    if (what & ~(VV10_TUNE_PAIRSUMS | VV10_TUNE_BATCH)) {
+        h->set_error("vv10_autotune tunes VV10_TUNE_PAIRSUMS and VV10_TUNE_BATCH; the contraction "
+                     "width is tuned on first use (vv10_set_autotune)");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (stream_capturing(st)) {
+        h->set_error("vv10_autotune cannot run while the stream is being captured");
+        return VV10_ERR_INVALID_ARG;
+    }
+    const bool fp64 = (prec == VV10_FP64);
+    if (what & VV10_TUNE_PAIRSUMS) {
+        VV10_TRY(h->require_prepared());
+        for (int mode = 0; mode < 3; ++mode) VV10_TRY(h->tune_pairsum(mode, fp64, st, true));
+    }
+    if (what & VV10_TUNE_BATCH) {
+        if (!h->batch.prepared) {
+            h->set_error("vv10_batch_prepare has not been called on this handle");
+            return VV10_ERR_INVALID_ARG;
+        }
+        VV10_TRY(h->tune_batch(fp64, st, true));
+    }
+    return h->check_device_errors(st);
 }
 
 }  // extern "C"

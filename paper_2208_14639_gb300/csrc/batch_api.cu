@@ -71,11 +71,21 @@ void vv10_ctx::batch_drop_graph() {
     batch.graph_P.clear();
 }
 
+// Rows per thread and j tiles per split of the batched pair sums: vv10_set_tiles, else the
+// autotuner's choice, else 2 (FP32) / 1 (FP64) rows per thread and 32 tiles (8,192 j).
+void vv10_ctx::batch_tiles(bool fp64, int* rpt, int* split_tiles) const {
+    const TileOverride& o = batch_over[fp64 ? 1 : 0];
+    *rpt = o.active && o.rows_per_thread > 0 ? o.rows_per_thread : (fp64 ? 1 : 2);
+    *split_tiles = o.active && o.n_split > 0 ? o.n_split : 32;
+}
+
 // Task table of the batched pair sums: (molecule, row tile, j-split), largest molecule first;
-// at most 8 splits per molecule, each of at least 32 tiles (8192 j).
-vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt) {
+// at most 8 splits per molecule, each of at least `split_tiles` tiles.
+vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt, int split_tiles) {
     BatchState& B = batch;
-    if (B.pair_tab_fp64 == (fp64 ? 1 : 0) && B.pair_tab_rpt == rpt) return VV10_OK;
+    if (B.pair_tab_fp64 == (fp64 ? 1 : 0) && B.pair_tab_rpt == rpt &&
+        B.pair_tab_split_tiles == split_tiles)
+        return VV10_OK;
     batch_drop_graph();  // the tables (and possibly their buffers) change under it
     const int rows = pairsum_rows_per_cta(fp64, rpt);
     std::vector<PairMol> mols(B.mol.size());
@@ -84,7 +94,8 @@ vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt) {
     for (size_t m = 0; m < B.mol.size(); ++m) {
         BatchMol& M = B.mol[m];
         const int64_t ntile = M.nk_pad / kJTile;
-        int S = static_cast<int>(std::min<int64_t>(8, std::max<int64_t>(1, (ntile + 31) / 32)));
+        int S = static_cast<int>(
+            std::min<int64_t>(8, std::max<int64_t>(1, (ntile + split_tiles - 1) / split_tiles)));
         const int64_t tps = ntile > 0 ? (ntile + S - 1) / S : 1;
         S = static_cast<int>(ntile > 0 ? (ntile + tps - 1) / tps : 1);
         M.n_split = S;
@@ -132,6 +143,7 @@ vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt) {
     B.n_pair_tasks = static_cast<int>(tasks.size());
     B.pair_tab_fp64 = fp64 ? 1 : 0;
     B.pair_tab_rpt = rpt;
+    B.pair_tab_split_tiles = split_tiles;
     return VV10_OK;
 }
 
@@ -139,8 +151,10 @@ vv10_status vv10_ctx::batch_ep(vv10_precision prec, double* energies, double* vr
                                double* vgamma, cudaStream_t st) {
     BatchState& B = batch;
     const bool fp64 = (prec == VV10_FP64);
-    const int rpt = tiles_for(MODE_EUW, fp64).rows_per_thread;
-    B_TRY(batch_pair_tables(fp64, rpt));
+    if (autotune & VV10_TUNE_BATCH) B_TRY(tune_batch(fp64, st, false));
+    int rpt, split_tiles;
+    batch_tiles(fp64, &rpt, &split_tiles);
+    B_TRY(batch_pair_tables(fp64, rpt, split_tiles));
     if (vrho) B_CUDA(cudaMemsetAsync(vrho, 0, sizeof(double) * B.n_total, st), "memset vrho");
     if (vgamma) B_CUDA(cudaMemsetAsync(vgamma, 0, sizeof(double) * B.n_total, st), "memset vgamma");
     int* err = static_cast<int*>(dev_err.p);
@@ -188,8 +202,9 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
 
     // A_i, B_i, C_i of the delta_ij / w_i terms
     if (!B.have_abc || (fp64 && !B.abc_fp64)) {
-        const int rpt = tiles_for(MODE_EUW, fp64).rows_per_thread;
-        B_TRY(batch_pair_tables(fp64, rpt));
+        int rpt, split_tiles;
+        batch_tiles(fp64, &rpt, &split_tiles);
+        B_TRY(batch_pair_tables(fp64, rpt, split_tiles));
         {
             PhaseScope ph(this, PH_PAIR_ABC, st, 1);
             B_CUDA(launch_pairsum_batch(at<PairMol>(B.pair_tab, B.pair_mols),
@@ -261,7 +276,8 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
         size_t rtgt = 0, split = 0, acc = 0, umax = 0;
         for (size_t m = 0; m < n_mol; ++m) {
             BatchMol& M = B.mol[m];
-            M.ng = (M.n_t + 191) / 192;
+            const int cap = tc_cap_for(M.n_t, M.nk);
+            M.ng = (M.n_t + cap - 1) / cap;
             M.pg = (M.n_t + M.ng - 1) / M.ng;
             M.ppad = hess_tc_ppad(M.pg);
             M.rows = static_cast<int64_t>(M.ng - 1) * M.pg + M.ppad;

@@ -78,39 +78,11 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
     }
 
     if (!fp64) {
-        // tensor-core path: trials in groups of at most 192 (the MMA N of one launch)
-        const int ng = (Pn + 191) / 192;
-        const int pg = (Pn + ng - 1) / ng;
-        const int ppad = hess_tc_ppad(pg);
-        const int64_t rows = static_cast<int64_t>(ng - 1) * pg + ppad;
-        const size_t sb = sizeof(float) * static_cast<size_t>(rows) * P.nk_pad;
-        H_TRY(ensure(tc_uh, sb, "trial u hi"));
-        H_TRY(ensure(tc_ul, sb, "trial u lo"));
-        H_TRY(ensure(tc_yh, sb, "trial y hi"));
-        H_TRY(ensure(tc_yl, sb, "trial y lo"));
-        {
-        PhaseScope ph(this, PH_TRIAL_PREP, st, 1);
-        H_CUDA(launch_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), Pn,
-                                  static_cast<int32_t>(rows), P.nk_pad, false,
-                                  static_cast<float*>(tc_uh.p), static_cast<float*>(tc_ul.p),
-                                  static_cast<float*>(tc_yh.p), static_cast<float*>(tc_yl.p), st),
-               "trial split");
-        }
-        const size_t ab = sizeof(double) * 2 * static_cast<size_t>(Pn) * P.nk_pad;
-        H_TRY(ensure(hacc, ab, "contraction partials"));
-        H_CUDA(cudaMemsetAsync(hacc.p, 0, ab, st), "zero contraction partials");
-        {
-        PhaseScope ph(this, PH_CONTRACT_TC, st, ng);
-        for (int g = 0; g < ng; ++g) {
-            const int t0 = g * pg;
-            const int pn = (Pn - t0 < pg) ? Pn - t0 : pg;
-            H_CUDA(launch_hess_tc(P, pn, t0, Pn, static_cast<float*>(tc_uh.p),
-                                  static_cast<float*>(tc_ul.p), static_cast<float*>(tc_yh.p),
-                                  static_cast<float*>(tc_yl.p), rows, n_sm, tc_flush,
-                                  static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
-                   "tensor-core contraction");
-        }
-        }
+        // tensor-core path: trials in groups of at most `cap` (<= 192, the MMA N of one launch)
+        int cap = tc_cap_for(Pn, P.nk);
+        if (autotune & VV10_TUNE_CONTRACTION) H_TRY(tune_tc_cap(Pn, st, &cap));
+        H_TRY(tc_contract(Pn, cap, st));
+        tc_cap_last = cap;
         PhaseScope ph2(this, PH_HESS_EPILOGUE, st, 1);
         H_CUDA(launch_hess_epilogue(P, Pn, static_cast<double*>(hacc.p), 1, P.nk_pad,
                                     static_cast<double*>(sumU.p), static_cast<double*>(sumW.p),
@@ -141,5 +113,41 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
                                 static_cast<double*>(tgt.p), f_rho_t, f_gamma_t,
                                 static_cast<int*>(dev_err.p), st),
            "Hessian epilogue");
+    return VV10_OK;
+}
+
+// Split u, y (already in tu, ty) and contract all Pn trials on the tensor cores in groups of
+// at most `cap` trials into hacc [2][Pn][nk_pad].
+vv10_status vv10_ctx::tc_contract(int32_t Pn, int cap, cudaStream_t st) {
+    const int ng = (Pn + cap - 1) / cap;
+    const int pg = (Pn + ng - 1) / ng;
+    const int ppad = hess_tc_ppad(pg);
+    const int64_t rows = static_cast<int64_t>(ng - 1) * pg + ppad;
+    const size_t sb = sizeof(float) * static_cast<size_t>(rows) * P.nk_pad;
+    H_TRY(ensure(tc_uh, sb, "trial u hi"));
+    H_TRY(ensure(tc_ul, sb, "trial u lo"));
+    H_TRY(ensure(tc_yh, sb, "trial y hi"));
+    H_TRY(ensure(tc_yl, sb, "trial y lo"));
+    {
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 1);
+        H_CUDA(launch_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), Pn,
+                                  static_cast<int32_t>(rows), P.nk_pad, false,
+                                  static_cast<float*>(tc_uh.p), static_cast<float*>(tc_ul.p),
+                                  static_cast<float*>(tc_yh.p), static_cast<float*>(tc_yl.p), st),
+               "trial split");
+    }
+    const size_t ab = sizeof(double) * 2 * static_cast<size_t>(Pn) * P.nk_pad;
+    H_TRY(ensure(hacc, ab, "contraction partials"));
+    H_CUDA(cudaMemsetAsync(hacc.p, 0, ab, st), "zero contraction partials");
+    PhaseScope ph(this, PH_CONTRACT_TC, st, ng);
+    for (int g = 0; g < ng; ++g) {
+        const int t0 = g * pg;
+        const int pn = (Pn - t0 < pg) ? Pn - t0 : pg;
+        H_CUDA(launch_hess_tc(P, pn, t0, Pn, static_cast<float*>(tc_uh.p),
+                              static_cast<float*>(tc_ul.p), static_cast<float*>(tc_yh.p),
+                              static_cast<float*>(tc_yl.p), rows, n_sm, tc_flush,
+                              static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
+               "tensor-core contraction");
+    }
     return VV10_OK;
 }

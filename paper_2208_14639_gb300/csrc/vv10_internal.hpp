@@ -24,11 +24,22 @@ struct TileChoice {
 
 struct TileOverride {
     bool active = false;
+    bool manual = false;  // set by vv10_set_tiles (the autotuner never replaces it)
     int mode = 0;
     bool fp64 = false;
     int rows_per_thread = 0;
-    int n_split = 0;
+    int n_split = 0;      // single system: j-splits (0 = from the SM count); batch: j tiles per split
+    int bucket = -1;      // tuned entries: the N bucket they were chosen for
 };
+
+// Process-wide cache of tuned choices (autotune.cu).
+enum TuneKind : int { TUNE_PAIRSUM = 0, TUNE_BATCH = 1, TUNE_TC_CAP = 2 };
+int n_bucket(int64_t n);
+bool tune_cache_get(int kind, int mode, int fp64, int nbucket, int pbucket, int n_sm, int* v0,
+                    int* v1);
+void tune_cache_put(int kind, int mode, int fp64, int nbucket, int pbucket, int n_sm, int v0,
+                    int v1);
+bool stream_capturing(cudaStream_t st);
 
 enum Phase : int {
     PH_PREPARE = 0, PH_PAIR_EUW, PH_EP_EPILOGUE, PH_PAIR_ABC, PH_TRIAL_PREP, PH_CONTRACT_F64,
@@ -75,7 +86,7 @@ struct BatchState {
     DevBuf scratch, small, arena, sums, part, eblk, pair_tab, counter;
     void* h_small = nullptr;
     size_t h_small_bytes = 0;
-    int pair_tab_fp64 = -1, pair_tab_rpt = 0, n_pair_tasks = 0;
+    int pair_tab_fp64 = -1, pair_tab_rpt = 0, pair_tab_split_tiles = 0, n_pair_tasks = 0;
     size_t pair_mols = 0, pair_tasks = 0;
     // Hessian layout (valid for hess_P)
     std::vector<int32_t> hess_P;
@@ -127,6 +138,10 @@ struct vv10_ctx {
 
     // tile overrides (index = mode + 3 * fp64), set by vv10_set_tiles / the autotuner
     vv10::TileOverride overrides[6];
+    vv10::TileOverride batch_over[2];  // batched pair sums (index = fp64)
+    int tc_cap_manual = 0;             // widest trial group of the contraction (0 = automatic)
+    int tc_cap_last = 0;               // the width used by the last mixed Hessian call
+    int autotune = 0;                  // VV10_TUNE_* flags: tune on first use
 
     // stages between FP64 flushes of the tensor-core contraction's register accumulators
     int tc_flush = 512;
@@ -142,7 +157,8 @@ struct vv10_ctx {
 
     // batched molecules (vv10_batch_*)
     vv10::BatchState batch;
-    vv10_status batch_pair_tables(bool fp64, int rpt);
+    vv10_status batch_pair_tables(bool fp64, int rpt, int split_tiles);
+    void batch_tiles(bool fp64, int* rpt, int* split_tiles) const;
     vv10_status batch_ep(vv10_precision prec, double* energies, double* vrho, double* vgamma,
                          cudaStream_t st);
     vv10_status batch_hess(vv10_precision prec, const int32_t* P, const double* rho_t,
@@ -165,6 +181,12 @@ struct vv10_ctx {
     vv10::PointsDev points() const;
     vv10::TileChoice tiles_for(int mode, bool fp64) const;
     vv10_status run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_split_out);
+    // autotuner (autotune.cu)
+    vv10_status tune_pairsum(int mode, bool fp64, cudaStream_t st, bool force);
+    vv10_status tune_batch(bool fp64, cudaStream_t st, bool force);
+    int tc_cap_for(int32_t P, int64_t nk) const;
+    vv10_status tc_contract(int32_t P, int cap, cudaStream_t st);
+    vv10_status tune_tc_cap(int32_t P, cudaStream_t st, int* cap);
     vv10_status hessian(vv10_precision prec, int32_t P, const double* rho_t,
                         const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
                         cudaStream_t st);

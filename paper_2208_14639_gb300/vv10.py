@@ -29,6 +29,12 @@ VV10_MIXED_BF16X3 = 2
 PRECISIONS = {"fp64": VV10_FP64, "tf32x3": VV10_MIXED_TF32X3, "bf16x3": VV10_MIXED_BF16X3,
               "mixed": VV10_MIXED_TF32X3}
 
+VV10_TUNE_PAIRSUMS = 1
+VV10_TUNE_BATCH = 2
+VV10_TUNE_CONTRACTION = 4
+TILES_BATCH = 6        # vv10_set_tiles / vv10_get_tiles: 6 + fp64 = batched pair sums
+TILES_CONTRACTION = 8  # the widest trial group of the tensor-core contraction
+
 VV10_DEBUG_FAIL_ALLOC = 1
 VV10_DEBUG_STALL_COPY = 2
 
@@ -39,7 +45,7 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_debug_inject", "vv10_profile_enable", "vv10_profile_read",
            "vv10_profile_phase_name", "vv10_energy_potential_noalloc",
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
-           "vv10_batch_run")
+           "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_N_PHASES = 11
 
@@ -97,6 +103,10 @@ def load(build_if_missing: bool = False):
         "vv10_batch_energy_potential": (st, [P, st, P, P, P, P]),
         "vv10_batch_hessian_contract": (st, [P, st, P, P, P, P, P, P]),
         "vv10_batch_run": (st, [P, st, P, P, P, P, P, P, P, P, P]),
+        "vv10_get_tiles": (st, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]),
+        "vv10_autotune": (st, [P, st, ctypes.c_int, P]),
+        "vv10_set_autotune": (st, [P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -210,6 +220,22 @@ def vv10_sync(h, stream=None) -> None:
 def vv10_set_tiles(h, what: int, rows_per_thread: int, n_split: int) -> None:
     _check(h, load().vv10_set_tiles(h, int(what), int(rows_per_thread), int(n_split)),
            "vv10_set_tiles")
+
+
+def vv10_get_tiles(h, what: int) -> tuple:
+    """(rows_per_thread, n_split) in effect for `what` (see vv10_set_tiles)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(h, load().vv10_get_tiles(h, int(what), ctypes.byref(a), ctypes.byref(b)),
+           "vv10_get_tiles")
+    return int(a.value), int(b.value)
+
+
+def vv10_autotune(h, prec: int, what: int, stream=None) -> None:
+    _check(h, load().vv10_autotune(h, int(prec), int(what), _stream(stream)), "vv10_autotune")
+
+
+def vv10_set_autotune(h, flags: int) -> None:
+    _check(h, load().vv10_set_autotune(h, int(flags)), "vv10_set_autotune")
 
 
 def vv10_profile_enable(h, on: bool) -> None:
