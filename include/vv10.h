@@ -130,7 +130,8 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
  *   f_rho_t      P x n device out
  *   f_gamma_t    P x n device out
  * vv10_energy_potential must have been called on the current point set first (it
- * provides U_i, W_i); otherwise INVALID_ARG.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
+ * provides U_i, W_i; an FP64 contraction after a mixed-precision energy call forms them
+ * again in FP64); otherwise INVALID_ARG.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
  * CUDA, TIMEOUT. */
 vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P,
                                   const double* rho_t, const double* grad_rho_t,
@@ -254,6 +255,16 @@ vv10_status vv10_sync(vv10_handle h, void* stream);
  * last mixed vv10_hessian_contract used; 0 before any).  Errors: INVALID_ARG. */
 vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split);
 vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n_split);
+
+/* Handle options (the paper has no counterpart).
+ *   VV10_OPT_FUSE_HESSIAN_SUMS  vv10_energy_potential (and vv10_batch_energy_potential) also
+ *       form the A_i, B_i, C_i sums of the Hessian diagonal (Sec. II.B) in the same pass over
+ *       the pairs, so that a following vv10_hessian_contract (vv10_batch_hessian_contract)
+ *       needs no pass of its own.  Worth it when the Hessian follows; costs about half a pass
+ *       extra when it does not.  vv10_batch_run always does this.
+ * Errors: INVALID_ARG (unknown flag). */
+#define VV10_OPT_FUSE_HESSIAN_SUMS 1
+vv10_status vv10_set_options(vv10_handle h, int flags);
 
 /* Autotuner (the paper has no counterpart).  Times every candidate shape of a kernel (see
  * vv10_set_tiles) on the handle's prepared data, on `stream`, and applies the fastest:

@@ -400,6 +400,7 @@ vv10_status vv10_ctx::require_prepared() {
 
 vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_split_out) {
     if (autotune & VV10_TUNE_PAIRSUMS) VV10_TRY(tune_pairsum(mode, fp64, st, false));
+    const int nq = pair_mode_nq(mode);
     PairLaunch cfg;
     const TileChoice tc = tiles_for(mode, fp64);
     cfg.rows_per_thread = tc.rows_per_thread;
@@ -415,10 +416,11 @@ vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_s
     const int64_t tps = ntile > 0 ? (ntile + req - 1) / req : 1;
     const int ns = static_cast<int>(ntile > 0 ? (ntile + tps - 1) / tps : 1);
     cfg.n_split = req;
-    VV10_TRY(ensure(part, sizeof(double) * 3 * static_cast<size_t>(ns) * (P.nk_pad > 0 ? P.nk_pad : 1),
+    VV10_TRY(ensure(part, sizeof(double) * nq * static_cast<size_t>(ns) * (P.nk_pad > 0 ? P.nk_pad : 1),
                     "pair-sum partials"));
     {
-        PhaseScope ph(this, mode == MODE_EUW ? PH_PAIR_EUW : (mode == MODE_ABC ? PH_PAIR_ABC : PH_PAIR_GRAD),
+        PhaseScope ph(this, (mode == MODE_EUW || mode == MODE_EUWABC) ? PH_PAIR_EUW
+                            : (mode == MODE_ABC ? PH_PAIR_ABC : PH_PAIR_GRAD),
                       st, 1);
         VV10_CUDA(this, launch_pairsum(P, mode, fp64, cfg, static_cast<double*>(part.p),
                                        static_cast<int*>(dev_err.p), st),
@@ -428,15 +430,19 @@ vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_s
     return VV10_OK;
 }
 
+// Tiles of a pair-sum mode: its own override (fixed or tuned), else (fused mode) the
+// energy sums' override, else 2 (FP32) / 1 (FP64) rows per thread and SM-derived splits.
 TileChoice vv10_ctx::tiles_for(int mode, bool fp64) const {
     TileChoice t;
     t.rows_per_thread = fp64 ? 1 : 2;
     t.n_split = 0;
-    for (const TileOverride& o : overrides)
-        if (o.active && o.mode == mode && o.fp64 == fp64) {
-            t.rows_per_thread = o.rows_per_thread;
-            t.n_split = o.n_split;
-        }
+    const TileOverride& o = overrides[mode + 4 * (fp64 ? 1 : 0)];
+    const TileOverride& e = overrides[MODE_EUW + 4 * (fp64 ? 1 : 0)];
+    const TileOverride* use = o.active ? &o : ((mode == MODE_EUWABC && e.active) ? &e : nullptr);
+    if (use) {
+        t.rows_per_thread = use->rows_per_thread;
+        t.n_split = use->n_split;
+    }
     return t;
 }
 
@@ -470,9 +476,23 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
     if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
     if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
     double* escal = static_cast<double*>(h->scal.p);
+    const bool fuse = (h->options & VV10_OPT_FUSE_HESSIAN_SUMS) != 0;
+    if (fuse) {
+        VV10_TRY(h->ensure(h->sumA, nkb, "A_i"));
+        VV10_TRY(h->ensure(h->sumB, nkb, "B_i"));
+        VV10_TRY(h->ensure(h->sumC, nkb, "C_i"));
+    }
     if (P.nk > 0) {
         int ns = 1;
-        VV10_TRY(h->run_pairsum(MODE_EUW, fp64, st, &ns));
+        VV10_TRY(h->run_pairsum(fuse ? MODE_EUWABC : MODE_EUW, fp64, st, &ns));
+        if (fuse) {  // A_i, B_i, C_i are the partial buffer's quantities 3..5
+            PhaseScope ph(h, PH_PAIR_ABC, st, 1);
+            VV10_CUDA(h, launch_abc_epilogue(P, static_cast<double*>(h->part.p) + 3 * static_cast<size_t>(ns) * P.nk_pad,
+                                             ns, static_cast<double*>(h->sumA.p),
+                                             static_cast<double*>(h->sumB.p),
+                                             static_cast<double*>(h->sumC.p), st),
+                      "A/B/C epilogue");
+        }
         PhaseScope ph(h, PH_EP_EPILOGUE, st, 2);
         VV10_CUDA(h, launch_ep_epilogue(P, static_cast<double*>(h->part.p), ns,
                                         static_cast<double*>(h->sumE.p),
@@ -487,7 +507,8 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
         VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
     }
     h->have_euw = true;
-    h->have_abc = false;
+    h->have_abc = fuse && P.nk > 0;
+    h->abc_fp64 = fp64;
     h->euw_fp64 = fp64;
     if (energy) {
         double* he = reinterpret_cast<double*>(h->h_pinned) + 2;
@@ -576,6 +597,24 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
     if (EUW_Bgr)
         VV10_CUDA(h, cudaMemsetAsync(EUW_Bgr, 0, sizeof(double) * 9 * P.n * P.n_atom, st), "memset");
     if (P.nk == 0) return VV10_OK;
+    if (EUW_Bgr) {
+        // one pass gives the atom-resolved terms and, summed over atoms, the point gradient
+        const bool want_grad = grad_points || grad_atoms;
+        if (want_grad) VV10_TRY(h->ensure(h->gk, sizeof(double) * 3 * h->soa_ld, "kept gradient"));
+        {
+            PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
+            VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr,
+                                              want_grad ? static_cast<double*>(h->gk.p) : nullptr,
+                                              grad_points, static_cast<int*>(h->dev_err.p), st),
+                      "atom-resolved terms");
+        }
+        if (grad_atoms) {
+            PhaseScope ph(h, PH_GRAD_EPILOGUE, st, 1);
+            VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
+                      "atom sums");
+        }
+        return VV10_OK;
+    }
     if (grad_points || grad_atoms) {
         int ns = 1;
         VV10_TRY(h->run_pairsum(MODE_GRAD, fp64, st, &ns));
@@ -587,11 +626,6 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
         if (grad_atoms)
             VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
                       "atom sums");
-    }
-    if (EUW_Bgr) {
-        PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
-        VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr, static_cast<int*>(h->dev_err.p), st),
-                  "atom-resolved terms");
     }
     return VV10_OK;
 }
@@ -666,7 +700,7 @@ vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_s
         h->set_error("rows_per_thread must be 0, 1, 2 or %d", max_rpt);
         return VV10_ERR_INVALID_ARG;
     }
-    TileOverride& o = what >= 6 ? h->batch_over[what - 6] : h->overrides[what];
+    TileOverride& o = what >= 6 ? h->batch_over[what - 6] : h->overrides[what % 3 + 4 * (what >= 3)];
     o = TileOverride{};
     o.mode = what >= 6 ? 0 : what % 3;
     o.fp64 = what >= 6 ? what == 7 : what >= 3;
@@ -691,6 +725,13 @@ vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n
         *rows_per_thread = t.rows_per_thread;
         *n_split = t.n_split;
     }
+    return VV10_OK;
+}
+
+vv10_status vv10_set_options(vv10_handle h, int flags) {
+    VV10_CHECK_HANDLE(h);
+    if (flags & ~VV10_OPT_FUSE_HESSIAN_SUMS) return VV10_ERR_INVALID_ARG;
+    h->options = flags;
     return VV10_OK;
 }
 
@@ -722,6 +763,8 @@ vv10_status vv10_autotune(vv10_handle h, vv10_precision prec, int what, void* st
     if (what & VV10_TUNE_PAIRSUMS) {
         VV10_TRY(h->require_prepared());
         for (int mode = 0; mode < 3; ++mode) VV10_TRY(h->tune_pairsum(mode, fp64, st, true));
+        if (h->options & VV10_OPT_FUSE_HESSIAN_SUMS)
+            VV10_TRY(h->tune_pairsum(MODE_EUWABC, fp64, st, true));
     }
     if (what & VV10_TUNE_BATCH) {
         if (!h->batch.prepared) {

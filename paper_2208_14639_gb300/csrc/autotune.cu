@@ -118,7 +118,7 @@ bool stream_capturing(cudaStream_t st) {
 
 // Single-system pair sums of one mode: rows per thread x j-splits.
 vv10_status vv10_ctx::tune_pairsum(int mode, bool fp64, cudaStream_t st, bool force) {
-    TileOverride& o = overrides[mode + 3 * (fp64 ? 1 : 0)];
+    TileOverride& o = overrides[mode + 4 * (fp64 ? 1 : 0)];
     if (o.manual || P.nk == 0) return VV10_OK;
     const int nb = n_bucket(P.nk);
     if (!force && o.active && o.bucket == nb) return VV10_OK;
@@ -158,7 +158,8 @@ vv10_status vv10_ctx::tune_pairsum(int mode, bool fp64, cudaStream_t st, bool fo
     return VV10_OK;
 }
 
-// Batched pair sums: rows per thread x j tiles per split, timed on the energy sums.
+// Batched pair sums: rows per thread x j tiles per split, timed on the fused energy and
+// A/B/C sums (the pass vv10_batch_run makes).
 vv10_status vv10_ctx::tune_batch(bool fp64, cudaStream_t st, bool force) {
     BatchState& B = batch;
     TileOverride& o = batch_over[fp64 ? 1 : 0];
@@ -191,7 +192,7 @@ vv10_status vv10_ctx::tune_batch(bool fp64, cudaStream_t st, bool force) {
                 cudaError_t e = launch_pairsum_batch(
                     reinterpret_cast<PairMol*>(static_cast<char*>(B.pair_tab.p) + B.pair_mols),
                     reinterpret_cast<PairTask*>(static_cast<char*>(B.pair_tab.p) + B.pair_tasks),
-                    B.n_pair_tasks, static_cast<int*>(B.counter.p), MODE_EUW, fp64, r, n_sm, err, st);
+                    B.n_pair_tasks, static_cast<int*>(B.counter.p), MODE_EUWABC, fp64, r, n_sm, err, st);
                 return e == cudaSuccess ? VV10_OK : cuda_fail(e, "batched pair sums");
             }, &ms);
             if (s != VV10_OK) return s;

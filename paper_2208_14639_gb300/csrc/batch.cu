@@ -41,7 +41,7 @@ k_pairsum_batch(const PairMol* __restrict__ mols, const PairTask* __restrict__ t
         const int64_t i0 = static_cast<int64_t>(tk.row_tile) * (NT * RPT);
         const int64_t jb = static_cast<int64_t>(tk.split) * m.j_per_split;
         const int64_t je = min(m.nk_pad, jb + m.j_per_split);
-        double dacc[RPT][3];
+        double dacc[RPT][pair_mode_nq(MODE)];
         const bool ok = pairsum_range<T, MODE, RPT, NT>(sa, sb, bar, gtile, ra, rb, m.nk, i0, jb, je,
                                                         dacc, err, false);
 #pragma unroll
@@ -49,7 +49,7 @@ k_pairsum_batch(const PairMol* __restrict__ mols, const PairTask* __restrict__ t
             const int64_t i = i0 + r * NT + tid;
             if (i < m.nk) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < pair_mode_nq(MODE); ++c)
                     m.part[(static_cast<int64_t>(c) * m.n_split + tk.split) * m.nk_pad + i] = dacc[r][c];
             }
         }
@@ -94,6 +94,7 @@ cudaError_t launch_pairsum_batch(const PairMol* mols, const PairTask* tasks, int
     switch (mode) {
         case MODE_EUW: return launch_batch_mode<MODE_EUW>(mols, tasks, n_tasks, counter, fp64, rows_per_thread, n_sm, err, st);
         case MODE_ABC: return launch_batch_mode<MODE_ABC>(mols, tasks, n_tasks, counter, fp64, rows_per_thread, n_sm, err, st);
+        case MODE_EUWABC: return launch_batch_mode<MODE_EUWABC>(mols, tasks, n_tasks, counter, fp64, rows_per_thread, n_sm, err, st);
         default: return launch_batch_mode<MODE_GRAD>(mols, tasks, n_tasks, counter, fp64, rows_per_thread, n_sm, err, st);
     }
 }

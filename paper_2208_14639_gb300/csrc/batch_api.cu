@@ -101,7 +101,7 @@ vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt, int split_tiles) {
         M.n_split = S;
         M.j_per_split = tps * kJTile;
         M.part = part_bytes;
-        part_bytes += a256(sizeof(double) * 3 * S * (M.cap));
+        part_bytes += a256(sizeof(double) * pair_mode_nq(MODE_EUWABC) * S * (M.cap));
         M.nblk = ep_epilogue_blocks(M.nk);
         M.eblk = eblk_bytes;
         eblk_bytes += a256(sizeof(double) * M.nblk);
@@ -148,7 +148,7 @@ vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt, int split_tiles) {
 }
 
 vv10_status vv10_ctx::batch_ep(vv10_precision prec, double* energies, double* vrho,
-                               double* vgamma, cudaStream_t st) {
+                               double* vgamma, bool with_abc, cudaStream_t st) {
     BatchState& B = batch;
     const bool fp64 = (prec == VV10_FP64);
     if (autotune & VV10_TUNE_BATCH) B_TRY(tune_batch(fp64, st, false));
@@ -162,8 +162,19 @@ vv10_status vv10_ctx::batch_ep(vv10_precision prec, double* energies, double* vr
         PhaseScope ph(this, PH_PAIR_EUW, st, 1);
         B_CUDA(launch_pairsum_batch(at<PairMol>(B.pair_tab, B.pair_mols),
                                     at<PairTask>(B.pair_tab, B.pair_tasks), B.n_pair_tasks,
-                                    static_cast<int*>(B.counter.p), MODE_EUW, fp64, rpt, n_sm, err, st),
+                                    static_cast<int*>(B.counter.p), with_abc ? MODE_EUWABC : MODE_EUW,
+                                    fp64, rpt, n_sm, err, st),
                "batched pair sums");
+    }
+    if (with_abc) {  // A_i, B_i, C_i: quantities 3..5 of each molecule's partial buffer
+        PhaseScope ph(this, PH_PAIR_ABC, st, static_cast<int>(B.mol.size()));
+        for (size_t m = 0; m < B.mol.size(); ++m) {
+            BatchMol& M = B.mol[m];
+            double* s = at<double>(B.sums, M.sums);
+            B_CUDA(launch_abc_epilogue(M.P, at<double>(B.part, M.part) + 3 * static_cast<size_t>(M.n_split) * M.nk_pad,
+                                       M.n_split, s + 3 * M.cap, s + 4 * M.cap, s + 5 * M.cap, st),
+                   "batched A/B/C epilogue");
+        }
     }
     PhaseScope ph(this, PH_EP_EPILOGUE, st, 2 * static_cast<int>(B.mol.size()));
     for (size_t m = 0; m < B.mol.size(); ++m) {
@@ -177,7 +188,8 @@ vv10_status vv10_ctx::batch_ep(vv10_precision prec, double* energies, double* vr
                "batched energy sum");
     }
     B.have_euw = true;
-    B.have_abc = false;
+    B.have_abc = with_abc;
+    B.abc_fp64 = fp64;
     return VV10_OK;
 }
 
@@ -617,7 +629,8 @@ vv10_status vv10_batch_energy_potential(vv10_handle h, vv10_precision prec, doub
         h->set_error("energies / vrho / vgamma must be device pointers");
         return VV10_ERR_INVALID_ARG;
     }
-    return h->batch_ep(prec, energies, vrho, vgamma, static_cast<cudaStream_t>(stream));
+    return h->batch_ep(prec, energies, vrho, vgamma, (h->options & VV10_OPT_FUSE_HESSIAN_SUMS) != 0,
+                       static_cast<cudaStream_t>(stream));
 }
 
 vv10_status vv10_batch_hessian_contract(vv10_handle h, vv10_precision prec, const int32_t* P,
@@ -675,7 +688,14 @@ vv10_status vv10_batch_run(vv10_handle h, vv10_precision prec, const int32_t* P,
     }
     h->batch_drop_graph();
     // first call for this configuration: run eagerly (allocates, builds the tables) ...
-    s = vv10_batch_energy_potential(h, prec, energies, vrho, vgamma, stream);
+    if (!dev_ok(energies, h->device) || (vrho && !dev_ok(vrho, h->device)) ||
+        (vgamma && !dev_ok(vgamma, h->device))) {
+        h->set_error("energies / vrho / vgamma must be device pointers");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3)
+        return VV10_ERR_INVALID_ARG;
+    s = h->batch_ep(prec, energies, vrho, vgamma, true, st);  // A/B/C in the same pass
     if (s != VV10_OK) return s;
     s = vv10_batch_hessian_contract(h, prec, P, rho_t, grad_rho_t, f_rho_t, f_gamma_t, stream);
     if (s != VV10_OK) return s;
@@ -690,7 +710,7 @@ vv10_status vv10_batch_run(vv10_handle h, vv10_precision prec, const int32_t* P,
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     cudaGraph_t g = nullptr;
     if (e == cudaSuccess) {
-        s = h->batch_ep(prec, energies, vrho, vgamma, cs);
+        s = h->batch_ep(prec, energies, vrho, vgamma, true, cs);
         if (s == VV10_OK) s = h->batch_hess(prec, P, rho_t, grad_rho_t, f_rho_t, f_gamma_t, cs);
         e = cudaStreamEndCapture(cs, &g);
         if (s == VV10_OK && e == cudaSuccess) e = cudaGraphInstantiate(&B.graph, g, 0);

@@ -10,6 +10,8 @@
 //   W_i^{Bgr} =  2 sum w_j rho_j Phi [R^2 D (1/s + 1/g) + R^2 (omega_i/g^2 + (omega_i+omega_j)/s^2)
 //                                     - (1/s + 1/g)] (r_j - r_i)
 // and for B = atom(i) minus the sum over the other atoms (translational invariance).
+// The E part summed over every atom B (own atom included) is the point-gradient sum G_i,
+// so the same pass also writes dE/dr_i = -2 w_i rho_i G_i when asked to.
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -71,7 +73,8 @@ constexpr int kArJT = 128;
 template <class T>
 __global__ void __launch_bounds__(kArThreads)
 k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
-                const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ out) {
+                const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ out,
+                double* __restrict__ gk, double* __restrict__ grad_points) {
     using RA = typename RecsAR<T>::A;
     using RB = typename RecsAR<T>::B;
     __shared__ RA sa[kArJT];
@@ -92,6 +95,7 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
     double rest[9];  // running sum over atoms B != atom(i)
 #pragma unroll
     for (int q = 0; q < 9; ++q) rest[q] = 0.0;
+    double gsum[3] = {0.0, 0.0, 0.0};  // E part over every atom: the point-gradient sum
 
     for (int B = 0; B < P.n_atom; ++B) {
         const int64_t s0 = P.seg[B], s1 = P.seg[B + 1];
@@ -135,6 +139,9 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
 #pragma unroll
             for (int q = 0; q < 9; ++q) tot[q] += static_cast<double>(acc[q]);
         }
+        gsum[0] += tot[0];
+        gsum[1] += tot[1];
+        gsum[2] += tot[2];
         // (r_i - r_j) was accumulated: E = +2 acc, U = -2 acc, W = -2 acc
         if (valid && B != ai) {
 #pragma unroll
@@ -150,15 +157,23 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
         for (int q = 0; q < 9; ++q)
             out[((static_cast<int64_t>(q / 3) * n + oi_idx) * na + ai) * 3 + (q % 3)] = -rest[q];
     }
+    if (valid && gk) {
+        const double c = -2.0 * P.w[i] * P.rho[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            gk[3 * i + d] = c * gsum[d];
+            if (grad_points) grad_points[3 * oi_idx + d] = c * gsum[d];
+        }
+    }
 }
 
-cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, int* err,
-                                 cudaStream_t st) {
+cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, double* gk,
+                                 double* grad_points, int* err, cudaStream_t st) {
     (void)err;
     if (p.nk == 0 || p.n_atom <= 0) return cudaSuccess;
     const unsigned g = static_cast<unsigned>(cdiv64(p.nk, kArThreads));
-    if (fp64) k_atom_resolved<double><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out);
-    else k_atom_resolved<float><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out);
+    if (fp64) k_atom_resolved<double><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out, gk, grad_points);
+    else k_atom_resolved<float><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out, gk, grad_points);
     return cudaGetLastError();
 }
 

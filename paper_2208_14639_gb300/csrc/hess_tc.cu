@@ -10,13 +10,17 @@
 //     operand tiles into tensor memory (tcgen05.st);
 //   * the producer warp fetches the stage's j-records (1-D bulk copy) and the four
 //     16 x P trial tiles u_hi, u_lo, y_hi, y_lo (2-D TMA, 64-byte swizzle) into a ring;
-//   * one thread issues 12 MMAs (2 k-steps x 6 products) into a TMEM accumulator
-//     (double-buffered), the first of each stage overwriting it;
+//   * one thread issues 12 MMAs per output kind (2 k-steps x 6 products) into a TMEM
+//     accumulator (double-buffered), the first of each stage overwriting it, and commits
+//     the stage once;
 //   * the generator warps drain the finished stage's accumulator into FP32 registers
-//     (round-to-nearest adds) and every `flush` stages add those into the FP64 partial
-//     output in global memory (each tile's rows are owned by one CTA: no atomics).
+//     (round-to-nearest adds), release the stage's ring slot, and every `flush` stages
+//     add the registers into the FP64 partial output in global memory (each tile's rows
+//     are owned by one CTA: no atomics).
 // The tensor core accumulates with truncation, so each TMEM accumulation run is kept to
-// one stage (12 adds); the register and FP64 levels bound the rest of the rounding.
+// one stage, with the hi*lo and lo*hi products first and the four hi*hi products last
+// (bits are lost at the scale of the stage sum only in those four adds); the register and
+// FP64 levels bound the rest of the rounding.
 #include <cstring>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -216,7 +220,7 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
     if (threadIdx.x == 0) {
         for (int b = 0; b < kTcRing; ++b) {
             mbar_init(&b_full[b], 1);
-            mbar_init(&b_empty[b], 1 + kTcGenWarps);
+            mbar_init(&b_empty[b], kTcGenWarps);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&a_full[b], kTcGenWarps);
@@ -305,26 +309,33 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     for (int k = 0; k < NK; ++k) {
                         const uint32_t d = tmem + d_col<NK>(NK == 2 ? k : kind0, ab);
                         const uint32_t at = a + 64u * k;  // this kind's 4 operand tiles
+                        // K-step kk: 8 tf32 along K inside the 64-B rows of the trial tiles
+                        const uint64_t duh0 = tc::sdesc_kmajor_sw64(base + 0 * L.tile_bytes);
+                        const uint64_t dul0 = tc::sdesc_kmajor_sw64(base + 1 * L.tile_bytes);
+                        const uint64_t dyh0 = tc::sdesc_kmajor_sw64(base + 2 * L.tile_bytes);
+                        const uint64_t dyl0 = tc::sdesc_kmajor_sw64(base + 3 * L.tile_bytes);
+                        constexpr uint64_t kStep = 32u >> 4;  // +32 B in the descriptor's address field
+                        // The small products (hi*lo, lo*hi) go first, while the accumulator is
+                        // still small, and the four hi*hi products last: the truncating
+                        // accumulation then loses bits at the scale of the stage sum only four
+                        // times per stage.
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
-                            const uint32_t ko = 32u * kk;  // 8 tf32 along K inside the 64-B row
-                            const uint64_t duh = tc::sdesc_kmajor_sw64(base + 0 * L.tile_bytes + ko);
-                            const uint64_t dul = tc::sdesc_kmajor_sw64(base + 1 * L.tile_bytes + ko);
-                            const uint64_t dyh = tc::sdesc_kmajor_sw64(base + 2 * L.tile_bytes + ko);
-                            const uint64_t dyl = tc::sdesc_kmajor_sw64(base + 3 * L.tile_bytes + ko);
                             const uint32_t ah = at + 0 + 8 * kk, al = at + 16 + 8 * kk;
                             const uint32_t bh = at + 32 + 8 * kk, bl = at + 48 + 8 * kk;
-                            tc::mma_tf32_ts(d, ah, duh, idesc, kk);  // the stage's first MMA overwrites
-                            tc::mma_tf32_ts(d, ah, dul, idesc, 1);
-                            tc::mma_tf32_ts(d, al, duh, idesc, 1);
-                            tc::mma_tf32_ts(d, bh, dyh, idesc, 1);
-                            tc::mma_tf32_ts(d, bh, dyl, idesc, 1);
-                            tc::mma_tf32_ts(d, bl, dyh, idesc, 1);
+                            tc::mma_tf32_ts(d, ah, dul0 + kStep * kk, idesc, kk);  // the first overwrites
+                            tc::mma_tf32_ts(d, al, duh0 + kStep * kk, idesc, 1);
+                            tc::mma_tf32_ts(d, bh, dyl0 + kStep * kk, idesc, 1);
+                            tc::mma_tf32_ts(d, bl, dyh0 + kStep * kk, idesc, 1);
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            tc::mma_tf32_ts(d, at + 0 + 8 * kk, duh0 + kStep * kk, idesc, 1);
+                            tc::mma_tf32_ts(d, at + 32 + 8 * kk, dyh0 + kStep * kk, idesc, 1);
                         }
                     }
                     issued_any = true;
-                    tc::commit(&mma_done[ab]);
-                    tc::commit(&b_empty[slot]);
+                    tc::commit(&mma_done[ab]);  // the ring slot is released by the generators
                     if (++slot == kTcRing) {
                         slot = 0;
                         ph ^= 1u;
@@ -349,31 +360,39 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
             for (int c = 0; c < PQ; ++c) acc[k][c] = 0.0f;
         bool ok = true;
 
-        // issue the TMEM loads of a finished accumulator (all kinds of this tile)
-        auto drain_issue = [&](int db, uint32_t dphase, int kind0, uint32_t (&r)[NK][PQ]) -> bool {
+        // Drain a finished accumulator (all kinds of this tile) into the FP32 registers, in
+        // chunks of at most 32 columns so that the staging registers stay few.
+        auto drain = [&](int db, uint32_t dphase, int kind0) -> bool {
             const bool got = wait_or_abort(&mma_done[db], dphase, args.err, abort_flag);
             if (!__all_sync(0xffffffffu, got)) return false;  // warp-uniform exit
             tc::fence_after();
+            constexpr int kCols = NK * PQ;  // this thread's accumulator columns
+            constexpr int kChunk = kCols < 32 ? kCols : 32;
 #pragma unroll
-            for (int k = 0; k < NK; ++k)
+            for (int c0 = 0; c0 < kCols; c0 += kChunk) {
+                uint32_t r[kChunk];
 #pragma unroll
-                for (int c = 0; c < PQ / 8; ++c) {
-                    uint32_t (&rc)[8] = *reinterpret_cast<uint32_t(*)[8]>(&r[k][8 * c]);
-                    tc::ld_x8(tmem + lane_off + d_col<NK>(NK == 2 ? k : kind0, db) + part * PQ + 8 * c, rc);
+                for (int c = 0; c < kChunk; c += 8) {
+                    const int col = c0 + c, k = col / PQ, cc = col % PQ;
+                    if (col < kCols) {
+                        uint32_t (&rc)[8] = *reinterpret_cast<uint32_t(*)[8]>(&r[c]);
+                        tc::ld_x8(tmem + lane_off + d_col<NK>(NK == 2 ? k : kind0, db) + part * PQ + cc, rc);
+                    }
                 }
+                tc::wait_ld();
+#pragma unroll
+                for (int c = 0; c < kChunk; c += 2) {
+                    const int col = c0 + c, k = col / PQ, cc = col % PQ;
+                    if (col < kCols) {
+                        const float2 v = __fadd2_rn(make_float2(acc[k][cc], acc[k][cc + 1]),
+                                                    make_float2(__uint_as_float(r[c]), __uint_as_float(r[c + 1])));
+                        acc[k][cc] = v.x;
+                        acc[k][cc + 1] = v.y;
+                    }
+                }
+            }
+            tc::fence_before();
             return true;
-        };
-        auto drain_add = [&](uint32_t (&r)[NK][PQ]) {
-#pragma unroll
-            for (int k = 0; k < NK; ++k)
-#pragma unroll
-                for (int c = 0; c < PQ; c += 2) {
-                    const float2 v = __fadd2_rn(make_float2(acc[k][c], acc[k][c + 1]),
-                                                make_float2(__uint_as_float(r[k][c]),
-                                                            __uint_as_float(r[k][c + 1])));
-                    acc[k][c] = v.x;
-                    acc[k][c + 1] = v.y;
-                }
         };
         // descriptor fields are read where they are used (not held across the stage loop)
         auto flush = [&](int mol, int kind0, int64_t i) {
@@ -402,6 +421,7 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
 
         int slot = 0, ab = 0;
         uint32_t ph = 0, aph = 0;
+        int pslot = 0;         // ring slot of the previous stage
         int dbuf = 0;          // accumulator buffer of the previous stage
         uint32_t dph = 0;      // and its phase bit
         for (int64_t q = blockIdx.x; q < n_tiles && ok; q += gridDim.x) {
@@ -462,20 +482,16 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                 tc::wait_st();
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) {  // hand the operands to the MMA issuer before draining
-                    mbar_arrive(&a_full[ab]);
-                    mbar_arrive(&b_empty[slot]);
-                }
+                if (lane == 0) mbar_arrive(&a_full[ab]);  // hand the operands to the MMA issuer
                 // drain the previous stage while this stage's MMAs run
                 if (s > 0) {
-                    uint32_t r[NK][PQ];
-                    if (!drain_issue(dbuf, dph, kind0, r)) {
+                    if (!drain(dbuf, dph, kind0)) {
                         ok = false;
                         break;
                     }
-                    tc::wait_ld();
-                    drain_add(r);
-                    tc::fence_before();
+                    // its MMAs are done, and so is this warp's use of its records: the ring
+                    // slot of the previous stage can be refilled
+                    if (lane == 0) mbar_arrive(&b_empty[pslot]);
                     if (--until_flush == 0) {
                         flush(tk.mol, kind0, i);
                         until_flush = args.flush;
@@ -483,6 +499,7 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                 }
                 dbuf = ab;
                 dph = aph;
+                pslot = slot;
                 if (++slot == kTcRing) {
                     slot = 0;
                     ph ^= 1u;
@@ -491,14 +508,11 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                 if (ab == 0) aph ^= 1u;
             }
             if (!ok) break;
-            uint32_t r[NK][PQ];
-            if (!drain_issue(dbuf, dph, kind0, r)) {
+            if (!drain(dbuf, dph, kind0)) {
                 ok = false;
                 break;
             }
-            tc::wait_ld();
-            drain_add(r);
-            tc::fence_before();
+            if (lane == 0) mbar_arrive(&b_empty[pslot]);
             flush(tk.mol, kind0, i);
         }
         tc::wait_st();  // nothing of ours is in flight to TMEM on any exit path

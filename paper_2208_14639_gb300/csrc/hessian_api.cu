@@ -45,6 +45,17 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
         return VV10_ERR_UNSUPPORTED;
     }
 
+    // U_i, W_i of the diagonal terms in FP64 too when the energy call was mixed
+    if (fp64 && !euw_fp64) {
+        int ns = 1;
+        H_TRY(run_pairsum(MODE_EUW, true, st, &ns));
+        PhaseScope ph(this, PH_EP_EPILOGUE, st, 1);
+        H_CUDA(launch_ep_epilogue(P, static_cast<double*>(part.p), ns, static_cast<double*>(sumE.p),
+                                  static_cast<double*>(sumU.p), static_cast<double*>(sumW.p), nullptr,
+                                  nullptr, static_cast<double*>(eblk.p), static_cast<int*>(dev_err.p), st),
+               "E/U/W epilogue");
+        euw_fp64 = true;
+    }
     // A_i, B_i, C_i (pair sums of the diagonal terms), in the requested precision
     const size_t nkb = sizeof(double) * static_cast<size_t>(soa_ld);
     if (!have_abc || (fp64 && !abc_fp64)) {

@@ -61,21 +61,23 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
                                    float4* r32p, cudaStream_t st);
 
 // ---------------------------------------------------------------- pair sums (pairsum.cu)
-enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2 };
+enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2, MODE_EUWABC = 3 };
+// Quantities a mode accumulates per row (the leading dimension of its partial buffer).
+constexpr int pair_mode_nq(int mode) { return mode == MODE_EUWABC ? 6 : 3; }
 
 struct PairLaunch {
     int rows_per_thread = 2;  // FP32: 1, 2, 4; FP64: 1, 2
     int n_split = 1;          // j-splits (partials reduced by the epilogue)
     int stall = 0;            // test hook: CTA (0,0) issues no copies, so its waits time out
 };
-// part: [3][n_split][nk_pad] FP64 partial sums (quantity-major).
+// part: [nq][n_split][nk_pad] FP64 partial sums (quantity-major, nq = pair_mode_nq(mode)).
 cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLaunch& cfg,
                            double* part, int* err, cudaStream_t st);
 int pairsum_default_split(const PointsDev& p, bool fp64, int rows_per_thread, int n_sm);
 
 // Batched pair sums (batch.cu): one persistent launch over a task table with an atomic
 // work counter.  PairMol describes one molecule's records and partial buffer
-// part[3][n_split][nk_pad]; PairTask one (molecule, row tile, j-split) unit.
+// part[nq][n_split][nk_pad]; PairTask one (molecule, row tile, j-split) unit.
 struct PairMol {
     const void* ra32;
     const void* rb32;
@@ -161,7 +163,9 @@ cudaError_t launch_grad_epilogue(const PointsDev& p, const double* part, int n_s
                                  cudaStream_t st);
 cudaError_t launch_atom_sums(const PointsDev& p, const double* gk, double* grad_atoms,
                              cudaStream_t st);
-cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, int* err,
-                                 cudaStream_t st);
+// out: E/U/W^Bgr; gk (nk x 3, kept order) and grad_points (n x 3, caller order), when not
+// null, receive the point gradient dE/dr_i from the same pass.
+cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, double* gk,
+                                 double* grad_points, int* err, cudaStream_t st);
 
 }  // namespace vv10

@@ -13,6 +13,7 @@
 //   MODE_ABC  sum_j w_j rho_j Phi_ij (1/s^2 + 1/(s g) + 1/g^2) {1, R^2, R^4}
 //             (A_i, B_i, C_i of Sec. II.B up to the factor 2)
 //   MODE_GRAD sum_j w_j rho_j Phi_ij D_ij (r_i - r_j), D_ij the bracket of Eq. grad_gr
+//   MODE_EUWABC the six sums of MODE_EUW and MODE_ABC from one pass (partials [6][..])
 // with g = omega_i R^2 + kappa_i, g' = omega_j R^2 + kappa_j, s = g + g' and all of
 // 1/g, 1/g', 1/s, Phi obtained from the single reciprocal inv = 1/(g g' s).
 //
@@ -50,14 +51,14 @@ k_pairsum(const typename Recs<T>::A* __restrict__ ra, const typename Recs<T>::B*
     // Test hook: a stalled CTA never issues its copies, so its first wait runs out.
     const bool stalled = stall && blockIdx.x == 0 && blockIdx.y == 0;
     uint32_t gtile = 0;
-    double dacc[RPT][3];
+    double dacc[RPT][pair_mode_nq(MODE)];
     pairsum_range<T, MODE, RPT, NT>(sa, sb, bar, gtile, ra, rb, nk, i0, jb, je, dacc, err, stalled);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int64_t i = i0 + r * NT + tid;
         if (i < nk) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
+            for (int q = 0; q < pair_mode_nq(MODE); ++q)
                 part[(static_cast<int64_t>(q) * n_split + split) * nk_pad + i] = dacc[r][q];
         }
     }
@@ -121,6 +122,7 @@ cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLa
     switch (mode) {
         case MODE_EUW: return launch_mode<MODE_EUW>(p, fp64, cfg, part, err, st);
         case MODE_ABC: return launch_mode<MODE_ABC>(p, fp64, cfg, part, err, st);
+        case MODE_EUWABC: return launch_mode<MODE_EUWABC>(p, fp64, cfg, part, err, st);
         default: return launch_mode<MODE_GRAD>(p, fp64, cfg, part, err, st);
     }
 }

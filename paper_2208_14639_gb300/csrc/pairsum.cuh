@@ -19,10 +19,10 @@ struct Row {
     T x, y, z, om, ka;
 };
 
-// Accumulate one (i, j) pair into acc[0..2] for the given mode.
+// Accumulate one (i, j) pair into acc[0 .. nq-1] for the given mode.
 template <class T, int MODE, class RA, class RB>
 __device__ __forceinline__ void pair_accumulate(const Row<T>& r, const RA& a, const RB& b,
-                                                T (&acc)[3]) {
+                                                T (&acc)[pair_mode_nq(MODE)]) {
     const T dx = r.x - a.x, dy = r.y - a.y, dz = r.z - a.z;
     T r2 = dx * dx;
     r2 = fmadd(dy, dy, r2);
@@ -39,6 +39,20 @@ __device__ __forceinline__ void pair_accumulate(const Row<T>& r, const RA& a, co
         acc[0] += ph;
         acc[1] += pt;
         acc[2] = fmadd(pt, r2, acc[2]);
+    } else if constexpr (MODE == MODE_EUWABC) {
+        // both of the above from one evaluation of the pair
+        const T L = ggp * inv;          // 1/s
+        const T Gi = (gp * s) * inv;    // 1/g
+        const T t = L + Gi;             // 1/s + 1/g
+        const T pt = ph * t;
+        acc[0] += ph;
+        acc[1] += pt;
+        acc[2] = fmadd(pt, r2, acc[2]);
+        const T v = ph * fmadd(L, t, Gi * Gi);
+        acc[3] += v;
+        const T v2 = v * r2;
+        acc[4] += v2;
+        acc[5] = fmadd(v2, r2, acc[5]);
     } else if constexpr (MODE == MODE_ABC) {
         const T L = ggp * inv;         // 1/s
         const T Gi = (gp * s) * inv;   // 1/g
@@ -69,7 +83,9 @@ __device__ __forceinline__ bool pairsum_range(typename Recs<T>::A (*sa)[kJTile],
                                               uint32_t& gtile, const typename Recs<T>::A* ra,
                                               const typename Recs<T>::B* rb, int64_t nk,
                                               int64_t i0, int64_t jb, int64_t je,
-                                              double (&dacc)[RPT][3], int* err, bool stalled) {
+                                              double (&dacc)[RPT][pair_mode_nq(MODE)], int* err,
+                                              bool stalled) {
+    constexpr int NQ = pair_mode_nq(MODE);
     using RA = typename Recs<T>::A;
     using RB = typename Recs<T>::B;
     const int tid = threadIdx.x;
@@ -86,11 +102,11 @@ __device__ __forceinline__ bool pairsum_range(typename Recs<T>::A (*sa)[kJTile],
             row[r] = Row<T>{T(0), T(0), T(0), T(1), T(1)};
         }
     }
-    T acc[RPT][3];
+    T acc[RPT][NQ];
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             acc[r][q] = T(0);
             dacc[r][q] = 0.0;
         }
@@ -123,7 +139,7 @@ __device__ __forceinline__ bool pairsum_range(typename Recs<T>::A (*sa)[kJTile],
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 dacc[r][q] += static_cast<double>(acc[r][q]);
                 acc[r][q] = T(0);
             }

@@ -136,8 +136,10 @@ struct vv10_ctx {
     // coordinate scratch
     vv10::DevBuf gk;
 
-    // tile overrides (index = mode + 3 * fp64), set by vv10_set_tiles / the autotuner
-    vv10::TileOverride overrides[6];
+    // tile overrides (index = mode + 4 * fp64, modes MODE_EUW..MODE_EUWABC), set by
+    // vv10_set_tiles / the autotuner
+    vv10::TileOverride overrides[8];
+    int options = 0;  // VV10_OPT_* flags
     vv10::TileOverride batch_over[2];  // batched pair sums (index = fp64)
     int tc_cap_manual = 0;             // widest trial group of the contraction (0 = automatic)
     int tc_cap_last = 0;               // the width used by the last mixed Hessian call
@@ -160,7 +162,7 @@ struct vv10_ctx {
     vv10_status batch_pair_tables(bool fp64, int rpt, int split_tiles);
     void batch_tiles(bool fp64, int* rpt, int* split_tiles) const;
     vv10_status batch_ep(vv10_precision prec, double* energies, double* vrho, double* vgamma,
-                         cudaStream_t st);
+                         bool with_abc, cudaStream_t st);
     vv10_status batch_hess(vv10_precision prec, const int32_t* P, const double* rho_t,
                            const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
                            cudaStream_t st);

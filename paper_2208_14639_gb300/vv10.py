@@ -29,6 +29,7 @@ VV10_MIXED_BF16X3 = 2
 PRECISIONS = {"fp64": VV10_FP64, "tf32x3": VV10_MIXED_TF32X3, "bf16x3": VV10_MIXED_BF16X3,
               "mixed": VV10_MIXED_TF32X3}
 
+VV10_OPT_FUSE_HESSIAN_SUMS = 1
 VV10_TUNE_PAIRSUMS = 1
 VV10_TUNE_BATCH = 2
 VV10_TUNE_CONTRACTION = 4
@@ -45,7 +46,8 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_debug_inject", "vv10_profile_enable", "vv10_profile_read",
            "vv10_profile_phase_name", "vv10_energy_potential_noalloc",
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
-           "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune")
+           "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
+           "vv10_set_options")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_N_PHASES = 11
 
@@ -107,6 +109,7 @@ def load(build_if_missing: bool = False):
                                 ctypes.POINTER(ctypes.c_int)]),
         "vv10_autotune": (st, [P, st, ctypes.c_int, P]),
         "vv10_set_autotune": (st, [P, ctypes.c_int]),
+        "vv10_set_options": (st, [P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -232,6 +235,10 @@ def vv10_get_tiles(h, what: int) -> tuple:
 
 def vv10_autotune(h, prec: int, what: int, stream=None) -> None:
     _check(h, load().vv10_autotune(h, int(prec), int(what), _stream(stream)), "vv10_autotune")
+
+
+def vv10_set_options(h, flags: int) -> None:
+    _check(h, load().vv10_set_options(h, int(flags)), "vv10_set_options")
 
 
 def vv10_set_autotune(h, flags: int) -> None:

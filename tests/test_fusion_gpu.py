@@ -1,0 +1,102 @@
+"""Fused passes: the A/B/C sums formed in the energy pass (VV10_OPT_FUSE_HESSIAN_SUMS) and the
+point gradient taken from the atom-resolved pass give the oracle's results, and the calls
+that follow run no pair pass of their own."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2208_14639_gb300 import synth, vv10
+
+pytestmark = pytest.mark.gpu
+
+FP64 = vv10.VV10_FP64
+MIXED = vv10.VV10_MIXED_TF32X3
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    vv10.load(build_if_missing=True)
+    return torch.device("cuda", 0)
+
+
+def T(a, dev, dt=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
+
+
+@pytest.fixture(scope="module")
+def case(oracle_mod):
+    g = synth.random_points(1500, seed=101, n_atom=4)
+    rng = np.random.default_rng(7)
+    P = 20
+    rt = rng.normal(size=(P, g.n)) * g.rho
+    gt = rng.normal(size=(P, g.n, 3)) * (np.abs(g.grad_rho) + 1e-3 * g.rho[:, None])
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    e, vr, vg = oracle_mod.potential(*args)
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    gp = oracle_mod.point_grad(*args)
+    ga = oracle_mod.atom_grad(*args, g.atom_of_point, g.molecule.n_atom)
+    euw = np.stack(oracle_mod.atom_resolved(*args, g.atom_of_point, g.molecule.n_atom))
+    return g, rt, gt, dict(e=e, vr=vr, vg=vg, fr=fr, fg=fg, gp=gp, ga=ga, euw=euw)
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
+def test_fused_hessian_sums(dev, case, prec, tol):
+    g, rt, gt, ref = case
+    eng = vv10.VV10(0)
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                T(g.atom_of_point, dev, torch.int32), g.molecule.n_atom)
+    vv10.vv10_set_options(eng.h, vv10.VV10_OPT_FUSE_HESSIAN_SUMS)
+    vv10.vv10_profile_enable(eng.h, True)
+    vv10.vv10_profile_read(eng.h)
+    e, vr, vg = eng.energy_potential(prec)
+    p_energy = vv10.vv10_profile_read(eng.h)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), prec)
+    vv10.vv10_sync(eng.h)
+    p_hess = vv10.vv10_profile_read(eng.h)
+    assert p_energy["pair_sums_EUW"][1] == 1 and p_energy["pair_sums_ABC"][1] == 1  # 1 pass + A/B/C epilogue
+    assert p_hess["pair_sums_ABC"][1] == 0 and p_hess["pair_sums_EUW"][1] == 0      # no pair pass
+    if prec == FP64:
+        assert abs(e - ref["e"]) <= 1e-11 * abs(ref["e"])
+    else:
+        assert abs(e - ref["e"]) <= 1e-7
+    for x, y in ((vr, ref["vr"]), (vg, ref["vg"]), (fr, ref["fr"]), (fg, ref["fg"])):
+        assert rel(x.cpu().numpy(), y) <= tol
+    # after an unfused energy call of the other precision the Hessian recomputes what it needs
+    vv10.vv10_set_options(eng.h, 0)
+    eng.energy_potential(MIXED if prec == FP64 else FP64)
+    fr2, fg2 = eng.hessian_contract(T(rt, dev), T(gt, dev), prec)
+    assert rel(fr2.cpu().numpy(), ref["fr"]) <= tol and rel(fg2.cpu().numpy(), ref["fg"]) <= tol
+    with pytest.raises(vv10.VV10Error):
+        vv10.vv10_set_options(eng.h, 2)
+    eng.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
+def test_gradient_from_atom_resolved_pass(dev, case, prec, tol):
+    g, _, _, ref = case
+    eng = vv10.VV10(0)
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                T(g.atom_of_point, dev, torch.int32), g.molecule.n_atom)
+    eng.energy_potential(prec)
+    vv10.vv10_profile_enable(eng.h, True)
+    vv10.vv10_profile_read(eng.h)
+    gp, ga, euw = eng.coord_grad(prec, atoms=True, resolved=True)
+    vv10.vv10_sync(eng.h)
+    prof = vv10.vv10_profile_read(eng.h)
+    assert prof["pair_sums_grad"][1] == 0 and prof["atom_resolved"][1] == 1
+    assert rel(gp.cpu().numpy(), ref["gp"]) <= tol
+    assert rel(ga.cpu().numpy(), ref["ga"]) <= tol
+    assert rel(euw.cpu().numpy(), ref["euw"]) <= tol
+    # the same gradient as the separate gradient pass
+    gp2, ga2, _ = eng.coord_grad(prec, atoms=True, resolved=False)
+    assert rel(gp.cpu().numpy(), gp2.cpu().numpy()) <= (1e-13 if prec == FP64 else 1e-6)
+    assert rel(ga.cpu().numpy(), ga2.cpu().numpy()) <= (1e-13 if prec == FP64 else 1e-6)
+    eng.close()
