@@ -47,7 +47,7 @@ ALU_OPS_PER_PAIR_TC = 40
 ALU_OPS_PER_PAIR_TC_SPLIT = 65
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
 # (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
-PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.228e9}
+PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.2312e9}
 
 
 def workloads():

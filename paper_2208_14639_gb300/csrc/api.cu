@@ -404,7 +404,7 @@ vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_s
     PairLaunch cfg;
     const TileChoice tc = tiles_for(mode, fp64);
     cfg.rows_per_thread = tc.rows_per_thread;
-    cfg.n_split = tc.n_split > 0 ? tc.n_split : pairsum_default_split(P, fp64, cfg.rows_per_thread, n_sm);
+    cfg.n_split = tc.n_split > 0 ? tc.n_split : pairsum_default_split(P, mode, fp64, cfg.rows_per_thread, n_sm);
     if (debug_stall) {
         cfg.stall = 1;
         debug_stall = 0;

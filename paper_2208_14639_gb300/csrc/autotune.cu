@@ -133,7 +133,7 @@ vv10_status vv10_ctx::tune_pairsum(int mode, bool fp64, cudaStream_t st, bool fo
     float best = 3.0e38f;
     int best_r = fp64 ? 1 : 2, best_s = 0;
     for (int r : rpts) {
-        const int d = pairsum_default_split(P, fp64, r, n_sm);
+        const int d = pairsum_default_split(P, mode, fp64, r, n_sm);
         std::vector<int> splits = {d};
         if (d / 2 >= 1) splits.push_back(d / 2);
         splits.push_back(2 * d);

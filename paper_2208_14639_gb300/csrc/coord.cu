@@ -14,6 +14,7 @@
 // so the same pass also writes dE/dr_i = -2 w_i rho_i G_i when asked to.
 #include "common.cuh"
 #include "kernels.hpp"
+#include "pairsum.cuh"
 
 namespace vv10 {
 
@@ -71,7 +72,9 @@ constexpr int kArThreads = 128;
 constexpr int kArJT = 128;
 
 template <class T>
-__global__ void __launch_bounds__(kArThreads)
+// 8 resident CTAs per SM (at most 64 registers a thread): the grid of one row per thread
+// then fits the GPU in about one wave for grids of ~150 k kept points.
+__global__ void __launch_bounds__(kArThreads, sizeof(T) == 4 ? 8 : 4)
 k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
                 const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ out,
                 double* __restrict__ gk, double* __restrict__ grad_points) {
@@ -92,9 +95,6 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
     }
     const int64_t n = P.n, na = P.n_atom;
     const int64_t oi_idx = valid ? P.orig[i] : 0;
-    double rest[9];  // running sum over atoms B != atom(i)
-#pragma unroll
-    for (int q = 0; q < 9; ++q) rest[q] = 0.0;
     double gsum[3] = {0.0, 0.0, 0.0};  // E part over every atom: the point-gradient sum
 
     for (int B = 0; B < P.n_atom; ++B) {
@@ -124,14 +124,19 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
                 const T ggp = g * gp;
                 const T inv = recip(ggp * s);
                 const T ph = a.w * inv;          // w_j rho_j Phi_ij
+                const T sinv = s * inv;          // 1/(g g')
                 const T L = ggp * inv;           // 1/s
-                const T Gi = (gp * s) * inv;     // 1/g
-                const T D = (oi * gp * (s + g) + b.x * g * (s + gp)) * inv;
+                const T Gi = gp * sinv;          // 1/g
+                const T Gj = g * sinv;           // 1/g'
+                const T q = (oi + b.x) * L;      // (omega_i + omega_j)/s
+                const T oG = oi * Gi;            // omega_i/g
+                const T D = fmadd(b.x, Gj, oG + q);
                 const T t1 = L + Gi;
-                const T t3 = oi * Gi * Gi + (oi + b.x) * L * L;
+                // omega_i/g^2 + (omega_i + omega_j)/s^2 = oG Gi + q L
+                const T X = fmadd(D, t1, fmadd(oG, Gi, q * L));
                 const T cE = ph * D;
-                const T cU = ph * (D * t1 + t3);
-                const T cW = ph * (r2 * (D * t1 + t3) - t1);
+                const T cU = ph * X;
+                const T cW = fmadd(r2, cU, -(ph * t1));
                 acc[0] += cE * dx; acc[1] += cE * dy; acc[2] += cE * dz;
                 acc[3] += cU * dx; acc[4] += cU * dy; acc[5] += cU * dz;
                 acc[6] += cW * dx; acc[7] += cW * dy; acc[8] += cW * dz;
@@ -145,17 +150,20 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
         // (r_i - r_j) was accumulated: E = +2 acc, U = -2 acc, W = -2 acc
         if (valid && B != ai) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const double v = (q < 3 ? 2.0 : -2.0) * tot[q];
-                rest[q] += v;
-                out[((static_cast<int64_t>(q / 3) * n + oi_idx) * na + B) * 3 + (q % 3)] = v;
-            }
+            for (int q = 0; q < 9; ++q)
+                out[((static_cast<int64_t>(q / 3) * n + oi_idx) * na + B) * 3 + (q % 3)] =
+                    (q < 3 ? 2.0 : -2.0) * tot[q];
         }
     }
     if (valid && ai >= 0 && ai < P.n_atom) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-            out[((static_cast<int64_t>(q / 3) * n + oi_idx) * na + ai) * 3 + (q % 3)] = -rest[q];
+        // own atom: minus the sum over the other atoms, read back from this thread's writes
+        for (int q = 0; q < 9; ++q) {
+            double* row = out + (static_cast<int64_t>(q / 3) * n + oi_idx) * na * 3 + (q % 3);
+            double rest = 0.0;
+            for (int B = 0; B < P.n_atom; ++B)
+                if (B != ai) rest += row[3 * B];
+            row[3 * ai] = -rest;
+        }
     }
     if (valid && gk) {
         const double c = -2.0 * P.w[i] * P.rho[i];
@@ -169,9 +177,9 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
 
 cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, double* gk,
                                  double* grad_points, int* err, cudaStream_t st) {
-    (void)err;
     if (p.nk == 0 || p.n_atom <= 0) return cudaSuccess;
     const unsigned g = static_cast<unsigned>(cdiv64(p.nk, kArThreads));
+    (void)err;
     if (fp64) k_atom_resolved<double><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out, gk, grad_points);
     else k_atom_resolved<float><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out, gk, grad_points);
     return cudaGetLastError();

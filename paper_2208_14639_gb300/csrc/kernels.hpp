@@ -73,7 +73,7 @@ struct PairLaunch {
 // part: [nq][n_split][nk_pad] FP64 partial sums (quantity-major, nq = pair_mode_nq(mode)).
 cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLaunch& cfg,
                            double* part, int* err, cudaStream_t st);
-int pairsum_default_split(const PointsDev& p, bool fp64, int rows_per_thread, int n_sm);
+int pairsum_default_split(const PointsDev& p, int mode, bool fp64, int rows_per_thread, int n_sm);
 
 // Batched pair sums (batch.cu): one persistent launch over a task table with an atomic
 // work counter.  PairMol describes one molecule's records and partial buffer

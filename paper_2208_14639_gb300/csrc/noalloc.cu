@@ -259,7 +259,7 @@ extern "C" vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xy
     P.r32b = r32b;
     PairLaunch cfg;
     cfg.rows_per_thread = fp64 ? 1 : 2;
-    int ns = pairsum_default_split(P, fp64, cfg.rows_per_thread, n_sm);
+    int ns = pairsum_default_split(P, MODE_EUW, fp64, cfg.rows_per_thread, n_sm);
     if (ns > kNaMaxSplit) ns = kNaMaxSplit;
     // the launcher normalises the split count; recompute the count it will use
     const int64_t ntile = n_pad / kJTile;

@@ -19,6 +19,8 @@
 //
 // FP32 variant: recentred FP32 coordinates, FP32 pair arithmetic, FP32 sums within a
 // tile, promoted to FP64 once per tile.  FP64 variant: everything in FP64.
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.hpp"
 #include "pairsum.cuh"
@@ -76,15 +78,53 @@ static inline void split_geometry(int64_t nk_pad, int req, int64_t& j_per_split,
     n_split = static_cast<int>(ntile > 0 ? cdiv(ntile, tps) : 1);
 }
 
-int pairsum_default_split(const PointsDev& p, bool fp64, int rpt, int n_sm) {
+template <class T, int MODE, int RPT, int NT>
+static int blocks_per_sm_t() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pairsum<T, MODE, RPT, NT>, NT, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+template <int MODE>
+static int blocks_per_sm_mode(bool fp64, int rpt) {
+    if (fp64) return rpt >= 2 ? blocks_per_sm_t<double, MODE, 2, 128>() : blocks_per_sm_t<double, MODE, 1, 128>();
+    if (rpt >= 4) return blocks_per_sm_t<float, MODE, 4, 256>();
+    return rpt == 2 ? blocks_per_sm_t<float, MODE, 2, 256>() : blocks_per_sm_t<float, MODE, 1, 256>();
+}
+
+static int pairsum_blocks_per_sm(int mode, bool fp64, int rpt) {
+    switch (mode) {
+        case MODE_EUW: return blocks_per_sm_mode<MODE_EUW>(fp64, rpt);
+        case MODE_ABC: return blocks_per_sm_mode<MODE_ABC>(fp64, rpt);
+        case MODE_EUWABC: return blocks_per_sm_mode<MODE_EUWABC>(fp64, rpt);
+        default: return blocks_per_sm_mode<MODE_GRAD>(fp64, rpt);
+    }
+}
+
+// j-splits for a launch: the grid (row tiles x splits) is sized to fill the resident CTA
+// slots in as close to whole waves as possible (a partial last wave leaves SMs idle while
+// it runs); among choices within 1 % of the best, the fewest splits.
+int pairsum_default_split(const PointsDev& p, int mode, bool fp64, int rpt, int n_sm) {
     const int NT = fp64 ? 128 : 256;
     const int64_t n_itile = cdiv(p.nk, static_cast<int64_t>(NT) * rpt);
-    const int64_t target = static_cast<int64_t>(n_sm) * (fp64 ? 8 : 4);
-    int req = static_cast<int>(cdiv(target, n_itile > 0 ? n_itile : 1));
-    int64_t jps;
-    int ns;
-    split_geometry(p.nk_pad, req, jps, ns);
-    return ns;
+    const double slots = static_cast<double>(n_sm) * pairsum_blocks_per_sm(mode, fp64, rpt);
+    int best = 1;
+    double best_eff = -1.0;
+    for (int req = 1; req <= 16; ++req) {
+        int64_t jps;
+        int ns;
+        split_geometry(p.nk_pad, req, jps, ns);
+        const double w = static_cast<double>(n_itile * ns) / slots;
+        const double eff = w / std::ceil(w);
+        if (eff > best_eff + 0.01) {
+            best_eff = eff;
+            best = ns;
+        }
+    }
+    return best;
 }
 
 template <class T, int MODE, int RPT, int NT>
