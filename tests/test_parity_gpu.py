@@ -305,3 +305,33 @@ def test_error_paths(dev):
                     T(atoms, dev, torch.int32), 2)
     assert ei.value.status == vv10.VV10_ERR_INVALID_ARG
     eng.close()
+
+
+# ----------------------------------------------------------------- 60-atom CHON, 1.36 M points
+
+def test_full_size_chon60_mixed(dev, oracle_mod):
+    """60-atom CHON molecule, 75 x 302 points per atom (1,359,000 points), P = 180, mixed
+    precision: the energy against the FP64 GPU path (|dE| <= 1e-7 Eh), sampled rows of the
+    potential, the Hessian contraction and the point gradient against the oracle (full j
+    sums)."""
+    g = synth.config_chon60()
+    eng = make_engine(g, dev)
+    xyz = T(g.coords, dev)
+    rt, gt = synth.trial_densities_torch(g.molecule, xyz)
+    assert rt.shape == (180, g.n)
+    e_mixed, vr, vg = eng.energy_potential(MIXED)
+    fr, fg = eng.hessian_contract(rt, gt, MIXED)
+    gp, _, _ = eng.coord_grad(MIXED, atoms=False)
+    vv10.vv10_sync(eng.h)
+    rows = np.linspace(0, g.n - 1, 16).astype(np.int64)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    _, vr_ref, vg_ref = oracle_mod.potential(*args, rows=rows)
+    assert rel(vr.cpu().numpy()[rows], vr_ref) <= 1e-6
+    assert rel(vg.cpu().numpy()[rows], vg_ref) <= 1e-6
+    fr_ref, fg_ref = oracle_mod.hessian_contract(*args, rt.cpu().numpy(), gt.cpu().numpy(), rows=rows)
+    assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-6
+    assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-6
+    assert rel(gp.cpu().numpy()[rows], oracle_mod.point_grad(*args, rows=rows)) <= 1e-6
+    e_fp64, _, _ = eng.energy_potential(FP64, want_energy=True)
+    assert abs(e_mixed - e_fp64) <= 1e-7
+    eng.close()
