@@ -335,3 +335,47 @@ def test_full_size_chon60_mixed(dev, oracle_mod):
     e_fp64, _, _ = eng.energy_potential(FP64, want_energy=True)
     assert abs(e_mixed - e_fp64) <= 1e-7
     eng.close()
+
+
+# ----------------------------------------------------------------- limits and degenerate inputs
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
+def test_hessian_maximum_trial_count(dev, oracle_mod, prec, tol):
+    """P = VV10_MAX_TRIALS (4096): 22 tensor-core groups of 187 trials, or 128 FP64 chunks."""
+    g = synth.random_points(96, seed=23, n_atom=2)
+    P = 4096
+    rng = np.random.default_rng(5)
+    rt = rng.normal(size=(P, g.n)) * g.rho
+    gt = rng.normal(size=(P, g.n, 3)) * np.abs(g.grad_rho)[None]
+    fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+    eng = make_engine(g, dev)
+    eng.energy_potential(prec)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), prec)
+    vv10.vv10_sync(eng.h)
+    assert rel(fr.cpu().numpy(), fr_ref) <= tol
+    assert rel(fg.cpu().numpy(), fg_ref) <= tol
+    with pytest.raises(vv10.VV10Error):  # one more is refused
+        eng.hessian_contract(T(np.zeros((P + 1, g.n)), dev), T(np.zeros((P + 1, g.n, 3)), dev), prec)
+    eng.close()
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_all_points_below_cutoff(dev, prec):
+    """Every point below rho_cut: no kept point, zero energy and zero outputs everywhere."""
+    g0 = synth.random_points(50, seed=29, n_atom=2)
+    g = synth.GridDensity(g0.coords, g0.weights, np.full(g0.n, 1e-12), g0.grad_rho * 1e-12,
+                          g0.atom_of_point, g0.molecule)
+    eng = vv10.VV10(0)
+    nk = eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                     T(g.atom_of_point, dev, torch.int32), g.molecule.n_atom)
+    assert nk == 0
+    e, vr, vg = eng.energy_potential(prec)
+    assert e == 0.0 and not vr.any() and not vg.any()
+    rt = torch.ones(3, g.n, dtype=torch.float64, device=dev)
+    gt = torch.ones(3, g.n, 3, dtype=torch.float64, device=dev)
+    fr, fg = eng.hessian_contract(rt, gt, prec)
+    gp, ga, euw = eng.coord_grad(prec, atoms=True, resolved=True)
+    vv10.vv10_sync(eng.h)
+    for t in (fr, fg, gp, ga, euw):
+        assert not t.any()
+    eng.close()
