@@ -2,9 +2,10 @@
 """VV10 pair-evaluation throughput on GB300 (and the FP64 CPU oracle as the reference arm).
 
 One step = one pass of the whole hot path over the workload's synthetic grid, through the
-C ABI: vv10_prepare_points -> vv10_energy_potential -> vv10_hessian_contract (P trials) ->
-vv10_coord_grad (point gradient, atom sums, atom-resolved E/U/W^Bgr).  Each of the three
-pair-sum entry points evaluates N_kept^2 ordered pairs per call, so
+C ABI: vv10_prepare_points -> vv10_evaluate (energy, potential, Hessian contraction with P
+trials, point gradient, atom sums, atom-resolved E/U/W^Bgr).  The step evaluates the three
+pair quantities of the separate entry points (energy/potential, Hessian, coordinate terms),
+N_kept^2 ordered pairs each, so
     value = 3 * N_kept^2 * steps / (time of the timed steps)         [pair evals/s]
 with inputs resident in HBM when the timed region starts.  The same step in FP64 and
 per-call rates are reported beside it.  N > 1 (torchrun): every rank runs its own copy of
@@ -185,12 +186,13 @@ class Problem:
 
 
 def run_step(vv, h, pb, prec):
-    """One pass of the whole path through the C ABI; returns (n_kept, energy)."""
+    """One pass of the whole path through the C ABI (prepare, then energy, potential, Hessian
+    contraction and coordinate terms in one vv10_evaluate call); returns (n_kept, energy)."""
     d, o = pb.d, pb.out
     nk = vv.vv10_prepare_points(h, d["xyz"], d["w"], d["rho"], d["grad"], d["atom"], pb.n_atom)
-    e = vv.vv10_energy_potential(h, prec, o["vrho"], o["vgamma"])
-    vv.vv10_hessian_contract(h, prec, d["rt"], d["gt"], o["frt"], o["fgt"])
-    vv.vv10_coord_grad(h, prec, o["gp"], o["ga"], o["euw"])
+    e = vv.vv10_evaluate(h, prec, d["rt"], d["gt"], o["frt"], o["fgt"], vrho=o["vrho"],
+                         vgamma=o["vgamma"], grad_points=o["gp"], grad_atoms=o["ga"],
+                         EUW_Bgr=o["euw"])
     return nk, e
 
 
@@ -320,7 +322,7 @@ def gpu_arm(args):
     t_ep = per["pair_sums_EUW"] + per["energy_epilogue"]
     t_hess = (per["pair_sums_ABC"] + per["trial_prep"] + per["contraction_fp64"] +
               per["contraction_tensor_core"] + per["hessian_epilogue"])
-    t_coord = per["pair_sums_grad"] + per["grad_epilogue"] + per["atom_resolved"]
+    t_coord = per["pair_sums_grad"] + per["grad_epilogue"] + per["atom_resolved"]  # incl. the fused sums
     hess_flops = 8.0 * pairs_call * pb.P
     breakdown = {
         "energy_potential_pairs_per_s": pairs_call / (t_ep / 1e3) if t_ep else None,
@@ -329,8 +331,8 @@ def gpu_arm(args):
         "hessian_alg_tflops": hess_flops / (t_hess / 1e3) / 1e12 if t_hess else None,
         "coord_grad_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
-        "note": "pair_sums_EUW is the fused E/U/W + A/B/C pass; the point gradient comes from "
-                "the atom-resolved pass",
+        "note": "one pass over the pairs (phase atom_resolved) forms the E/U/W and A/B/C row "
+                "sums, the atom-resolved terms and the point gradient; then the contraction",
     }
 
     # roofline of the dominant kernel

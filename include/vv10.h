@@ -256,6 +256,24 @@ vv10_status vv10_sync(vv10_handle h, void* stream);
 vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split);
 vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n_split);
 
+/* Everything of one evaluation in one call (the quantities of vv10_energy_potential,
+ * vv10_hessian_contract and vv10_coord_grad, Sec. II.A and Sec. II.B; the call itself has no
+ * counterpart in the paper).  When EUW_Bgr is requested, one pass over the pairs forms the
+ * E/U/W and A/B/C row sums, the atom-resolved terms and the point gradient together (the
+ * separate calls need two passes); otherwise it is the three calls in sequence with the
+ * A/B/C sums formed in the energy pass.
+ *   P            number of trials, 0 <= P <= VV10_MAX_TRIALS (0: no Hessian contraction;
+ *                rho_t, grad_rho_t, f_rho_t, f_gamma_t then unused and may be NULL)
+ *   energy       HOST double out (may be NULL; when given the call synchronises `stream`)
+ *   other arrays as for the three calls; vrho, vgamma, grad_points, grad_atoms, EUW_Bgr
+ *                may be NULL (grad_atoms, EUW_Bgr need atom_of_point at prepare time)
+ * Leaves the handle as the three calls would (the cached sums serve later calls).
+ * Errors: as for the three calls. */
+vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P, const double* rho_t,
+                          const double* grad_rho_t, double* energy, double* vrho, double* vgamma,
+                          double* f_rho_t, double* f_gamma_t, double* grad_points,
+                          double* grad_atoms, double* EUW_Bgr, void* stream);
+
 /* Handle options (the paper has no counterpart).
  *   VV10_OPT_FUSE_HESSIAN_SUMS  vv10_energy_potential (and vv10_batch_energy_potential) also
  *       form the A_i, B_i, C_i sums of the Hessian diagonal (Sec. II.B) in the same pass over

@@ -605,7 +605,7 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
             PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
             VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr,
                                               want_grad ? static_cast<double*>(h->gk.p) : nullptr,
-                                              grad_points, static_cast<int*>(h->dev_err.p), st),
+                                              grad_points, nullptr, static_cast<int*>(h->dev_err.p), st),
                       "atom-resolved terms");
         }
         if (grad_atoms) {
@@ -626,6 +626,117 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
         if (grad_atoms)
             VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
                       "atom sums");
+    }
+    return VV10_OK;
+}
+
+vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
+                          const double* rho_t, const double* grad_rho_t, double* energy,
+                          double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
+                          double* grad_points, double* grad_atoms, double* EUW_Bgr,
+                          void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (P_trials < 0 || P_trials > VV10_MAX_TRIALS) {
+        h->set_error("P must be in [0, VV10_MAX_TRIALS]");
+        return P_trials < 0 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    if (P_trials > 0 && prec == VV10_MIXED_BF16X3) {
+        h->set_error("the BF16x3 Hessian contraction is not available in this build");
+        return VV10_ERR_UNSUPPORTED;
+    }
+    if ((grad_atoms || EUW_Bgr) && h->P.n_atom == 0) {
+        h->set_error("atom outputs need atom_of_point at prepare time");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    void* outs[] = {vrho, vgamma, grad_points, grad_atoms, EUW_Bgr};
+    for (void* q : outs)
+        if (q && (!device_ptr_ok(q, h->device) || !aligned(q, 8))) {
+            h->set_error("outputs must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    if (P_trials > 0) {
+        const void* ptrs[] = {rho_t, grad_rho_t, f_rho_t, f_gamma_t};
+        for (const void* q : ptrs)
+            if (!device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+                h->set_error("trial and output arrays must be 8-byte aligned device pointers");
+                return VV10_ERR_INVALID_ARG;
+            }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PointsDev& P = h->P;
+    if (!EUW_Bgr) {
+        // the separate calls, with the A/B/C sums formed in the energy pass
+        const int saved = h->options;
+        if (P_trials > 0) h->options |= VV10_OPT_FUSE_HESSIAN_SUMS;
+        vv10_status s = vv10_energy_potential(h, prec, nullptr, vrho, vgamma, stream);
+        h->options = saved;
+        VV10_TRY(s);
+        if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
+        if (grad_points || grad_atoms)
+            VV10_TRY(vv10_coord_grad(h, prec, grad_points, grad_atoms, nullptr, stream));
+    } else {
+        // one pass over the pairs: E/U/W/A/B/C row sums, atom-resolved terms, point gradient
+        const bool fp64 = (prec == VV10_FP64);
+        const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
+        DevBuf* sums[] = {&h->sumE, &h->sumU, &h->sumW, &h->sumA, &h->sumB, &h->sumC};
+        for (DevBuf* b : sums) VV10_TRY(h->ensure(*b, nkb, "row sums"));
+        const int nblk = ep_epilogue_blocks(P.nk);
+        VV10_TRY(h->ensure(h->eblk, sizeof(double) * nblk, "energy partials"));
+        VV10_TRY(h->ensure(h->scal, 64, "energy"));
+        VV10_TRY(h->ensure(h->part, 6 * nkb, "pair-sum partials"));
+        VV10_TRY(h->ensure(h->gk, 3 * nkb, "kept gradient"));
+        if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
+        if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
+        if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
+        if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
+        VV10_CUDA(h, cudaMemsetAsync(EUW_Bgr, 0, sizeof(double) * 9 * P.n * P.n_atom, st), "memset");
+        double* escal = static_cast<double*>(h->scal.p);
+        if (P.nk > 0) {
+            double* part = static_cast<double*>(h->part.p);
+            {
+                PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
+                VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr, static_cast<double*>(h->gk.p),
+                                                  grad_points, part, static_cast<int*>(h->dev_err.p), st),
+                          "fused pair pass");
+            }
+            PhaseScope ph(h, PH_EP_EPILOGUE, st, grad_atoms ? 4 : 3);
+            VV10_CUDA(h, launch_ep_epilogue(P, part, 1, static_cast<double*>(h->sumE.p),
+                                            static_cast<double*>(h->sumU.p),
+                                            static_cast<double*>(h->sumW.p), vrho, vgamma,
+                                            static_cast<double*>(h->eblk.p),
+                                            static_cast<int*>(h->dev_err.p), st),
+                      "energy epilogue");
+            VV10_CUDA(h, launch_sum_blocks(static_cast<double*>(h->eblk.p), nblk, escal, st), "energy sum");
+            VV10_CUDA(h, launch_abc_epilogue(P, part + 3 * static_cast<size_t>(P.nk_pad), 1,
+                                             static_cast<double*>(h->sumA.p),
+                                             static_cast<double*>(h->sumB.p),
+                                             static_cast<double*>(h->sumC.p), st),
+                      "A/B/C epilogue");
+            if (grad_atoms)
+                VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
+                          "atom sums");
+        } else {
+            VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
+        }
+        h->have_euw = true;
+        h->euw_fp64 = fp64;
+        h->have_abc = P.nk > 0;
+        h->abc_fp64 = fp64;
+        if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
+    }
+    if (energy) {
+        double* he = reinterpret_cast<double*>(h->h_pinned) + 2;
+        VV10_CUDA(h, cudaMemcpyAsync(he, h->scal.p, sizeof(double), cudaMemcpyDeviceToHost, st),
+                  "read energy");
+        VV10_TRY(h->check_device_errors(st));  // synchronises
+        *energy = *he;
     }
     return VV10_OK;
 }

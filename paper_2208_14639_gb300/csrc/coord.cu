@@ -71,13 +71,21 @@ template <> struct RecsAR<double> { using A = double4; using B = double4; };
 constexpr int kArThreads = 128;
 constexpr int kArJT = 128;
 
-template <class T>
-// 8 resident CTAs per SM (at most 64 registers a thread): the grid of one row per thread
-// then fits the GPU in about one wave for grids of ~150 k kept points.
-__global__ void __launch_bounds__(kArThreads, sizeof(T) == 4 ? 8 : 4)
+// Resident CTAs per SM: 8 (at most 64 registers a thread) for the FP32 kernel, so that its
+// grid of one row per thread fits the GPU in about one wave for grids of ~150 k kept points;
+// 6 when it also forms the six E/U/W/A/B/C row sums.
+template <class T, bool SUMS>
+constexpr int ar_min_blocks() { return sizeof(T) == 4 ? (SUMS ? 6 : 8) : (SUMS ? 3 : 4); }
+
+// SUMS: the same pass also forms the row sums of the fused energy + A/B/C mode (the
+// pair-sum kernel's MODE_EUWABC) into part[6][nk_pad] (one split), so that a full
+// evaluation makes a single pass over the pairs.
+template <class T, bool SUMS>
+__global__ void __launch_bounds__(kArThreads, ar_min_blocks<T, SUMS>())
 k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
                 const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ out,
-                double* __restrict__ gk, double* __restrict__ grad_points) {
+                double* __restrict__ gk, double* __restrict__ grad_points,
+                double* __restrict__ part) {
     using RA = typename RecsAR<T>::A;
     using RB = typename RecsAR<T>::B;
     __shared__ RA sa[kArJT];
@@ -96,6 +104,9 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
     const int64_t n = P.n, na = P.n_atom;
     const int64_t oi_idx = valid ? P.orig[i] : 0;
     double gsum[3] = {0.0, 0.0, 0.0};  // E part over every atom: the point-gradient sum
+    double rs[SUMS ? 6 : 1];           // E/U/W/A/B/C row sums (SUMS)
+#pragma unroll
+    for (int q = 0; q < (SUMS ? 6 : 1); ++q) rs[q] = 0.0;
 
     for (int B = 0; B < P.n_atom; ++B) {
         const int64_t s0 = P.seg[B], s1 = P.seg[B + 1];
@@ -113,6 +124,9 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
             T acc[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) acc[q] = T(0);
+            T sacc[SUMS ? 6 : 1];
+#pragma unroll
+            for (int q = 0; q < (SUMS ? 6 : 1); ++q) sacc[q] = T(0);
             for (int jj = 0; jj < cnt; ++jj) {
                 const RA a = sa[jj];
                 const RB b = sb[jj];
@@ -140,9 +154,24 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
                 acc[0] += cE * dx; acc[1] += cE * dy; acc[2] += cE * dz;
                 acc[3] += cU * dx; acc[4] += cU * dy; acc[5] += cU * dz;
                 acc[6] += cW * dx; acc[7] += cW * dy; acc[8] += cW * dz;
+                if constexpr (SUMS) {
+                    const T pt = ph * t1;
+                    sacc[0] += ph;
+                    sacc[1] += pt;
+                    sacc[2] = fmadd(pt, r2, sacc[2]);
+                    const T v = ph * fmadd(L, t1, Gi * Gi);  // 1/s^2 + 1/(s g) + 1/g^2
+                    sacc[3] += v;
+                    const T v2 = v * r2;
+                    sacc[4] += v2;
+                    sacc[5] = fmadd(v2, r2, sacc[5]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < 9; ++q) tot[q] += static_cast<double>(acc[q]);
+            if constexpr (SUMS) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) rs[q] += static_cast<double>(sacc[q]);
+            }
         }
         gsum[0] += tot[0];
         gsum[1] += tot[1];
@@ -165,6 +194,12 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
             row[3 * ai] = -rest;
         }
     }
+    if constexpr (SUMS) {
+        if (valid) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) part[static_cast<int64_t>(q) * P.nk_pad + i] = rs[q];
+        }
+    }
     if (valid && gk) {
         const double c = -2.0 * P.w[i] * P.rho[i];
 #pragma unroll
@@ -176,12 +211,17 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
 }
 
 cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, double* gk,
-                                 double* grad_points, int* err, cudaStream_t st) {
+                                 double* grad_points, double* sums, int* err, cudaStream_t st) {
     if (p.nk == 0 || p.n_atom <= 0) return cudaSuccess;
     const unsigned g = static_cast<unsigned>(cdiv64(p.nk, kArThreads));
     (void)err;
-    if (fp64) k_atom_resolved<double><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out, gk, grad_points);
-    else k_atom_resolved<float><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out, gk, grad_points);
+    if (sums) {
+        if (fp64) k_atom_resolved<double, true><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out, gk, grad_points, sums);
+        else k_atom_resolved<float, true><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out, gk, grad_points, sums);
+    } else {
+        if (fp64) k_atom_resolved<double, false><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, out, gk, grad_points, nullptr);
+        else k_atom_resolved<float, false><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, out, gk, grad_points, nullptr);
+    }
     return cudaGetLastError();
 }
 

@@ -164,8 +164,9 @@ cudaError_t launch_grad_epilogue(const PointsDev& p, const double* part, int n_s
 cudaError_t launch_atom_sums(const PointsDev& p, const double* gk, double* grad_atoms,
                              cudaStream_t st);
 // out: E/U/W^Bgr; gk (nk x 3, kept order) and grad_points (n x 3, caller order), when not
-// null, receive the point gradient dE/dr_i from the same pass.
+// null, receive the point gradient dE/dr_i from the same pass; sums, when not null,
+// receives the MODE_EUWABC row sums as part[6][1][nk_pad] (one split) from the same pass.
 cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, double* gk,
-                                 double* grad_points, int* err, cudaStream_t st);
+                                 double* grad_points, double* sums, int* err, cudaStream_t st);
 
 }  // namespace vv10

@@ -47,7 +47,7 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_profile_phase_name", "vv10_energy_potential_noalloc",
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
-           "vv10_set_options")
+           "vv10_set_options", "vv10_evaluate")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_N_PHASES = 11
 
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = False):
         "vv10_autotune": (st, [P, st, ctypes.c_int, P]),
         "vv10_set_autotune": (st, [P, ctypes.c_int]),
         "vv10_set_options": (st, [P, ctypes.c_int]),
+        "vv10_evaluate": (st, [P, st, I32, P, P, ctypes.POINTER(D), P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -235,6 +236,28 @@ def vv10_get_tiles(h, what: int) -> tuple:
 
 def vv10_autotune(h, prec: int, what: int, stream=None) -> None:
     _check(h, load().vv10_autotune(h, int(prec), int(what), _stream(stream)), "vv10_autotune")
+
+
+def vv10_evaluate(h, prec: int, rho_t=None, grad_rho_t=None, f_rho_t=None, f_gamma_t=None,
+                  vrho=None, vgamma=None, grad_points=None, grad_atoms=None, EUW_Bgr=None,
+                  stream=None, want_energy: bool = True) -> Optional[float]:
+    """Energy, potential, Hessian contraction (when trials are given) and coordinate terms
+    in one call; returns the energy (synchronising) when want_energy."""
+    P = 0 if rho_t is None else int(rho_t.shape[0])
+    e = ctypes.c_double()
+    if P:
+        n = int(rho_t.shape[1])
+        args = (_dptr(rho_t, "rho_t", shape=(P, n)), _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)),
+                _dptr(f_rho_t, "f_rho_t", shape=(P, n)), _dptr(f_gamma_t, "f_gamma_t", shape=(P, n)))
+    else:
+        args = (None, None, None, None)
+    st = load().vv10_evaluate(h, int(prec), P, args[0], args[1],
+                              ctypes.byref(e) if want_energy else None, _dptr(vrho, "vrho"),
+                              _dptr(vgamma, "vgamma"), args[2], args[3],
+                              _dptr(grad_points, "grad_points"), _dptr(grad_atoms, "grad_atoms"),
+                              _dptr(EUW_Bgr, "EUW_Bgr"), _stream(stream))
+    _check(h, st, "vv10_evaluate")
+    return float(e.value) if want_energy else None
 
 
 def vv10_set_options(h, flags: int) -> None:

@@ -100,3 +100,44 @@ def test_gradient_from_atom_resolved_pass(dev, case, prec, tol):
     assert rel(gp.cpu().numpy(), gp2.cpu().numpy()) <= (1e-13 if prec == FP64 else 1e-6)
     assert rel(ga.cpu().numpy(), ga2.cpu().numpy()) <= (1e-13 if prec == FP64 else 1e-6)
     eng.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("resolved", [True, False], ids=["one-pass", "three-calls"])
+def test_evaluate_everything_in_one_call(dev, case, prec, tol, resolved):
+    g, rt, gt, ref = case
+    eng = vv10.VV10(0)
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                T(g.atom_of_point, dev, torch.int32), g.molecule.n_atom)
+    f64 = dict(dtype=torch.float64, device=dev)
+    n, na, P = g.n, g.molecule.n_atom, rt.shape[0]
+    out = dict(vrho=torch.empty(n, **f64), vgamma=torch.empty(n, **f64),
+               f_rho_t=torch.empty(P, n, **f64), f_gamma_t=torch.empty(P, n, **f64),
+               grad_points=torch.empty(n, 3, **f64), grad_atoms=torch.empty(na, 3, **f64),
+               EUW_Bgr=torch.empty(3, n, na, 3, **f64) if resolved else None)
+    vv10.vv10_profile_enable(eng.h, True)
+    vv10.vv10_profile_read(eng.h)
+    e = vv10.vv10_evaluate(eng.h, prec, T(rt, dev), T(gt, dev), **out)
+    prof = vv10.vv10_profile_read(eng.h)
+    if resolved:  # a single pass over the pairs
+        assert prof["atom_resolved"][1] == 1 and prof["pair_sums_EUW"][1] == 0
+        assert prof["pair_sums_grad"][1] == 0
+    else:  # the fused energy + A/B/C pass and the gradient pass
+        assert prof["pair_sums_EUW"][1] == 1 and prof["pair_sums_grad"][1] == 1
+    if prec == FP64:
+        assert abs(e - ref["e"]) <= 1e-11 * abs(ref["e"])
+    else:
+        assert abs(e - ref["e"]) <= 1e-7
+    for name, key in (("vrho", "vr"), ("vgamma", "vg"), ("f_rho_t", "fr"), ("f_gamma_t", "fg"),
+                      ("grad_points", "gp"), ("grad_atoms", "ga")):
+        assert rel(out[name].cpu().numpy(), ref[key]) <= tol, name
+    if resolved:
+        assert rel(out["EUW_Bgr"].cpu().numpy(), ref["euw"]) <= tol
+    # the cached sums serve a later Hessian call
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), prec)
+    assert rel(fr.cpu().numpy(), ref["fr"]) <= tol
+    # no trials: energy and coordinate terms only
+    e0 = vv10.vv10_evaluate(eng.h, prec, vrho=out["vrho"], grad_points=out["grad_points"])
+    # (the one-pass and the pair-sum kernels sum their FP32 tiles in different orders)
+    assert abs(e0 - e) <= (1e-12 * abs(e) if prec == FP64 else 1e-7)
+    eng.close()
