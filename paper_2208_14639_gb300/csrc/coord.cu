@@ -69,7 +69,7 @@ template <> struct RecsAR<float> { using A = float4; using B = float4; };
 template <> struct RecsAR<double> { using A = double4; using B = double4; };
 
 constexpr int kArThreads = 128;
-constexpr int kArJT = 128;
+constexpr int kArJT = 256;  // j per shared-memory tile (two records per thread)
 
 // Resident CTAs per SM: 8 (at most 64 registers a thread) for the FP32 kernel, so that its
 // grid of one row per thread fits the GPU in about one wave for grids of ~150 k kept points;
@@ -115,10 +115,11 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
         for (int q = 0; q < 9; ++q) tot[q] = 0.0;
         for (int64_t j0 = s0; j0 < s1; j0 += kArJT) {
             __syncthreads();
-            if (j0 + tid < s1) {
-                sa[tid] = ra[j0 + tid];
-                sb[tid] = rb[j0 + tid];
-            }
+            for (int t = tid; t < kArJT; t += kArThreads)
+                if (j0 + t < s1) {
+                    sa[t] = ra[j0 + t];
+                    sb[t] = rb[j0 + t];
+                }
             __syncthreads();
             const int cnt = static_cast<int>(s1 - j0 < kArJT ? s1 - j0 : kArJT);
             T acc[9];
