@@ -46,6 +46,9 @@ FP32_LANES_PER_SM = 128
 ALU_OPS_PER_PAIR_TC = 40
 # the same when each output kind has its own tile generation (Ppad > 64): 2 x (25 + 5.5 + 2)
 ALU_OPS_PER_PAIR_TC_SPLIT = 65
+#   plain energy/potential pass: 13 shared (R^2, g, g', s, g g' s, reciprocal with its Newton
+#   step, Phi c) + 7 (1/s + 1/g and the three sums)
+ALU_OPS_PER_PAIR_EUW = 20
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
 # (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
 PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.2312e9}
@@ -221,6 +224,35 @@ def time_steps(vv, h, pb, prec, steps, warmup, world):
     return ms, nk, e, prof
 
 
+def time_calls(vv, h, pb, prec, reps):
+    """The two metric quantities on their own, device-resident, after the timed steps: the
+    energy + potential call (the plain E/U/W pass and its epilogue) and the Hessian
+    contraction call (trial preparation, contraction, epilogue; its A/B/C sums are formed
+    by the untimed first call and reused).  Milliseconds per call."""
+    import torch
+    d, o = pb.d, pb.out
+    vv.vv10_set_options(h, 0)
+    vv.vv10_prepare_points(h, d["xyz"], d["w"], d["rho"], d["grad"], d["atom"], pb.n_atom)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    vv.vv10_energy_potential(h, prec, o["vrho"], o["vgamma"], want_energy=False)
+    vv.vv10_hessian_contract(h, prec, d["rt"], d["gt"], o["frt"], o["fgt"])
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        vv.vv10_energy_potential(h, prec, o["vrho"], o["vgamma"], want_energy=False)
+    ev[1].record(stream)
+    vv.vv10_hessian_contract(h, prec, d["rt"], d["gt"], o["frt"], o["fgt"])  # A/B/C of this pass
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    for _ in range(reps):
+        vv.vv10_hessian_contract(h, prec, d["rt"], d["gt"], o["frt"], o["fgt"])
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    vv.vv10_set_options(h, vv.VV10_OPT_FUSE_HESSIAN_SUMS)  # as the step runs
+    return ev[0].elapsed_time(ev[1]) / reps, ev[2].elapsed_time(ev[3]) / reps
+
+
 def time_e2e(vv, h, pb, prec, steps, warmup):
     """Same step with host inputs: pinned H2D of every input and D2H of every output inside
     the timed region."""
@@ -319,20 +351,25 @@ def gpu_arm(args):
     K = args.steps
     per = {k: v[0] / K for k, v in prof.items()}
     launches = sum(v[1] for v in prof.values())
-    t_ep = per["pair_sums_EUW"] + per["energy_epilogue"]
-    t_hess = (per["pair_sums_ABC"] + per["trial_prep"] + per["contraction_fp64"] +
-              per["contraction_tensor_core"] + per["hessian_epilogue"])
     t_coord = per["pair_sums_grad"] + per["grad_epilogue"] + per["atom_resolved"]  # incl. the fused sums
     hess_flops = 8.0 * pairs_call * pb.P
+    ms_ep, ms_hc = time_calls(vv, h, pb, prec, 3)
+    alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     breakdown = {
-        "energy_potential_pairs_per_s": pairs_call / (t_ep / 1e3) if t_ep else None,
-        "hessian_pairs_per_s": pairs_call / (t_hess / 1e3) if t_hess else None,
-        "hessian_P_pairs_per_s": pb.P * pairs_call / (t_hess / 1e3) if t_hess else None,
-        "hessian_alg_tflops": hess_flops / (t_hess / 1e3) / 1e12 if t_hess else None,
-        "coord_grad_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
+        # the two metric quantities, each timed as its own entry point (3 calls each)
+        "energy_potential_call_ms": ms_ep,
+        "energy_potential_pairs_per_s": pairs_call / (ms_ep / 1e3),
+        "energy_potential_alu_frac": ALU_OPS_PER_PAIR_EUW * pairs_call / (ms_ep / 1e3) / alu_peak_ops,
+        "hessian_call_ms": ms_hc,
+        "hessian_pairs_per_s": pairs_call / (ms_hc / 1e3),
+        "hessian_P_pairs_per_s": pb.P * pairs_call / (ms_hc / 1e3),
+        "hessian_alg_tflops": hess_flops / (ms_hc / 1e3) / 1e12,
+        # the step's own phases
+        "step_pair_pass_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
-        "note": "one pass over the pairs (phase atom_resolved) forms the E/U/W and A/B/C row "
-                "sums, the atom-resolved terms and the point gradient; then the contraction",
+        "note": "in the step one pass over the pairs (phase atom_resolved) forms the E/U/W and "
+                "A/B/C row sums, the atom-resolved terms and the point gradient; then the "
+                "contraction",
     }
 
     # roofline of the dominant kernel
@@ -389,15 +426,16 @@ def gpu_arm(args):
         vv.vv10_set_autotune(h, 0)  # FP64 baseline at its default shapes
         ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
         per64 = {k: v[0] for k, v in prof64.items()}
-        t_h64 = (per64["pair_sums_ABC"] + per64["trial_prep"] + per64["contraction_fp64"] +
-                 per64["hessian_epilogue"])
+        ms_ep64, ms_hc64 = time_calls(vv, h, pb, vv.VV10_FP64, 1)
         result["fp64"] = {
             "value": 3.0 * pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
             "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
-            "energy_potential_pairs_per_s": pairs_call / ((per64["pair_sums_EUW"] + per64["energy_epilogue"]) / 1e3),
-            "hessian_pairs_per_s": pairs_call / (t_h64 / 1e3),
+            "energy_potential_pairs_per_s": pairs_call / (ms_ep64 / 1e3),
+            "hessian_pairs_per_s": pairs_call / (ms_hc64 / 1e3),
             "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
         }
+        result["speedup_mixed_vs_fp64_energy_potential"] = ms_ep64 / ms_ep
+        result["speedup_mixed_vs_fp64_hessian"] = ms_hc64 / ms_hc
         result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
 
     sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, max(1, min(K, 3)), 1)
@@ -634,7 +672,7 @@ def gpu_batch_arm(args):
                    "pair_count": "2 sum_m N_kept,m^2 (energy/potential + Hessian contraction)"},
         "roofline": roof, "gpu_launches": launches, "clocks": clocks,
         "tiles": {"batch_rows_per_thread_tiles_per_split": vv.vv10_get_tiles(h, vv.TILES_BATCH)},
-        "breakdown": {"energy_potential_pairs_per_s": pairs_step / (t_ep / 1e3) if t_ep else None,
+        "breakdown": {"energy_abc_pass_pairs_per_s": pairs_step / (t_ep / 1e3) if t_ep else None,
                       "hessian_pairs_per_s": pairs_step / (t_hess / 1e3) if t_hess else None,
                       "hessian_alg_tflops": hess_flops / (t_hess / 1e3) / 1e12 if t_hess else None,
                       "phase_ms_per_step": {k: round(v, 3) for k, v in per.items() if v}},
