@@ -424,6 +424,21 @@ class VV10:
         vv10_coord_grad(self.h, prec, gp, ga, euw, stream)
         return gp, ga, euw
 
+    def evaluate(self, prec=VV10_FP64, rho_t=None, grad_rho_t=None, resolved=False, stream=None):
+        """Energy, potential, Hessian contraction (when trials are given) and coordinate terms
+        in one vv10_evaluate call: (energy, vrho, vgamma, f_rho_t, f_gamma_t, grad_points,
+        grad_atoms, EUW_Bgr); atom outputs need atom labels at prepare time."""
+        dev = torch.device("cuda", self.device)
+        f64 = dict(dtype=torch.float64, device=dev)
+        vrho, vgamma = torch.empty(self.n, **f64), torch.empty(self.n, **f64)
+        fr = torch.empty_like(rho_t) if rho_t is not None else None
+        fg = torch.empty_like(rho_t) if rho_t is not None else None
+        gp = torch.empty(self.n, 3, **f64)
+        ga = torch.empty(self.n_atom, 3, **f64) if self.n_atom else None
+        euw = torch.empty(3, self.n, self.n_atom, 3, **f64) if resolved and self.n_atom else None
+        e = vv10_evaluate(self.h, prec, rho_t, grad_rho_t, fr, fg, vrho, vgamma, gp, ga, euw, stream)
+        return e, vrho, vgamma, fr, fg, gp, ga, euw
+
     def weight_grad(self, stream=None):
         out = torch.empty(self.n, dtype=torch.float64, device=torch.device("cuda", self.device))
         vv10_weight_grad(self.h, out, stream)
