@@ -141,3 +141,16 @@ def test_evaluate_everything_in_one_call(dev, case, prec, tol, resolved):
     # (the one-pass and the pair-sum kernels sum their FP32 tiles in different orders)
     assert abs(e0 - e) <= (1e-12 * abs(e) if prec == FP64 else 1e-7)
     eng.close()
+
+
+def test_engine_evaluate_convenience(dev, case):
+    g, rt, gt, ref = case
+    eng = vv10.VV10(0)
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
+                T(g.atom_of_point, dev, torch.int32), g.molecule.n_atom)
+    e, vr, vg, fr, fg, gp, ga, euw = eng.evaluate(MIXED, T(rt, dev), T(gt, dev), resolved=True)
+    assert abs(e - ref["e"]) <= 1e-7
+    assert rel(fr.cpu().numpy(), ref["fr"]) <= 1e-6 and rel(euw.cpu().numpy(), ref["euw"]) <= 1e-6
+    e2, *_ = eng.evaluate(MIXED)  # no trials, no atom-resolved terms
+    assert abs(e2 - ref["e"]) <= 1e-7
+    eng.close()
