@@ -71,10 +71,13 @@ def _load():
     lib.orc_point_grad.argtypes = [I64, P, P, P, P, D, D, D, I64, P, P]
     lib.orc_atom_grad.argtypes = [I64, P, P, P, P, P, I32, D, D, D, P]
     lib.orc_atom_resolved.argtypes = [I64, P, P, P, P, P, I32, D, D, D, I64, P, P, P, P]
+    lib.orc_point_coord_hessian.argtypes = [I64, P, P, P, P, P, I32, D, D, D, I64, P, P]
+    lib.orc_coord_hessian.argtypes = [I64, P, P, P, P, P, I32, D, D, D, P]
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_num_threads.argtypes = [ctypes.c_int]
     for name in ("orc_energy", "orc_pair_sums", "orc_potential", "orc_hessian_contract",
-                 "orc_point_grad", "orc_atom_grad", "orc_atom_resolved"):
+                 "orc_point_grad", "orc_atom_grad", "orc_atom_resolved", "orc_point_coord_hessian",
+                 "orc_coord_hessian"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -227,3 +230,28 @@ def atom_resolved(coords, weights, rho, grad_rho, atom_of_point, n_atom, rows=No
                                      b, C, rho_cut, nr, _ptr(rr), _ptr(oE), _ptr(oU), _ptr(oW)),
            "atom_resolved")
     return oE, oU, oW
+
+
+def point_coord_hessian(coords, weights, rho, grad_rho, atom_of_point, n_atom, rows=None,
+                        b=B_DEFAULT, C=C_DEFAULT, rho_cut=RHO_CUT_DEFAULT) -> np.ndarray:
+    """D_i^B (Sec. II.B), n_rows x n_atom x 3 x 3, zero for B = atom(i)."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    aop = np.ascontiguousarray(np.asarray(atom_of_point, dtype=np.int32))
+    rr, nr = _rows(rows, n)
+    out = np.zeros((nr, n_atom, 3, 3))
+    _check(_load().orc_point_coord_hessian(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), _ptr(aop),
+                                           n_atom, b, C, rho_cut, nr, _ptr(rr), _ptr(out)),
+           "point_coord_hessian")
+    return out
+
+
+def coord_hessian(coords, weights, rho, grad_rho, atom_of_point, n_atom, b=B_DEFAULT,
+                  C=C_DEFAULT, rho_cut=RHO_CUT_DEFAULT) -> np.ndarray:
+    """E^{AB}_{gr,gr} (Sec. II.B), n_atom x n_atom x 3 x 3: the grid-grid block of the
+    nuclear Hessian (points move with their atoms; rho, grad rho and w held fixed)."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    aop = np.ascontiguousarray(np.asarray(atom_of_point, dtype=np.int32))
+    out = np.zeros((n_atom, n_atom, 3, 3))
+    _check(_load().orc_coord_hessian(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), _ptr(aop), n_atom,
+                                     b, C, rho_cut, _ptr(out)), "coord_hessian")
+    return out

@@ -537,6 +537,120 @@ int orc_atom_resolved(int64_t n, const double* xyz, const double* w, const doubl
     return rc;
 }
 
+/* D_i^B, the three-by-three matrix of the grid-grid block (Sec. II.B, the equation for
+ * D_i^B), for i not in B:
+ *   D_i^B = -2 sum_{j in B} w_j rho_j Phi_ij [ 2 (D^2 + (omega_i/g)^2 + (omega_j/g')^2
+ *           + ((omega_i+omega_j)/(g+g'))^2) (r_j - r_i)(r_j - r_i)^T - D I_3 ],
+ * D the bracket of Eq. grad_gr.  pair_D adds the j term into acc[9] (row-major 3x3). */
+static void orc_pair_D(const orc_sys* s, int64_t i, int64_t j, nsum acc[9]) {
+    const orc_point* pi = &s->pt[i];
+    const orc_point* pj = &s->pt[j];
+    double R2 = orc_r2(s, i, j);
+    double g = pi->omega * R2 + pi->kappa;
+    double gp = pj->omega * R2 + pj->kappa;
+    double sg = g + gp;
+    double phi = -3.0 / (2.0 * g * gp * sg);
+    double D = orc_bracket(pi, pj, g, gp);
+    double a = pi->omega / g, bb = pj->omega / gp, c = (pi->omega + pj->omega) / sg;
+    double sq = 2.0 * (D * D + a * a + bb * bb + c * c);
+    double pre = -2.0 * s->w[j] * pj->rho * phi;
+    double dr[3];
+    for (int d = 0; d < 3; ++d) dr[d] = s->xyz[3 * j + d] - s->xyz[3 * i + d];
+    for (int u = 0; u < 3; ++u)
+        for (int v = 0; v < 3; ++v)
+            nsum_add(&acc[3 * u + v], pre * (sq * dr[u] * dr[v] - (u == v ? D : 0.0)));
+}
+
+/* D_i^B for selected rows: out n_rows x n_atom x 9 (zero for B = atom(i) and for rows
+ * below the cutoff). */
+int orc_point_coord_hessian(int64_t n, const double* xyz, const double* w, const double* rho,
+                            const double* grad, const int32_t* atom_of_point, int32_t n_atom,
+                            double b, double C, double rho_cut, int64_t n_rows,
+                            const int64_t* rows, double* out) {
+    orc_sys s;
+    if (orc_sys_init(&s, n, xyz, w, rho, grad, b, C, rho_cut)) return -1;
+    int rc = 0;
+#pragma omp parallel
+    {
+        nsum* acc = (nsum*)malloc(sizeof(nsum) * 9 * (size_t)n_atom);
+        if (!acc) {
+#pragma omp atomic write
+            rc = -1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t r = 0; r < n_rows; ++r) {
+            if (!acc) continue;
+            int64_t oi = rows ? rows[r] : r;
+            int64_t i = s.slot[oi];
+            double* o = out + (size_t)r * n_atom * 9;
+            memset(o, 0, sizeof(double) * 9 * (size_t)n_atom);
+            if (i < 0) continue;
+            memset(acc, 0, sizeof(nsum) * 9 * (size_t)n_atom);
+            int Ai = atom_of_point[oi];
+            for (int64_t j = 0; j < s.nk; ++j) {
+                int Bj = atom_of_point[s.kept[j]];
+                if (Bj == Ai) continue;
+                orc_pair_D(&s, i, j, &acc[9 * Bj]);
+            }
+            for (int32_t B = 0; B < n_atom; ++B)
+                if (B != Ai)
+                    for (int q = 0; q < 9; ++q) o[9 * B + q] = nsum_get(&acc[9 * B + q]);
+        }
+        free(acc);
+    }
+    orc_sys_free(&s);
+    return rc;
+}
+
+/* E^{AB}_{gr,gr} = sum_{i in A} w_i rho_i D_i^B for A != B, and E^{AA}_{gr,gr} = minus the
+ * sum over B != A (Sec. II.B): out n_atom x n_atom x 9, block (A, B) row-major 3x3. */
+int orc_coord_hessian(int64_t n, const double* xyz, const double* w, const double* rho,
+                      const double* grad, const int32_t* atom_of_point, int32_t n_atom, double b,
+                      double C, double rho_cut, double* out) {
+    orc_sys s;
+    if (orc_sys_init(&s, n, xyz, w, rho, grad, b, C, rho_cut)) return -1;
+    int rc = 0;
+#pragma omp parallel
+    {
+        nsum* acc = (nsum*)malloc(sizeof(nsum) * 9 * (size_t)n_atom);
+        nsum* dB = (nsum*)malloc(sizeof(nsum) * 9 * (size_t)n_atom);
+        if (!acc || !dB) {
+#pragma omp atomic write
+            rc = -1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t A = 0; A < n_atom; ++A) {
+            if (!acc || !dB) continue;
+            memset(acc, 0, sizeof(nsum) * 9 * (size_t)n_atom);
+            for (int64_t i = 0; i < s.nk; ++i) {
+                if (atom_of_point[s.kept[i]] != A) continue;
+                memset(dB, 0, sizeof(nsum) * 9 * (size_t)n_atom);
+                for (int64_t j = 0; j < s.nk; ++j) {
+                    int Bj = atom_of_point[s.kept[j]];
+                    if (Bj == A) continue;
+                    orc_pair_D(&s, i, j, &dB[9 * Bj]);
+                }
+                double ci = s.w[i] * s.pt[i].rho;
+                for (int32_t B = 0; B < n_atom; ++B)
+                    for (int q = 0; q < 9; ++q) nsum_add(&acc[9 * B + q], ci * nsum_get(&dB[9 * B + q]));
+            }
+            double* o = out + (size_t)A * n_atom * 9;
+            for (int32_t B = 0; B < n_atom; ++B)
+                for (int q = 0; q < 9; ++q) o[9 * B + q] = (B == A) ? 0.0 : nsum_get(&acc[9 * B + q]);
+            for (int q = 0; q < 9; ++q) {
+                nsum d = {0, 0};
+                for (int32_t B = 0; B < n_atom; ++B)
+                    if (B != A) nsum_add(&d, -o[9 * B + q]);
+                o[9 * A + q] = nsum_get(&d);
+            }
+        }
+        free(acc);
+        free(dB);
+    }
+    orc_sys_free(&s);
+    return rc;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -326,3 +326,58 @@ def test_row_sampling_matches_full(oracle_mod):
     fr2, fg2 = oracle_mod.hessian_contract(*args, rt, gt, rows=rows)
     np.testing.assert_array_equal(fr2, fr[:, rows])
     np.testing.assert_array_equal(fg2, fg[:, rows])
+
+
+# ----------------------------------------------------------------- grid-grid Hessian block
+
+def _rigid(g, atom, d, h):
+    c = g.coords.copy()
+    c[g.atom_of_point == atom, d] += h
+    return c
+
+
+def test_coord_hessian_is_derivative_of_atom_gradient(oracle_mod):
+    """E^{AB}_{gr,gr} (the D_i^B sums and the minus-sum diagonal) equals central finite
+    differences of E^A_gr when the points of atom B move rigidly (rho, grad rho, w fixed)."""
+    g = synth.random_points(70, seed=31, n_atom=3)
+    na = 3
+    H = oracle_mod.coord_hessian(g.coords, g.weights, g.rho, g.grad_rho, g.atom_of_point, na)
+    h = 1e-4
+    for B in range(na):
+        for d in range(3):
+            gp = oracle_mod.atom_grad(_rigid(g, B, d, h), g.weights, g.rho, g.grad_rho, g.atom_of_point, na)
+            gm = oracle_mod.atom_grad(_rigid(g, B, d, -h), g.weights, g.rho, g.grad_rho, g.atom_of_point, na)
+            fd = (gp - gm) / (2 * h)  # fd[A, c] = d E^A_{gr,c} / d R_{B,d}
+            for A in range(na):
+                np.testing.assert_allclose(H[A, B, :, d], fd[A], rtol=1e-6, atol=1e-9 * np.abs(H).max())
+
+
+def test_coord_hessian_symmetry_and_invariances(oracle_mod):
+    g = synth.random_points(80, seed=33, n_atom=4)
+    na = 4
+    args = (g.coords, g.weights, g.rho, g.grad_rho, g.atom_of_point, na)
+    H = oracle_mod.coord_hessian(*args)
+    scale = np.abs(H).max()
+    # a symmetric Hessian: E^{AB} = (E^{BA})^T, each off-diagonal block itself symmetric
+    np.testing.assert_allclose(H, H.transpose(1, 0, 3, 2), atol=1e-13 * scale)
+    np.testing.assert_allclose(H, H.transpose(0, 1, 3, 2), atol=1e-13 * scale)
+    # translational invariance: every block row sums to zero
+    np.testing.assert_allclose(H.sum(axis=1), 0.0, atol=1e-12 * scale)
+    # rotating the whole system (coordinates and density gradients) rotates every block
+    th = 0.7
+    Rm = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]]) @ \
+        np.array([[1, 0, 0], [0, np.cos(0.3), -np.sin(0.3)], [0, np.sin(0.3), np.cos(0.3)]])
+    Hr = oracle_mod.coord_hessian(g.coords @ Rm.T, g.weights, g.rho, g.grad_rho @ Rm.T,
+                                  g.atom_of_point, na)
+    np.testing.assert_allclose(Hr, np.einsum("uv,abvw,xw->abux", Rm, H, Rm), atol=1e-11 * scale)
+    # the per-point matrices sum to the blocks: E^{AB} = sum_{i in A} w_i rho_i D_i^B
+    Dp = oracle_mod.point_coord_hessian(*args)
+    kept = g.rho >= 1e-10
+    for A in range(na):
+        m = (g.atom_of_point == A) & kept
+        blk = np.einsum("i,ibuv->buv", (g.weights * g.rho)[m], Dp[m])
+        for B in range(na):
+            if B != A:
+                np.testing.assert_allclose(blk[B], H[A, B], rtol=1e-10, atol=1e-13 * scale)
+            else:
+                assert not Dp[m][:, A].any()  # D_i^B is defined for i not in B only
