@@ -150,6 +150,27 @@ vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P,
 vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_points,
                             double* grad_atoms, double* EUW_Bgr, void* stream);
 
+/* Grid-grid block of the nuclear Hessian (Sec. II.B, the E^{AB}_{gr,gr} line of the nuclear
+ * second derivative and the D_i^B equation that follows it): for a kept point i and an atom
+ * B that does not own it,
+ *   D_i^B = -2 sum_{j in B} w_j rho_j Phi_ij [ 2 (D_ij^2 + (omega_i/g)^2 + (omega_j/g')^2
+ *           + ((omega_i + omega_j)/(g + g'))^2) (r_j - r_i)(r_j - r_i)^T - D_ij I_3 ],
+ * D_ij as for vv10_coord_grad, and
+ *   E^{AB}_{gr,gr} = sum_{i in A} w_i rho_i D_i^B (A != B),
+ *   E^{AA}_{gr,gr} = -sum_{B != A} E^{AB}_{gr,gr} (translational invariance).
+ * This is the second derivative of E with respect to the positions of the grid points
+ * (each moving with its atom) with rho, grad rho and w held fixed.
+ *   E_grgr     n_atom x n_atom x 3 x 3 device out (may be NULL): block (A, B) row-major
+ *   D_points   n x n_atom x 3 x 3 device out (may be NULL): D_i^B in the caller's point
+ *              order; zero for B = atom(i) and for points below rho_cut
+ *   prec       VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ * Needs atom_of_point at prepare time (else INVALID_ARG) and no earlier call other than
+ * vv10_prepare_points.  Holds about 48 n_atom (n / 128 + n_atom) bytes of scratch.  The
+ * blocks are summed in a fixed order: repeated calls give identical results.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grgr,
+                               double* D_points, void* stream);
+
 /* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
  * by the last vv10_energy_potential call.  dEdw: n device out. */
 vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
@@ -315,7 +336,7 @@ vv10_status vv10_set_autotune(vv10_handle h, int flags);
  * vv10_profile_read synchronises the device, writes for phases 0..n-1 (n <= VV10_N_PHASES)
  * the accumulated milliseconds (ms, may be NULL; 0 when timing was off) and launch counts
  * (launches, may be NULL), then resets both.  Phase names: vv10_profile_phase_name. */
-#define VV10_N_PHASES 11
+#define VV10_N_PHASES 12
 vv10_status vv10_profile_enable(vv10_handle h, int on);
 vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches);
 const char* vv10_profile_phase_name(int phase);

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -630,6 +630,44 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
     return VV10_OK;
 }
 
+vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grgr,
+                               double* D_points, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (h->P.n_atom == 0) {
+        h->set_error("the grid-grid Hessian needs atom_of_point at prepare time");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    void* outs[] = {E_grgr, D_points};
+    for (void* q : outs)
+        if (q && (!device_ptr_ok(q, h->device) || !aligned(q, 8))) {
+            h->set_error("outputs must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    if (!E_grgr && !D_points) return VV10_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool fp64 = (prec == VV10_FP64);
+    PointsDev& P = h->P;
+    const size_t na = static_cast<size_t>(P.n_atom);
+    // per-CTA partials, then room for the blocks when only D_i^B is asked for
+    const size_t n_part = 6 * na * static_cast<size_t>(coord_hessian_cta_bound(P.nk, P.n_atom));
+    VV10_TRY(h->ensure(h->chpart, sizeof(double) * (n_part + (E_grgr ? 0 : 9 * na * na)),
+                       "grid-grid Hessian partials"));
+    double* part = static_cast<double*>(h->chpart.p);
+    double* E = E_grgr ? E_grgr : part + n_part;
+    if (D_points)
+        VV10_CUDA(h, cudaMemsetAsync(D_points, 0, sizeof(double) * 9 * na * P.n, st), "memset");
+    PhaseScope ph(h, PH_COORD_HESSIAN, st, P.nk > 0 ? 2 : 1);
+    VV10_CUDA(h, launch_coord_hessian(P, fp64, part, E, D_points, st), "grid-grid Hessian");
+    return VV10_OK;
+}
+
 vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
                           const double* rho_t, const double* grad_rho_t, double* energy,
                           double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
@@ -773,7 +811,7 @@ const char* vv10_profile_phase_name(int phase) {
     static const char* names[PH_COUNT] = {
         "prepare", "pair_sums_EUW", "energy_epilogue", "pair_sums_ABC", "trial_prep",
         "contraction_fp64", "contraction_tensor_core", "hessian_epilogue", "pair_sums_grad",
-        "grad_epilogue", "atom_resolved"};
+        "grad_epilogue", "atom_resolved", "coord_hessian"};
     return (phase >= 0 && phase < PH_COUNT) ? names[phase] : "unknown";
 }
 

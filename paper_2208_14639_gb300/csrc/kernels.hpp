@@ -169,4 +169,12 @@ cudaError_t launch_atom_sums(const PointsDev& p, const double* gk, double* grad_
 cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, double* gk,
                                  double* grad_points, double* sums, int* err, cudaStream_t st);
 
+// Grid-grid block of the nuclear Hessian (Sec. II.B): E (n_atom x n_atom x 3 x 3) receives
+// the blocks E^{AB}_{gr,gr}, Dout (n x n_atom x 3 x 3, zeroed beforehand), when not null,
+// the D_i^B of the kept rows.  part: coord_hessian_cta_bound(nk, n_atom) x n_atom x 6
+// scratch.  An empty grid gives zero blocks.
+int64_t coord_hessian_cta_bound(int64_t nk, int32_t n_atom);
+cudaError_t launch_coord_hessian(const PointsDev& p, bool fp64, double* part, double* E,
+                                 double* Dout, cudaStream_t st);
+
 }  // namespace vv10

@@ -47,9 +47,9 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_profile_phase_name", "vv10_energy_potential_noalloc",
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
-           "vv10_set_options", "vv10_evaluate")
+           "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian")
 VV10_NOALLOC_MAX_POINTS = 32768
-VV10_N_PHASES = 11
+VV10_N_PHASES = 12
 
 
 class VV10Params(ctypes.Structure):
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = False):
         "vv10_energy_potential": (st, [P, st, ctypes.POINTER(D), P, P, P]),
         "vv10_hessian_contract": (st, [P, st, I32, P, P, P, P, P]),
         "vv10_coord_grad": (st, [P, st, P, P, P, P]),
+        "vv10_coord_hessian": (st, [P, st, P, P, P]),
         "vv10_weight_grad": (st, [P, P, P]),
         "vv10_sync": (st, [P, P]),
         "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -210,6 +211,12 @@ def vv10_coord_grad(h, prec: int, grad_points=None, grad_atoms=None, EUW_Bgr=Non
                                 _dptr(grad_atoms, "grad_atoms"), _dptr(EUW_Bgr, "EUW_Bgr"),
                                 _stream(stream))
     _check(h, st, "vv10_coord_grad")
+
+
+def vv10_coord_hessian(h, prec: int, E_grgr=None, D_points=None, stream=None) -> None:
+    st = load().vv10_coord_hessian(h, int(prec), _dptr(E_grgr, "E_grgr"),
+                                   _dptr(D_points, "D_points"), _stream(stream))
+    _check(h, st, "vv10_coord_hessian")
 
 
 def vv10_weight_grad(h, dEdw, stream=None) -> None:
@@ -423,6 +430,16 @@ class VV10:
                if resolved and self.n_atom else None)
         vv10_coord_grad(self.h, prec, gp, ga, euw, stream)
         return gp, ga, euw
+
+    def coord_hessian(self, prec=VV10_FP64, points=False, stream=None):
+        """Grid-grid nuclear Hessian blocks E^{AB}_{gr,gr} as (n_atom, n_atom, 3, 3) and, when
+        points is set, D_i^B as (n, n_atom, 3, 3); needs atom labels at prepare time."""
+        dev = torch.device("cuda", self.device)
+        f64 = dict(dtype=torch.float64, device=dev)
+        E = torch.empty(self.n_atom, self.n_atom, 3, 3, **f64)
+        D = torch.empty(self.n, self.n_atom, 3, 3, **f64) if points else None
+        vv10_coord_hessian(self.h, prec, E, D, stream)
+        return E, D
 
     def evaluate(self, prec=VV10_FP64, rho_t=None, grad_rho_t=None, resolved=False, stream=None):
         """Energy, potential, Hessian contraction (when trials are given) and coordinate terms
