@@ -49,6 +49,10 @@ ALU_OPS_PER_PAIR_TC_SPLIT = 65
 #   plain energy/potential pass: 13 shared (R^2, g, g', s, g g' s, reciprocal with its Newton
 #   step, Phi c) + 7 (1/s + 1/g and the three sums)
 ALU_OPS_PER_PAIR_EUW = 20
+#   grid-grid Hessian block D_i^B: the same 13 shared, 10 for 1/(g g'), 1/s, omega_i/g,
+#   omega_j/g', (omega_i+omega_j)/s and D, 4 for the squared bracket, 4 for the scaled
+#   displacement, 6 outer-product and 1 identity-term accumulations
+ALU_OPS_PER_PAIR_CH = 38
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
 # (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
 PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.2312e9}
@@ -257,6 +261,31 @@ def time_calls(vv, h, pb, prec, reps):
     return ev[0].elapsed_time(ev[1]) / reps, ev[2].elapsed_time(ev[3]) / reps
 
 
+def coord_hessian_pairs(pb):
+    """Pairs the grid-grid Hessian blocks need: the unordered pairs {i, j} of kept points of
+    different atoms (the pair term is symmetric, so E^{BA} = E^{AB})."""
+    kept = pb.host["rho"] >= 1e-10
+    n_a = np.bincount(pb.host["atom"][kept], minlength=pb.n_atom).astype(np.float64)
+    return float(n_a.sum() ** 2 - (n_a ** 2).sum()) / 2.0
+
+
+def time_coord_hessian(vv, h, pb, prec, reps):
+    """The grid-grid nuclear Hessian block (vv10_coord_hessian, the E^{AB}_{gr,gr} blocks
+    only) on the prepared points, device-resident: milliseconds per call."""
+    import torch
+    E = torch.empty(pb.n_atom, pb.n_atom, 3, 3, dtype=torch.float64, device=pb.d["xyz"].device)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    vv.vv10_coord_hessian(h, prec, E, None)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        vv.vv10_coord_hessian(h, prec, E, None)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps
+
+
 def time_e2e(vv, h, pb, prec, steps, warmup):
     """The same step with host inputs: every step copies all of its inputs from pinned host
     memory to the device and all of its outputs back, inside the timed region.  The copies
@@ -385,6 +414,8 @@ def gpu_arm(args):
     t_coord = per["pair_sums_grad"] + per["grad_epilogue"] + per["atom_resolved"]  # incl. the fused sums
     hess_flops = 8.0 * pairs_call * pb.P
     ms_ep, ms_hc = time_calls(vv, h, pb, prec, 3)
+    ms_ch = time_coord_hessian(vv, h, pb, prec, 3)
+    pairs_ch = coord_hessian_pairs(pb)
     alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     breakdown = {
         # the two metric quantities, each timed as its own entry point (3 calls each)
@@ -395,6 +426,11 @@ def gpu_arm(args):
         "hessian_pairs_per_s": pairs_call / (ms_hc / 1e3),
         "hessian_P_pairs_per_s": pb.P * pairs_call / (ms_hc / 1e3),
         "hessian_alg_tflops": hess_flops / (ms_hc / 1e3) / 1e12,
+        # the grid-grid nuclear Hessian block (not part of the step)
+        "coord_hessian_call_ms": ms_ch,
+        "coord_hessian_pairs": pairs_ch,
+        "coord_hessian_pairs_per_s": pairs_ch / (ms_ch / 1e3),
+        "coord_hessian_alu_frac": ALU_OPS_PER_PAIR_CH * pairs_ch / (ms_ch / 1e3) / alu_peak_ops,
         # the step's own phases
         "step_pair_pass_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
@@ -461,15 +497,18 @@ def gpu_arm(args):
         ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
         per64 = {k: v[0] for k, v in prof64.items()}
         ms_ep64, ms_hc64 = time_calls(vv, h, pb, vv.VV10_FP64, 1)
+        ms_ch64 = time_coord_hessian(vv, h, pb, vv.VV10_FP64, 1)
         result["fp64"] = {
             "value": 3.0 * pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
             "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
             "energy_potential_pairs_per_s": pairs_call / (ms_ep64 / 1e3),
             "hessian_pairs_per_s": pairs_call / (ms_hc64 / 1e3),
+            "coord_hessian_pairs_per_s": pairs_ch / (ms_ch64 / 1e3),
             "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
         }
         result["speedup_mixed_vs_fp64_energy_potential"] = ms_ep64 / ms_ep
         result["speedup_mixed_vs_fp64_hessian"] = ms_hc64 / ms_hc
+        result["speedup_mixed_vs_fp64_coord_hessian"] = ms_ch64 / ms_ch
         result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
 
     sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, K, 1)

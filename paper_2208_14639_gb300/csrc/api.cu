@@ -655,16 +655,18 @@ vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grg
     const bool fp64 = (prec == VV10_FP64);
     PointsDev& P = h->P;
     const size_t na = static_cast<size_t>(P.n_atom);
-    // per-CTA partials, then room for the blocks when only D_i^B is asked for
-    const size_t n_part = 6 * na * static_cast<size_t>(coord_hessian_cta_bound(P.nk, P.n_atom));
-    VV10_TRY(h->ensure(h->chpart, sizeof(double) * (n_part + (E_grgr ? 0 : 9 * na * na)),
+    // chunk offsets, per-task partials, then room for the blocks when only D_i^B is asked for
+    const size_t n_off = (na + 1 + 1) & ~static_cast<size_t>(1);  // keeps part 16-byte aligned
+    const size_t n_part = 6 * na * static_cast<size_t>(coord_hessian_chunk_bound(P.nk, P.n_atom));
+    VV10_TRY(h->ensure(h->chpart, sizeof(double) * (n_off + n_part + (E_grgr ? 0 : 9 * na * na)),
                        "grid-grid Hessian partials"));
-    double* part = static_cast<double*>(h->chpart.p);
+    int64_t* off = static_cast<int64_t*>(h->chpart.p);
+    double* part = static_cast<double*>(h->chpart.p) + n_off;
     double* E = E_grgr ? E_grgr : part + n_part;
     if (D_points)
         VV10_CUDA(h, cudaMemsetAsync(D_points, 0, sizeof(double) * 9 * na * P.n, st), "memset");
-    PhaseScope ph(h, PH_COORD_HESSIAN, st, P.nk > 0 ? 2 : 1);
-    VV10_CUDA(h, launch_coord_hessian(P, fp64, part, E, D_points, st), "grid-grid Hessian");
+    PhaseScope ph(h, PH_COORD_HESSIAN, st, (P.nk > 0 && P.n_atom > 1) ? 3 : 2);
+    VV10_CUDA(h, launch_coord_hessian(P, fp64, off, part, E, D_points, st), "grid-grid Hessian");
     return VV10_OK;
 }
 

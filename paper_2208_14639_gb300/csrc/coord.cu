@@ -217,152 +217,148 @@ k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
 //           + ((omega_i+omega_j)/s)^2) (r_j - r_i)(r_j - r_i)^T - D I_3 ],
 // D = omega_i/g + omega_j/g' + (omega_i+omega_j)/s, and the blocks
 //   E^{AB}_{gr,gr} = sum_{i in A} w_i rho_i D_i^B (A != B),  E^{AA} = -sum_{B != A} E^{AB}.
-// Kept rows are grouped by atom, so each CTA takes up to 128 rows of one atom A: the own
-// atom is skipped by the whole CTA, and the CTA reduces w_i rho_i D_i^B over its rows
-// (fixed order) into part[cta][B][6] (the 6 entries of the symmetric 3x3).  FP32 (or
-// FP64) arithmetic within a j tile, FP64 across tiles.
+// Kept rows are grouped by atom and cut into chunks of kArThreads rows within one atom; a
+// task is (chunk c of atom A, atom B != A), one CTA each, and reduces w_i rho_i D_i^B over
+// its rows (fixed order) into part[c][B][6] (the 6 entries of the symmetric 3x3).  FP32
+// (or FP64) arithmetic within a j tile, FP64 across tiles.
+//
+// The pair term is symmetric in i <-> j, so E^{AB} = E^{BA} (and each block is symmetric):
+// when only the blocks are asked for, the tasks with B < A are skipped and E^{BA} is read
+// from the same partials, which halves the pair evaluations.
 
-// CTA c's atom and first row, with the CTAs of each atom's segment numbered in atom order
-// (chunks of kArThreads rows); c past the last chunk gives atom -1.
-__device__ __forceinline__ int coord_hess_chunk(const PointsDev& P, int64_t c, int64_t* row0) {
-    int64_t base = 0;
+// off[a] = chunks of the atoms before a, off[n_atom] = all chunks.
+__global__ void k_chunk_offsets(PointsDev P, int64_t* __restrict__ off) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t c = 0;
     for (int a = 0; a < P.n_atom; ++a) {
-        const int64_t na = P.seg[a + 1] - P.seg[a];
-        const int64_t nc = (na + kArThreads - 1) / kArThreads;
-        if (c < base + nc) {
-            *row0 = P.seg[a] + (c - base) * kArThreads;
-            return a;
-        }
-        base += nc;
+        off[a] = c;
+        c += (P.seg[a + 1] - P.seg[a] + kArThreads - 1) / kArThreads;
     }
-    *row0 = 0;
-    return -1;
+    off[P.n_atom] = c;
 }
 
-template <class T>
+template <class T, bool HALF>
 __global__ void __launch_bounds__(kArThreads)
 k_coord_hessian(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
-                const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ part,
-                double* __restrict__ Dout) {
+                const typename RecsAR<T>::B* __restrict__ rb, const int64_t* __restrict__ off,
+                double* __restrict__ part, double* __restrict__ Dout) {
     using RA = typename RecsAR<T>::A;
     using RB = typename RecsAR<T>::B;
     __shared__ RA sa[kArJT];
     __shared__ RB sb[kArJT];
     __shared__ double sred[6][kArThreads / 32];
-    __shared__ int s_atom;
-    __shared__ int64_t s_row0;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) {
-        int64_t r0 = 0;
-        s_atom = coord_hess_chunk(P, blockIdx.x, &r0);
-        s_row0 = r0;
+    const int64_t c = blockIdx.x;
+    const int B = blockIdx.y;
+    if (c >= off[P.n_atom]) return;  // every exit below is uniform over the CTA
+    int lo = 0, hi = P.n_atom;       // atom A of chunk c: the last a with off[a] <= c
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= c) lo = mid;
+        else hi = mid;
     }
-    __syncthreads();
-    const int A = s_atom;
-    if (A < 0) return;  // whole CTA
-    const int64_t i = s_row0 + tid;
+    const int A = lo;
+    if (B == A || (HALF && B < A)) return;
+    const int64_t s0 = P.seg[B], s1 = P.seg[B + 1];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t i = P.seg[A] + (c - off[A]) * kArThreads + tid;
     const bool valid = i < P.seg[A + 1];
     T xi = 0, yi = 0, zi = 0, oi = 1, ki = 1;
     double ci = 0.0;
-    int64_t oi_idx = 0;
     if (valid) {
         const RA a = ra[i];
         const RB b = rb[i];
         xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y;
         ci = P.w[i] * P.rho[i];
-        oi_idx = P.orig[i];
     }
-    for (int B = 0; B < P.n_atom; ++B) {
-        if (B == A) continue;  // uniform over the CTA
-        const int64_t s0 = P.seg[B], s1 = P.seg[B + 1];
-        double tot[7] = {0, 0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz of the outer products; I term
-        for (int64_t j0 = s0; j0 < s1; j0 += kArJT) {
-            __syncthreads();
-            for (int t = tid; t < kArJT; t += kArThreads)
-                if (j0 + t < s1) {
-                    sa[t] = ra[j0 + t];
-                    sb[t] = rb[j0 + t];
-                }
-            __syncthreads();
-            const int cnt = static_cast<int>(s1 - j0 < kArJT ? s1 - j0 : kArJT);
-            T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-            for (int jj = 0; jj < cnt; ++jj) {
-                const RA a = sa[jj];
-                const RB b = sb[jj];
-                const T dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
-                const T r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
-                const T g = fmadd(oi, r2, ki);
-                const T gp = fmadd(b.x, r2, b.y);
-                const T s = g + gp;
-                const T ggp = g * gp;
-                const T inv = recip(ggp * s);
-                const T ph = a.w * inv;          // w_j rho_j Phi_ij
-                const T sinv = s * inv;          // 1/(g g')
-                const T L = ggp * inv;           // 1/s
-                const T oG = oi * (gp * sinv);   // omega_i/g
-                const T bG = b.x * (g * sinv);   // omega_j/g'
-                const T q = (oi + b.x) * L;      // (omega_i + omega_j)/s
-                const T D = oG + bG + q;
-                const T sq = T(2) * fmadd(D, D, fmadd(oG, oG, fmadd(bG, bG, q * q)));
-                const T av = ph * sq;
-                const T tx = av * dx, ty = av * dy;
-                acc[0] = fmadd(tx, dx, acc[0]);
-                acc[1] = fmadd(tx, dy, acc[1]);
-                acc[2] = fmadd(tx, dz, acc[2]);
-                acc[3] = fmadd(ty, dy, acc[3]);
-                acc[4] = fmadd(ty, dz, acc[4]);
-                acc[5] = fmadd(av * dz, dz, acc[5]);
-                acc[6] = fmadd(ph, D, acc[6]);
+    double tot[7] = {0, 0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz of the outer products; I term
+    for (int64_t j0 = s0; j0 < s1; j0 += kArJT) {
+        __syncthreads();
+        for (int t = tid; t < kArJT; t += kArThreads)
+            if (j0 + t < s1) {
+                sa[t] = ra[j0 + t];
+                sb[t] = rb[j0 + t];
             }
-#pragma unroll
-            for (int k = 0; k < 7; ++k) tot[k] += static_cast<double>(acc[k]);
-        }
-        // D_i^B = -2 (S - S_I I), S the outer-product sum, S_I the identity term
-        double d6[6] = {-2.0 * (tot[0] - tot[6]), -2.0 * tot[1], -2.0 * tot[2],
-                        -2.0 * (tot[3] - tot[6]), -2.0 * tot[4], -2.0 * (tot[5] - tot[6])};
-        if (!valid) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) d6[k] = 0.0;
-        } else if (Dout) {
-            double* o = Dout + (oi_idx * P.n_atom + B) * 9;
-            o[0] = d6[0]; o[1] = d6[1]; o[2] = d6[2];
-            o[3] = d6[1]; o[4] = d6[3]; o[5] = d6[4];
-            o[6] = d6[2]; o[7] = d6[4]; o[8] = d6[5];
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const double v = warp_sum(ci * d6[k]);
-            if (lane == 0) sred[k][wid] = v;
-        }
         __syncthreads();
-        if (tid < 6) {
-            double v = 0.0;
-#pragma unroll
-            for (int w = 0; w < kArThreads / 32; ++w) v += sred[tid][w];
-            part[(static_cast<int64_t>(blockIdx.x) * P.n_atom + B) * 6 + tid] = v;
+        const int cnt = static_cast<int>(s1 - j0 < kArJT ? s1 - j0 : kArJT);
+        T acc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        for (int jj = 0; jj < cnt; ++jj) {
+            const RA a = sa[jj];
+            const RB b = sb[jj];
+            const T dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+            const T r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
+            const T g = fmadd(oi, r2, ki);
+            const T gp = fmadd(b.x, r2, b.y);
+            const T s = g + gp;
+            const T ggp = g * gp;
+            const T inv = recip(ggp * s);
+            const T ph = a.w * inv;          // w_j rho_j Phi_ij
+            const T sinv = s * inv;          // 1/(g g')
+            const T L = ggp * inv;           // 1/s
+            const T oG = oi * (gp * sinv);   // omega_i/g
+            const T bG = b.x * (g * sinv);   // omega_j/g'
+            const T q = (oi + b.x) * L;      // (omega_i + omega_j)/s
+            const T D = oG + bG + q;
+            // half the squared bracket; the factor 2 is applied to the sums
+            const T av = ph * fmadd(D, D, fmadd(oG, oG, fmadd(bG, bG, q * q)));
+            const T tx = av * dx, ty = av * dy;
+            acc[0] = fmadd(tx, dx, acc[0]);
+            acc[1] = fmadd(tx, dy, acc[1]);
+            acc[2] = fmadd(tx, dz, acc[2]);
+            acc[3] = fmadd(ty, dy, acc[3]);
+            acc[4] = fmadd(ty, dz, acc[4]);
+            acc[5] = fmadd(av * dz, dz, acc[5]);
+            acc[6] = fmadd(ph, D, acc[6]);
         }
-        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 7; ++k) tot[k] += static_cast<double>(acc[k]);
+    }
+    // D_i^B = -2 (2 S - S_I I), S the (halved) outer-product sum, S_I the identity term
+    double d6[6] = {-2.0 * (2.0 * tot[0] - tot[6]), -4.0 * tot[1], -4.0 * tot[2],
+                    -2.0 * (2.0 * tot[3] - tot[6]), -4.0 * tot[4], -2.0 * (2.0 * tot[5] - tot[6])};
+    if (!valid) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) d6[k] = 0.0;
+    } else if (Dout) {
+        double* o = Dout + (P.orig[i] * P.n_atom + B) * 9;
+        o[0] = d6[0]; o[1] = d6[1]; o[2] = d6[2];
+        o[3] = d6[1]; o[4] = d6[3]; o[5] = d6[4];
+        o[6] = d6[2]; o[7] = d6[4]; o[8] = d6[5];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = warp_sum(ci * d6[k]);
+        if (lane == 0) sred[k][wid] = v;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kArThreads / 32; ++w) v += sred[tid][w];
+        part[(c * P.n_atom + B) * 6 + tid] = v;
     }
 }
 
-// One CTA per atom A: warp k sums the CTA partials of A for B = k, k + 8, ... (fixed order,
-// lane-strided then a fixed shuffle tree), writes E^{AB}; then the diagonal block.
+// One CTA per atom A: warp k forms the blocks E^{AB} for B = k, k + 8, ... from the CTA
+// partials (lane-strided over the chunks in a fixed order, then a fixed shuffle tree), then
+// the diagonal block.  With HALF, E^{AB} for B < A is the sum that the CTA of atom B forms
+// for E^{BA} (chunks of B, column A), so the two agree exactly.
 constexpr int kChBlkThreads = 256;
+template <bool HALF>
 __global__ void __launch_bounds__(kChBlkThreads)
-k_coord_hessian_blocks(PointsDev P, const double* __restrict__ part, double* __restrict__ E) {
+k_coord_hessian_blocks(PointsDev P, const int64_t* __restrict__ off,
+                       const double* __restrict__ part, double* __restrict__ E) {
     const int A = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // CTAs of atom A: [c0, c1)
-    int64_t c0 = 0;
-    for (int a = 0; a < A; ++a) c0 += (P.seg[a + 1] - P.seg[a] + kArThreads - 1) / kArThreads;
-    const int64_t c1 = c0 + (P.seg[A + 1] - P.seg[A] + kArThreads - 1) / kArThreads;
     const int64_t na = P.n_atom;
     for (int B = wid; B < P.n_atom; B += kChBlkThreads / 32) {
         if (B == A) continue;
+        const bool mirror = HALF && B < A;
+        const int owner = mirror ? B : A, col = mirror ? A : B;
+        const int64_t c0 = off[owner], c1 = off[owner + 1];
         double v[6] = {0, 0, 0, 0, 0, 0};
         for (int64_t c = c0 + lane; c < c1; c += 32)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] += part[(c * na + B) * 6 + k];
+            for (int k = 0; k < 6; ++k) v[k] += part[(c * na + col) * 6 + k];
 #pragma unroll
         for (int k = 0; k < 6; ++k) v[k] = warp_sum(v[k]);
         if (lane == 0) {
@@ -381,23 +377,33 @@ k_coord_hessian_blocks(PointsDev P, const double* __restrict__ part, double* __r
     }
 }
 
-// Upper bound on the CTAs of k_coord_hessian: one per kArThreads rows, plus one partial
-// chunk per atom.
-int64_t coord_hessian_cta_bound(int64_t nk, int32_t n_atom) {
+// Upper bound on the row chunks: one per kArThreads rows, plus one partial chunk per atom.
+int64_t coord_hessian_chunk_bound(int64_t nk, int32_t n_atom) {
     return cdiv64(nk, kArThreads) + (n_atom > 0 ? n_atom : 0);
 }
 
-cudaError_t launch_coord_hessian(const PointsDev& p, bool fp64, double* part, double* E,
-                                 double* Dout, cudaStream_t st) {
+cudaError_t launch_coord_hessian(const PointsDev& p, bool fp64, int64_t* off, double* part,
+                                 double* E, double* Dout, cudaStream_t st) {
     if (p.n_atom <= 0) return cudaSuccess;
-    if (p.nk > 0) {
-        const unsigned g = static_cast<unsigned>(coord_hessian_cta_bound(p.nk, p.n_atom));
-        if (fp64) k_coord_hessian<double><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, part, Dout);
-        else k_coord_hessian<float><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, part, Dout);
-        cudaError_t e = cudaGetLastError();
+    k_chunk_offsets<<<1, 32, 0, st>>>(p, off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const bool half = (Dout == nullptr);
+    if (p.nk > 0 && p.n_atom > 1) {
+        const dim3 g(static_cast<unsigned>(coord_hessian_chunk_bound(p.nk, p.n_atom)),
+                     static_cast<unsigned>(p.n_atom));
+        if (fp64) {
+            if (half) k_coord_hessian<double, true><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, off, part, Dout);
+            else k_coord_hessian<double, false><<<g, kArThreads, 0, st>>>(p, p.r64a, p.r64b, off, part, Dout);
+        } else {
+            if (half) k_coord_hessian<float, true><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, off, part, Dout);
+            else k_coord_hessian<float, false><<<g, kArThreads, 0, st>>>(p, p.r32a, p.r32b, off, part, Dout);
+        }
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_coord_hessian_blocks<<<p.n_atom, kChBlkThreads, 0, st>>>(p, part, E);
+    if (half) k_coord_hessian_blocks<true><<<p.n_atom, kChBlkThreads, 0, st>>>(p, off, part, E);
+    else k_coord_hessian_blocks<false><<<p.n_atom, kChBlkThreads, 0, st>>>(p, off, part, E);
     return cudaGetLastError();
 }
 

@@ -171,10 +171,11 @@ cudaError_t launch_atom_resolved(const PointsDev& p, bool fp64, double* out, dou
 
 // Grid-grid block of the nuclear Hessian (Sec. II.B): E (n_atom x n_atom x 3 x 3) receives
 // the blocks E^{AB}_{gr,gr}, Dout (n x n_atom x 3 x 3, zeroed beforehand), when not null,
-// the D_i^B of the kept rows.  part: coord_hessian_cta_bound(nk, n_atom) x n_atom x 6
-// scratch.  An empty grid gives zero blocks.
-int64_t coord_hessian_cta_bound(int64_t nk, int32_t n_atom);
-cudaError_t launch_coord_hessian(const PointsDev& p, bool fp64, double* part, double* E,
-                                 double* Dout, cudaStream_t st);
+// the D_i^B of the kept rows; without Dout only the atom pairs A < B are evaluated.
+// Scratch: off (n_atom + 1 int64), part (coord_hessian_chunk_bound(nk, n_atom) x n_atom x 6
+// doubles).  An empty grid gives zero blocks.
+int64_t coord_hessian_chunk_bound(int64_t nk, int32_t n_atom);
+cudaError_t launch_coord_hessian(const PointsDev& p, bool fp64, int64_t* off, double* part,
+                                 double* E, double* Dout, cudaStream_t st);
 
 }  // namespace vv10

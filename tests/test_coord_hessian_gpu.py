@@ -9,6 +9,8 @@ Tolerances against the FP64 oracle (relative Frobenius norm over the whole outpu
 Small systems compare every element; the full-size water-hexamer grid compares sampled
 D_i^B rows with the oracle's full j sums, and the blocks through properties that hold at
 any size: symmetry, the per-point sums, and finite differences of the atom gradient.
+Without the per-point output the library evaluates only the atom pairs A < B (the pair
+term is symmetric in i and j); both ways are checked.
 """
 import numpy as np
 import pytest
@@ -76,6 +78,8 @@ def test_small_systems(dev, oracle_mod, name, g, prec):
     E, D = E.cpu().numpy(), D.cpu().numpy()
     assert rel(E, E_ref) <= TOL_BLOCKS[prec]
     assert rel(D, D_ref) <= TOL_POINTS[prec]
+    Eh, _ = eng.coord_hessian(prec, points=False)
+    assert rel(Eh.cpu().numpy(), E_ref) <= TOL_BLOCKS[prec]
     # D_i^B is zero for the own atom
     na = g.molecule.n_atom
     assert not D[np.arange(g.n), g.atom_of_point].any()
@@ -90,9 +94,13 @@ def test_outputs_optional_and_repeatable(dev):
     eng = make_engine(g, dev)
     for prec in (FP64, MIXED):
         E1, D1 = eng.coord_hessian(prec, points=True)
-        E2, _ = eng.coord_hessian(prec, points=False)
+        E2, _ = eng.coord_hessian(prec, points=False)  # the atom pairs A < B only
         E3, D3 = eng.coord_hessian(prec, points=True)
-        assert torch.equal(E1, E2) and torch.equal(E1, E3) and torch.equal(D1, D3)
+        E4, _ = eng.coord_hessian(prec, points=False)
+        assert torch.equal(E1, E3) and torch.equal(D1, D3) and torch.equal(E2, E4)
+        # the half evaluation is exactly symmetric and agrees with the full one
+        assert torch.equal(E2, E2.transpose(0, 1).transpose(2, 3))
+        assert rel(E2.cpu().numpy(), E1.cpu().numpy()) <= (1e-13 if prec == FP64 else 1e-6)
         # D_i^B alone (the blocks go to scratch)
         D4 = torch.full_like(D1, 7.0)
         vv10.vv10_coord_hessian(eng.h, prec, None, D4)
@@ -117,6 +125,8 @@ def test_interleaved_atoms_and_empty_atoms(dev, oracle_mod):
     E, D = eng.coord_hessian(FP64, points=True)
     E, D = E.cpu().numpy(), D.cpu().numpy()
     assert rel(E, E_ref) <= 1e-10 and rel(D, D_ref) <= 1e-10
+    Eh, _ = eng.coord_hessian(FP64, points=False)
+    assert rel(Eh.cpu().numpy(), E_ref) <= 1e-10
     for a in (1, 3):
         assert not E[a].any() and not E[:, a].any()
     assert not D[h.atom_of_point == 1].any()
@@ -169,6 +179,12 @@ def test_full_size_hexamer(dev, oracle_mod, hexamer):
             off = [B for B in range(na) if B != A]
             assert rel(E[A, off], blk[off]) <= 1e-12
     assert rel(out[MIXED], out[FP64]) <= TOL_BLOCKS[MIXED]
+    # the blocks alone: the atom pairs A < B only, exactly symmetric
+    for prec in (FP64, MIXED):
+        Eh, _ = eng.coord_hessian(prec)
+        Eh = Eh.cpu().numpy()
+        assert np.array_equal(Eh, Eh.transpose(1, 0, 3, 2))
+        assert rel(Eh, out[FP64]) <= TOL_BLOCKS[prec]
     eng.close()
     # finite differences of the FP64 atom gradient when the points of one atom move rigidly
     B, hstep = 4, 1e-4
