@@ -73,11 +73,12 @@ def _load():
     lib.orc_atom_resolved.argtypes = [I64, P, P, P, P, P, I32, D, D, D, I64, P, P, P, P]
     lib.orc_point_coord_hessian.argtypes = [I64, P, P, P, P, P, I32, D, D, D, I64, P, P]
     lib.orc_coord_hessian.argtypes = [I64, P, P, P, P, P, I32, D, D, D, P]
+    lib.orc_weight_response.argtypes = [I64, P, P, P, P, D, D, D, I32, P, I64, P, P, P, P]
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_num_threads.argtypes = [ctypes.c_int]
     for name in ("orc_energy", "orc_pair_sums", "orc_potential", "orc_hessian_contract",
                  "orc_point_grad", "orc_atom_grad", "orc_atom_resolved", "orc_point_coord_hessian",
-                 "orc_coord_hessian"):
+                 "orc_coord_hessian", "orc_weight_response"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -255,3 +256,18 @@ def coord_hessian(coords, weights, rho, grad_rho, atom_of_point, n_atom, b=B_DEF
     _check(_load().orc_coord_hessian(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), _ptr(aop), n_atom,
                                      b, C, rho_cut, _ptr(out)), "coord_hessian")
     return out
+
+
+def weight_response(coords, weights, rho, grad_rho, w_t, rows=None, b=B_DEFAULT, C=C_DEFAULT,
+                    rho_cut=RHO_CUT_DEFAULT):
+    """E_i^{Bw}, U_i^{Bw}, W_i^{Bw} (Sec. II.B) for P weight directions w_t (P x n, e.g. the
+    components of w^B): three arrays P x n_rows."""
+    n, xyz, w, r, g = _sys(coords, weights, rho, grad_rho)
+    wt = _f64(w_t).reshape(-1, n)
+    P = wt.shape[0]
+    rr, nr = _rows(rows, n)
+    out = [np.zeros((P, nr)) for _ in range(3)]
+    _check(_load().orc_weight_response(n, _ptr(xyz), _ptr(w), _ptr(r), _ptr(g), b, C, rho_cut, P,
+                                       _ptr(wt), nr, _ptr(rr), *[_ptr(o) for o in out]),
+           "weight_response")
+    return tuple(out)

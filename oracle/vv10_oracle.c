@@ -18,6 +18,7 @@
  *   f^{rho,t}, f^{gamma,t} with f^{rho rho}, f^{gamma rho}, f^{rho gamma},
  *   f^{gamma gamma} and A_i, B_i, C_i                               (Sec. II.B, Eq. frhot)
  *   E^A_gr (first, unsimplified form) and E/U/W_i^{Bgr}             (Eqs. grad_gr, EiBgr)
+ *   D_i^B and E^{AB}_{gr,gr}; E/U/W_i^{Bw} for given weight directions (Sec. II.B)
  *
  * Readings where the paper is silent:
  *   - the inner sums over j include j = i (Phi_ii = -3/(4 kappa_i^3) is finite, and the
@@ -646,6 +647,65 @@ int orc_coord_hessian(int64_t n, const double* xyz, const double* w, const doubl
         }
         free(acc);
         free(dB);
+    }
+    orc_sys_free(&s);
+    return rc;
+}
+
+/* ---------------------------------------------------------------- weight-derivative sums */
+/* E_i^{Bw}, U_i^{Bw}, W_i^{Bw} (Sec. II.B, the three sums printed after the nuclear-Hessian
+ * blocks) for P weight directions: with v_j = wt[p][j] in place of w_j^B,
+ *   E_i^v = sum_j v_j rho_j Phi_ij
+ *   U_i^v = -sum_j v_j rho_j Phi_ij (1/(g + g') + 1/g)
+ *   W_i^v = -sum_j v_j rho_j Phi_ij R^2 (1/(g + g') + 1/g),
+ * the sums E_i, U_i, W_i of Sec. II.A with v in place of w (j = i included, kept points
+ * only).  wt: P x n (caller order); outE/outU/outW: P x n_rows, zero for dropped rows. */
+int orc_weight_response(int64_t n, const double* xyz, const double* w, const double* rho,
+                        const double* grad, double b, double C, double rho_cut, int32_t P,
+                        const double* wt, int64_t n_rows, const int64_t* rows, double* outE,
+                        double* outU, double* outW) {
+    orc_sys s;
+    if (orc_sys_init(&s, n, xyz, w, rho, grad, b, C, rho_cut)) return -1;
+    int rc = 0;
+#pragma omp parallel
+    {
+        nsum* acc = (nsum*)malloc(sizeof(nsum) * 3 * (size_t)(P > 0 ? P : 1));
+        if (!acc) {
+#pragma omp atomic write
+            rc = -1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t r = 0; r < n_rows; ++r) {
+            if (!acc) continue;
+            int64_t oi = rows ? rows[r] : r;
+            int64_t i = s.slot[oi];
+            memset(acc, 0, sizeof(nsum) * 3 * (size_t)P);
+            if (i >= 0) {
+                const orc_point* pi = &s.pt[i];
+                for (int64_t j = 0; j < s.nk; ++j) {
+                    const orc_point* pj = &s.pt[j];
+                    double R2 = orc_r2(&s, i, j);
+                    double g = pi->omega * R2 + pi->kappa;
+                    double gp = pj->omega * R2 + pj->kappa;
+                    double sg = g + gp;
+                    double phi = -3.0 / (2.0 * g * gp * sg);
+                    double t1 = 1.0 / sg + 1.0 / g;
+                    int64_t oj = s.kept[j];
+                    for (int32_t p = 0; p < P; ++p) {
+                        double vj = wt[(size_t)p * n + oj] * pj->rho;
+                        nsum_add(&acc[3 * p], vj * phi);
+                        nsum_add(&acc[3 * p + 1], -vj * phi * t1);
+                        nsum_add(&acc[3 * p + 2], -vj * phi * R2 * t1);
+                    }
+                }
+            }
+            for (int32_t p = 0; p < P; ++p) {
+                outE[(size_t)p * n_rows + r] = nsum_get(&acc[3 * p]);
+                outU[(size_t)p * n_rows + r] = nsum_get(&acc[3 * p + 1]);
+                outW[(size_t)p * n_rows + r] = nsum_get(&acc[3 * p + 2]);
+            }
+        }
+        free(acc);
     }
     orc_sys_free(&s);
     return rc;

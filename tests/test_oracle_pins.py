@@ -381,3 +381,62 @@ def test_coord_hessian_symmetry_and_invariances(oracle_mod):
                 np.testing.assert_allclose(blk[B], H[A, B], rtol=1e-10, atol=1e-13 * scale)
             else:
                 assert not Dp[m][:, A].any()  # D_i^B is defined for i not in B only
+
+
+# --------------------------------------------------------------------- weight-derivative sums
+
+def _directions(g, P, seed):
+    """P weight directions with the weights' scale and sign changes (like the components of
+    w^B, which change sign across a Becke cell boundary)."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(P, g.n)) * g.weights[None, :]
+
+
+def test_weight_sums_with_w_as_direction_are_row_sums(oracle_mod):
+    """With w itself as the direction, E^{Bw}, U^{Bw}, W^{Bw} (Sec. II.B) are the row sums
+    E_i, U_i, W_i of Sec. II.A."""
+    g, args = _sys(seed=51, n=60, n_atom=3)
+    ps = oracle_mod.pair_sums(*args)
+    E, U, W = oracle_mod.weight_response(*args, g.weights[None, :])
+    for got, key in ((E, "E"), (U, "U"), (W, "W")):
+        np.testing.assert_allclose(got[0], ps[key], rtol=1e-12, atol=1e-14 * np.abs(ps[key]).max())
+
+
+def test_weight_sums_are_second_weight_derivatives_of_energy(oracle_mod):
+    """E is quadratic in w, with d^2E/dw_i dw_j = rho_i rho_j Phi_ij, so for directions a, b
+    the mixed second difference of the energy is sum_i a_i rho_i E_i^{b} exactly (the
+    E_i^{Bw} term of E^{AB}_{w,w}, Sec. II.B)."""
+    g, args = _sys(seed=52, n=40, n_atom=3)
+    V = _directions(g, 3, seed=1)
+    E, _, _ = oracle_mod.weight_response(*args, V)
+    h = 0.3
+    en = lambda w: oracle_mod.energy(g.coords, w, g.rho, g.grad_rho)
+    for a in range(3):
+        for b in range(3):
+            fd = (en(g.weights + h * V[a] + h * V[b]) - en(g.weights + h * V[a] - h * V[b])
+                  - en(g.weights - h * V[a] + h * V[b]) + en(g.weights - h * V[a] - h * V[b])) / (4 * h * h)
+            an = np.sum(V[a] * g.rho * E[b])
+            assert fd == pytest.approx(an, rel=1e-8)
+            # and the symmetry of the second derivative
+            assert an == pytest.approx(np.sum(V[b] * g.rho * E[a]), rel=1e-12)
+
+
+def test_weight_sums_are_potential_derivatives(oracle_mod):
+    """f^rho_i = beta + E_i + rho_i (kappa'_i U_i + omega_rho,i W_i) and f^gamma_i =
+    rho_i omega_gamma,i W_i are linear in w: their derivative along a weight direction v is
+    the same expression in E_i^v, U_i^v, W_i^v.  f^gamma pins W^v, then f^rho pins U^v."""
+    g, args = _sys(seed=53, n=40, n_atom=3)
+    V = _directions(g, 2, seed=2)
+    E, U, W = oracle_mod.weight_response(*args, V)
+    pp = oracle_mod.point_props(g.rho, g.grad_rho)
+    h = 0.5
+    for p in range(2):
+        _, vr_p, vg_p = oracle_mod.potential(g.coords, g.weights + h * V[p], g.rho, g.grad_rho)
+        _, vr_m, vg_m = oracle_mod.potential(g.coords, g.weights - h * V[p], g.rho, g.grad_rho)
+        dvr, dvg = (vr_p - vr_m) / (2 * h), (vg_p - vg_m) / (2 * h)
+        np.testing.assert_allclose(g.rho * pp["omega_gamma"] * W[p], dvg, rtol=1e-8,
+                                   atol=1e-12 * np.abs(dvg).max())
+        an = E[p] + g.rho * (pp["kappa_rho"] * U[p] + pp["omega_rho"] * W[p])
+        np.testing.assert_allclose(an, dvr, rtol=1e-8, atol=1e-12 * np.abs(dvr).max())
+        # the three sums are independent: each term alone is far from the derivative
+        assert np.abs(E[p] - dvr).max() > 1e-3 * np.abs(dvr).max()
