@@ -22,7 +22,10 @@ Recipe (all lengths in bohr, FP64):
 * density: per atom three normalised s-Gaussians, exponents 0.3, sqrt(0.3*20), 20,
   each holding Z/3 electrons; analytic gradient;
 * trial densities: analytic nuclear-displacement derivatives d rho/d R_{A,c}
-  and their spatial gradients, P = 3 N_atom, ordered t = 3A + c.
+  and their spatial gradients, P = 3 N_atom, ordered t = 3A + c;
+* weight directions: analytic nuclear derivatives of the weights w^B = d w / d R_B
+  (Becke partition differentiated with the points moving with their atoms), 3 N_atom
+  directions ordered t = 3B + c.
 """
 from __future__ import annotations
 
@@ -254,6 +257,83 @@ def molecular_grid(mol: Molecule, n_rad: int, n_ang: int, chunk: int = 100_000):
         wts.append(w * frac)
         own.append(np.full(p.shape[0], a, dtype=np.int32))
     return np.concatenate(pts), np.concatenate(wts), np.concatenate(own)
+
+
+def _becke_s_ds(mu: np.ndarray):
+    """Becke's cutoff s(mu) and ds/dmu (three iterations of p -> 1.5 p - 0.5 p^3)."""
+    p, dp = mu, np.ones_like(mu)
+    for _ in range(3):
+        dp = (1.5 - 1.5 * p * p) * dp
+        p = 1.5 * p - 0.5 * p ** 3
+    return 0.5 * (1.0 - p), -0.5 * dp
+
+
+def _becke_fraction_grad(points: np.ndarray, owner: int, atoms: np.ndarray):
+    """The Becke cell weight of atom `owner` at each point (as _becke_fraction) and its
+    derivative with respect to every atom position, the points moving with their owner:
+    (frac (n,), grad (n, n_atom, 3)).  Atoms outside a point's neighbour set contribute
+    nothing; the owner's derivative follows from translational invariance."""
+    n_atom, n = atoms.shape[0], points.shape[0]
+    grad = np.zeros((n, n_atom, 3))
+    if n_atom == 1:
+        return np.ones(n), grad
+    d = np.linalg.norm(points[:, None, :] - atoms[None, :, :], axis=-1)
+    k = min(BECKE_NEIGHBOURS, n_atom - 1)
+    d_other = d.copy()
+    d_other[:, owner] = np.inf
+    nbr = np.argpartition(d_other, k - 1, axis=1)[:, :k]
+    idx = np.concatenate([np.full((n, 1), owner), nbr], axis=1)          # (n, m)
+    m = idx.shape[1]
+    ra = atoms[idx]                                                      # (n, m, 3)
+    dvec = points[:, None, :] - ra
+    dm = np.linalg.norm(dvec, axis=-1)                                   # (n, m)
+    u = dvec / dm[..., None]
+    Rv = ra[:, :, None, :] - ra[:, None, :, :]                           # (n, m, m, 3)
+    rab = np.linalg.norm(Rv, axis=-1)
+    eye = np.eye(m, dtype=bool)[None]
+    safe = np.where(eye, 1.0, rab)
+    mu = np.clip(np.where(eye, 0.0, (dm[:, :, None] - dm[:, None, :]) / safe), -1.0, 1.0)
+    e = Rv / safe[..., None]
+    sv, ds = _becke_s_ds(mu)
+    sv = np.where(eye, 1.0, sv)
+    ds = np.where(eye, 0.0, ds)
+    cell = np.prod(sv, axis=2)                                           # (n, m)
+    # product over E != D of s_CE, from prefix and suffix products along E
+    pre = np.ones_like(sv)
+    pre[:, :, 1:] = np.cumprod(sv[:, :, :-1], axis=2)
+    suf = np.ones_like(sv)
+    suf[:, :, :-1] = np.cumprod(sv[:, :, ::-1], axis=2)[:, :, ::-1][:, :, 1:]
+    G = ds * pre * suf                                                   # (n, C, D)
+    # d mu_CD / d R_C = -(u_C + mu_CD e_CD)/R_CD,  d mu_CD / d R_D = (u_D + mu_CD e_CD)/R_CD
+    dC = np.where(eye[..., None], 0.0, -(u[:, :, None, :] + mu[..., None] * e) / safe[..., None])
+    dD = np.where(eye[..., None], 0.0, (u[:, None, :, :] + mu[..., None] * e) / safe[..., None])
+    dcell = G[..., None] * dD                                            # (n, C, X, 3), X != C
+    ar = np.arange(m)
+    dcell[:, ar, ar, :] += np.einsum("ncd,ncdk->nck", G, dC)             # X = C
+    Z = cell.sum(axis=1)
+    dZ = dcell.sum(axis=1)                                               # (n, X, 3)
+    frac = cell[:, 0] / Z
+    dP = (dcell[:, 0] * Z[:, None, None] - cell[:, 0][:, None, None] * dZ) / (Z * Z)[:, None, None]
+    dP[:, 0] = -dP[:, 1:].sum(axis=1)
+    grad[np.arange(n)[:, None], idx] = dP
+    return frac, grad
+
+
+def weight_directions(mol: Molecule, n_rad: int, n_ang: int, chunk: int = 20_000) -> np.ndarray:
+    """Nuclear derivatives of the quadrature weights of molecular_grid(mol, n_rad, n_ang):
+    w^B_j = d w_j / d R_{B,c} with every point moving with its atom (the w^A, w^B of
+    Sec. II), as 3 N_atom directions ordered t = 3 B + c: array (3 N_atom, N)."""
+    u, wa = fibonacci_sphere(n_ang)
+    out = []
+    for a, (sym, centre) in enumerate(zip(mol.symbols, mol.coords)):
+        r, wr = radial_grid(n_rad, RADIAL_SCALE[sym])
+        p = (r[:, None, None] * u[None, :, :]).reshape(-1, 3) + centre
+        base = (wr[:, None] * wa[None, :]).reshape(-1)
+        gw = np.empty((p.shape[0], mol.n_atom, 3))
+        for s0 in range(0, p.shape[0], chunk):
+            _, gw[s0:s0 + chunk] = _becke_fraction_grad(p[s0:s0 + chunk], a, mol.coords)
+        out.append(base[:, None, None] * gw)
+    return np.ascontiguousarray(np.concatenate(out).reshape(-1, 3 * mol.n_atom).T)
 
 
 # ----------------------------------------------------------------------------- densities

@@ -76,3 +76,31 @@ def test_config_batch_parallel_is_identical():
     for x, y in zip(a, b):
         for f in ("coords", "weights", "rho", "grad_rho", "atom_of_point"):
             assert np.array_equal(getattr(x, f), getattr(y, f))
+
+
+def test_weight_directions_are_becke_weight_derivatives():
+    """The analytic nuclear derivatives of the Becke partition agree with central
+    differences (the owner atom's points move with it) and sum to zero over the atoms."""
+    mol = synth.random_chon(np.random.default_rng(0), 10)
+    pts, _, own = synth.molecular_grid(mol, 6, 14)
+    for a in (0, 4):
+        p = pts[own == a][:120]
+        f, gr = synth._becke_fraction_grad(p, a, mol.coords)
+        np.testing.assert_array_equal(f, synth._becke_fraction(p, a, mol.coords))
+        h = 1e-6
+        for B in range(mol.n_atom):
+            for c in range(3):
+                ap, am = mol.coords.copy(), mol.coords.copy()
+                ap[B, c] += h
+                am[B, c] -= h
+                pp, pm = p.copy(), p.copy()
+                if B == a:
+                    pp[:, c] += h
+                    pm[:, c] -= h
+                fd = (synth._becke_fraction(pp, a, ap) - synth._becke_fraction(pm, a, am)) / (2 * h)
+                np.testing.assert_allclose(gr[:, B, c], fd, atol=1e-7)
+        np.testing.assert_allclose(gr.sum(axis=1), 0.0, atol=1e-12)
+    V = synth.weight_directions(mol, 6, 14)
+    assert V.shape == (3 * mol.n_atom, pts.shape[0])
+    np.testing.assert_allclose(V.reshape(mol.n_atom, 3, -1).sum(axis=0), 0.0,
+                               atol=1e-12 * np.abs(V).max())
