@@ -171,6 +171,24 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
 vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grgr,
                                double* D_points, void* stream);
 
+/* Weight-derivative sums (Sec. II.B, the sums E_i^{Bw}, U_i^{Bw}, W_i^{Bw} that enter the
+ * E^{AB}_{w,w} and E^{AB}_{G,w} blocks of the nuclear Hessian): for P weight directions v
+ * (for the nuclear Hessian the 3 N_atom components of w^B = d w / d R_B),
+ *   E_i^v =  sum_j v_j rho_j Phi_ij
+ *   U_i^v = -sum_j v_j rho_j Phi_ij (1/(g + g') + 1/g)
+ *   W_i^v = -sum_j v_j rho_j Phi_ij R^2 (1/(g + g') + 1/g)
+ * (the E_i, U_i, W_i of Sec. II.A with v in place of w; j = i included).
+ *   P          number of directions, 1 <= P <= VV10_MAX_TRIALS
+ *   w_t        P x n device in, direction p of point i at w_t[p n + i] (caller order)
+ *   E_t, U_t, W_t   P x n device out, same layout (each may be NULL); zero for points
+ *              below rho_cut
+ *   prec       VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ * Needs no earlier call other than vv10_prepare_points.  Holds 8 P n_kept bytes of scratch.
+ * Errors: INVALID_ARG, UNSUPPORTED (P too large), OOM, CUDA. */
+vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
+                                 const double* w_t, double* E_t, double* U_t, double* W_t,
+                                 void* stream);
+
 /* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
  * by the last vv10_energy_potential call.  dEdw: n device out. */
 vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
@@ -336,7 +354,7 @@ vv10_status vv10_set_autotune(vv10_handle h, int flags);
  * vv10_profile_read synchronises the device, writes for phases 0..n-1 (n <= VV10_N_PHASES)
  * the accumulated milliseconds (ms, may be NULL; 0 when timing was off) and launch counts
  * (launches, may be NULL), then resets both.  Phase names: vv10_profile_phase_name. */
-#define VV10_N_PHASES 12
+#define VV10_N_PHASES 13
 vv10_status vv10_profile_enable(vv10_handle h, int on);
 vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches);
 const char* vv10_profile_phase_name(int phase);

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -670,6 +670,48 @@ vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grg
     return VV10_OK;
 }
 
+vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
+                                 const double* w_t, double* E_t, double* U_t, double* W_t,
+                                 void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (P < 1 || P > VV10_MAX_TRIALS) {
+        h->set_error("P must be in [1, VV10_MAX_TRIALS]");
+        return P < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    VV10_TRY(h->bind());
+    if (!device_ptr_ok(w_t, h->device) || !aligned(w_t, 8)) {
+        h->set_error("w_t must be an 8-byte aligned device pointer");
+        return VV10_ERR_INVALID_ARG;
+    }
+    void* outs[] = {E_t, U_t, W_t};
+    for (void* q : outs)
+        if (q && (!device_ptr_ok(q, h->device) || !aligned(q, 8))) {
+            h->set_error("outputs must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    if (!E_t && !U_t && !W_t) return VV10_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PointsDev& Pd = h->P;
+    const size_t pn = static_cast<size_t>(P) * static_cast<size_t>(Pd.n);
+    for (void* q : outs)
+        if (q) VV10_CUDA(h, cudaMemsetAsync(q, 0, sizeof(double) * pn, st), "memset");
+    if (Pd.nk == 0) return VV10_OK;
+    VV10_TRY(h->ensure(h->wdir, sizeof(double) * static_cast<size_t>(P) * Pd.nk_pad,
+                       "weight directions"));
+    double* yk = static_cast<double*>(h->wdir.p);
+    PhaseScope ph(h, PH_WEIGHT_RESPONSE, st, 2);
+    VV10_CUDA(h, launch_weight_dirs(Pd, P, w_t, yk, st), "weight directions");
+    VV10_CUDA(h, launch_weight_response(Pd, prec == VV10_FP64, P, yk, E_t, U_t, W_t, st),
+              "weight-derivative sums");
+    return VV10_OK;
+}
+
 vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
                           const double* rho_t, const double* grad_rho_t, double* energy,
                           double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
@@ -813,7 +855,7 @@ const char* vv10_profile_phase_name(int phase) {
     static const char* names[PH_COUNT] = {
         "prepare", "pair_sums_EUW", "energy_epilogue", "pair_sums_ABC", "trial_prep",
         "contraction_fp64", "contraction_tensor_core", "hessian_epilogue", "pair_sums_grad",
-        "grad_epilogue", "atom_resolved", "coord_hessian"};
+        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response"};
     return (phase >= 0 && phase < PH_COUNT) ? names[phase] : "unknown";
 }
 

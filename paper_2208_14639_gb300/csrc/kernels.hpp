@@ -178,4 +178,12 @@ int64_t coord_hessian_chunk_bound(int64_t nk, int32_t n_atom);
 cudaError_t launch_coord_hessian(const PointsDev& p, bool fp64, int64_t* off, double* part,
                                  double* E, double* Dout, cudaStream_t st);
 
+// Weight-derivative sums (Sec. II.B): yk (Pn x nk_pad) = -3/2 rho_k v_k of the caller's
+// directions wt (Pn x n) in kept order; E, U, W (Pn x n, caller order, may be null) receive
+// E_i^v, U_i^v, W_i^v for the kept rows (other rows untouched).
+cudaError_t launch_weight_dirs(const PointsDev& p, int32_t Pn, const double* wt, double* yk,
+                               cudaStream_t st);
+cudaError_t launch_weight_response(const PointsDev& p, bool fp64, int32_t Pn, const double* yk,
+                                   double* E, double* U, double* W, cudaStream_t st);
+
 }  // namespace vv10

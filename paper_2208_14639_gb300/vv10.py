@@ -47,9 +47,11 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_profile_phase_name", "vv10_energy_potential_noalloc",
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
-           "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian")
+           "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
+           "vv10_weight_response")
 VV10_NOALLOC_MAX_POINTS = 32768
-VV10_N_PHASES = 12
+VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
+VV10_N_PHASES = 13
 
 
 class VV10Params(ctypes.Structure):
@@ -94,6 +96,7 @@ def load(build_if_missing: bool = False):
         "vv10_hessian_contract": (st, [P, st, I32, P, P, P, P, P]),
         "vv10_coord_grad": (st, [P, st, P, P, P, P]),
         "vv10_coord_hessian": (st, [P, st, P, P, P]),
+        "vv10_weight_response": (st, [P, st, ctypes.c_int32, P, P, P, P, P]),
         "vv10_weight_grad": (st, [P, P, P]),
         "vv10_sync": (st, [P, P]),
         "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -217,6 +220,14 @@ def vv10_coord_hessian(h, prec: int, E_grgr=None, D_points=None, stream=None) ->
     st = load().vv10_coord_hessian(h, int(prec), _dptr(E_grgr, "E_grgr"),
                                    _dptr(D_points, "D_points"), _stream(stream))
     _check(h, st, "vv10_coord_hessian")
+
+
+def vv10_weight_response(h, prec: int, w_t, E_t=None, U_t=None, W_t=None, stream=None) -> None:
+    P, n = w_t.shape
+    st = load().vv10_weight_response(h, int(prec), int(P), _dptr(w_t, "w_t", shape=(P, n)),
+                                     _dptr(E_t, "E_t", shape=(P, n)), _dptr(U_t, "U_t", shape=(P, n)),
+                                     _dptr(W_t, "W_t", shape=(P, n)), _stream(stream))
+    _check(h, st, "vv10_weight_response")
 
 
 def vv10_weight_grad(h, dEdw, stream=None) -> None:
@@ -440,6 +451,12 @@ class VV10:
         D = torch.empty(self.n, self.n_atom, 3, 3, **f64) if points else None
         vv10_coord_hessian(self.h, prec, E, D, stream)
         return E, D
+
+    def weight_response(self, w_t, prec=VV10_FP64, stream=None):
+        """E_i^{Bw}, U_i^{Bw}, W_i^{Bw} for the weight directions w_t (P x n): three P x n."""
+        E, U, W = (torch.empty_like(w_t) for _ in range(3))
+        vv10_weight_response(self.h, prec, w_t, E, U, W, stream)
+        return E, U, W
 
     def evaluate(self, prec=VV10_FP64, rho_t=None, grad_rho_t=None, resolved=False, stream=None):
         """Energy, potential, Hessian contraction (when trials are given) and coordinate terms
