@@ -53,6 +53,9 @@ ALU_OPS_PER_PAIR_EUW = 20
 #   omega_j/g', (omega_i+omega_j)/s and D, 4 for the squared bracket, 4 for the scaled
 #   displacement, 6 outer-product and 1 identity-term accumulations
 ALU_OPS_PER_PAIR_CH = 38
+#   weight-derivative sums: 19 to form 1/(g g' s), 1/s + 1/g and the three kernel values,
+#   then 3 FMAs per direction
+ALU_OPS_PER_PAIR_WR = 19
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
 # (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
 PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.2312e9}
@@ -69,6 +72,11 @@ def workloads():
         "chon60": ("60-atom CHON molecule, 75x302 points per atom (1,359,000 points), P=180",
                    synth.config_chon60),
     }
+
+
+# Radial x angular points per atom of each workload's grid (for its weight derivatives).
+GRID_SHAPES = {"water": (30, 110), "hexamer": (50, 194), "cluster24": (30, 139),
+               "chon60": (75, 302)}
 
 
 # ------------------------------------------------------------------ host-side rank logic
@@ -190,6 +198,16 @@ class Problem:
             "euw": torch.empty(3, self.n, self.n_atom, 3, **f64) if resolved else None,
         }
 
+    def weight_dirs(self):
+        """The 3 N_atom nuclear derivatives of the Becke weights (P x n, on the device); made
+        on first use (a few seconds of host work), for the grids whose recipe is known."""
+        import torch
+        if getattr(self, "_wdirs", None) is None:
+            from paper_2208_14639_gb300 import synth
+            V = synth.weight_directions(self.g.molecule, *self.grid_shape)
+            self._wdirs = torch.from_numpy(V).to(self.d["xyz"].device)
+        return self._wdirs
+
     def input_bytes(self):
         return int(sum(v.nbytes for v in self.host.values()))
 
@@ -281,6 +299,23 @@ def time_coord_hessian(vv, h, pb, prec, reps):
     ev[0].record(stream)
     for _ in range(reps):
         vv.vv10_coord_hessian(h, prec, E, None)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps
+
+
+def time_weight_response(vv, h, pb, prec, V, reps):
+    """The weight-derivative sums (vv10_weight_response) for the directions V (P x n, on the
+    device) on the prepared points: milliseconds per call."""
+    import torch
+    E, U, W = (torch.empty_like(V) for _ in range(3))
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    vv.vv10_weight_response(h, prec, V, E, U, W)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        vv.vv10_weight_response(h, prec, V, E, U, W)
     ev[1].record(stream)
     torch.cuda.synchronize()
     return ev[0].elapsed_time(ev[1]) / reps
@@ -390,6 +425,7 @@ def gpu_arm(args):
     label, make = workloads()[args.workload]
     g = make()
     pb = Problem(g, dev, resolved=(args.workload != "chon60"))
+    pb.grid_shape = GRID_SHAPES[args.workload]
     h = vv.vv10_create(local)
     prec = vv.PRECISIONS[args.precision]
     peaks, peak_src = load_peaks()
@@ -416,6 +452,9 @@ def gpu_arm(args):
     ms_ep, ms_hc = time_calls(vv, h, pb, prec, 3)
     ms_ch = time_coord_hessian(vv, h, pb, prec, 3)
     pairs_ch = coord_hessian_pairs(pb)
+    wdirs = pb.weight_dirs()
+    P_w = int(wdirs.shape[0])
+    ms_wr = time_weight_response(vv, h, pb, prec, wdirs, 3)
     alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     breakdown = {
         # the two metric quantities, each timed as its own entry point (3 calls each)
@@ -431,6 +470,11 @@ def gpu_arm(args):
         "coord_hessian_pairs": pairs_ch,
         "coord_hessian_pairs_per_s": pairs_ch / (ms_ch / 1e3),
         "coord_hessian_alu_frac": ALU_OPS_PER_PAIR_CH * pairs_ch / (ms_ch / 1e3) / alu_peak_ops,
+        # weight-derivative sums for the 3 N_atom Becke weight directions (not part of the step)
+        "weight_response_P": P_w,
+        "weight_response_call_ms": ms_wr,
+        "weight_response_pairs_per_s": pairs_call / (ms_wr / 1e3),
+        "weight_response_alu_frac": (ALU_OPS_PER_PAIR_WR + 3 * P_w) * pairs_call / (ms_wr / 1e3) / alu_peak_ops,
         # the step's own phases
         "step_pair_pass_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
@@ -498,17 +542,20 @@ def gpu_arm(args):
         per64 = {k: v[0] for k, v in prof64.items()}
         ms_ep64, ms_hc64 = time_calls(vv, h, pb, vv.VV10_FP64, 1)
         ms_ch64 = time_coord_hessian(vv, h, pb, vv.VV10_FP64, 1)
+        ms_wr64 = time_weight_response(vv, h, pb, vv.VV10_FP64, wdirs, 1)
         result["fp64"] = {
             "value": 3.0 * pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
             "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
             "energy_potential_pairs_per_s": pairs_call / (ms_ep64 / 1e3),
             "hessian_pairs_per_s": pairs_call / (ms_hc64 / 1e3),
             "coord_hessian_pairs_per_s": pairs_ch / (ms_ch64 / 1e3),
+            "weight_response_pairs_per_s": pairs_call / (ms_wr64 / 1e3),
             "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
         }
         result["speedup_mixed_vs_fp64_energy_potential"] = ms_ep64 / ms_ep
         result["speedup_mixed_vs_fp64_hessian"] = ms_hc64 / ms_hc
         result["speedup_mixed_vs_fp64_coord_hessian"] = ms_ch64 / ms_ch
+        result["speedup_mixed_vs_fp64_weight_response"] = ms_wr64 / ms_wr
         result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
 
     sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, K, 1)

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -705,6 +705,23 @@ vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
     VV10_TRY(h->ensure(h->wdir, sizeof(double) * static_cast<size_t>(P) * Pd.nk_pad,
                        "weight directions"));
     double* yk = static_cast<double*>(h->wdir.p);
+    if (prec != VV10_FP64 && P > 4) {
+        // tensor cores (below 5 directions a 32-wide MMA is mostly padding)
+        int ng = 0, ppad = 0;
+        weight_tc_groups(P, &ng, &ppad);
+        const int32_t rows = ng * ppad;
+        const size_t nsplit = static_cast<size_t>(rows) * static_cast<size_t>(Pd.nk_pad);
+        VV10_TRY(h->ensure(h->wsplit, 2 * sizeof(float) * nsplit, "weight direction split"));
+        float* yh = static_cast<float*>(h->wsplit.p);
+        PhaseScope ph(h, PH_WEIGHT_RESPONSE, st, 3);
+        VV10_CUDA(h, launch_weight_dirs(Pd, P, w_t, yk, st), "weight directions");
+        VV10_CUDA(h, launch_weight_split(yk, P, rows, Pd.nk_pad, yh, yh + nsplit, st),
+                  "weight direction split");
+        VV10_CUDA(h, launch_weight_tc(Pd, P, yh, yh + nsplit, rows, E_t, U_t, W_t, h->n_sm,
+                                      static_cast<int*>(h->dev_err.p), st),
+                  "weight-derivative sums (tensor cores)");
+        return VV10_OK;
+    }
     PhaseScope ph(h, PH_WEIGHT_RESPONSE, st, 2);
     VV10_CUDA(h, launch_weight_dirs(Pd, P, w_t, yk, st), "weight directions");
     VV10_CUDA(h, launch_weight_response(Pd, prec == VV10_FP64, P, yk, E_t, U_t, W_t, st),

@@ -587,6 +587,10 @@ static bool make_map(CUtensorMap* m, const float* base, int64_t nk_pad, int64_t 
     return r == CUDA_SUCCESS;
 }
 
+bool tc_make_map_f32(void* out, const float* base, int64_t nk_pad, int64_t rows, int ppad) {
+    return make_map(static_cast<CUtensorMap*>(out), base, nk_pad, rows, ppad);
+}
+
 int hess_tc_ppad(int32_t P) {
     const int p = ((P + 31) / 32) * 32;
     return p < 32 ? 32 : p;

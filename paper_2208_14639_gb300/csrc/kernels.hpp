@@ -185,5 +185,17 @@ cudaError_t launch_weight_dirs(const PointsDev& p, int32_t Pn, const double* wt,
                                cudaStream_t st);
 cudaError_t launch_weight_response(const PointsDev& p, bool fp64, int32_t Pn, const double* yk,
                                    double* E, double* U, double* W, cudaStream_t st);
+// The same sums on tensor cores (mixed precision): directions in groups of at most 64
+// (weight_tc_groups), yk split into TF32 hi / FP32 lo arrays of `rows` >= groups x Ppad
+// rows (launch_weight_split); E, U, W must be zero on entry (the kernel adds into them).
+void weight_tc_groups(int32_t P, int* n_groups, int* ppad);
+cudaError_t launch_weight_split(const double* yk, int32_t Pn, int32_t rows, int64_t nk_pad,
+                                float* yh, float* yl, cudaStream_t st);
+cudaError_t launch_weight_tc(const PointsDev& p, int32_t Pn, const float* yh, const float* yl,
+                             int32_t rows, double* E, double* U, double* W, int n_sm, int* err,
+                             cudaStream_t st);
+// 2-D tensor map over a [rows][nk_pad] FP32 array, box 16 j x ppad rows, 64-byte swizzle.
+bool tc_make_map_f32(void* out /* CUtensorMap */, const float* base, int64_t nk_pad, int64_t rows,
+                     int ppad);
 
 }  // namespace vv10

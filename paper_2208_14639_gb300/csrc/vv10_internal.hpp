@@ -137,6 +137,7 @@ struct vv10_ctx {
     vv10::DevBuf gk;
     vv10::DevBuf chpart;  // per-CTA partials of the grid-grid Hessian blocks
     vv10::DevBuf wdir;    // weight directions in kept order (weight-derivative sums)
+    vv10::DevBuf wsplit;  // their TF32 hi / FP32 lo split (tensor-core path)
 
     // tile overrides (index = mode + 4 * fp64, modes MODE_EUW..MODE_EUWABC), set by
     // vv10_set_tiles / the autotuner

@@ -2,11 +2,12 @@
 directions) with the FP64 oracle, through the C ABI.
 
 Tolerances against the FP64 oracle (relative Frobenius norm over each output, E, U and W
-separately): FP64 path <= 1e-10, mixed path <= 1e-6.  Small systems compare every element;
-the full-size water-hexamer grid with its 54 Becke weight directions compares sampled rows
-(full j sums) and checks properties that hold at any size: the symmetry of the weight-weight
-second derivative sum_i a_i rho_i E_i^b, and, with w itself as the direction, the row sums
-E_i that vv10_weight_grad reports.
+separately): FP64 path <= 1e-10, mixed path <= 1e-6.  The mixed path runs on tensor cores
+(split TF32) from 5 directions up and as FP32 SIMT arithmetic below.  Small systems compare
+every element; the full-size water-hexamer grid with its 54 Becke weight directions compares
+sampled rows (full j sums) and checks properties that hold at any size: the symmetry of the
+weight-weight second derivative sum_i a_i rho_i E_i^b, and, with w itself as the direction,
+the row sums E_i that vv10_weight_grad reports.
 """
 import numpy as np
 import pytest
@@ -79,6 +80,17 @@ def test_random_systems(dev, oracle_mod, name, n, seed, P, prec):
     g = synth.random_points(n, seed=seed, n_atom=3)
     eng = make_engine(g, dev)
     check(eng, g, random_dirs(g, P, seed + 100), prec, oracle_mod)
+    eng.close()
+
+
+@pytest.mark.parametrize("P", [4, 5, 32, 33, 63, 64, 65, 130])
+def test_direction_groups(dev, oracle_mod, P):
+    """Direction counts around the tensor-core path's limits: below 5 directions the mixed
+    path uses the SIMT kernel, up to 32 one 32-wide group, up to 64 one 64-wide group, then
+    several groups."""
+    g = synth.random_points(900, seed=70 + P, n_atom=3)
+    eng = make_engine(g, dev)
+    check(eng, g, random_dirs(g, P, P), MIXED, oracle_mod)
     eng.close()
 
 
