@@ -321,6 +321,26 @@ def time_weight_response(vv, h, pb, prec, V, reps):
     return ev[0].elapsed_time(ev[1]) / reps
 
 
+def weight_response_roofline(prec, P, pairs, ms, alu_peak_ops, peaks):
+    """Roofline view of one weight-derivative call: 6 P algorithmic flops per pair (three
+    kernel matrices times P directions).  The mixed path from 5 directions up runs on tensor
+    cores: 3 split products x 2 x 3 x Ppad issued flops per pair against the tf32 dense peak;
+    otherwise FP32 ALU work (19 + 3 P operations per pair) against the ALU peak."""
+    from paper_2208_14639_gb300 import vv10 as vv
+    t = ms / 1e3
+    out = {"weight_response_alg_tflops": 6.0 * P * pairs / t / 1e12}
+    if prec != vv.VV10_FP64 and P > 4:
+        groups = -(-P // 64)
+        pg = -(-P // groups)
+        ppad = 32 if pg <= 32 else 64
+        tf32_peak = peaks["bf16_tflops"] * 0.5 * 1e12
+        out["weight_response_issued_mma_frac"] = 3 * 6.0 * ppad * groups * pairs / t / tf32_peak
+        out["weight_response_tc_alu_frac"] = 28.0 * groups * pairs / t / alu_peak_ops
+    else:
+        out["weight_response_alu_frac"] = (ALU_OPS_PER_PAIR_WR + 3 * P) * pairs / t / alu_peak_ops
+    return out
+
+
 def time_e2e(vv, h, pb, prec, steps, warmup):
     """The same step with host inputs: every step copies all of its inputs from pinned host
     memory to the device and all of its outputs back, inside the timed region.  The copies
@@ -474,7 +494,7 @@ def gpu_arm(args):
         "weight_response_P": P_w,
         "weight_response_call_ms": ms_wr,
         "weight_response_pairs_per_s": pairs_call / (ms_wr / 1e3),
-        "weight_response_alu_frac": (ALU_OPS_PER_PAIR_WR + 3 * P_w) * pairs_call / (ms_wr / 1e3) / alu_peak_ops,
+        **weight_response_roofline(prec, P_w, pairs_call, ms_wr, alu_peak_ops, peaks),
         # the step's own phases
         "step_pair_pass_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
