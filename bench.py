@@ -304,6 +304,18 @@ def time_coord_hessian(vv, h, pb, prec, reps):
     return ev[0].elapsed_time(ev[1]) / reps
 
 
+def time_energy_only(vv, h, prec, reps):
+    """vv10_energy (the energy from the unordered pairs) on the prepared points: ms per call
+    (each call ends with the host read of the energy)."""
+    import torch
+    vv.vv10_energy(h, prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        vv.vv10_energy(h, prec)
+    return (time.perf_counter() - t0) * 1e3 / reps
+
+
 def time_weight_response(vv, h, pb, prec, V, reps):
     """The weight-derivative sums (vv10_weight_response) for the directions V (P x n, on the
     device) on the prepared points: milliseconds per call."""
@@ -470,6 +482,7 @@ def gpu_arm(args):
     t_coord = per["pair_sums_grad"] + per["grad_epilogue"] + per["atom_resolved"]  # incl. the fused sums
     hess_flops = 8.0 * pairs_call * pb.P
     ms_ep, ms_hc = time_calls(vv, h, pb, prec, 3)
+    ms_e = time_energy_only(vv, h, prec, 3)
     ms_ch = time_coord_hessian(vv, h, pb, prec, 3)
     pairs_ch = coord_hessian_pairs(pb)
     wdirs = pb.weight_dirs()
@@ -481,6 +494,9 @@ def gpu_arm(args):
         "energy_potential_call_ms": ms_ep,
         "energy_potential_pairs_per_s": pairs_call / (ms_ep / 1e3),
         "energy_potential_alu_frac": ALU_OPS_PER_PAIR_EUW * pairs_call / (ms_ep / 1e3) / alu_peak_ops,
+        # the energy alone from the unordered pairs (vv10_energy; half the pair evaluations)
+        "energy_only_call_ms": ms_e,
+        "energy_only_pairs_per_s": pairs_call / (ms_e / 1e3),
         "hessian_call_ms": ms_hc,
         "hessian_pairs_per_s": pairs_call / (ms_hc / 1e3),
         "hessian_P_pairs_per_s": pb.P * pairs_call / (ms_hc / 1e3),

@@ -118,6 +118,15 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
 vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* energy,
                                   double* vrho, double* vgamma, void* stream);
 
+/* The energy alone (Sec. II.A, the quadrature form of E^VV10), from the unordered pairs:
+ *   E = beta sum_i c_i + sum_{i<j} c_i c_j Phi_ij + 1/2 sum_i c_i^2 Phi_ii,   c_i = w_i rho_i,
+ * the same E as vv10_energy_potential with half the pair evaluations (Phi_ij = Phi_ji).
+ *   prec     VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ *   energy   HOST pointer, receives E (required; the call synchronises `stream`)
+ * Leaves the row sums cached by vv10_energy_potential as they were.  The sum is formed in a
+ * fixed order: repeated calls give identical results.  Errors: INVALID_ARG, OOM, CUDA. */
+vv10_status vv10_energy(vv10_handle h, vv10_precision prec, double* energy, void* stream);
+
 /* Nonlocal response contracted with P trial densities (Sec. II.B, Eq. frhot):
  *   f^{rho,t}_i   = sum_j w_j (f^{rho rho}_ij rho^t_j + 2 f^{rho gamma}_ij gamma^t_j)
  *   f^{gamma,t}_i = sum_j w_j (f^{gamma rho}_ij rho^t_j + 2 f^{gamma gamma}_ij gamma^t_j)
@@ -354,7 +363,7 @@ vv10_status vv10_set_autotune(vv10_handle h, int flags);
  * vv10_profile_read synchronises the device, writes for phases 0..n-1 (n <= VV10_N_PHASES)
  * the accumulated milliseconds (ms, may be NULL; 0 when timing was off) and launch counts
  * (launches, may be NULL), then resets both.  Phase names: vv10_profile_phase_name. */
-#define VV10_N_PHASES 13
+#define VV10_N_PHASES 14
 vv10_status vv10_profile_enable(vv10_handle h, int on);
 vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches);
 const char* vv10_profile_phase_name(int phase);

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -729,6 +729,36 @@ vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
     return VV10_OK;
 }
 
+vv10_status vv10_energy(vv10_handle h, vv10_precision prec, double* energy, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (!energy) {
+        h->set_error("energy must be a host pointer");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool fp64 = (prec == VV10_FP64);
+    const int grid = energy_half_grid(fp64, h->n_sm);
+    VV10_TRY(h->ensure(h->ehalf, sizeof(double) * (static_cast<size_t>(grid) + 8), "energy partials"));
+    double* dev_e = static_cast<double*>(h->ehalf.p) + grid;  // after the per-CTA totals
+    {
+        PhaseScope ph(h, PH_ENERGY_HALF, st, h->P.nk > 0 ? 2 : 0);
+        VV10_CUDA(h, launch_energy_half(h->P, fp64, grid, static_cast<double*>(h->ehalf.p), dev_e, st),
+                  "energy");
+    }
+    double* he = reinterpret_cast<double*>(h->h_pinned) + 2;
+    VV10_CUDA(h, cudaMemcpyAsync(he, dev_e, sizeof(double), cudaMemcpyDeviceToHost, st), "read energy");
+    VV10_TRY(h->check_device_errors(st));  // synchronises
+    *energy = *he;
+    return VV10_OK;
+}
+
 vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
                           const double* rho_t, const double* grad_rho_t, double* energy,
                           double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
@@ -872,7 +902,7 @@ const char* vv10_profile_phase_name(int phase) {
     static const char* names[PH_COUNT] = {
         "prepare", "pair_sums_EUW", "energy_epilogue", "pair_sums_ABC", "trial_prep",
         "contraction_fp64", "contraction_tensor_core", "hessian_epilogue", "pair_sums_grad",
-        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response"};
+        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response", "energy_half"};
     return (phase >= 0 && phase < PH_COUNT) ? names[phase] : "unknown";
 }
 

@@ -198,4 +198,11 @@ cudaError_t launch_weight_tc(const PointsDev& p, int32_t Pn, const float* yh, co
 bool tc_make_map_f32(void* out /* CUtensorMap */, const float* base, int64_t nk_pad, int64_t rows,
                      int ppad);
 
+// Energy alone from the unordered pairs (Sec. II.A): one persistent launch of `grid` CTAs
+// (energy_half_grid) writing cta_total[grid], then their fixed-order sum into *energy
+// (device).
+int energy_half_grid(bool fp64, int n_sm);
+cudaError_t launch_energy_half(const PointsDev& p, bool fp64, int grid, double* cta_total,
+                               double* energy, cudaStream_t st);
+
 }  // namespace vv10

@@ -48,10 +48,10 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
            "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
-           "vv10_weight_response")
+           "vv10_weight_response", "vv10_energy")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
-VV10_N_PHASES = 13
+VV10_N_PHASES = 14
 
 
 class VV10Params(ctypes.Structure):
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = False):
         "vv10_coord_grad": (st, [P, st, P, P, P, P]),
         "vv10_coord_hessian": (st, [P, st, P, P, P]),
         "vv10_weight_response": (st, [P, st, ctypes.c_int32, P, P, P, P, P]),
+        "vv10_energy": (st, [P, st, ctypes.POINTER(D), P]),
         "vv10_weight_grad": (st, [P, P, P]),
         "vv10_sync": (st, [P, P]),
         "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -228,6 +229,12 @@ def vv10_weight_response(h, prec: int, w_t, E_t=None, U_t=None, W_t=None, stream
                                      _dptr(E_t, "E_t", shape=(P, n)), _dptr(U_t, "U_t", shape=(P, n)),
                                      _dptr(W_t, "W_t", shape=(P, n)), _stream(stream))
     _check(h, st, "vv10_weight_response")
+
+
+def vv10_energy(h, prec: int, stream=None) -> float:
+    e = ctypes.c_double()
+    _check(h, load().vv10_energy(h, int(prec), ctypes.byref(e), _stream(stream)), "vv10_energy")
+    return e.value
 
 
 def vv10_weight_grad(h, dEdw, stream=None) -> None:
@@ -451,6 +458,10 @@ class VV10:
         D = torch.empty(self.n, self.n_atom, 3, 3, **f64) if points else None
         vv10_coord_hessian(self.h, prec, E, D, stream)
         return E, D
+
+    def energy(self, prec=VV10_FP64, stream=None) -> float:
+        """E alone, from the unordered pairs (half the pair evaluations)."""
+        return vv10_energy(self.h, prec, stream)
 
     def weight_response(self, w_t, prec=VV10_FP64, stream=None):
         """E_i^{Bw}, U_i^{Bw}, W_i^{Bw} for the weight directions w_t (P x n): three P x n."""
