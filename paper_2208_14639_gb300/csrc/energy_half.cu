@@ -68,17 +68,24 @@ k_energy_half(PointsDev P, const typename EhRecs<T>::A* __restrict__ ra,
             sb[tid] = rb[j0 + tid];
         }
         __syncthreads();
-        T acc = T(0);
-        const bool diag = (I == J);
-        for (int jj = diag ? tid : 0; jj < cnt; ++jj) {
+        // c_j Phi_ij of the pair (i, jj) (a.w = -3/2 c_j)
+        auto term = [&](int jj) -> T {
             const RA a = sa[jj];
             const RB b = sb[jj];
             const T dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
             const T r2 = fmadd(dz, dz, fmadd(dy, dy, dx * dx));
             const T g = fmadd(oi, r2, ki);
             const T gp = fmadd(b.x, r2, b.y);
-            const T v = a.w * recip(g * gp * (g + gp));  // c_j Phi_ij (a.w = -3/2 c_j)
-            acc += (diag && jj == tid) ? T(0.5) * v : v;
+            return a.w * recip(g * gp * (g + gp));
+        };
+        T acc = T(0);
+        const bool diag = (I == J);
+        if (!diag) {
+#pragma unroll 4
+            for (int jj = 0; jj < cnt; ++jj) acc += term(jj);
+        } else if (tid < cnt) {
+            acc = T(0.5) * term(tid);  // j = i
+            for (int jj = tid + 1; jj < cnt; ++jj) acc += term(jj);
         }
         double v = valid ? ci * static_cast<double>(acc) : 0.0;
         if (diag && valid) v += P.beta * ci;
