@@ -271,3 +271,41 @@ def weight_response(coords, weights, rho, grad_rho, w_t, rows=None, b=B_DEFAULT,
                                        _ptr(wt), nr, _ptr(rr), *[_ptr(o) for o in out]),
            "weight_response")
     return tuple(out)
+
+
+# ---------------------------------------------------------------- AO-side assembly (numpy)
+
+def fock_matrix(weights, grad_rho, vrho, vgamma, phi, grad_phi) -> np.ndarray:
+    """The VV10 contribution to the Fock matrix (Sec. II.A):
+    F_mu_nu = sum_i w_i [f^rho_i phi_mu,i phi_nu,i
+                         + 2 f^gamma_i grad rho_i . (phi_nu,i grad phi_mu,i + phi_mu,i grad phi_nu,i)]
+    with f^rho = vrho, f^gamma = vgamma (per unit weight, zero at dropped points).
+    phi: n x nbf, grad_phi: n x nbf x 3.  Returns nbf x nbf."""
+    w = _f64(weights)
+    s = w * _f64(vrho)
+    v = 2.0 * (w * _f64(vgamma))[:, None] * _f64(grad_rho).reshape(-1, 3)
+    phi = _f64(phi)
+    vdphi = np.einsum("nk,nmk->nm", v, _f64(grad_phi))  # v_i . grad phi_mu,i
+    return phi.T @ (s[:, None] * phi) + vdphi.T @ phi + phi.T @ vdphi
+
+
+def orbital_hessian(weights, grad_rho, vgamma, f_rho_t, f_gamma_t, grad_rho_t, phi,
+                    grad_phi) -> np.ndarray:
+    """The contracted orbital Hessian (Sec. II.B):
+    G^t_mu_nu = sum_i w_i [f^{rho,t}_i phi_mu phi_nu
+                           + 2 (f^{gamma,t}_i grad rho_i + f^gamma_i grad rho^t_i)
+                             . (phi_nu grad phi_mu + phi_mu grad phi_nu)]
+    for each trial t (f_rho_t, f_gamma_t: P x n; grad_rho_t: P x n x 3).  Returns P x nbf x nbf."""
+    w = _f64(weights)
+    g = _f64(grad_rho).reshape(-1, 3)
+    fr, fg = _f64(f_rho_t), _f64(f_gamma_t)
+    gt = _f64(grad_rho_t).reshape(fr.shape[0], -1, 3)
+    phi, dphi = _f64(phi), _f64(grad_phi)
+    vg = _f64(vgamma)
+    out = np.zeros((fr.shape[0], phi.shape[1], phi.shape[1]))
+    for t in range(fr.shape[0]):
+        s = w * fr[t]
+        v = 2.0 * w[:, None] * (fg[t][:, None] * g + vg[:, None] * gt[t])
+        vdphi = np.einsum("nk,nmk->nm", v, dphi)
+        out[t] = phi.T @ (s[:, None] * phi) + vdphi.T @ phi + phi.T @ vdphi
+    return out

@@ -430,6 +430,102 @@ def make_system(mol: Molecule, n_rad: int, n_ang: int) -> GridDensity:
 SEED_BASE = 20220830
 
 
+# ----------------------------------------------------------------------------- AO basis
+
+# Uncontracted Cartesian Gaussian shells per element, (l, exponent in bohr^-2), l = 0 (s) or 1 (p):
+# a free choice of this recipe, loosely double-zeta-like.
+AO_SHELLS = {
+    "H": [(0, 1.3), (0, 0.25)],
+    "C": [(0, 6.0), (0, 1.0), (0, 0.25), (1, 1.2), (1, 0.3)],
+    "N": [(0, 7.5), (0, 1.3), (0, 0.3), (1, 1.5), (1, 0.35)],
+    "O": [(0, 9.0), (0, 1.6), (0, 0.35), (1, 1.8), (1, 0.4)],
+}
+
+
+@dataclasses.dataclass
+class AOBasis:
+    """Basis functions phi_mu = N r_c^l exp(-alpha |r - A|^2) (c = the Cartesian component of
+    a p function), each normalised to unit self-overlap."""
+
+    centers: np.ndarray  # (nbf, 3)
+    alpha: np.ndarray    # (nbf,)
+    comp: np.ndarray     # (nbf,) int: -1 for s, 0/1/2 for p_x/p_y/p_z
+    atom: np.ndarray     # (nbf,) int
+    norm: np.ndarray     # (nbf,)
+
+    @property
+    def nbf(self) -> int:
+        return int(self.alpha.shape[0])
+
+
+def ao_basis(mol: Molecule) -> AOBasis:
+    cen, al, cp, at = [], [], [], []
+    for a, (sym, c) in enumerate(zip(mol.symbols, mol.coords)):
+        for l, e in AO_SHELLS[sym]:
+            for k in ([-1] if l == 0 else [0, 1, 2]):
+                cen.append(c)
+                al.append(e)
+                cp.append(k)
+                at.append(a)
+    al = np.array(al)
+    cp = np.array(cp, dtype=np.int64)
+    # unit self-overlap: s: (2 alpha/pi)^(3/4); p: (2 alpha/pi)^(3/4) * 2 sqrt(alpha)
+    norm = (2.0 * al / math.pi) ** 0.75 * np.where(cp >= 0, 2.0 * np.sqrt(al), 1.0)
+    return AOBasis(np.array(cen), al, cp, np.array(at, dtype=np.int64), norm)
+
+
+def ao_values(basis: AOBasis, points: np.ndarray):
+    """(phi (n, nbf), grad phi (n, nbf, 3)) at the points."""
+    d = points[:, None, :] - basis.centers[None, :, :]          # (n, nbf, 3)
+    r2 = np.einsum("nmk,nmk->nm", d, d)
+    g = basis.norm[None, :] * np.exp(-basis.alpha[None, :] * r2)  # radial part
+    is_p = basis.comp >= 0
+    cidx = np.where(is_p, basis.comp, 0)
+    dc = np.take_along_axis(d, cidx[None, :, None].repeat(d.shape[0], 0), axis=2)[..., 0]
+    ang = np.where(is_p[None, :], dc, 1.0)
+    phi = ang * g
+    dphi = -2.0 * basis.alpha[None, :, None] * d * phi[..., None]
+    # p functions: + N exp(-alpha r^2) along their own component
+    eye = np.zeros((basis.nbf, 3))
+    eye[np.arange(basis.nbf)[is_p], basis.comp[is_p]] = 1.0
+    dphi += g[..., None] * eye[None, :, :]
+    return np.ascontiguousarray(phi), np.ascontiguousarray(dphi)
+
+
+def ao_density(phi: np.ndarray, dphi: np.ndarray, P: np.ndarray):
+    """rho = sum_{mu nu} P_mu_nu phi_mu phi_nu and its gradient (P symmetric), as in the
+    definition of the trial density rho^t from P^t (Sec. II.B)."""
+    Pphi = phi @ P                                              # (n, nbf)
+    rho = np.einsum("nm,nm->n", Pphi, phi)
+    grad = 2.0 * np.einsum("nm,nmk->nk", Pphi, dphi)
+    return rho, grad
+
+
+def density_matrix(basis: AOBasis, n_occ: int, rng: np.random.Generator) -> np.ndarray:
+    """A random symmetric positive semi-definite P = 2 C C^T with n_occ orbitals."""
+    C = rng.normal(size=(basis.nbf, n_occ)) * 0.4
+    return 2.0 * C @ C.T
+
+
+def ao_system(mol: Molecule, n_rad: int, n_ang: int, seed: int, n_trials: int = 0):
+    """The molecular grid of mol with an AO-built density: (GridDensity, phi, grad phi, P,
+    P^t (n_trials x nbf x nbf, symmetric), rho^t (n_trials x N), grad rho^t)."""
+    rng = np.random.default_rng(seed)
+    pts, w, own = molecular_grid(mol, n_rad, n_ang)
+    basis = ao_basis(mol)
+    phi, dphi = ao_values(basis, pts)
+    P = density_matrix(basis, max(1, int(mol.charges.sum()) // 2), rng)
+    rho, grad = ao_density(phi, dphi, P)
+    Pt = rng.normal(size=(n_trials, basis.nbf, basis.nbf)) * 0.1
+    Pt = Pt + Pt.transpose(0, 2, 1)
+    rt = np.zeros((n_trials, pts.shape[0]))
+    gt = np.zeros((n_trials, pts.shape[0], 3))
+    for t in range(n_trials):
+        rt[t], gt[t] = ao_density(phi, dphi, Pt[t])
+    g = GridDensity(pts, w, rho, grad, own, mol)
+    return g, phi, dphi, P, Pt, rt, gt
+
+
 def config_water(n_rad: int = 30, n_ang: int = 110) -> GridDensity:
     """Water, 30 x 110 points per atom = 9,900 points."""
     return make_system(water(), n_rad, n_ang)

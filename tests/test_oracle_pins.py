@@ -440,3 +440,55 @@ def test_weight_sums_are_potential_derivatives(oracle_mod):
         np.testing.assert_allclose(an, dvr, rtol=1e-8, atol=1e-12 * np.abs(dvr).max())
         # the three sums are independent: each term alone is far from the derivative
         assert np.abs(E[p] - dvr).max() > 1e-3 * np.abs(dvr).max()
+
+
+# --------------------------------------------------------------------- AO-side assembly
+
+def _ao_case(n_trials=0, seed=5):
+    """A water grid with an AO-built density, restricted to points well above the cutoff so
+    that finite differences of the density matrix move no point across it."""
+    g, phi, dphi, P, Pt, rt, gt = synth.ao_system(synth.water(), 8, 14, seed, n_trials)
+    m = g.rho > 1e-6
+    h = synth.GridDensity(g.coords[m], g.weights[m], g.rho[m], g.grad_rho[m],
+                          g.atom_of_point[m], g.molecule)
+    return h, phi[m], dphi[m], P, Pt, rt[:, m], gt[:, m]
+
+
+def test_fock_matrix_is_energy_derivative(oracle_mod):
+    """F_mu_nu = dE/dP_mu_nu for rho = sum P_mu_nu phi_mu phi_nu (Sec. II.A): central
+    differences of the oracle energy along the symmetric direction E_mu_nu + E_nu_mu."""
+    g, phi, dphi, P, _, _, _ = _ao_case()
+    _, vr, vg = oracle_mod.potential(g.coords, g.weights, g.rho, g.grad_rho)
+    F = oracle_mod.fock_matrix(g.weights, g.grad_rho, vr, vg, phi, dphi)
+    np.testing.assert_allclose(F, F.T, rtol=1e-12, atol=1e-14 * np.abs(F).max())
+    nbf = P.shape[0]
+    h = 1e-5
+    for mu, nu in [(0, 0), (0, 3), (2, 7), (5, 5), (4, nbf - 1), (nbf - 1, nbf - 1)]:
+        D = np.zeros_like(P)
+        D[mu, nu] += 1.0
+        D[nu, mu] += 1.0
+        def energy(Pm):
+            r, gr = synth.ao_density(phi, dphi, Pm)
+            return oracle_mod.energy(g.coords, g.weights, r, gr)
+        fd = (energy(P + h * D) - energy(P - h * D)) / (2 * h)
+        assert fd == pytest.approx(2.0 * F[mu, nu], rel=1e-6, abs=1e-9 * np.abs(F).max())
+
+
+def test_orbital_hessian_is_fock_derivative(oracle_mod):
+    """G^t_mu_nu = dF_mu_nu/dP along P^t (Sec. II.B; the trial density is rho^t = sum P^t phi
+    phi): central differences of the oracle Fock matrix, with the oracle potential at P +- h P^t,
+    against the assembly of the oracle Hessian contraction."""
+    g, phi, dphi, P, Pt, rt, gt = _ao_case(n_trials=2, seed=6)
+    _, vr, vg = oracle_mod.potential(g.coords, g.weights, g.rho, g.grad_rho)
+    fr, fg = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+    G = oracle_mod.orbital_hessian(g.weights, g.grad_rho, vg, fr, fg, gt, phi, dphi)
+    h = 1e-5
+    for t in range(2):
+        np.testing.assert_allclose(G[t], G[t].T, rtol=1e-12, atol=1e-14 * np.abs(G[t]).max())
+        Fs = []
+        for sgn in (1, -1):
+            r, gr = synth.ao_density(phi, dphi, P + sgn * h * Pt[t])
+            _, vr2, vg2 = oracle_mod.potential(g.coords, g.weights, r, gr)
+            Fs.append(oracle_mod.fock_matrix(g.weights, gr, vr2, vg2, phi, dphi))
+        fd = (Fs[0] - Fs[1]) / (2 * h)
+        np.testing.assert_allclose(G[t], fd, rtol=1e-5, atol=1e-8 * np.abs(G[t]).max())

@@ -104,3 +104,28 @@ def test_weight_directions_are_becke_weight_derivatives():
     assert V.shape == (3 * mol.n_atom, pts.shape[0])
     np.testing.assert_allclose(V.reshape(mol.n_atom, 3, -1).sum(axis=0), 0.0,
                                atol=1e-12 * np.abs(V).max())
+
+
+def test_ao_basis_values_gradients_and_density():
+    """Basis functions normalised to unit self-overlap, analytic gradients against central
+    differences, and the AO density's gradient against central differences."""
+    mol = synth.water()
+    b = synth.ao_basis(mol)
+    rng = np.random.default_rng(3)
+    pts = rng.normal(size=(40, 3)) * 1.5
+    phi, dphi = synth.ao_values(b, pts)
+    P = synth.density_matrix(b, 5, rng)
+    rho, grad = synth.ao_density(phi, dphi, P)
+    h = 1e-6
+    for d in range(3):
+        pp, pm = pts.copy(), pts.copy()
+        pp[:, d] += h
+        pm[:, d] -= h
+        fp, fm = synth.ao_values(b, pp)[0], synth.ao_values(b, pm)[0]
+        np.testing.assert_allclose(dphi[:, :, d], (fp - fm) / (2 * h), atol=1e-8)
+        rp = synth.ao_density(fp, synth.ao_values(b, pp)[1], P)[0]
+        rm = synth.ao_density(fm, synth.ao_values(b, pm)[1], P)[0]
+        np.testing.assert_allclose(grad[:, d], (rp - rm) / (2 * h), atol=1e-8 * np.abs(grad).max())
+    assert (rho >= 0).all()  # P is positive semi-definite
+    g, phi, _, _, _, _, _ = synth.ao_system(mol, 30, 110, 1)
+    np.testing.assert_allclose((g.weights[:, None] * phi ** 2).sum(axis=0), 1.0, atol=5e-3)
