@@ -65,6 +65,7 @@ typedef struct vv10_ctx* vv10_handle;
 /* Limits of this build. */
 #define VV10_MAX_ATOMS 4096
 #define VV10_MAX_TRIALS 4096
+#define VV10_MAX_BASIS 4096
 
 /* Create a handle bound to CUDA device `device`.  Allocates no large buffers yet.
  * Errors: INVALID_ARG (h NULL, bad device), CUDA. */
@@ -197,6 +198,33 @@ vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grg
 vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
                                  const double* w_t, double* E_t, double* U_t, double* W_t,
                                  void* stream);
+
+/* AO-side assembly (Sec. II.A, the VV10 contribution to the Fock matrix; Sec. II.B, the
+ * contracted orbital Hessian), from the per-point results of the calls above:
+ *   F_mu_nu   = sum_i w_i [f^rho_i phi_mu phi_nu
+ *                          + 2 f^gamma_i grad rho_i . (phi_nu grad phi_mu + phi_mu grad phi_nu)]
+ *   G^t_mu_nu = sum_i w_i [f^{rho,t}_i phi_mu phi_nu
+ *                          + 2 (f^{gamma,t}_i grad rho_i + f^gamma_i grad rho^t_i)
+ *                            . (phi_nu grad phi_mu + phi_mu grad phi_nu)]
+ * over the points kept at vv10_prepare_points (w and grad rho as prepared), in FP64 (a batched
+ * cuBLAS DGEMM over the points).  For rho = sum P_mu_nu phi_mu phi_nu, F_mu_nu = dE/dP_mu_nu
+ * and G^t = dF along P^t.
+ *   nbf          number of basis functions, 1 <= nbf <= VV10_MAX_BASIS
+ *   phi          n x nbf device in, phi_mu at point i at phi[i nbf + mu] (caller order)
+ *   grad_phi     n x nbf x 3 device in
+ *   vrho, vgamma n device in: f^rho, f^gamma from vv10_energy_potential / vv10_evaluate
+ *   F            nbf x nbf device out (symmetric)
+ *   P            trials, f_rho_t, f_gamma_t (P x n) from vv10_hessian_contract, grad_rho_t
+ *                (P x n x 3) its input
+ *   G            P x nbf x nbf device out (each symmetric)
+ * Scratch: nbf n_kept doubles, and about 1 GB at most for the per-trial operands (trials are
+ * taken in chunks).  Errors: INVALID_ARG, UNSUPPORTED (nbf or P too large), OOM, CUDA. */
+vv10_status vv10_fock_matrix(vv10_handle h, int32_t nbf, const double* phi, const double* grad_phi,
+                             const double* vrho, const double* vgamma, double* F, void* stream);
+vv10_status vv10_orbital_hessian(vv10_handle h, int32_t nbf, const double* phi,
+                                 const double* grad_phi, int32_t P, const double* f_rho_t,
+                                 const double* f_gamma_t, const double* grad_rho_t,
+                                 const double* vgamma, double* G, void* stream);
 
 /* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
  * by the last vv10_energy_potential call.  dEdw: n device out. */
@@ -363,7 +391,7 @@ vv10_status vv10_set_autotune(vv10_handle h, int flags);
  * vv10_profile_read synchronises the device, writes for phases 0..n-1 (n <= VV10_N_PHASES)
  * the accumulated milliseconds (ms, may be NULL; 0 when timing was off) and launch counts
  * (launches, may be NULL), then resets both.  Phase names: vv10_profile_phase_name. */
-#define VV10_N_PHASES 14
+#define VV10_N_PHASES 15
 vv10_status vv10_profile_enable(vv10_handle h, int on);
 vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches);
 const char* vv10_profile_phase_name(int phase);

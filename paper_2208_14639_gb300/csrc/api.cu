@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -63,6 +63,8 @@ void vv10_ctx::release_all() {
     }
     if (h_pinned) cudaFreeHost(h_pinned);
     h_pinned = nullptr;
+    ao_blas_destroy(blas);
+    blas = nullptr;
     for (ProfRec& r : prof) {
         event_pool.push_back(r.a);
         event_pool.push_back(r.b);
@@ -759,6 +761,79 @@ vv10_status vv10_energy(vv10_handle h, vv10_precision prec, double* energy, void
     return VV10_OK;
 }
 
+// Shared part of vv10_fock_matrix and vv10_orbital_hessian.
+static vv10_status ao_assemble(vv10_handle h, int32_t nbf, const double* phi, const double* dphi,
+                               int32_t n_ch, const double* s, const double* fg, const double* vg,
+                               const double* gt, double* out, void* stream) {
+    PointsDev& P = h->P;
+    if (nbf < 1 || nbf > VV10_MAX_BASIS) {
+        h->set_error("nbf must be in [1, VV10_MAX_BASIS]");
+        return nbf < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    const void* ins[] = {phi, dphi, s, fg, out};
+    for (const void* q : ins)
+        if (!device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+            h->set_error("arrays must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    if ((vg != nullptr) != (gt != nullptr) ||
+        (vg && (!device_ptr_ok(vg, h->device) || !device_ptr_ok(gt, h->device)))) {
+        h->set_error("vgamma and grad_rho_t must be device pointers");
+        return VV10_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!h->blas && ao_blas_create(&h->blas) != 0) {
+        h->blas = nullptr;
+        h->set_error("cuBLAS handle creation failed");
+        return VV10_ERR_CUDA;
+    }
+    const size_t nk = static_cast<size_t>(P.nk > 0 ? P.nk : 1);
+    const int64_t chunk = ao_channels_per_chunk(P.nk, nbf, n_ch, size_t(1) << 30);
+    VV10_TRY(h->ensure(h->aophik, sizeof(double) * nk * nbf, "gathered basis values"));
+    VV10_TRY(h->ensure(h->aoz, sizeof(double) * nk * nbf * chunk, "assembly operand"));
+    VV10_TRY(h->ensure(h->aom, sizeof(double) * static_cast<size_t>(nbf) * nbf * chunk, "assembly products"));
+    int bs = 0;
+    PhaseScope ph(h, PH_AO_ASSEMBLY, st, P.nk > 0 ? 1 + 2 * static_cast<int>((n_ch + chunk - 1) / chunk) : 0);
+    VV10_CUDA(h, launch_ao_assemble(P, h->blas, nbf, phi, dphi, n_ch, s, fg, vg, gt, chunk,
+                                    static_cast<double*>(h->aophik.p), static_cast<double*>(h->aoz.p),
+                                    static_cast<double*>(h->aom.p), out, st, &bs),
+              "AO assembly");
+    if (bs != 0) {
+        h->set_error("cuBLAS failed (status %d) in the AO assembly", bs);
+        return VV10_ERR_CUDA;
+    }
+    return VV10_OK;
+}
+
+vv10_status vv10_fock_matrix(vv10_handle h, int32_t nbf, const double* phi, const double* grad_phi,
+                             const double* vrho, const double* vgamma, double* F, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    VV10_TRY(h->bind());
+    return ao_assemble(h, nbf, phi, grad_phi, 1, vrho, vgamma, nullptr, nullptr, F, stream);
+}
+
+vv10_status vv10_orbital_hessian(vv10_handle h, int32_t nbf, const double* phi,
+                                 const double* grad_phi, int32_t P_trials, const double* f_rho_t,
+                                 const double* f_gamma_t, const double* grad_rho_t,
+                                 const double* vgamma, double* G, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (P_trials < 1 || P_trials > VV10_MAX_TRIALS) {
+        h->set_error("P must be in [1, VV10_MAX_TRIALS]");
+        return P_trials < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    if (!vgamma || !grad_rho_t) {
+        h->set_error("vgamma and grad_rho_t are required");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    return ao_assemble(h, nbf, phi, grad_phi, P_trials, f_rho_t, f_gamma_t, vgamma, grad_rho_t, G,
+                       stream);
+}
+
 vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
                           const double* rho_t, const double* grad_rho_t, double* energy,
                           double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
@@ -902,7 +977,7 @@ const char* vv10_profile_phase_name(int phase) {
     static const char* names[PH_COUNT] = {
         "prepare", "pair_sums_EUW", "energy_epilogue", "pair_sums_ABC", "trial_prep",
         "contraction_fp64", "contraction_tensor_core", "hessian_epilogue", "pair_sums_grad",
-        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response", "energy_half"};
+        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response", "energy_half", "ao_assembly"};
     return (phase >= 0 && phase < PH_COUNT) ? names[phase] : "unknown";
 }
 

@@ -205,4 +205,17 @@ int energy_half_grid(bool fp64, int n_sm);
 cudaError_t launch_energy_half(const PointsDev& p, bool fp64, int grid, double* cta_total,
                                double* energy, cudaStream_t st);
 
+// AO-side assembly (Sec. II.A Fock matrix, Sec. II.B contracted orbital Hessian): out[c] =
+// M_c + M_c^T, M_c = Phi^T Z_c over the kept points, channels in chunks of `chunk`
+// (ao_channels_per_chunk).  blas: a cuBLAS handle (ao_blas_create).  Scratch: phik (nk x nbf),
+// Z (chunk x nk x nbf), M (chunk x nbf x nbf).  *blas_status != 0 reports a cuBLAS failure.
+int64_t ao_channels_per_chunk(int64_t nk, int32_t nbf, int32_t n_ch, size_t max_bytes);
+cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, const double* phi,
+                               const double* dphi, int32_t n_ch, const double* s,
+                               const double* fg, const double* vg, const double* gt,
+                               int64_t chunk, double* phik, double* Z, double* M, double* out,
+                               cudaStream_t st, int* blas_status);
+int ao_blas_create(void** blas);
+void ao_blas_destroy(void* blas);
+
 }  // namespace vv10

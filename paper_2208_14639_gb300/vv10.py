@@ -48,10 +48,11 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_batch_prepare", "vv10_batch_energy_potential", "vv10_batch_hessian_contract",
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
            "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
-           "vv10_weight_response", "vv10_energy")
+           "vv10_weight_response", "vv10_energy", "vv10_fock_matrix",
+           "vv10_orbital_hessian")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
-VV10_N_PHASES = 14
+VV10_N_PHASES = 15
 
 
 class VV10Params(ctypes.Structure):
@@ -98,6 +99,8 @@ def load(build_if_missing: bool = False):
         "vv10_coord_hessian": (st, [P, st, P, P, P]),
         "vv10_weight_response": (st, [P, st, ctypes.c_int32, P, P, P, P, P]),
         "vv10_energy": (st, [P, st, ctypes.POINTER(D), P]),
+        "vv10_fock_matrix": (st, [P, I32, P, P, P, P, P, P]),
+        "vv10_orbital_hessian": (st, [P, I32, P, P, I32, P, P, P, P, P, P]),
         "vv10_weight_grad": (st, [P, P, P]),
         "vv10_sync": (st, [P, P]),
         "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -235,6 +238,27 @@ def vv10_energy(h, prec: int, stream=None) -> float:
     e = ctypes.c_double()
     _check(h, load().vv10_energy(h, int(prec), ctypes.byref(e), _stream(stream)), "vv10_energy")
     return e.value
+
+
+def vv10_fock_matrix(h, phi, grad_phi, vrho, vgamma, F, stream=None) -> None:
+    n, nbf = phi.shape
+    st = load().vv10_fock_matrix(h, int(nbf), _dptr(phi, "phi", shape=(n, nbf)),
+                                 _dptr(grad_phi, "grad_phi", shape=(n, nbf, 3)),
+                                 _dptr(vrho, "vrho", shape=(n,)), _dptr(vgamma, "vgamma", shape=(n,)),
+                                 _dptr(F, "F", shape=(nbf, nbf)), _stream(stream))
+    _check(h, st, "vv10_fock_matrix")
+
+
+def vv10_orbital_hessian(h, phi, grad_phi, f_rho_t, f_gamma_t, grad_rho_t, vgamma, G,
+                         stream=None) -> None:
+    n, nbf = phi.shape
+    P = int(f_rho_t.shape[0])
+    st = load().vv10_orbital_hessian(
+        h, int(nbf), _dptr(phi, "phi", shape=(n, nbf)), _dptr(grad_phi, "grad_phi", shape=(n, nbf, 3)),
+        P, _dptr(f_rho_t, "f_rho_t", shape=(P, n)), _dptr(f_gamma_t, "f_gamma_t", shape=(P, n)),
+        _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)), _dptr(vgamma, "vgamma", shape=(n,)),
+        _dptr(G, "G", shape=(P, nbf, nbf)), _stream(stream))
+    _check(h, st, "vv10_orbital_hessian")
 
 
 def vv10_weight_grad(h, dEdw, stream=None) -> None:
@@ -458,6 +482,19 @@ class VV10:
         D = torch.empty(self.n, self.n_atom, 3, 3, **f64) if points else None
         vv10_coord_hessian(self.h, prec, E, D, stream)
         return E, D
+
+    def fock_matrix(self, phi, grad_phi, vrho, vgamma, stream=None):
+        """The VV10 Fock matrix (nbf x nbf) from f^rho, f^gamma and the basis on the grid."""
+        F = torch.empty(phi.shape[1], phi.shape[1], dtype=torch.float64, device=phi.device)
+        vv10_fock_matrix(self.h, phi, grad_phi, vrho, vgamma, F, stream)
+        return F
+
+    def orbital_hessian(self, phi, grad_phi, f_rho_t, f_gamma_t, grad_rho_t, vgamma, stream=None):
+        """G^t (P x nbf x nbf) from the Hessian contraction and the basis on the grid."""
+        G = torch.empty(f_rho_t.shape[0], phi.shape[1], phi.shape[1], dtype=torch.float64,
+                        device=phi.device)
+        vv10_orbital_hessian(self.h, phi, grad_phi, f_rho_t, f_gamma_t, grad_rho_t, vgamma, G, stream)
+        return G
 
     def energy(self, prec=VV10_FP64, stream=None) -> float:
         """E alone, from the unordered pairs (half the pair evaluations)."""
