@@ -353,6 +353,37 @@ def weight_response_roofline(prec, P, pairs, ms, alu_peak_ops, peaks):
     return out
 
 
+def time_ao_assembly(vv, h, pb, reps):
+    """The AO-side assembly (vv10_fock_matrix, vv10_orbital_hessian) of the step's outputs with
+    the synthetic Gaussian basis of the molecule on the grid: (ms per Fock matrix, ms per
+    orbital-Hessian call for the P trials, nbf)."""
+    import torch
+    from paper_2208_14639_gb300 import synth
+    basis = synth.ao_basis(pb.g.molecule)
+    phi, dphi = synth.ao_values(basis, pb.host["xyz"])
+    dev = pb.d["xyz"].device
+    phi, dphi = torch.from_numpy(phi).to(dev), torch.from_numpy(dphi).to(dev)
+    o, d = pb.out, pb.d
+    nbf = basis.nbf
+    F = torch.empty(nbf, nbf, dtype=torch.float64, device=dev)
+    G = torch.empty(pb.P, nbf, nbf, dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    stream = torch.cuda.current_stream()
+    vv.vv10_fock_matrix(h, phi, dphi, o["vrho"], o["vgamma"], F)
+    vv.vv10_orbital_hessian(h, phi, dphi, o["frt"], o["fgt"], d["gt"], o["vgamma"], G)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        vv.vv10_fock_matrix(h, phi, dphi, o["vrho"], o["vgamma"], F)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(reps):
+        vv.vv10_orbital_hessian(h, phi, dphi, o["frt"], o["fgt"], d["gt"], o["vgamma"], G)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps, ev[2].elapsed_time(ev[3]) / reps, nbf
+
+
 def time_e2e(vv, h, pb, prec, steps, warmup):
     """The same step with host inputs: every step copies all of its inputs from pinned host
     memory to the device and all of its outputs back, inside the timed region.  The copies
@@ -488,6 +519,7 @@ def gpu_arm(args):
     wdirs = pb.weight_dirs()
     P_w = int(wdirs.shape[0])
     ms_wr = time_weight_response(vv, h, pb, prec, wdirs, 3)
+    ms_fock, ms_gt, nbf = time_ao_assembly(vv, h, pb, 3)
     alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     breakdown = {
         # the two metric quantities, each timed as its own entry point (3 calls each)
@@ -506,6 +538,12 @@ def gpu_arm(args):
         "coord_hessian_pairs": pairs_ch,
         "coord_hessian_pairs_per_s": pairs_ch / (ms_ch / 1e3),
         "coord_hessian_alu_frac": ALU_OPS_PER_PAIR_CH * pairs_ch / (ms_ch / 1e3) / alu_peak_ops,
+        # AO-side assembly of the step's outputs (FP64 cuBLAS GEMM over the kept points;
+        # not part of the step): 2 nbf^2 flops per point and channel
+        "ao_nbf": nbf,
+        "fock_matrix_call_ms": ms_fock,
+        "orbital_hessian_call_ms": ms_gt,
+        "orbital_hessian_fp64_tflops": 2.0 * nbf * nbf * nk * pb.P / (ms_gt / 1e3) / 1e12,
         # weight-derivative sums for the 3 N_atom Becke weight directions (not part of the step)
         "weight_response_P": P_w,
         "weight_response_call_ms": ms_wr,
