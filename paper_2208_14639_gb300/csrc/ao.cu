@@ -3,8 +3,8 @@
 //   M_mu_nu = sum_i w_i [s_i phi_mu phi_nu + 2 v_i . (phi_nu grad phi_mu + phi_mu grad phi_nu)]
 // with (s, v) = (f^rho, f^gamma grad rho) for F and (f^{rho,t}, f^{gamma,t} grad rho +
 // f^gamma grad rho^t) for G^t.  With Z_i,mu = w_i (s_i phi_i,mu / 2 + 2 v_i . grad phi_i,mu),
-// M = Phi^T Z + Z^T Phi: a plain FP64 GEMM over the kept points (cuBLAS, batched over
-// channels), then the symmetrisation.
+// M = Phi^T Z + Z^T Phi: a plain FP64 GEMM over the kept points (cuBLAS; the channels of a
+// chunk side by side as the columns of one product), then the symmetrisation.
 #include <cublas_v2.h>
 
 #include "common.cuh"
@@ -23,9 +23,9 @@ __global__ void k_ao_gather(PointsDev P, int32_t nbf, const double* __restrict__
     phik[e] = phi[P.orig[k] * nbf + mu];
 }
 
-// Z[c][k][mu] for the channels c0 .. c0 + gridDim.y - 1.  s: channel c's scalar at caller
-// point i = s[c n + i]; the vector part is fg[c n + i] grad rho_k (+ vg[i] gt[(c n + i) 3 + d]
-// when gt is given).
+// Z[k][c - c0][mu] (rows of nc x nbf) for the channels c0 .. c0 + nc - 1, nc = gridDim.y.
+// s: channel c's scalar at caller point i = s[c n + i]; the vector part is fg[c n + i]
+// grad rho_k (+ vg[i] gt[(c n + i) 3 + d] when gt is given).
 __global__ void k_ao_z(PointsDev P, int32_t nbf, const double* __restrict__ phi,
                        const double* __restrict__ dphi, const double* __restrict__ s,
                        const double* __restrict__ fg, const double* __restrict__ vg,
@@ -47,7 +47,7 @@ __global__ void k_ao_z(PointsDev P, int32_t nbf, const double* __restrict__ phi,
     }
     const int64_t a = i * nbf + mu;
     const double* d = dphi + 3 * a;
-    Z[static_cast<int64_t>(blockIdx.y) * P.nk * nbf + e] =
+    Z[(k * gridDim.y + blockIdx.y) * nbf + mu] =
         w * (0.5 * s[ci] * phi[a] + 2.0 * (vx * d[0] + vy * d[1] + vz * d[2]));
 }
 
@@ -95,10 +95,12 @@ cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, cons
         k_ao_z<<<dim3(gx, static_cast<unsigned>(nc)), 256, 0, st>>>(p, nbf, phi, dphi, s, fg, vg, gt, c0, Z);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        // M_c (column-major) = A B^T with A = phik viewed as nbf x nk (column-major), B = Z_c
-        const cublasStatus_t bs = cublasDgemmStridedBatched(
-            h, CUBLAS_OP_N, CUBLAS_OP_T, nbf, nbf, static_cast<int>(p.nk), &one, phik, nbf, 0, Z, nbf,
-            ne, &zero, M, nbf, nn, nc);
+        // one GEMM for the chunk: M (column-major nbf x nc nbf) = A B^T with A = phik viewed
+        // as nbf x nk and B = Z viewed as (nc nbf) x nk (both column-major); column c nbf + nu
+        // of M is column nu of M_c
+        const cublasStatus_t bs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nbf, nc * nbf,
+                                              static_cast<int>(p.nk), &one, phik, nbf, Z, nc * nbf,
+                                              &zero, M, nbf);
         if (bs != CUBLAS_STATUS_SUCCESS) {
             *blas_status = static_cast<int>(bs);
             return cudaSuccess;
