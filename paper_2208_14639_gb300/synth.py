@@ -389,6 +389,36 @@ def trial_densities(mol: Molecule, points: np.ndarray, atoms: Optional[Sequence[
     return rho_t, grad_t
 
 
+def density_hessian(mol: Molecule, points: np.ndarray) -> np.ndarray:
+    """The spatial Hessian of rho (N, 3, 3) for the sum of atomic s-Gaussians."""
+    H = np.zeros((points.shape[0], 3, 3))
+    alphas = np.array(GAUSS_EXPONENTS)
+    eye = np.eye(3)
+    for z, centre in zip(mol.charges, mol.coords):
+        d = points - centre
+        r2 = np.einsum("ij,ij->i", d, d)
+        for c, a in zip(_gauss_coeffs(z), alphas):
+            e = c * np.exp(-a * r2)
+            H += e[:, None, None] * (4.0 * a * a * d[:, :, None] * d[:, None, :] - 2.0 * a * eye[None])
+    return H
+
+
+def nuclear_density_derivatives(mol: Molecule, points: np.ndarray, atom_of_point: np.ndarray):
+    """d rho_i / d R_{A,c} and d grad rho_i / d R_{A,c} at grid points that move with their atom
+    (r_i - R_owner fixed): the derivative at a fixed point (trial_densities) plus, for the
+    owner atom, the spatial derivative at the point.  (3 N_atom, N) and (3 N_atom, N, 3),
+    t = 3 A + c."""
+    rt, gt = trial_densities(mol, points)
+    _, grad = density(mol, points)
+    H = density_hessian(mol, points)
+    for A in range(mol.n_atom):
+        m = atom_of_point == A
+        for c in range(3):
+            rt[3 * A + c, m] += grad[m, c]
+            gt[3 * A + c, m] += H[m, c, :]
+    return rt, gt
+
+
 def trial_densities_torch(mol: Molecule, points, atoms: Optional[Sequence[int]] = None,
                           out_rho=None, out_grad=None):
     """trial_densities evaluated with torch on the device of `points` (an (N, 3) float64

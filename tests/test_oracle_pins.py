@@ -492,3 +492,40 @@ def test_orbital_hessian_is_fock_derivative(oracle_mod):
             Fs.append(oracle_mod.fock_matrix(g.weights, gr, vr2, vg2, phi, dphi))
         fd = (Fs[0] - Fs[1]) / (2 * h)
         np.testing.assert_allclose(G[t], fd, rtol=1e-5, atol=1e-8 * np.abs(G[t]).max())
+
+
+# --------------------------------------------------------------------- nuclear gradient
+
+def test_nuclear_gradient_from_its_terms(oracle_mod):
+    """E^A = E^A_G + E^A_w + E^A_gr (Sec. II.A) against central differences of the energy of
+    the whole synthetic pipeline (grid points, Becke weights and density all moving with the
+    atoms): E^A_G from the potential and the density derivatives at the moving points, E^A_w
+    from dE/dw_i = rho_i (beta + E_i) and the Becke weight derivatives, E^A_gr from the first
+    form of the grid-position gradient."""
+    mol = synth.water()
+    nr, na = 10, 26
+    g = synth.make_system(mol, nr, na)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    kept = g.rho >= 1e-10
+    _, vr, vg = oracle_mod.potential(*args)
+    E = oracle_mod.pair_sums(*args)["E"]
+    rt, gt = synth.nuclear_density_derivatives(mol, g.coords, g.atom_of_point)
+    W = synth.weight_directions(mol, nr, na)
+    ga = oracle_mod.atom_grad(*args, g.atom_of_point, mol.n_atom)
+    an = np.zeros(3 * mol.n_atom)
+    for p in range(an.size):
+        e_g = np.sum(g.weights * (vr * rt[p] + 2 * vg * np.einsum("nd,nd->n", g.grad_rho, gt[p])))
+        e_w = np.sum((W[p] * g.rho * (oracle_mod.beta() + E))[kept])
+        an[p] = e_g + e_w + ga[p // 3, p % 3]
+    h = 1e-4
+    for p in range(an.size):
+        es = []
+        for sg in (1, -1):
+            c = mol.coords.copy()
+            c[p // 3, p % 3] += sg * h
+            g2 = synth.make_system(synth.Molecule(mol.symbols, c), nr, na)
+            assert np.array_equal(g2.rho >= 1e-10, kept)  # no point crosses the cutoff
+            es.append(oracle_mod.energy(g2.coords, g2.weights, g2.rho, g2.grad_rho))
+        assert (es[0] - es[1]) / (2 * h) == pytest.approx(an[p], rel=1e-6, abs=1e-7 * np.abs(an).max())
+    # translational invariance of the whole gradient
+    assert np.abs(an.reshape(-1, 3).sum(axis=0)).max() <= 1e-6 * np.abs(an).max()
