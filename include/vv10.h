@@ -226,6 +226,23 @@ vv10_status vv10_orbital_hessian(vv10_handle h, int32_t nbf, const double* phi,
                                  const double* f_gamma_t, const double* grad_rho_t,
                                  const double* vgamma, double* G, void* stream);
 
+/* The density and weight terms of the VV10 nuclear gradient (Sec. II.A, E^A_G and E^A_w) along
+ * P directions p:
+ *   out[p] = sum_i w_i (f^rho_i rho^p_i + 2 f^gamma_i grad rho_i . grad rho^p_i)
+ *          + sum_i w^p_i rho_i (beta + E_i)
+ * with f^rho, f^gamma, E_i from the row sums cached by the last vv10_energy_potential (or
+ * vv10_evaluate) call, which must precede (else INVALID_ARG).  For p = (A, c), rho^p and
+ * grad rho^p the derivatives of the density at grid points that move with their atoms and
+ * w^p the derivatives of the weights, out[3 A + c] plus E^A_gr (vv10_coord_grad's grad_atoms)
+ * is the VV10 nuclear gradient.
+ *   rho_t, grad_rho_t   P x n and P x n x 3 device in (caller order; both or neither)
+ *   w_t                 P x n device in (may be NULL; at least one of the two terms)
+ *   out                 P device out
+ * Sums over the kept points in a fixed order.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+vv10_status vv10_nuclear_gradient(vv10_handle h, int32_t P, const double* rho_t,
+                                  const double* grad_rho_t, const double* w_t, double* out,
+                                  void* stream);
+
 /* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
  * by the last vv10_energy_potential call.  dEdw: n device out. */
 vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
@@ -391,7 +408,7 @@ vv10_status vv10_set_autotune(vv10_handle h, int flags);
  * vv10_profile_read synchronises the device, writes for phases 0..n-1 (n <= VV10_N_PHASES)
  * the accumulated milliseconds (ms, may be NULL; 0 when timing was off) and launch counts
  * (launches, may be NULL), then resets both.  Phase names: vv10_profile_phase_name. */
-#define VV10_N_PHASES 15
+#define VV10_N_PHASES 16
 vv10_status vv10_profile_enable(vv10_handle h, int on);
 vv10_status vv10_profile_read(vv10_handle h, int n, double* ms, int64_t* launches);
 const char* vv10_profile_phase_name(int phase);

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &ngpart, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -542,6 +542,47 @@ vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream) {
     return VV10_OK;
 }
 
+vv10_status vv10_nuclear_gradient(vv10_handle h, int32_t P_dir, const double* rho_t,
+                                  const double* grad_rho_t, const double* w_t, double* out,
+                                  void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (!h->have_euw) {
+        h->set_error("vv10_energy_potential must be called first");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (P_dir < 1 || P_dir > VV10_MAX_TRIALS) {
+        h->set_error("P must be in [1, VV10_MAX_TRIALS]");
+        return P_dir < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    if ((rho_t != nullptr) != (grad_rho_t != nullptr) || (!rho_t && !w_t)) {
+        h->set_error("give rho_t with grad_rho_t, w_t, or both");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    const void* ptrs[] = {rho_t, grad_rho_t, w_t, out};
+    for (const void* q : ptrs)
+        if (q && (!device_ptr_ok(q, h->device) || !aligned(q, 8))) {
+            h->set_error("arrays must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    if (!out) {
+        h->set_error("out is required");
+        return VV10_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t np = static_cast<size_t>(P_dir) * static_cast<size_t>(ngrad_blocks(h->P.nk));
+    VV10_TRY(h->ensure(h->ngpart, sizeof(double) * np, "nuclear-gradient partials"));
+    PhaseScope ph(h, PH_NUCLEAR_GRADIENT, st, h->P.nk > 0 ? 2 : 0);
+    VV10_CUDA(h, launch_nuclear_gradient(h->P, static_cast<double*>(h->sumE.p),
+                                         static_cast<double*>(h->sumU.p), static_cast<double*>(h->sumW.p),
+                                         P_dir, rho_t, grad_rho_t, w_t,
+                                         static_cast<double*>(h->ngpart.p), out, st),
+              "nuclear gradient terms");
+    return VV10_OK;
+}
+
 vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P_trials,
                                   const double* rho_t, const double* grad_rho_t,
                                   double* f_rho_t, double* f_gamma_t, void* stream) {
@@ -977,7 +1018,7 @@ const char* vv10_profile_phase_name(int phase) {
     static const char* names[PH_COUNT] = {
         "prepare", "pair_sums_EUW", "energy_epilogue", "pair_sums_ABC", "trial_prep",
         "contraction_fp64", "contraction_tensor_core", "hessian_epilogue", "pair_sums_grad",
-        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response", "energy_half", "ao_assembly"};
+        "grad_epilogue", "atom_resolved", "coord_hessian", "weight_response", "energy_half", "ao_assembly", "nuclear_gradient"};
     return (phase >= 0 && phase < PH_COUNT) ? names[phase] : "unknown";
 }
 

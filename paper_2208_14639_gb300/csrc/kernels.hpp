@@ -218,4 +218,13 @@ cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, cons
 int ao_blas_create(void** blas);
 void ao_blas_destroy(void* blas);
 
+// E^A_G + E^A_w (Sec. II.A) for Pn directions from the cached row sums sE, sU, sW (kept
+// order); rt, gt (Pn x n, Pn x n x 3) and wt (Pn x n) in caller order, either pair may be
+// null.  partial: Pn x ngrad_blocks(nk) scratch; out: Pn (device).
+int ngrad_blocks(int64_t nk);
+cudaError_t launch_nuclear_gradient(const PointsDev& p, const double* sE, const double* sU,
+                                    const double* sW, int32_t Pn, const double* rt,
+                                    const double* gt, const double* wt, double* partial,
+                                    double* out, cudaStream_t st);
+
 }  // namespace vv10

@@ -44,7 +44,8 @@ bool stream_capturing(cudaStream_t st);
 enum Phase : int {
     PH_PREPARE = 0, PH_PAIR_EUW, PH_EP_EPILOGUE, PH_PAIR_ABC, PH_TRIAL_PREP, PH_CONTRACT_F64,
     PH_CONTRACT_TC, PH_HESS_EPILOGUE, PH_PAIR_GRAD, PH_GRAD_EPILOGUE, PH_ATOM_RESOLVED,
-    PH_COORD_HESSIAN, PH_WEIGHT_RESPONSE, PH_ENERGY_HALF, PH_AO_ASSEMBLY, PH_COUNT
+    PH_COORD_HESSIAN, PH_WEIGHT_RESPONSE, PH_ENERGY_HALF, PH_AO_ASSEMBLY,
+    PH_NUCLEAR_GRADIENT, PH_COUNT
 };
 
 struct ProfRec {
@@ -140,6 +141,7 @@ struct vv10_ctx {
     vv10::DevBuf wsplit;  // their TF32 hi / FP32 lo split (tensor-core path)
     vv10::DevBuf ehalf;   // per-CTA totals of the energy-only kernel
     vv10::DevBuf aophik, aoz, aom;  // AO assembly: gathered phi, Z, GEMM results
+    vv10::DevBuf ngpart;            // per-block partials of the nuclear-gradient terms
     void* blas = nullptr;            // cuBLAS handle of the AO assembly (made on first use)
 
     // tile overrides (index = mode + 4 * fp64, modes MODE_EUW..MODE_EUWABC), set by

@@ -49,10 +49,10 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
            "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
            "vv10_weight_response", "vv10_energy", "vv10_fock_matrix",
-           "vv10_orbital_hessian")
+           "vv10_orbital_hessian", "vv10_nuclear_gradient")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
-VV10_N_PHASES = 15
+VV10_N_PHASES = 16
 
 
 class VV10Params(ctypes.Structure):
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False):
         "vv10_weight_response": (st, [P, st, ctypes.c_int32, P, P, P, P, P]),
         "vv10_energy": (st, [P, st, ctypes.POINTER(D), P]),
         "vv10_fock_matrix": (st, [P, I32, P, P, P, P, P, P]),
+        "vv10_nuclear_gradient": (st, [P, I32, P, P, P, P, P]),
         "vv10_orbital_hessian": (st, [P, I32, P, P, I32, P, P, P, P, P, P]),
         "vv10_weight_grad": (st, [P, P, P]),
         "vv10_sync": (st, [P, P]),
@@ -259,6 +260,15 @@ def vv10_orbital_hessian(h, phi, grad_phi, f_rho_t, f_gamma_t, grad_rho_t, vgamm
         _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)), _dptr(vgamma, "vgamma", shape=(n,)),
         _dptr(G, "G", shape=(P, nbf, nbf)), _stream(stream))
     _check(h, st, "vv10_orbital_hessian")
+
+
+def vv10_nuclear_gradient(h, out, rho_t=None, grad_rho_t=None, w_t=None, stream=None) -> None:
+    P = int(out.shape[0])
+    n = int((rho_t if rho_t is not None else w_t).shape[1])
+    st = load().vv10_nuclear_gradient(
+        h, P, _dptr(rho_t, "rho_t", shape=(P, n)), _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)),
+        _dptr(w_t, "w_t", shape=(P, n)), _dptr(out, "out", shape=(P,)), _stream(stream))
+    _check(h, st, "vv10_nuclear_gradient")
 
 
 def vv10_weight_grad(h, dEdw, stream=None) -> None:
@@ -482,6 +492,13 @@ class VV10:
         D = torch.empty(self.n, self.n_atom, 3, 3, **f64) if points else None
         vv10_coord_hessian(self.h, prec, E, D, stream)
         return E, D
+
+    def nuclear_gradient(self, rho_t=None, grad_rho_t=None, w_t=None, stream=None):
+        """E^A_G + E^A_w along the P directions (P,), after an energy call."""
+        ref = rho_t if rho_t is not None else w_t
+        out = torch.empty(ref.shape[0], dtype=torch.float64, device=ref.device)
+        vv10_nuclear_gradient(self.h, out, rho_t, grad_rho_t, w_t, stream)
+        return out
 
     def fock_matrix(self, phi, grad_phi, vrho, vgamma, stream=None):
         """The VV10 Fock matrix (nbf x nbf) from f^rho, f^gamma and the basis on the grid."""
