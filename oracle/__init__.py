@@ -309,3 +309,50 @@ def orbital_hessian(weights, grad_rho, vgamma, f_rho_t, f_gamma_t, grad_rho_t, p
         vdphi = np.einsum("nk,nmk->nm", v, dphi)
         out[t] = phi.T @ (s[:, None] * phi) + vdphi.T @ phi + phi.T @ vdphi
     return out
+
+
+# ---------------------------------------------------------------- nuclear Hessian (numpy)
+
+def nuclear_hessian(weights, rho, grad_rho, kept, kappa_rho, omega_rho, omega_gamma, vrho, vgamma,
+                    E, rho_a, grad_rho_a, rho_ab, grad_rho_ab, w_a, w_ab, E_w, U_w, W_w,
+                    E_gr, U_gr, W_gr, f_rho_a, f_gamma_a, H_grgr) -> np.ndarray:
+    """The nine terms of the VV10 nuclear Hessian (Sec. II.B, Eq. E_hess):
+      E^{ab} = E_GG + E_ww + E_grgr + E_Gw + E_Gw^T + E_Ggr + E_Ggr^T + E_wgr + E_wgr^T
+    with, over the kept points i (a, b = 3 A + c):
+      E_GG  = sum w [f^rho rho^{ab} + f^gamma gamma^{ab} + rho^a f^{rho,b} + gamma^a f^{gamma,b}]
+      E_ww  = sum w^{ab} rho (beta + E) + sum w^a rho E^{bw}
+      E_wgr = sum w^a rho E^{b,gr}
+      E_Gw  = sum w^b (f^rho rho^a + f^gamma gamma^a)
+              + sum w rho^a [E^{bw} + rho (kappa' U^{bw} + omega_rho W^{bw})]
+              + sum w gamma^a rho omega_gamma W^{bw}
+      E_Ggr = sum w rho^a [E^{b,gr} + rho (kappa' U^{b,gr} + omega_rho W^{b,gr})]
+              + sum w gamma^a rho omega_gamma W^{b,gr}
+    gamma^a = 2 grad rho . grad rho^a and gamma^{ab} = 2 (grad rho^a . grad rho^b + grad rho .
+    grad rho^{ab}) are full derivatives of gamma; f^{rho,b}, f^{gamma,b} are the Hessian
+    contraction with the trial (rho^b, grad rho^b); E = the row sums E_i (beta not included);
+    H_grgr = E^{AB}_{gr,gr} flattened to (3 N_atom, 3 N_atom).  Per-point arrays are over all
+    n points (caller order), direction arrays (P, n), second-derivative arrays (P, P, n).
+    Returns (P, P)."""
+    m = np.asarray(kept, dtype=float)
+    w = _f64(weights) * m
+    rho, g = _f64(rho), _f64(grad_rho).reshape(-1, 3)
+    mask = lambda a: np.where(m > 0, np.nan_to_num(_f64(a)), 0.0)
+    kr, omr, omg = mask(kappa_rho), mask(omega_rho), mask(omega_gamma)
+    vr, vg, E = mask(vrho), mask(vgamma), mask(E)
+    ra, ga = _f64(rho_a), _f64(grad_rho_a)
+    gam_a = 2.0 * np.einsum("nd,pnd->pn", g, ga)
+    gam_ab = 2.0 * (np.einsum("and,bnd->abn", ga, ga) + np.einsum("nd,abnd->abn", g, _f64(grad_rho_ab)))
+    wa, wab = _f64(w_a), _f64(w_ab)
+    rb = beta()
+    EGG = (np.einsum("n,abn->ab", w * vr, _f64(rho_ab)) + np.einsum("n,abn->ab", w * vg, gam_ab)
+           + np.einsum("n,an,bn->ab", w, ra, _f64(f_rho_a))
+           + np.einsum("n,an,bn->ab", w, gam_a, _f64(f_gamma_a)))
+    Eww = (np.einsum("abn,n->ab", wab, m * rho * (rb + E))
+           + np.einsum("an,n,bn->ab", wa, m * rho, _f64(E_w)))
+    Ewgr = np.einsum("an,n,bn->ab", wa, m * rho, _f64(E_gr))
+    EGw = (np.einsum("bn,an->ab", wa * m, vr * ra + vg * gam_a)
+           + np.einsum("n,an,bn->ab", w, ra, _f64(E_w) + rho * (kr * _f64(U_w) + omr * _f64(W_w)))
+           + np.einsum("n,an,bn->ab", w, gam_a, rho * omg * _f64(W_w)))
+    EGgr = (np.einsum("n,an,bn->ab", w, ra, _f64(E_gr) + rho * (kr * _f64(U_gr) + omr * _f64(W_gr)))
+            + np.einsum("n,an,bn->ab", w, gam_a, rho * omg * _f64(W_gr)))
+    return EGG + Eww + _f64(H_grgr) + EGw + EGw.T + EGgr + EGgr.T + Ewgr + Ewgr.T

@@ -419,6 +419,56 @@ def nuclear_density_derivatives(mol: Molecule, points: np.ndarray, atom_of_point
     return rt, gt
 
 
+def nuclear_density_second_derivatives(mol: Molecule, points: np.ndarray,
+                                       atom_of_point: np.ndarray):
+    """d^2 rho_i / dR_a dR_b and d^2 grad rho_i / dR_a dR_b (a = 3 A + c) at grid points that move
+    with their atom.  With x_C = r_i - R_C and f_A(i) = [A owns i] - [A = C], each atomic
+    density rho_C contributes f_A f_B d^2 rho_C / dx_c dx_d (and the third derivatives for the
+    gradient).  (3 N_atom, 3 N_atom, N) and (3 N_atom, 3 N_atom, N, 3)."""
+    n, na = points.shape[0], mol.n_atom
+    P = 3 * na
+    r2d = np.zeros((P, P, n))
+    g2d = np.zeros((P, P, n, 3))
+    alphas = np.array(GAUSS_EXPONENTS)
+    eye = np.eye(3)
+    for C, (z, cen) in enumerate(zip(mol.charges, mol.coords)):
+        x = points - cen
+        xx = np.einsum("ij,ij->i", x, x)
+        H = np.zeros((n, 3, 3))
+        T = np.zeros((n, 3, 3, 3))  # T[e, c, d] = d^3 rho_C / dx_e dx_c dx_d
+        for c, a in zip(_gauss_coeffs(z), alphas):
+            e = c * np.exp(-a * xx)
+            H += e[:, None, None] * (4 * a * a * x[:, :, None] * x[:, None, :] - 2 * a * eye[None])
+            T += e[:, None, None, None] * (
+                -8 * a ** 3 * x[:, :, None, None] * x[:, None, :, None] * x[:, None, None, :]
+                + 4 * a * a * (eye[None, :, :, None] * x[:, None, None, :]
+                               + eye[None, :, None, :] * x[:, None, :, None]
+                               + eye[None, None, :, :] * x[:, :, None, None]))
+        f = np.stack([(atom_of_point == A).astype(float) - (1.0 if A == C else 0.0)
+                      for A in range(na)])                                  # (na, n)
+        ff = f[:, None, :] * f[None, :, :]                                  # (na, na, n)
+        r2d += np.einsum("abn,ncd->acbdn", ff, H).reshape(P, P, n)
+        g2d += np.einsum("abn,necd->acbdne", ff, T).reshape(P, P, n, 3)
+    return r2d, g2d
+
+
+def weight_second_derivatives(mol: Molecule, n_rad: int, n_ang: int, h: float = 1e-5) -> np.ndarray:
+    """d^2 w_i / dR_a dR_b (3 N_atom, 3 N_atom, N): central differences (step h bohr) of the
+    analytic first derivatives of weight_directions."""
+    P = 3 * mol.n_atom
+    out = None
+    for b in range(P):
+        Ws = []
+        for sg in (1.0, -1.0):
+            c = mol.coords.copy()
+            c[b // 3, b % 3] += sg * h
+            Ws.append(weight_directions(Molecule(mol.symbols, c), n_rad, n_ang))
+        if out is None:
+            out = np.zeros((P, P, Ws[0].shape[1]))
+        out[:, b] = (Ws[0] - Ws[1]) / (2 * h)
+    return out
+
+
 def trial_densities_torch(mol: Molecule, points, atoms: Optional[Sequence[int]] = None,
                           out_rho=None, out_grad=None):
     """trial_densities evaluated with torch on the device of `points` (an (N, 3) float64

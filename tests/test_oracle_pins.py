@@ -529,3 +529,63 @@ def test_nuclear_gradient_from_its_terms(oracle_mod):
         assert (es[0] - es[1]) / (2 * h) == pytest.approx(an[p], rel=1e-6, abs=1e-7 * np.abs(an).max())
     # translational invariance of the whole gradient
     assert np.abs(an.reshape(-1, 3).sum(axis=0)).max() <= 1e-6 * np.abs(an).max()
+
+
+def _nuclear_case(mol, nr, na):
+    g = synth.make_system(mol, nr, na)
+    rt, gt = synth.nuclear_density_derivatives(mol, g.coords, g.atom_of_point)
+    return g, rt, gt, synth.weight_directions(mol, nr, na)
+
+
+def _nuclear_gradient(oracle_mod, g, rt, gt, W):
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    kept = g.rho >= 1e-10
+    _, vr, vg = oracle_mod.potential(*args)
+    E = oracle_mod.pair_sums(*args)["E"]
+    ga = oracle_mod.atom_grad(*args, g.atom_of_point, g.molecule.n_atom).reshape(-1)
+    return np.array([np.sum(g.weights * (vr * rt[p] + 2 * vg * np.einsum("nd,nd->n", g.grad_rho, gt[p])))
+                     + np.sum((W[p] * g.rho * (oracle_mod.beta() + E))[kept]) + ga[p]
+                     for p in range(rt.shape[0])])
+
+
+def test_nuclear_hessian_from_its_nine_terms(oracle_mod):
+    """E^{AB} = E_GG + E_ww + E_grgr + (E_Gw + E_Ggr + E_wgr) + transposes (Sec. II.B, Eq. E_hess)
+    from the oracle's pair sums (the Hessian contraction with the nuclear trials, the
+    weight-derivative and atom-resolved sums, the grid-grid blocks) and the local derivatives,
+    against central differences of the nuclear gradient (itself pinned to the pipeline's
+    energy) with the whole synthetic pipeline moving with the atoms."""
+    mol, nr, na = synth.water(), 10, 26
+    g, rt, gt, W = _nuclear_case(mol, nr, na)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    kept = g.rho >= 1e-10
+    NA = mol.n_atom
+    P = 3 * NA
+    _, vr, vg = oracle_mod.potential(*args)
+    E = oracle_mod.pair_sums(*args)["E"]
+    pp = oracle_mod.point_props(g.rho, g.grad_rho)
+    r2, g2 = synth.nuclear_density_second_derivatives(mol, g.coords, g.atom_of_point)
+    Wab = synth.weight_second_derivatives(mol, nr, na)
+    Ew, Uw, Ww = oracle_mod.weight_response(*args, W)
+    Egr, Ugr, Wgr = (x.reshape(g.n, P).T for x in oracle_mod.atom_resolved(*args, g.atom_of_point, NA))
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    Hgg = oracle_mod.coord_hessian(*args, g.atom_of_point, NA).transpose(0, 2, 1, 3).reshape(P, P)
+    H = oracle_mod.nuclear_hessian(g.weights, g.rho, g.grad_rho, kept, pp["kappa_rho"],
+                                   pp["omega_rho"], pp["omega_gamma"], vr, vg, E, rt, gt, r2, g2,
+                                   W, Wab, Ew, Uw, Ww, Egr, Ugr, Wgr, fr, fg, Hgg)
+    h = 1e-4
+    fd = np.zeros((P, P))
+    for b in range(P):
+        gs = []
+        for sg in (1, -1):
+            c = mol.coords.copy()
+            c[b // 3, b % 3] += sg * h
+            m2 = synth.Molecule(mol.symbols, c)
+            g2s, rt2, gt2, W2 = _nuclear_case(m2, nr, na)
+            assert np.array_equal(g2s.rho >= 1e-10, kept)
+            gs.append(_nuclear_gradient(oracle_mod, g2s, rt2, gt2, W2))
+        fd[:, b] = (gs[0] - gs[1]) / (2 * h)
+    scale = np.abs(fd).max()
+    assert np.abs(H - fd).max() <= 1e-6 * scale
+    assert np.abs(H - H.T).max() <= 1e-8 * scale  # w^{ab} comes from central differences
+    # translational invariance: every row sums to zero over the atoms (per component)
+    assert np.abs(H.reshape(P, NA, 3).sum(axis=1)).max() <= 1e-6 * scale

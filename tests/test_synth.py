@@ -129,3 +129,25 @@ def test_ao_basis_values_gradients_and_density():
     assert (rho >= 0).all()  # P is positive semi-definite
     g, phi, _, _, _, _, _ = synth.ao_system(mol, 30, 110, 1)
     np.testing.assert_allclose((g.weights[:, None] * phi ** 2).sum(axis=0), 1.0, atol=5e-3)
+
+
+def test_nuclear_density_derivatives_at_moving_points():
+    """The first and second derivatives of rho and grad rho at grid points that move with their
+    atoms against central differences of the pipeline (grid and density rebuilt per geometry)."""
+    mol, nr, na = synth.water(), 6, 14
+    g = synth.make_system(mol, nr, na)
+    rt, gt = synth.nuclear_density_derivatives(mol, g.coords, g.atom_of_point)
+    r2, g2 = synth.nuclear_density_second_derivatives(mol, g.coords, g.atom_of_point)
+    h = 1e-5
+    for b in (0, 4, 8):
+        out = []
+        for sg in (1, -1):
+            c = mol.coords.copy()
+            c[b // 3, b % 3] += sg * h
+            m2 = synth.Molecule(mol.symbols, c)
+            gg = synth.make_system(m2, nr, na)
+            out.append((gg.rho, gg.grad_rho) + synth.nuclear_density_derivatives(m2, gg.coords, gg.atom_of_point))
+        np.testing.assert_allclose(rt[b], (out[0][0] - out[1][0]) / (2 * h), atol=1e-7 * np.abs(rt).max())
+        np.testing.assert_allclose(gt[b], (out[0][1] - out[1][1]) / (2 * h), atol=1e-7 * np.abs(gt).max())
+        np.testing.assert_allclose(r2[:, b], (out[0][2] - out[1][2]) / (2 * h), atol=1e-7 * np.abs(r2).max())
+        np.testing.assert_allclose(g2[:, b], (out[0][3] - out[1][3]) / (2 * h), atol=1e-7 * np.abs(g2).max())
