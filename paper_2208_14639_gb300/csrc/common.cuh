@@ -86,6 +86,12 @@ __device__ __forceinline__ float rcp_refined(float x) {
 __device__ __forceinline__ float recip(float x) { return rcp_refined(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Packed per-point records of the pair kernels for arithmetic type T (PointsDev r32a/r32b or
+// r64a/r64b): A = {x, y, z, -3/2 w rho}, B = {omega, kappa, rho kappa', rho omega_rho}.
+template <class T> struct PairRecs;
+template <> struct PairRecs<float> { using A = float4; using B = float4; };
+template <> struct PairRecs<double> { using A = double4; using B = double4; };
+
 // ------------------------------------------------------------------ reductions
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

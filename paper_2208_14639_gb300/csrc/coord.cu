@@ -64,10 +64,6 @@ cudaError_t launch_atom_sums(const PointsDev& p, const double* gk, double* grad_
 }
 
 // ------------------------------------------------------------------ atom-resolved
-template <class T> struct RecsAR;
-template <> struct RecsAR<float> { using A = float4; using B = float4; };
-template <> struct RecsAR<double> { using A = double4; using B = double4; };
-
 constexpr int kArThreads = 128;
 constexpr int kArJT = 256;  // j per shared-memory tile (two records per thread)
 
@@ -82,12 +78,12 @@ constexpr int ar_min_blocks() { return sizeof(T) == 4 ? (SUMS ? 6 : 8) : (SUMS ?
 // evaluation makes a single pass over the pairs.
 template <class T, bool SUMS>
 __global__ void __launch_bounds__(kArThreads, ar_min_blocks<T, SUMS>())
-k_atom_resolved(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
-                const typename RecsAR<T>::B* __restrict__ rb, double* __restrict__ out,
+k_atom_resolved(PointsDev P, const typename PairRecs<T>::A* __restrict__ ra,
+                const typename PairRecs<T>::B* __restrict__ rb, double* __restrict__ out,
                 double* __restrict__ gk, double* __restrict__ grad_points,
                 double* __restrict__ part) {
-    using RA = typename RecsAR<T>::A;
-    using RB = typename RecsAR<T>::B;
+    using RA = typename PairRecs<T>::A;
+    using RB = typename PairRecs<T>::B;
     __shared__ RA sa[kArJT];
     __shared__ RB sb[kArJT];
     const int tid = threadIdx.x;
@@ -239,11 +235,11 @@ __global__ void k_chunk_offsets(PointsDev P, int64_t* __restrict__ off) {
 
 template <class T, bool HALF>
 __global__ void __launch_bounds__(kArThreads)
-k_coord_hessian(PointsDev P, const typename RecsAR<T>::A* __restrict__ ra,
-                const typename RecsAR<T>::B* __restrict__ rb, const int64_t* __restrict__ off,
+k_coord_hessian(PointsDev P, const typename PairRecs<T>::A* __restrict__ ra,
+                const typename PairRecs<T>::B* __restrict__ rb, const int64_t* __restrict__ off,
                 double* __restrict__ part, double* __restrict__ Dout) {
-    using RA = typename RecsAR<T>::A;
-    using RB = typename RecsAR<T>::B;
+    using RA = typename PairRecs<T>::A;
+    using RB = typename PairRecs<T>::B;
     __shared__ RA sa[kArJT];
     __shared__ RB sb[kArJT];
     __shared__ double sred[6][kArThreads / 32];

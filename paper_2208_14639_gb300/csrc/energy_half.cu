@@ -15,10 +15,6 @@ namespace vv10 {
 
 namespace {
 
-template <class T> struct EhRecs;
-template <> struct EhRecs<float> { using A = float4; using B = float4; };
-template <> struct EhRecs<double> { using A = double4; using B = double4; };
-
 constexpr int kEhThreads = 128;  // rows per block and points per j block
 
 // Block pair of linear task index t (tasks ordered by I, then J = I .. nb - 1).
@@ -37,11 +33,11 @@ __device__ __forceinline__ void eh_task(int64_t t, int64_t nb, int64_t* I, int64
 
 template <class T>
 __global__ void __launch_bounds__(kEhThreads)
-k_energy_half(PointsDev P, const typename EhRecs<T>::A* __restrict__ ra,
-              const typename EhRecs<T>::B* __restrict__ rb, int64_t nb, int64_t n_tasks,
+k_energy_half(PointsDev P, const typename PairRecs<T>::A* __restrict__ ra,
+              const typename PairRecs<T>::B* __restrict__ rb, int64_t nb, int64_t n_tasks,
               double* __restrict__ cta_total) {
-    using RA = typename EhRecs<T>::A;
-    using RB = typename EhRecs<T>::B;
+    using RA = typename PairRecs<T>::A;
+    using RB = typename PairRecs<T>::B;
     __shared__ RA sa[kEhThreads];
     __shared__ RB sb[kEhThreads];
     __shared__ double sh[kEhThreads / 32];
@@ -96,8 +92,8 @@ k_energy_half(PointsDev P, const typename EhRecs<T>::A* __restrict__ ra,
 }
 
 template <class T>
-cudaError_t launch_eh(const PointsDev& p, const typename EhRecs<T>::A* ra,
-                      const typename EhRecs<T>::B* rb, int grid, double* cta_total,
+cudaError_t launch_eh(const PointsDev& p, const typename PairRecs<T>::A* ra,
+                      const typename PairRecs<T>::B* rb, int grid, double* cta_total,
                       double* energy, cudaStream_t st) {
     const int64_t nb = (p.nk + kEhThreads - 1) / kEhThreads;
     const int64_t n_tasks = nb * (nb + 1) / 2;

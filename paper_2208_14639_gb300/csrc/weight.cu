@@ -16,10 +16,6 @@ namespace vv10 {
 
 namespace {
 
-template <class T> struct WRecs;
-template <> struct WRecs<float> { using A = float4; using B = float4; };
-template <> struct WRecs<double> { using A = double4; using B = double4; };
-
 constexpr int kWrThreads = 128;
 constexpr int kWrJT = 128;  // j per shared-memory tile
 
@@ -35,20 +31,20 @@ __global__ void k_weight_dirs(PointsDev P, int32_t Pn, const double* __restrict_
 
 template <class T, int PC>
 struct WrSmem {
-    typename WRecs<T>::A a[kWrJT];
-    typename WRecs<T>::B b[kWrJT];
+    typename PairRecs<T>::A a[kWrJT];
+    typename PairRecs<T>::B b[kWrJT];
     T y[kWrJT][PC];
     double tot[3 * PC][kWrThreads];
 };
 
 template <class T, int PC>
 __global__ void __launch_bounds__(kWrThreads)
-k_weight_resp(PointsDev P, const typename WRecs<T>::A* __restrict__ ra,
-              const typename WRecs<T>::B* __restrict__ rb, const double* __restrict__ yk,
+k_weight_resp(PointsDev P, const typename PairRecs<T>::A* __restrict__ ra,
+              const typename PairRecs<T>::B* __restrict__ rb, const double* __restrict__ yk,
               int32_t Pn, double* __restrict__ outE, double* __restrict__ outU,
               double* __restrict__ outW) {
-    using RA = typename WRecs<T>::A;
-    using RB = typename WRecs<T>::B;
+    using RA = typename PairRecs<T>::A;
+    using RB = typename PairRecs<T>::B;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     WrSmem<T, PC>& S = *reinterpret_cast<WrSmem<T, PC>*>(smem_raw);
     const int tid = threadIdx.x;
@@ -122,8 +118,8 @@ k_weight_resp(PointsDev P, const typename WRecs<T>::A* __restrict__ ra,
 }
 
 template <class T, int PC>
-cudaError_t launch_wr(const PointsDev& p, const typename WRecs<T>::A* ra,
-                      const typename WRecs<T>::B* rb, const double* yk, int32_t Pn, double* E,
+cudaError_t launch_wr(const PointsDev& p, const typename PairRecs<T>::A* ra,
+                      const typename PairRecs<T>::B* rb, const double* yk, int32_t Pn, double* E,
                       double* U, double* W, cudaStream_t st) {
     const int bytes = static_cast<int>(sizeof(WrSmem<T, PC>));
     cudaError_t e = cudaFuncSetAttribute(k_weight_resp<T, PC>,
