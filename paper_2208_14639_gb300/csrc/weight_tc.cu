@@ -8,13 +8,15 @@
 // Work unit ("task"): 128 rows i x one group of at most 64 directions (N of the MMA) x every
 // j.  A persistent CTA walks its tasks; per stage of 16 j:
 //   * 16 generator warps (4 per row quadrant, 4 j each) evaluate K1, K2, K3 for their row in
-//     FP32, split them into TF32 hi/lo and store the six 128 x 16 operand tiles into shared
-//     memory in the 64-byte-swizzled K-major layout the MMA reads (double-buffered);
+//     FP32 and split them into TF32 hi/lo: the three hi tiles go to tensor memory (their MMAs
+//     read no shared memory for A), the three lo tiles to shared memory in the
+//     64-byte-swizzled K-major layout (both double-buffered);
 //   * the producer warp fetches the stage's j-records (1-D bulk copy) and the two 16 x Ppad
 //     direction tiles y_hi, y_lo (2-D TMA, 64-byte swizzle) into a ring;
-//   * one thread issues 6 MMAs per kind (2 k-steps x 3 products; A and B from shared memory)
-//     into that kind's TMEM accumulator (double-buffered: 3 kinds x 2 x 64 columns), the
-//     first of each kind overwriting it, and commits the stage once;
+//   * one thread issues 6 MMAs per kind (2 k-steps x 3 products; B from shared memory, A from
+//     tensor memory (hi) or shared memory (lo)) into that kind's TMEM accumulator
+//     (double-buffered: 3 kinds x 2 x 64 columns), the first of each kind overwriting it,
+//     and commits the stage once;
 //   * the generator warps drain the finished stage's accumulators into FP32 registers,
 //     release the ring slot, and every `flush` stages add the registers into the FP64
 //     outputs (each task's rows and directions are owned by one CTA: no atomics).
@@ -41,7 +43,8 @@ constexpr int kWtKinds = 3;                     // E, U, W
 constexpr int kWtMaxPpad = 64;
 constexpr uint32_t kWtTmemCols = 512;
 constexpr uint32_t kWtATile = 128u * 64u;       // one 128 x 16 tf32 operand tile (bytes)
-constexpr uint32_t kWtABuf = 2u * kWtKinds * kWtATile;  // hi and lo of the three kernel tiles
+constexpr uint32_t kWtABuf = kWtKinds * kWtATile;  // the lo parts of the three kernel tiles
+constexpr uint32_t kWtAHiCol = 384u;            // TMEM: hi tiles of buffer b, kind k at 384 + 48 b + 16 k
 
 struct WtLayout {
     uint32_t ring_off;    // direction-tile ring (after the two A buffers)
@@ -223,16 +226,16 @@ k_wresp_tc(const __grid_constant__ CUtensorMap tm_yh, const __grid_constant__ CU
 #pragma unroll
                     for (int k = 0; k < kWtKinds; ++k) {
                         const uint32_t d = tmem + wt_dcol(k, ab);
-                        const uint64_t dah = tc::sdesc_kmajor_sw64(abase + (2 * k) * kWtATile);
-                        const uint64_t dal = tc::sdesc_kmajor_sw64(abase + (2 * k + 1) * kWtATile);
+                        const uint32_t ah = tmem + kWtAHiCol + 48u * ab + 16u * k;
+                        const uint64_t dal = tc::sdesc_kmajor_sw64(abase + k * kWtATile);
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
-                            tc::mma_tf32_ss(d, dah + kStep * kk, dyl + kStep * kk, idesc, kk);  // the first overwrites
+                            tc::mma_tf32_ts(d, ah + 8 * kk, dyl + kStep * kk, idesc, kk);  // the first overwrites
                             tc::mma_tf32_ss(d, dal + kStep * kk, dyh + kStep * kk, idesc, 1);
                         }
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)
-                            tc::mma_tf32_ss(d, dah + kStep * kk, dyh + kStep * kk, idesc, 1);
+                            tc::mma_tf32_ts(d, ah + 8 * kk, dyh + kStep * kk, idesc, 1);
                     }
                     issued_any = true;
                     tc::commit(&mma_done[ab]);  // the ring slot is released by the generators
@@ -349,11 +352,14 @@ k_wresp_tc(const __grid_constant__ CUtensorMap tm_yh, const __grid_constant__ CU
                     }
                 }
                 const uint32_t abuf = smem_u32(smem + ab * kWtABuf) + a_row;
+                const uint32_t ahi = tmem + lane_off + kWtAHiCol + 48u * ab + part * 4;
 #pragma unroll
                 for (int k = 0; k < kWtKinds; ++k) {
-                    tc::st_shared_v4(abuf + (2 * k) * kWtATile, hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
-                    tc::st_shared_v4(abuf + (2 * k + 1) * kWtATile, lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+                    tc::st_x4(ahi + 16u * k, hi[k]);
+                    tc::st_shared_v4(abuf + k * kWtATile, lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
                 }
+                tc::wait_st();
+                tc::fence_before();
                 tc::fence_proxy_async_smem();  // the operands are read by the tensor core
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&a_full[ab]);
@@ -387,7 +393,8 @@ k_wresp_tc(const __grid_constant__ CUtensorMap tm_yh, const __grid_constant__ CU
             if (lane == 0) mbar_arrive(&b_empty[pslot]);
             flush(t0, i);
         }
-        tc::wait_ld();  // nothing of ours is in flight from TMEM on any exit path
+        tc::wait_st();  // nothing of ours is in flight to or from TMEM on any exit path
+        tc::wait_ld();
     }
 
     tc::fence_before();
