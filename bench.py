@@ -74,6 +74,10 @@ def workloads():
     }
 
 
+# Largest grid on which the breakdown also times the weight-derivative sums and the AO-side
+# assembly (their host-side inputs grow as N x N_atom and N x nbf).
+EXTRA_CALLS_MAX_POINTS = 400_000
+
 # Radial x angular points per atom of each workload's grid (for its weight derivatives).
 GRID_SHAPES = {"water": (30, 110), "hexamer": (50, 194), "cluster24": (30, 139),
                "chon60": (75, 302)}
@@ -516,10 +520,14 @@ def gpu_arm(args):
     ms_e = time_energy_only(vv, h, prec, 3)
     ms_ch = time_coord_hessian(vv, h, pb, prec, 3)
     pairs_ch = coord_hessian_pairs(pb)
-    wdirs = pb.weight_dirs()
-    P_w = int(wdirs.shape[0])
-    ms_wr = time_weight_response(vv, h, pb, prec, wdirs, 3)
-    ms_fock, ms_gt, nbf = time_ao_assembly(vv, h, pb, 3)
+    # the calls beyond the step on grids whose host-side inputs stay small (the weight
+    # derivatives are 3 N_atom x N, the basis values and gradients 4 nbf x N doubles)
+    extras = pb.n <= EXTRA_CALLS_MAX_POINTS
+    if extras:
+        wdirs = pb.weight_dirs()
+        P_w = int(wdirs.shape[0])
+        ms_wr = time_weight_response(vv, h, pb, prec, wdirs, 3)
+        ms_fock, ms_gt, nbf = time_ao_assembly(vv, h, pb, 3)
     alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     breakdown = {
         # the two metric quantities, each timed as its own entry point (3 calls each)
@@ -538,17 +546,19 @@ def gpu_arm(args):
         "coord_hessian_pairs": pairs_ch,
         "coord_hessian_pairs_per_s": pairs_ch / (ms_ch / 1e3),
         "coord_hessian_alu_frac": ALU_OPS_PER_PAIR_CH * pairs_ch / (ms_ch / 1e3) / alu_peak_ops,
-        # AO-side assembly of the step's outputs (FP64 cuBLAS GEMM over the kept points;
-        # not part of the step): 2 nbf^2 flops per point and channel
-        "ao_nbf": nbf,
-        "fock_matrix_call_ms": ms_fock,
-        "orbital_hessian_call_ms": ms_gt,
-        "orbital_hessian_fp64_tflops": 2.0 * nbf * nbf * nk * pb.P / (ms_gt / 1e3) / 1e12,
-        # weight-derivative sums for the 3 N_atom Becke weight directions (not part of the step)
-        "weight_response_P": P_w,
-        "weight_response_call_ms": ms_wr,
-        "weight_response_pairs_per_s": pairs_call / (ms_wr / 1e3),
-        **weight_response_roofline(prec, P_w, pairs_call, ms_wr, alu_peak_ops, peaks),
+        **({
+            # AO-side assembly of the step's outputs (FP64 cuBLAS GEMM over the kept points;
+            # not part of the step): 2 nbf^2 flops per point and channel
+            "ao_nbf": nbf,
+            "fock_matrix_call_ms": ms_fock,
+            "orbital_hessian_call_ms": ms_gt,
+            "orbital_hessian_fp64_tflops": 2.0 * nbf * nbf * nk * pb.P / (ms_gt / 1e3) / 1e12,
+            # weight-derivative sums for the 3 N_atom Becke weight directions (not in the step)
+            "weight_response_P": P_w,
+            "weight_response_call_ms": ms_wr,
+            "weight_response_pairs_per_s": pairs_call / (ms_wr / 1e3),
+            **weight_response_roofline(prec, P_w, pairs_call, ms_wr, alu_peak_ops, peaks),
+        } if extras else {"calls_beyond_the_step": f"not timed above {EXTRA_CALLS_MAX_POINTS} points"}),
         # the step's own phases
         "step_pair_pass_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
@@ -616,20 +626,21 @@ def gpu_arm(args):
         per64 = {k: v[0] for k, v in prof64.items()}
         ms_ep64, ms_hc64 = time_calls(vv, h, pb, vv.VV10_FP64, 1)
         ms_ch64 = time_coord_hessian(vv, h, pb, vv.VV10_FP64, 1)
-        ms_wr64 = time_weight_response(vv, h, pb, vv.VV10_FP64, wdirs, 1)
+        ms_wr64 = time_weight_response(vv, h, pb, vv.VV10_FP64, wdirs, 1) if extras else None
         result["fp64"] = {
             "value": 3.0 * pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
             "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
             "energy_potential_pairs_per_s": pairs_call / (ms_ep64 / 1e3),
             "hessian_pairs_per_s": pairs_call / (ms_hc64 / 1e3),
             "coord_hessian_pairs_per_s": pairs_ch / (ms_ch64 / 1e3),
-            "weight_response_pairs_per_s": pairs_call / (ms_wr64 / 1e3),
+            "weight_response_pairs_per_s": pairs_call / (ms_wr64 / 1e3) if extras else None,
             "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
         }
         result["speedup_mixed_vs_fp64_energy_potential"] = ms_ep64 / ms_ep
         result["speedup_mixed_vs_fp64_hessian"] = ms_hc64 / ms_hc
         result["speedup_mixed_vs_fp64_coord_hessian"] = ms_ch64 / ms_ch
-        result["speedup_mixed_vs_fp64_weight_response"] = ms_wr64 / ms_wr
+        if extras:
+            result["speedup_mixed_vs_fp64_weight_response"] = ms_wr64 / ms_wr
         result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
 
     sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, K, 1)
