@@ -40,7 +40,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
                   "sm_max_mhz": 2070.0}
 N_SM = 152
 FP32_LANES_PER_SM = 128
-# FP32 operations per pair counted from the formulas each kernel evaluates (see DESIGN.md):
+# FP32 operations per pair counted from the formulas each kernel evaluates:
 #   tensor-core contraction: kernel tiles T1..T4 (36, the reciprocal counted once) and
 #   their four hi - lo subtractions
 ALU_OPS_PER_PAIR_TC = 40
