@@ -41,7 +41,7 @@ typedef enum {
     VV10_ERR_OOM = 3,          /* device allocation failed                                */
     VV10_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                      */
     VV10_ERR_NONFINITE = 5,    /* a NaN/Inf was produced in an output                     */
-    VV10_ERR_UNSUPPORTED = 6   /* valid request outside this build's limits               */
+    VV10_ERR_UNSUPPORTED = 6   /* valid request outside the library's limits             */
 } vv10_status;
 
 typedef enum {
@@ -62,7 +62,7 @@ typedef struct {
 
 typedef struct vv10_ctx* vv10_handle;
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define VV10_MAX_ATOMS 4096
 #define VV10_MAX_TRIALS 4096
 #define VV10_MAX_BASIS 4096

@@ -892,7 +892,7 @@ vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
         return P_trials < 0 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
     }
     if (P_trials > 0 && prec == VV10_MIXED_BF16X3) {
-        h->set_error("the BF16x3 Hessian contraction is not available in this build");
+        h->set_error("the BF16x3 Hessian contraction is not available in this library");
         return VV10_ERR_UNSUPPORTED;
     }
     if ((grad_atoms || EUW_Bgr) && h->P.n_atom == 0) {

@@ -643,7 +643,7 @@ vv10_status vv10_batch_hessian_contract(vv10_handle h, vv10_precision prec, cons
         return VV10_ERR_INVALID_ARG;
     }
     if (prec == VV10_MIXED_BF16X3) {
-        h->set_error("the BF16x3 Hessian contraction is not available in this build");
+        h->set_error("the BF16x3 Hessian contraction is not available in this library");
         return VV10_ERR_UNSUPPORTED;
     }
     if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3) return VV10_ERR_INVALID_ARG;

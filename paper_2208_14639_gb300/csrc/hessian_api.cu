@@ -41,7 +41,7 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
     H_CUDA(cudaMemsetAsync(f_gamma_t, 0, out_bytes, st), "memset f_gamma_t");
     if (P.nk == 0) return VV10_OK;
     if (prec == VV10_MIXED_BF16X3) {
-        set_error("the BF16x3 Hessian contraction is not available in this build");
+        set_error("the BF16x3 Hessian contraction is not available in this library");
         return VV10_ERR_UNSUPPORTED;
     }
 
