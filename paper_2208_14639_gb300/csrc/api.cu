@@ -421,7 +421,7 @@ vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_s
     VV10_TRY(ensure(part, sizeof(double) * nq * static_cast<size_t>(ns) * (P.nk_pad > 0 ? P.nk_pad : 1),
                     "pair-sum partials"));
     {
-        PhaseScope ph(this, (mode == MODE_EUW || mode == MODE_EUWABC) ? PH_PAIR_EUW
+        PhaseScope ph(this, (mode == MODE_EUW || mode == MODE_EUWABC || mode == MODE_EUWABCG) ? PH_PAIR_EUW
                             : (mode == MODE_ABC ? PH_PAIR_ABC : PH_PAIR_GRAD),
                       st, 1);
         VV10_CUDA(this, launch_pairsum(P, mode, fp64, cfg, static_cast<double*>(part.p),
@@ -438,9 +438,10 @@ TileChoice vv10_ctx::tiles_for(int mode, bool fp64) const {
     TileChoice t;
     t.rows_per_thread = fp64 ? 1 : 2;
     t.n_split = 0;
-    const TileOverride& o = overrides[mode + 4 * (fp64 ? 1 : 0)];
-    const TileOverride& e = overrides[MODE_EUW + 4 * (fp64 ? 1 : 0)];
-    const TileOverride* use = o.active ? &o : ((mode == MODE_EUWABC && e.active) ? &e : nullptr);
+    const TileOverride& o = overrides[mode + kPairModes * (fp64 ? 1 : 0)];
+    const TileOverride& e = overrides[MODE_EUW + kPairModes * (fp64 ? 1 : 0)];
+    const bool fused = (mode == MODE_EUWABC || mode == MODE_EUWABCG);
+    const TileOverride* use = o.active ? &o : ((fused && e.active) ? &e : nullptr);
     if (use) {
         t.rows_per_thread = use->rows_per_thread;
         t.n_split = use->n_split;
@@ -916,7 +917,57 @@ vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PointsDev& P = h->P;
-    if (!EUW_Bgr) {
+    if (!EUW_Bgr && (grad_points || grad_atoms)) {
+        // one pass over the pairs for the six row sums and the point gradient
+        // (MODE_EUWABCG), then the epilogues and the contraction
+        const bool fp64 = (prec == VV10_FP64);
+        const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
+        DevBuf* sums[] = {&h->sumE, &h->sumU, &h->sumW, &h->sumA, &h->sumB, &h->sumC};
+        for (DevBuf* b : sums) VV10_TRY(h->ensure(*b, nkb, "row sums"));
+        const int nblk = ep_epilogue_blocks(P.nk);
+        VV10_TRY(h->ensure(h->eblk, sizeof(double) * nblk, "energy partials"));
+        VV10_TRY(h->ensure(h->scal, 64, "energy"));
+        VV10_TRY(h->ensure(h->gk, 3 * nkb, "kept gradient"));
+        if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
+        if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
+        if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
+        if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
+        double* escal = static_cast<double*>(h->scal.p);
+        if (P.nk > 0) {
+            int ns = 1;
+            VV10_TRY(h->run_pairsum(MODE_EUWABCG, fp64, st, &ns));
+            double* part = static_cast<double*>(h->part.p);
+            const size_t blk = static_cast<size_t>(ns) * static_cast<size_t>(P.nk_pad);
+            {
+                PhaseScope ph(h, PH_EP_EPILOGUE, st, 3);
+                VV10_CUDA(h, launch_ep_epilogue(P, part, ns, static_cast<double*>(h->sumE.p),
+                                                static_cast<double*>(h->sumU.p),
+                                                static_cast<double*>(h->sumW.p), vrho, vgamma,
+                                                static_cast<double*>(h->eblk.p),
+                                                static_cast<int*>(h->dev_err.p), st),
+                          "energy epilogue");
+                VV10_CUDA(h, launch_sum_blocks(static_cast<double*>(h->eblk.p), nblk, escal, st), "energy sum");
+                VV10_CUDA(h, launch_abc_epilogue(P, part + 3 * blk, ns, static_cast<double*>(h->sumA.p),
+                                                 static_cast<double*>(h->sumB.p),
+                                                 static_cast<double*>(h->sumC.p), st),
+                          "A/B/C epilogue");
+            }
+            PhaseScope ph(h, PH_GRAD_EPILOGUE, st, grad_atoms ? 2 : 1);
+            VV10_CUDA(h, launch_grad_epilogue(P, part + 6 * blk, ns, static_cast<double*>(h->gk.p),
+                                              grad_points, st),
+                      "gradient epilogue");
+            if (grad_atoms)
+                VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
+                          "atom sums");
+        } else {
+            VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
+        }
+        h->have_euw = true;
+        h->euw_fp64 = fp64;
+        h->have_abc = P.nk > 0;
+        h->abc_fp64 = fp64;
+        if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
+    } else if (!EUW_Bgr) {
         // the separate calls, with the A/B/C sums formed in the energy pass
         const int saved = h->options;
         if (P_trials > 0) h->options |= VV10_OPT_FUSE_HESSIAN_SUMS;
@@ -1056,7 +1107,7 @@ vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_s
         h->set_error("rows_per_thread must be 0, 1, 2 or %d", max_rpt);
         return VV10_ERR_INVALID_ARG;
     }
-    TileOverride& o = what >= 6 ? h->batch_over[what - 6] : h->overrides[what % 3 + 4 * (what >= 3)];
+    TileOverride& o = what >= 6 ? h->batch_over[what - 6] : h->overrides[what % 3 + kPairModes * (what >= 3)];
     o = TileOverride{};
     o.mode = what >= 6 ? 0 : what % 3;
     o.fp64 = what >= 6 ? what == 7 : what >= 3;

@@ -118,7 +118,7 @@ bool stream_capturing(cudaStream_t st) {
 
 // Single-system pair sums of one mode: rows per thread x j-splits.
 vv10_status vv10_ctx::tune_pairsum(int mode, bool fp64, cudaStream_t st, bool force) {
-    TileOverride& o = overrides[mode + 4 * (fp64 ? 1 : 0)];
+    TileOverride& o = overrides[mode + kPairModes * (fp64 ? 1 : 0)];
     if (o.manual || P.nk == 0) return VV10_OK;
     const int nb = n_bucket(P.nk);
     if (!force && o.active && o.bucket == nb) return VV10_OK;

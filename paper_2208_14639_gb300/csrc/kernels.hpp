@@ -61,9 +61,10 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
                                    float4* r32p, cudaStream_t st);
 
 // ---------------------------------------------------------------- pair sums (pairsum.cu)
-enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2, MODE_EUWABC = 3 };
+enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2, MODE_EUWABC = 3, MODE_EUWABCG = 4 };
+constexpr int kPairModes = 5;
 // Quantities a mode accumulates per row (the leading dimension of its partial buffer).
-constexpr int pair_mode_nq(int mode) { return mode == MODE_EUWABC ? 6 : 3; }
+constexpr int pair_mode_nq(int mode) { return mode == MODE_EUWABCG ? 9 : (mode == MODE_EUWABC ? 6 : 3); }
 
 struct PairLaunch {
     int rows_per_thread = 2;  // FP32: 1, 2, 4; FP64: 1, 2

@@ -14,6 +14,7 @@
 //             (A_i, B_i, C_i of Sec. II.B up to the factor 2)
 //   MODE_GRAD sum_j w_j rho_j Phi_ij D_ij (r_i - r_j), D_ij the bracket of Eq. grad_gr
 //   MODE_EUWABC the six sums of MODE_EUW and MODE_ABC from one pass (partials [6][..])
+//   MODE_EUWABCG those six and the three of MODE_GRAD from one pass (partials [9][..])
 // with g = omega_i R^2 + kappa_i, g' = omega_j R^2 + kappa_j, s = g + g' and all of
 // 1/g, 1/g', 1/s, Phi obtained from the single reciprocal inv = 1/(g g' s).
 //
@@ -100,6 +101,7 @@ static int pairsum_blocks_per_sm(int mode, bool fp64, int rpt) {
         case MODE_EUW: return blocks_per_sm_mode<MODE_EUW>(fp64, rpt);
         case MODE_ABC: return blocks_per_sm_mode<MODE_ABC>(fp64, rpt);
         case MODE_EUWABC: return blocks_per_sm_mode<MODE_EUWABC>(fp64, rpt);
+        case MODE_EUWABCG: return blocks_per_sm_mode<MODE_EUWABCG>(fp64, rpt);
         default: return blocks_per_sm_mode<MODE_GRAD>(fp64, rpt);
     }
 }
@@ -163,6 +165,7 @@ cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLa
         case MODE_EUW: return launch_mode<MODE_EUW>(p, fp64, cfg, part, err, st);
         case MODE_ABC: return launch_mode<MODE_ABC>(p, fp64, cfg, part, err, st);
         case MODE_EUWABC: return launch_mode<MODE_EUWABC>(p, fp64, cfg, part, err, st);
+        case MODE_EUWABCG: return launch_mode<MODE_EUWABCG>(p, fp64, cfg, part, err, st);
         default: return launch_mode<MODE_GRAD>(p, fp64, cfg, part, err, st);
     }
 }

@@ -53,6 +53,27 @@ __device__ __forceinline__ void pair_accumulate(const Row<T>& r, const RA& a, co
         const T v2 = v * r2;
         acc[4] += v2;
         acc[5] = fmadd(v2, r2, acc[5]);
+    } else if constexpr (MODE == MODE_EUWABCG) {
+        // the six sums and the gradient sum of MODE_GRAD from one evaluation of the pair
+        const T L = ggp * inv;          // 1/s
+        const T Gi = (gp * s) * inv;    // 1/g
+        const T t = L + Gi;             // 1/s + 1/g
+        const T pt = ph * t;
+        acc[0] += ph;
+        acc[1] += pt;
+        acc[2] = fmadd(pt, r2, acc[2]);
+        const T v = ph * fmadd(L, t, Gi * Gi);
+        acc[3] += v;
+        const T v2 = v * r2;
+        acc[4] += v2;
+        acc[5] = fmadd(v2, r2, acc[5]);
+        // D = omega_i/g + omega_j/g' + (omega_i + omega_j)/s
+        const T Gj = (g * s) * inv;     // 1/g'
+        const T D = fmadd(r.om, Gi, fmadd(b.x, Gj, (r.om + b.x) * L));
+        const T f = ph * D;
+        acc[6] = fmadd(f, dx, acc[6]);
+        acc[7] = fmadd(f, dy, acc[7]);
+        acc[8] = fmadd(f, dz, acc[8]);
     } else if constexpr (MODE == MODE_ABC) {
         const T L = ggp * inv;         // 1/s
         const T Gi = (gp * s) * inv;   // 1/g

@@ -144,9 +144,9 @@ struct vv10_ctx {
     vv10::DevBuf ngpart;            // per-block partials of the nuclear-gradient terms
     void* blas = nullptr;            // cuBLAS handle of the AO assembly (made on first use)
 
-    // tile overrides (index = mode + 4 * fp64, modes MODE_EUW..MODE_EUWABC), set by
+    // tile overrides (index = mode + kPairModes * fp64, modes MODE_EUW..MODE_EUWABCG), set by
     // vv10_set_tiles / the autotuner
-    vv10::TileOverride overrides[8];
+    vv10::TileOverride overrides[2 * vv10::kPairModes];
     int options = 0;  // VV10_OPT_* flags
     vv10::TileOverride batch_over[2];  // batched pair sums (index = fp64)
     int tc_cap_manual = 0;             // widest trial group of the contraction (0 = automatic)

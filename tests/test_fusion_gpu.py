@@ -103,7 +103,7 @@ def test_gradient_from_atom_resolved_pass(dev, case, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
-@pytest.mark.parametrize("resolved", [True, False], ids=["one-pass", "three-calls"])
+@pytest.mark.parametrize("resolved", [True, False], ids=["atom-resolved-pass", "sums-and-gradient-pass"])
 def test_evaluate_everything_in_one_call(dev, case, prec, tol, resolved):
     g, rt, gt, ref = case
     eng = vv10.VV10(0)
@@ -122,8 +122,8 @@ def test_evaluate_everything_in_one_call(dev, case, prec, tol, resolved):
     if resolved:  # a single pass over the pairs
         assert prof["atom_resolved"][1] == 1 and prof["pair_sums_EUW"][1] == 0
         assert prof["pair_sums_grad"][1] == 0
-    else:  # the fused energy + A/B/C pass and the gradient pass
-        assert prof["pair_sums_EUW"][1] == 1 and prof["pair_sums_grad"][1] == 1
+    else:  # one pass for the six row sums and the gradient (MODE_EUWABCG)
+        assert prof["pair_sums_EUW"][1] == 1 and prof["pair_sums_grad"][1] == 0
     if prec == FP64:
         assert abs(e - ref["e"]) <= 1e-11 * abs(ref["e"])
     else:
