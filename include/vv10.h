@@ -353,8 +353,9 @@ vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n
  * vv10_hessian_contract and vv10_coord_grad, Sec. II.A and Sec. II.B; the call itself has no
  * counterpart in the paper).  When EUW_Bgr is requested, one pass over the pairs forms the
  * E/U/W and A/B/C row sums, the atom-resolved terms and the point gradient together (the
- * separate calls need two passes); otherwise it is the three calls in sequence with the
- * A/B/C sums formed in the energy pass.
+ * separate calls need two passes); when only grad_points / grad_atoms are, one pass forms
+ * the six row sums and the point gradient; otherwise it is the energy call (with the A/B/C
+ * sums formed in its pass when trials are given) and the contraction.
  *   P            number of trials, 0 <= P <= VV10_MAX_TRIALS (0: no Hessian contraction;
  *                rho_t, grad_rho_t, f_rho_t, f_gamma_t then unused and may be NULL)
  *   energy       HOST double out (may be NULL; when given the call synchronises `stream`)
