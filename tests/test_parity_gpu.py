@@ -378,4 +378,21 @@ def test_all_points_below_cutoff(dev, prec):
     vv10.vv10_sync(eng.h)
     for t in (fr, fg, gp, ga, euw):
         assert not t.any()
+    # the one-call evaluation (both of its pass layouts), the energy alone and the calls beyond
+    # the step: zero results, outputs given non-zero beforehand are overwritten
+    na = g.molecule.n_atom
+    full = lambda *shape: torch.full(shape, 5.0, dtype=torch.float64, device=dev)
+    for resolved in (True, False):
+        out = dict(vrho=full(g.n), vgamma=full(g.n), f_rho_t=full(3, g.n), f_gamma_t=full(3, g.n),
+                   grad_points=full(g.n, 3), grad_atoms=full(na, 3),
+                   EUW_Bgr=full(3, g.n, na, 3) if resolved else None)
+        assert vv10.vv10_evaluate(eng.h, prec, rt, gt, **out) == 0.0
+        assert not any(t.any() for t in out.values() if t is not None)
+    assert eng.energy(prec) == 0.0
+    E, D = eng.coord_hessian(prec, points=True)
+    Ew, Uw, Ww = eng.weight_response(torch.ones(2, g.n, dtype=torch.float64, device=dev), prec)
+    ng = eng.nuclear_gradient(w_t=torch.ones(2, g.n, dtype=torch.float64, device=dev))
+    vv10.vv10_sync(eng.h)
+    for t in (E, D, Ew, Uw, Ww, ng):
+        assert not t.any()
     eng.close()
