@@ -876,6 +876,80 @@ vv10_status vv10_orbital_hessian(vv10_handle h, int32_t nbf, const double* phi,
                        stream);
 }
 
+}  // extern "C"
+
+// The single pass over the pairs of vv10_evaluate.  With EUW_Bgr the atom-resolved kernel
+// forms the six row sums (E/U/W and A/B/C), the atom-resolved terms and the point gradient;
+// without it the pair-sum mode MODE_EUWABCG forms the six row sums and the gradient.  Then
+// the E/U/W and A/B/C epilogues (energy, f^rho, f^gamma), the gradient epilogue and the atom
+// sums.  Leaves the row sums cached as the energy call would.
+static vv10_status evaluate_single_pass(vv10_handle h, bool fp64, double* vrho, double* vgamma,
+                                        double* grad_points, double* grad_atoms, double* EUW_Bgr,
+                                        cudaStream_t st) {
+    PointsDev& P = h->P;
+    const bool resolved = (EUW_Bgr != nullptr);
+    const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
+    DevBuf* sums[] = {&h->sumE, &h->sumU, &h->sumW, &h->sumA, &h->sumB, &h->sumC};
+    for (DevBuf* b : sums) VV10_TRY(h->ensure(*b, nkb, "row sums"));
+    const int nblk = ep_epilogue_blocks(P.nk);
+    VV10_TRY(h->ensure(h->eblk, sizeof(double) * nblk, "energy partials"));
+    VV10_TRY(h->ensure(h->scal, 64, "energy"));
+    VV10_TRY(h->ensure(h->gk, 3 * nkb, "kept gradient"));
+    if (resolved) VV10_TRY(h->ensure(h->part, 6 * nkb, "pair-sum partials"));
+    if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
+    if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
+    if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
+    if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
+    if (resolved)
+        VV10_CUDA(h, cudaMemsetAsync(EUW_Bgr, 0, sizeof(double) * 9 * P.n * P.n_atom, st), "memset");
+    double* escal = static_cast<double*>(h->scal.p);
+    double* gk = static_cast<double*>(h->gk.p);
+    int* err = static_cast<int*>(h->dev_err.p);
+    if (P.nk > 0) {
+        int ns = 1;
+        if (resolved) {
+            PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
+            VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr, gk, grad_points,
+                                              static_cast<double*>(h->part.p), err, st),
+                      "fused pair pass");
+        } else {
+            VV10_TRY(h->run_pairsum(MODE_EUWABCG, fp64, st, &ns));
+        }
+        double* part = static_cast<double*>(h->part.p);
+        const size_t blk = static_cast<size_t>(ns) * static_cast<size_t>(P.nk_pad);
+        {
+            PhaseScope ph(h, PH_EP_EPILOGUE, st, (resolved && grad_atoms) ? 4 : 3);
+            VV10_CUDA(h, launch_ep_epilogue(P, part, ns, static_cast<double*>(h->sumE.p),
+                                            static_cast<double*>(h->sumU.p),
+                                            static_cast<double*>(h->sumW.p), vrho, vgamma,
+                                            static_cast<double*>(h->eblk.p), err, st),
+                      "energy epilogue");
+            VV10_CUDA(h, launch_sum_blocks(static_cast<double*>(h->eblk.p), nblk, escal, st), "energy sum");
+            VV10_CUDA(h, launch_abc_epilogue(P, part + 3 * blk, ns, static_cast<double*>(h->sumA.p),
+                                             static_cast<double*>(h->sumB.p),
+                                             static_cast<double*>(h->sumC.p), st),
+                      "A/B/C epilogue");
+            if (resolved && grad_atoms)
+                VV10_CUDA(h, launch_atom_sums(P, gk, grad_atoms, st), "atom sums");
+        }
+        if (!resolved) {
+            PhaseScope ph(h, PH_GRAD_EPILOGUE, st, grad_atoms ? 2 : 1);
+            VV10_CUDA(h, launch_grad_epilogue(P, part + 6 * blk, ns, gk, grad_points, st),
+                      "gradient epilogue");
+            if (grad_atoms) VV10_CUDA(h, launch_atom_sums(P, gk, grad_atoms, st), "atom sums");
+        }
+    } else {
+        VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
+    }
+    h->have_euw = true;
+    h->euw_fp64 = fp64;
+    h->have_abc = P.nk > 0;
+    h->abc_fp64 = fp64;
+    return VV10_OK;
+}
+
+extern "C" {
+
 vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
                           const double* rho_t, const double* grad_rho_t, double* energy,
                           double* vrho, double* vgamma, double* f_rho_t, double* f_gamma_t,
@@ -916,115 +990,17 @@ vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
             }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    PointsDev& P = h->P;
-    if (!EUW_Bgr && (grad_points || grad_atoms)) {
-        // one pass over the pairs for the six row sums and the point gradient
-        // (MODE_EUWABCG), then the epilogues and the contraction
-        const bool fp64 = (prec == VV10_FP64);
-        const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
-        DevBuf* sums[] = {&h->sumE, &h->sumU, &h->sumW, &h->sumA, &h->sumB, &h->sumC};
-        for (DevBuf* b : sums) VV10_TRY(h->ensure(*b, nkb, "row sums"));
-        const int nblk = ep_epilogue_blocks(P.nk);
-        VV10_TRY(h->ensure(h->eblk, sizeof(double) * nblk, "energy partials"));
-        VV10_TRY(h->ensure(h->scal, 64, "energy"));
-        VV10_TRY(h->ensure(h->gk, 3 * nkb, "kept gradient"));
-        if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
-        if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
-        if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
-        if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
-        double* escal = static_cast<double*>(h->scal.p);
-        if (P.nk > 0) {
-            int ns = 1;
-            VV10_TRY(h->run_pairsum(MODE_EUWABCG, fp64, st, &ns));
-            double* part = static_cast<double*>(h->part.p);
-            const size_t blk = static_cast<size_t>(ns) * static_cast<size_t>(P.nk_pad);
-            {
-                PhaseScope ph(h, PH_EP_EPILOGUE, st, 3);
-                VV10_CUDA(h, launch_ep_epilogue(P, part, ns, static_cast<double*>(h->sumE.p),
-                                                static_cast<double*>(h->sumU.p),
-                                                static_cast<double*>(h->sumW.p), vrho, vgamma,
-                                                static_cast<double*>(h->eblk.p),
-                                                static_cast<int*>(h->dev_err.p), st),
-                          "energy epilogue");
-                VV10_CUDA(h, launch_sum_blocks(static_cast<double*>(h->eblk.p), nblk, escal, st), "energy sum");
-                VV10_CUDA(h, launch_abc_epilogue(P, part + 3 * blk, ns, static_cast<double*>(h->sumA.p),
-                                                 static_cast<double*>(h->sumB.p),
-                                                 static_cast<double*>(h->sumC.p), st),
-                          "A/B/C epilogue");
-            }
-            PhaseScope ph(h, PH_GRAD_EPILOGUE, st, grad_atoms ? 2 : 1);
-            VV10_CUDA(h, launch_grad_epilogue(P, part + 6 * blk, ns, static_cast<double*>(h->gk.p),
-                                              grad_points, st),
-                      "gradient epilogue");
-            if (grad_atoms)
-                VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
-                          "atom sums");
-        } else {
-            VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
-        }
-        h->have_euw = true;
-        h->euw_fp64 = fp64;
-        h->have_abc = P.nk > 0;
-        h->abc_fp64 = fp64;
+    const bool fp64 = (prec == VV10_FP64);
+    if (EUW_Bgr || grad_points || grad_atoms) {
+        VV10_TRY(evaluate_single_pass(h, fp64, vrho, vgamma, grad_points, grad_atoms, EUW_Bgr, st));
         if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
-    } else if (!EUW_Bgr) {
-        // the separate calls, with the A/B/C sums formed in the energy pass
+    } else {
+        // the energy call, with the A/B/C sums formed in its pass when the contraction follows
         const int saved = h->options;
         if (P_trials > 0) h->options |= VV10_OPT_FUSE_HESSIAN_SUMS;
         vv10_status s = vv10_energy_potential(h, prec, nullptr, vrho, vgamma, stream);
         h->options = saved;
         VV10_TRY(s);
-        if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
-        if (grad_points || grad_atoms)
-            VV10_TRY(vv10_coord_grad(h, prec, grad_points, grad_atoms, nullptr, stream));
-    } else {
-        // one pass over the pairs: E/U/W/A/B/C row sums, atom-resolved terms, point gradient
-        const bool fp64 = (prec == VV10_FP64);
-        const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
-        DevBuf* sums[] = {&h->sumE, &h->sumU, &h->sumW, &h->sumA, &h->sumB, &h->sumC};
-        for (DevBuf* b : sums) VV10_TRY(h->ensure(*b, nkb, "row sums"));
-        const int nblk = ep_epilogue_blocks(P.nk);
-        VV10_TRY(h->ensure(h->eblk, sizeof(double) * nblk, "energy partials"));
-        VV10_TRY(h->ensure(h->scal, 64, "energy"));
-        VV10_TRY(h->ensure(h->part, 6 * nkb, "pair-sum partials"));
-        VV10_TRY(h->ensure(h->gk, 3 * nkb, "kept gradient"));
-        if (vrho) VV10_CUDA(h, cudaMemsetAsync(vrho, 0, sizeof(double) * P.n, st), "memset vrho");
-        if (vgamma) VV10_CUDA(h, cudaMemsetAsync(vgamma, 0, sizeof(double) * P.n, st), "memset vgamma");
-        if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
-        if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
-        VV10_CUDA(h, cudaMemsetAsync(EUW_Bgr, 0, sizeof(double) * 9 * P.n * P.n_atom, st), "memset");
-        double* escal = static_cast<double*>(h->scal.p);
-        if (P.nk > 0) {
-            double* part = static_cast<double*>(h->part.p);
-            {
-                PhaseScope ph(h, PH_ATOM_RESOLVED, st, 1);
-                VV10_CUDA(h, launch_atom_resolved(P, fp64, EUW_Bgr, static_cast<double*>(h->gk.p),
-                                                  grad_points, part, static_cast<int*>(h->dev_err.p), st),
-                          "fused pair pass");
-            }
-            PhaseScope ph(h, PH_EP_EPILOGUE, st, grad_atoms ? 4 : 3);
-            VV10_CUDA(h, launch_ep_epilogue(P, part, 1, static_cast<double*>(h->sumE.p),
-                                            static_cast<double*>(h->sumU.p),
-                                            static_cast<double*>(h->sumW.p), vrho, vgamma,
-                                            static_cast<double*>(h->eblk.p),
-                                            static_cast<int*>(h->dev_err.p), st),
-                      "energy epilogue");
-            VV10_CUDA(h, launch_sum_blocks(static_cast<double*>(h->eblk.p), nblk, escal, st), "energy sum");
-            VV10_CUDA(h, launch_abc_epilogue(P, part + 3 * static_cast<size_t>(P.nk_pad), 1,
-                                             static_cast<double*>(h->sumA.p),
-                                             static_cast<double*>(h->sumB.p),
-                                             static_cast<double*>(h->sumC.p), st),
-                      "A/B/C epilogue");
-            if (grad_atoms)
-                VV10_CUDA(h, launch_atom_sums(P, static_cast<double*>(h->gk.p), grad_atoms, st),
-                          "atom sums");
-        } else {
-            VV10_CUDA(h, cudaMemsetAsync(escal, 0, sizeof(double), st), "zero energy");
-        }
-        h->have_euw = true;
-        h->euw_fp64 = fp64;
-        h->have_abc = P.nk > 0;
-        h->abc_fp64 = fp64;
         if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
     }
     if (energy) {
