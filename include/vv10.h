@@ -206,8 +206,8 @@ vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
  *   G^t_mu_nu = sum_i w_i [f^{rho,t}_i phi_mu phi_nu
  *                          + 2 (f^{gamma,t}_i grad rho_i + f^gamma_i grad rho^t_i)
  *                            . (phi_nu grad phi_mu + phi_mu grad phi_nu)]
- * over the points kept at vv10_prepare_points (w and grad rho as prepared), in FP64 (a batched
- * cuBLAS DGEMM over the points).  For rho = sum P_mu_nu phi_mu phi_nu, F_mu_nu = dE/dP_mu_nu
+ * over the points kept at vv10_prepare_points (w and grad rho as prepared), in FP64 (a cuBLAS
+ * DGEMM over the points, the trials side by side).  For rho = sum P_mu_nu phi_mu phi_nu, F_mu_nu = dE/dP_mu_nu
  * and G^t = dF along P^t.
  *   nbf          number of basis functions, 1 <= nbf <= VV10_MAX_BASIS
  *   phi          n x nbf device in, phi_mu at point i at phi[i nbf + mu] (caller order)
