@@ -496,14 +496,18 @@ def test_orbital_hessian_is_fock_derivative(oracle_mod):
 
 # --------------------------------------------------------------------- nuclear gradient
 
-def test_nuclear_gradient_from_its_terms(oracle_mod):
+NUCLEAR_CASES = [("water", lambda: synth.water(), 10, 26),
+                 ("chon4", lambda: synth.random_chon(np.random.default_rng(2), 4), 8, 14)]
+
+
+@pytest.mark.parametrize("name,make,nr,na", NUCLEAR_CASES, ids=[c[0] for c in NUCLEAR_CASES])
+def test_nuclear_gradient_from_its_terms(oracle_mod, name, make, nr, na):
     """E^A = E^A_G + E^A_w + E^A_gr (Sec. II.A) against central differences of the energy of
     the whole synthetic pipeline (grid points, Becke weights and density all moving with the
     atoms): E^A_G from the potential and the density derivatives at the moving points, E^A_w
     from dE/dw_i = rho_i (beta + E_i) and the Becke weight derivatives, E^A_gr from the first
     form of the grid-position gradient."""
-    mol = synth.water()
-    nr, na = 10, 26
+    mol = make()
     g = synth.make_system(mol, nr, na)
     args = (g.coords, g.weights, g.rho, g.grad_rho)
     kept = g.rho >= 1e-10
@@ -548,13 +552,14 @@ def _nuclear_gradient(oracle_mod, g, rt, gt, W):
                      for p in range(rt.shape[0])])
 
 
-def test_nuclear_hessian_from_its_nine_terms(oracle_mod):
+@pytest.mark.parametrize("name,make,nr,na", NUCLEAR_CASES, ids=[c[0] for c in NUCLEAR_CASES])
+def test_nuclear_hessian_from_its_nine_terms(oracle_mod, name, make, nr, na):
     """E^{AB} = E_GG + E_ww + E_grgr + (E_Gw + E_Ggr + E_wgr) + transposes (Sec. II.B, Eq. E_hess)
     from the oracle's pair sums (the Hessian contraction with the nuclear trials, the
     weight-derivative and atom-resolved sums, the grid-grid blocks) and the local derivatives,
     against central differences of the nuclear gradient (itself pinned to the pipeline's
     energy) with the whole synthetic pipeline moving with the atoms."""
-    mol, nr, na = synth.water(), 10, 26
+    mol = make()
     g, rt, gt, W = _nuclear_case(mol, nr, na)
     args = (g.coords, g.weights, g.rho, g.grad_rho)
     kept = g.rho >= 1e-10
