@@ -29,3 +29,21 @@ def test_water_golden(oracle_mod):
     np.testing.assert_allclose(fg, gold["f_gamma_t"], rtol=1e-10, atol=1e-13 * np.abs(fg).max())
     pg = oracle_mod.point_grad(*args, rows=rows)
     np.testing.assert_allclose(pg, gold["point_grad"], rtol=1e-10, atol=1e-14)
+
+
+def test_water_nuclear_golden(oracle_mod):
+    """The nuclear-derivative quantities (grid-grid Hessian blocks, weight-derivative sums, the
+    nuclear gradient and the nine-term nuclear Hessian) reproduce their stored values (written
+    by tests/golden/make_golden_nuclear.py, which calls only oracle/)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden_nuclear",
+                                                  os.path.join(HERE, "golden", "make_golden_nuclear.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    with open(os.path.join(HERE, "golden", "water_780_nuclear.json")) as f:
+        gold = json.load(f)
+    assert gold["rows"] == mk.ROWS
+    q = mk.quantities()
+    for key, val in q.items():
+        ref = np.asarray(gold[key])
+        np.testing.assert_allclose(val, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max(), err_msg=key)
