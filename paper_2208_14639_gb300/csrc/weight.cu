@@ -7,7 +7,8 @@
 // directions into kept order with -3/2 rho_j folded in (y_j = -3/2 rho_j v_j, so that
 // y_j / (g g' s) = v_j rho_j Phi_ij); the contraction kernel takes one row per thread and PC
 // directions per CTA, j in shared-memory tiles, T arithmetic within a tile and FP64 across
-// tiles (per-thread totals in shared memory).
+// tiles (per-thread totals in shared memory).  It serves the FP64 path and the mixed path for
+// fewer than five directions (weight_tc.cu takes the others).
 #include "common.cuh"
 #include "kernels.hpp"
 #include "pairsum.cuh"
@@ -144,9 +145,9 @@ cudaError_t launch_weight_dirs(const PointsDev& p, int32_t Pn, const double* wt,
 cudaError_t launch_weight_response(const PointsDev& p, bool fp64, int32_t Pn, const double* yk,
                                    double* E, double* U, double* W, cudaStream_t st) {
     if (p.nk == 0 || Pn <= 0) return cudaSuccess;
+    // (the mixed path takes this kernel only for a few directions: tensor cores otherwise)
     if (fp64) return launch_wr<double, 8>(p, p.r64a, p.r64b, yk, Pn, E, U, W, st);
-    if (Pn <= 8) return launch_wr<float, 8>(p, p.r32a, p.r32b, yk, Pn, E, U, W, st);
-    return launch_wr<float, 16>(p, p.r32a, p.r32b, yk, Pn, E, U, W, st);
+    return launch_wr<float, 8>(p, p.r32a, p.r32b, yk, Pn, E, U, W, st);
 }
 
 }  // namespace vv10
