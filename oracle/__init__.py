@@ -356,3 +356,68 @@ def nuclear_hessian(weights, rho, grad_rho, kept, kappa_rho, omega_rho, omega_ga
     EGgr = (np.einsum("n,an,bn->ab", w, ra, _f64(E_gr) + rho * (kr * _f64(U_gr) + omr * _f64(W_gr)))
             + np.einsum("n,an,bn->ab", w, gam_a, rho * omg * _f64(W_gr)))
     return EGG + Eww + _f64(H_grgr) + EGw + EGw.T + EGgr + EGgr.T + Ewgr + Ewgr.T
+
+
+# ------------------------------------------------------- nuclear derivative of F (numpy)
+
+def fock_derivative(weights, rho, grad_rho, kept, kappa_rho, omega_rho, omega_gamma, vrho, vgamma,
+                    phi, grad_phi, hess_phi, bf_atom, atom_of_point, grad_rho_a, w_a, E_w, U_w,
+                    W_w, E_gr, U_gr, W_gr, f_rho_a, f_gamma_a) -> np.ndarray:
+    """The nuclear derivative of the VV10 Fock matrix (Sec. II.B), F^a = F^a_G + F^a_gr + F^a_w,
+    over the kept points i (a = 3 A + c), with B_mu_nu = grad(phi_mu phi_nu):
+      F_G  = sum w [f^rho d_a(phi_mu phi_nu) + 2 f^gamma d_a(grad rho . B_mu_nu)]
+             + sum w [phi_mu phi_nu f^{rho,a} + 2 grad rho . B_mu_nu f^{gamma,a}]
+      F_gr = sum w phi_mu phi_nu [E^{a,gr} + rho (kappa' U^{a,gr} + omega_rho W^{a,gr})]
+             + 2 sum w grad rho . B_mu_nu rho omega_gamma W^{a,gr}
+      F_w  = sum w^a [f^rho phi_mu phi_nu + 2 f^gamma grad rho . B_mu_nu]
+             + sum w phi_mu phi_nu [E^{aw} + rho (kappa' U^{aw} + omega_rho W^{aw})]
+             + 2 sum w grad rho . B_mu_nu rho omega_gamma W^{aw}
+    The basis functions and the grid points move with their atoms: phi^a_mu(i) = (delta(A, owner
+    of i) - delta(A, atom of mu)) d phi_mu / d x_c, and d_a(grad rho . B) = grad rho^a . B +
+    grad rho . d_a B.  f^{rho,a}, f^{gamma,a}: the Hessian contraction with the trial (rho^a,
+    grad rho^a); E/U/W^{aw} the weight-derivative sums along w^a; E/U/W^{a,gr} the atom-resolved
+    sums.  phi (n, nbf), grad_phi (n, nbf, 3), hess_phi (n, nbf, 3, 3), bf_atom (nbf,),
+    direction arrays (P, n) or (P, n, 3).  Returns (P, nbf, nbf)."""
+    m = np.asarray(kept, dtype=float)
+    w = _f64(weights) * m
+    rho, g = _f64(rho), _f64(grad_rho).reshape(-1, 3)
+    mask = lambda a: np.where(m > 0, np.nan_to_num(_f64(a)), 0.0)
+    kr, omr, omg = mask(kappa_rho), mask(omega_rho), mask(omega_gamma)
+    vr, vg = mask(vrho), mask(vgamma)
+    phi, dphi, d2phi = _f64(phi), _f64(grad_phi), _f64(hess_phi)
+    own = np.asarray(atom_of_point)
+    bfa = np.asarray(bf_atom)
+    ga, wa = _f64(grad_rho_a), _f64(w_a)
+    Ew, Uw, Ww = mask(E_w), mask(U_w), mask(W_w)
+    Eg, Ug, Wg = mask(E_gr), mask(U_gr), mask(W_gr)
+    fra, fga = mask(f_rho_a), mask(f_gamma_a)
+
+    def S(c):  # sum_i c_i phi_mu phi_nu
+        return (phi * c[:, None]).T @ phi
+
+    def D(v):  # sum_i v_i . B_mu_nu
+        X = np.einsum("nd,nmd->nm", v, dphi)
+        return X.T @ phi + phi.T @ X
+
+    P = fra.shape[0]
+    out = np.zeros((P, phi.shape[1], phi.shape[1]))
+    b = 2.0 * (w * vg)[:, None] * g                       # 2 w f^gamma grad rho
+    bdphi = np.einsum("nd,nmd->nm", b, dphi)
+    for a in range(P):
+        A, c = divmod(a, 3)
+        sig = (own == A).astype(float)[:, None] - (bfa == A).astype(float)[None, :]
+        pa = sig * dphi[:, :, c]                           # phi^a
+        gpa = sig[..., None] * d2phi[:, :, c, :]           # grad phi^a
+        wfp = (w * vr)[:, None] * phi
+        bga = np.einsum("nd,nmd->nm", b, gpa)
+        FG = (pa.T @ wfp + wfp.T @ pa
+              + D(2.0 * (w * vg)[:, None] * ga[a])
+              + bga.T @ phi + pa.T @ bdphi + bdphi.T @ pa + phi.T @ bga
+              + S(w * fra[a]) + D(2.0 * (w * fga[a])[:, None] * g))
+        Fgr = (S(w * (Eg[a] + rho * (kr * Ug[a] + omr * Wg[a])))
+               + D(2.0 * (w * rho * omg * Wg[a])[:, None] * g))
+        Fw = (S(wa[a] * m * vr) + D(2.0 * (wa[a] * m * vg)[:, None] * g)
+              + S(w * (Ew[a] + rho * (kr * Uw[a] + omr * Ww[a])))
+              + D(2.0 * (w * rho * omg * Ww[a])[:, None] * g))
+        out[a] = FG + Fgr + Fw
+    return out

@@ -572,6 +572,27 @@ def ao_values(basis: AOBasis, points: np.ndarray):
     return np.ascontiguousarray(phi), np.ascontiguousarray(dphi)
 
 
+def ao_second_derivatives(basis: AOBasis, points: np.ndarray) -> np.ndarray:
+    """The Hessians of the basis functions at the points, (n, nbf, 3, 3).  With d = r - A and
+    g = N exp(-alpha |d|^2): s functions (phi = g) d^2 phi = (4 alpha^2 d d^T - 2 alpha I) phi;
+    p functions (phi = d_c g) add -2 alpha g (e_c d^T + d e_c^T)."""
+    d = points[:, None, :] - basis.centers[None, :, :]          # (n, nbf, 3)
+    r2 = np.einsum("nmk,nmk->nm", d, d)
+    g = basis.norm[None, :] * np.exp(-basis.alpha[None, :] * r2)
+    is_p = basis.comp >= 0
+    cidx = np.where(is_p, basis.comp, 0)
+    dc = np.take_along_axis(d, cidx[None, :, None].repeat(d.shape[0], 0), axis=2)[..., 0]
+    phi = np.where(is_p[None, :], dc, 1.0) * g
+    al = basis.alpha[None, :, None, None]
+    H = (4.0 * al ** 2 * d[..., :, None] * d[..., None, :]
+         - 2.0 * al * np.eye(3)[None, None]) * phi[..., None, None]
+    e = np.zeros((basis.nbf, 3))
+    e[np.arange(basis.nbf)[is_p], basis.comp[is_p]] = 1.0
+    ed = e[None, :, :, None] * d[..., None, :]                   # e_c d^T
+    H -= 2.0 * al * g[..., None, None] * (ed + ed.transpose(0, 1, 3, 2))
+    return np.ascontiguousarray(H)
+
+
 def ao_density(phi: np.ndarray, dphi: np.ndarray, P: np.ndarray):
     """rho = sum_{mu nu} P_mu_nu phi_mu phi_nu and its gradient (P symmetric), as in the
     definition of the trial density rho^t from P^t (Sec. II.B)."""
@@ -579,6 +600,30 @@ def ao_density(phi: np.ndarray, dphi: np.ndarray, P: np.ndarray):
     rho = np.einsum("nm,nm->n", Pphi, phi)
     grad = 2.0 * np.einsum("nm,nmk->nk", Pphi, dphi)
     return rho, grad
+
+
+def ao_nuclear_derivatives(basis: AOBasis, P: np.ndarray, phi: np.ndarray, dphi: np.ndarray,
+                           d2phi: np.ndarray, atom_of_point: np.ndarray, n_atom: int):
+    """d rho_i / d R_{A,c} and d grad rho_i / d R_{A,c} of rho = sum P_mu_nu phi_mu phi_nu at grid
+    points that move with their atom, the density matrix held fixed: phi_mu(r_i - R_C(mu)) moves
+    by (delta(A, owner of i) - delta(A, C(mu))) d phi_mu / d x_c, so
+      rho^a = 2 sum_mu phi^a_mu (P phi)_mu,
+      grad rho^a = 2 sum_mu [grad phi^a_mu (P phi)_mu + phi^a_mu (P grad phi)_mu].
+    (3 n_atom, n) and (3 n_atom, n, 3), a = 3 A + c."""
+    n = phi.shape[0]
+    Pphi = phi @ P                                    # (n, nbf)
+    Pdphi = np.einsum("mk,nkd->nmd", P, dphi)         # (n, nbf, 3)
+    rt = np.zeros((3 * n_atom, n))
+    gt = np.zeros((3 * n_atom, n, 3))
+    for A in range(n_atom):
+        sig = (atom_of_point == A).astype(float)[:, None] - (basis.atom == A).astype(float)[None, :]
+        for c in range(3):
+            pa = sig * dphi[:, :, c]                  # phi^a (n, nbf)
+            ga = sig[..., None] * d2phi[:, :, c, :]   # grad phi^a (n, nbf, 3)
+            rt[3 * A + c] = 2.0 * np.einsum("nm,nm->n", pa, Pphi)
+            gt[3 * A + c] = 2.0 * (np.einsum("nmd,nm->nd", ga, Pphi)
+                                   + np.einsum("nm,nmd->nd", pa, Pdphi))
+    return rt, gt
 
 
 def density_matrix(basis: AOBasis, n_occ: int, rng: np.random.Generator) -> np.ndarray:
@@ -604,6 +649,32 @@ def ao_system(mol: Molecule, n_rad: int, n_ang: int, seed: int, n_trials: int = 
         rt[t], gt[t] = ao_density(phi, dphi, Pt[t])
     g = GridDensity(pts, w, rho, grad, own, mol)
     return g, phi, dphi, P, Pt, rt, gt
+
+
+def ao_moving_system(mol: Molecule, n_rad: int, n_ang: int, P: np.ndarray = None, seed: int = 0,
+                     rho_min: float = 1e-6, sel: np.ndarray = None):
+    """The molecular grid of mol with the AO-built density of the density matrix P (random from
+    seed when None) on a fixed subset of the grid points (sel, else those with rho > rho_min), the
+    inputs of the nuclear derivatives of the Fock matrix: (GridDensity, phi, grad phi, hess phi,
+    basis, P, sel, rho^a, grad rho^a, w^a), the derivatives along a = 3 A + c with the points,
+    the weights and the basis moving with the atoms.  Rebuilt at a displaced geometry with the
+    same P and sel, the subset holds the same points."""
+    pts, w, own = molecular_grid(mol, n_rad, n_ang)
+    basis = ao_basis(mol)
+    if P is None:
+        P = density_matrix(basis, max(1, int(mol.charges.sum()) // 2), np.random.default_rng(seed))
+    phi, dphi = ao_values(basis, pts)
+    rho, grad = ao_density(phi, dphi, P)
+    if sel is None:
+        sel = rho > rho_min
+    pts, w, own, phi, dphi = pts[sel], w[sel], own[sel], phi[sel], dphi[sel]
+    d2phi = ao_second_derivatives(basis, pts)
+    g = GridDensity(np.ascontiguousarray(pts), np.ascontiguousarray(w),
+                    np.ascontiguousarray(rho[sel]), np.ascontiguousarray(grad[sel]),
+                    np.ascontiguousarray(own), mol)
+    rt, gt = ao_nuclear_derivatives(basis, P, phi, dphi, d2phi, own, mol.n_atom)
+    W = np.ascontiguousarray(weight_directions(mol, n_rad, n_ang)[:, sel])
+    return g, np.ascontiguousarray(phi), np.ascontiguousarray(dphi), d2phi, basis, P, sel, rt, gt, W
 
 
 def config_water(n_rad: int = 30, n_ang: int = 110) -> GridDensity:

@@ -594,3 +594,53 @@ def test_nuclear_hessian_from_its_nine_terms(oracle_mod, name, make, nr, na):
     assert np.abs(H - H.T).max() <= 1e-8 * scale  # w^{ab} comes from central differences
     # translational invariance: every row sums to zero over the atoms (per component)
     assert np.abs(H.reshape(P, NA, 3).sum(axis=1)).max() <= 1e-6 * scale
+
+
+# ------------------------------------------------------ nuclear derivative of the Fock matrix
+
+def _fock_derivative_terms(oracle_mod, g, phi, dphi, d2phi, basis, rt, gt, W):
+    """The oracle's F^a from its pair sums: the potential, the Hessian contraction with the
+    nuclear trials, the weight-derivative and the atom-resolved sums."""
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    NA = g.molecule.n_atom
+    P = 3 * NA
+    _, vr, vg = oracle_mod.potential(*args)
+    Ew, Uw, Ww = oracle_mod.weight_response(*args, W)
+    Egr, Ugr, Wgr = (x.reshape(g.n, P).T for x in oracle_mod.atom_resolved(*args, g.atom_of_point, NA))
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    pp = oracle_mod.point_props(g.rho, g.grad_rho)
+    return oracle_mod.fock_derivative(g.weights, g.rho, g.grad_rho, g.rho >= 1e-10, pp["kappa_rho"],
+                                      pp["omega_rho"], pp["omega_gamma"], vr, vg, phi, dphi, d2phi,
+                                      basis.atom, g.atom_of_point, gt, W, Ew, Uw, Ww, Egr, Ugr, Wgr,
+                                      fr, fg)
+
+
+FOCK_NUCLEAR_CASES = [("water", lambda: synth.water(), 8, 14, 5),
+                      ("chon4", lambda: synth.random_chon(np.random.default_rng(2), 4), 8, 14, 6)]
+
+
+@pytest.mark.parametrize("name,make,nr,na,seed", FOCK_NUCLEAR_CASES,
+                         ids=[c[0] for c in FOCK_NUCLEAR_CASES])
+def test_fock_derivative_from_its_three_terms(oracle_mod, name, make, nr, na, seed):
+    """F^A_mu_nu = F^A_G + F^A_gr + F^A_w (Sec. II.B) against central differences of the oracle
+    Fock matrix of the whole moving pipeline (grid points, Becke weights, basis functions and
+    the AO density of a fixed density matrix; the same subset of points at every geometry).
+    Every term and both halves of the basis derivative (owner atom of the point, atom of the
+    function) are needed to meet it; F^A is symmetric and sums to zero over the atoms."""
+    mol = make()
+    g, phi, dphi, d2phi, basis, Pm, sel, rt, gt, W = synth.ao_moving_system(mol, nr, na, seed=seed)
+    FA = _fock_derivative_terms(oracle_mod, g, phi, dphi, d2phi, basis, rt, gt, W)
+    scale = np.abs(FA).max()
+    h = 1e-4
+    for a in range(3 * mol.n_atom):
+        Fs = []
+        for sg in (1, -1):
+            c = mol.coords.copy()
+            c[a // 3, a % 3] += sg * h
+            g2, f2, df2 = synth.ao_moving_system(synth.Molecule(mol.symbols, c), nr, na, P=Pm,
+                                                 sel=sel)[:3]
+            _, vr2, vg2 = oracle_mod.potential(g2.coords, g2.weights, g2.rho, g2.grad_rho)
+            Fs.append(oracle_mod.fock_matrix(g2.weights, g2.grad_rho, vr2, vg2, f2, df2))
+        assert np.abs(FA[a] - (Fs[0] - Fs[1]) / (2 * h)).max() <= 1e-6 * scale
+    assert np.abs(FA - FA.transpose(0, 2, 1)).max() <= 1e-14 * scale
+    assert np.abs(FA.reshape(mol.n_atom, 3, *FA.shape[1:]).sum(axis=0)).max() <= 1e-8 * scale

@@ -151,3 +151,40 @@ def test_nuclear_density_derivatives_at_moving_points():
         np.testing.assert_allclose(gt[b], (out[0][1] - out[1][1]) / (2 * h), atol=1e-7 * np.abs(gt).max())
         np.testing.assert_allclose(r2[:, b], (out[0][2] - out[1][2]) / (2 * h), atol=1e-7 * np.abs(r2).max())
         np.testing.assert_allclose(g2[:, b], (out[0][3] - out[1][3]) / (2 * h), atol=1e-7 * np.abs(g2).max())
+
+
+def test_ao_second_derivatives():
+    """The basis-function Hessians: symmetric, and the central differences of the analytic
+    gradients."""
+    mol = synth.random_chon(np.random.default_rng(4), 3)
+    b = synth.ao_basis(mol)
+    pts = np.random.default_rng(5).normal(size=(40, 3)) * 1.5
+    H = synth.ao_second_derivatives(b, pts)
+    np.testing.assert_allclose(H, H.transpose(0, 1, 3, 2), rtol=0, atol=1e-14 * np.abs(H).max())
+    h = 1e-5
+    for d in range(3):
+        pp, pm = pts.copy(), pts.copy()
+        pp[:, d] += h
+        pm[:, d] -= h
+        fd = (synth.ao_values(b, pp)[1] - synth.ao_values(b, pm)[1]) / (2 * h)
+        np.testing.assert_allclose(H[:, :, :, d], fd, atol=1e-8 * np.abs(H).max())
+
+
+def test_ao_nuclear_density_derivatives_at_moving_points():
+    """rho^a, grad rho^a of the AO density with the grid points and the basis moving with the
+    atoms (density matrix fixed) against central differences of the rebuilt pipeline; their
+    sum over the atoms vanishes (a rigid translation changes nothing at a moving point)."""
+    mol, nr, na = synth.water(), 8, 14
+    g, _, _, _, b, P, sel, rt, gt, _ = synth.ao_moving_system(mol, nr, na, seed=1)
+    h = 1e-5
+    for a in range(3 * mol.n_atom):
+        out = []
+        for sg in (1, -1):
+            c = mol.coords.copy()
+            c[a // 3, a % 3] += sg * h
+            gg = synth.ao_moving_system(synth.Molecule(mol.symbols, c), nr, na, P=P, sel=sel)[0]
+            out.append((gg.rho, gg.grad_rho))
+        np.testing.assert_allclose(rt[a], (out[0][0] - out[1][0]) / (2 * h), atol=1e-7 * np.abs(rt).max())
+        np.testing.assert_allclose(gt[a], (out[0][1] - out[1][1]) / (2 * h), atol=1e-7 * np.abs(gt).max())
+    np.testing.assert_allclose(rt.reshape(mol.n_atom, 3, -1).sum(axis=0), 0.0, atol=1e-13 * np.abs(rt).max())
+    np.testing.assert_allclose(gt.reshape(mol.n_atom, 3, -1, 3).sum(axis=0), 0.0, atol=1e-13 * np.abs(gt).max())
