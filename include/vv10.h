@@ -243,6 +243,41 @@ vv10_status vv10_nuclear_gradient(vv10_handle h, int32_t P, const double* rho_t,
                                   const double* grad_rho_t, const double* w_t, double* out,
                                   void* stream);
 
+/* The nuclear derivative of the VV10 Fock matrix (Sec. II.B, F^A = F^A_G + F^A_gr + F^A_w) along
+ * the 3 n_atom directions a = 3 A + c, for grid points and basis functions that move with their
+ * atoms, from the per-point results of the calls above (all in caller order, n points):
+ *   F^a_mu_nu = sum_i w^a_i [f^rho phi_mu phi_nu + 2 f^gamma grad rho . B_mu_nu]
+ *             + sum_i w_i [s^a_i phi_mu phi_nu + 2 t^a_i grad rho . B_mu_nu
+ *                          + 2 f^gamma grad rho^a . B_mu_nu]
+ *             + sum_i w_i [f^rho d_a(phi_mu phi_nu) + 2 f^gamma grad rho . d_a B_mu_nu]
+ * with B_mu_nu = grad(phi_mu phi_nu), s^a = f^{rho,a} + E^{aw} + E^{a,gr} + rho (kappa' (U^{aw} +
+ * U^{a,gr}) + omega_rho (W^{aw} + W^{a,gr})), t^a = f^{gamma,a} + rho omega_gamma (W^{aw} +
+ * W^{a,gr}) and d_a phi_mu(i) = ([A owns point i] - [A is the centre of mu]) d phi_mu / d x_c.
+ * Sums over the points kept at vv10_prepare_points, in FP64 (cuBLAS DGEMMs over the points).
+ * Needs atom_of_point at prepare time (n_atom >= 1, else INVALID_ARG).
+ *   nbf, phi, grad_phi   as for vv10_fock_matrix
+ *   hess_phi             n x nbf x 3 x 3 device in: second derivatives of phi_mu at point i
+ *   bf_atom              nbf int32 device in: the atom each basis function is centred on (a
+ *                        value outside [0, n_atom) marks a function that moves with no atom)
+ *   vrho, vgamma         n device in: f^rho, f^gamma (vv10_energy_potential)
+ *   f_rho_a, f_gamma_a   3 n_atom x n device in: vv10_hessian_contract with the trials
+ *                        (rho^a, grad rho^a), the density derivatives at the moving points
+ *   grad_rho_a           3 n_atom x n x 3 device in: that trial's grad rho^a
+ *   w_a                  3 n_atom x n device in: the weight derivatives w^a
+ *   E_w, U_w, W_w        3 n_atom x n device in: vv10_weight_response along w^a
+ *   EUW_gr               3 x n x n_atom x 3 device in: vv10_coord_grad's atom-resolved sums
+ *   FA                   3 n_atom x nbf x nbf device out (each symmetric)
+ * Scratch: (4 n_kept + the per-direction operands of at most about 1 GB) nbf doubles.  Reads the
+ * n_atom + 1 atom segment starts back to the host (the call synchronises the stream and cannot
+ * be captured in a CUDA graph).  Errors: INVALID_ARG, UNSUPPORTED (nbf too large), OOM, CUDA. */
+vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
+                                 const double* grad_phi, const double* hess_phi,
+                                 const int32_t* bf_atom, const double* vrho, const double* vgamma,
+                                 const double* f_rho_a, const double* f_gamma_a,
+                                 const double* grad_rho_a, const double* w_a, const double* E_w,
+                                 const double* U_w, const double* W_w, const double* EUW_gr,
+                                 double* FA, void* stream);
+
 /* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
  * by the last vv10_energy_potential call.  dEdw: n device out. */
 vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &ngpart, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aofa, &ngpart, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -874,6 +874,79 @@ vv10_status vv10_orbital_hessian(vv10_handle h, int32_t nbf, const double* phi,
     VV10_TRY(h->bind());
     return ao_assemble(h, nbf, phi, grad_phi, P_trials, f_rho_t, f_gamma_t, vgamma, grad_rho_t, G,
                        stream);
+}
+
+vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
+                                 const double* grad_phi, const double* hess_phi,
+                                 const int32_t* bf_atom, const double* vrho, const double* vgamma,
+                                 const double* f_rho_a, const double* f_gamma_a,
+                                 const double* grad_rho_a, const double* w_a, const double* E_w,
+                                 const double* U_w, const double* W_w, const double* EUW_gr,
+                                 double* FA, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    PointsDev& P = h->P;
+    if (P.n_atom == 0) {
+        h->set_error("the nuclear derivative of the Fock matrix needs atom_of_point at prepare time");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (nbf < 1 || nbf > VV10_MAX_BASIS) {
+        h->set_error("nbf must be in [1, VV10_MAX_BASIS]");
+        return nbf < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    const void* ins[] = {phi, grad_phi, hess_phi, vrho, vgamma, f_rho_a, f_gamma_a, grad_rho_a,
+                         w_a, E_w, U_w, W_w, EUW_gr, FA};
+    for (const void* q : ins)
+        if (!device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+            h->set_error("arrays must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    if (!device_ptr_ok(bf_atom, h->device) || !aligned(bf_atom, 4)) {
+        h->set_error("bf_atom must be a 4-byte aligned device pointer");
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (stream_capturing(st)) {
+        h->set_error("vv10_fock_derivative reads the atom segments on the host and cannot be captured");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (!h->blas && ao_blas_create(&h->blas) != 0) {
+        h->blas = nullptr;
+        h->set_error("cuBLAS handle creation failed");
+        return VV10_ERR_CUDA;
+    }
+    const int32_t n_dir = 3 * P.n_atom;
+    const size_t nk = static_cast<size_t>(P.nk > 0 ? P.nk : 1);
+    const size_t nn = static_cast<size_t>(nbf) * nbf;
+    const int64_t chunk = ao_channels_per_chunk(P.nk, nbf, n_dir, size_t(1) << 30);
+    VV10_TRY(h->ensure(h->aophik, sizeof(double) * nk * nbf, "gathered basis values"));
+    VV10_TRY(h->ensure(h->aoz, sizeof(double) * nk * nbf * chunk, "assembly operand"));
+    VV10_TRY(h->ensure(h->aom, sizeof(double) * nn * chunk, "assembly products"));
+    VV10_TRY(h->ensure(h->aofa, sizeof(double) * (4 * nk * nbf + 2 * nn), "basis-derivative factors"));
+    std::vector<int64_t> seg(static_cast<size_t>(P.n_atom) + 1);
+    VV10_CUDA(h, cudaMemcpyAsync(seg.data(), P.seg, sizeof(int64_t) * seg.size(),
+                                 cudaMemcpyDeviceToHost, st), "atom segments");
+    VV10_CUDA(h, cudaStreamSynchronize(st), "atom segments");
+    FockDerivIn in{nbf, phi, grad_phi, hess_phi, bf_atom, vrho, vgamma, f_rho_a, f_gamma_a,
+                   grad_rho_a, w_a, E_w, U_w, W_w, EUW_gr};
+    double* fa = static_cast<double*>(h->aofa.p);
+    const int n_launch =
+        P.nk > 0 ? 2 + 2 * static_cast<int>((n_dir + chunk - 1) / chunk) + 3 * (1 + P.n_atom) : 0;
+    int bs = 0;
+    PhaseScope ph(h, PH_AO_ASSEMBLY, st, n_launch);
+    VV10_CUDA(h, launch_fock_derivative(P, h->blas, in, seg.data(), chunk,
+                                        static_cast<double*>(h->aophik.p),
+                                        static_cast<double*>(h->aoz.p),
+                                        static_cast<double*>(h->aom.p), fa, fa + 4 * nk * nbf, FA,
+                                        st, &bs),
+              "nuclear derivative of the Fock matrix");
+    if (bs != 0) {
+        h->set_error("cuBLAS failed (status %d) in the nuclear derivative of the Fock matrix", bs);
+        return VV10_ERR_CUDA;
+    }
+    return VV10_OK;
 }
 
 }  // extern "C"

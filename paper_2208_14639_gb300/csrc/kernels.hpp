@@ -216,6 +216,21 @@ cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, cons
                                const double* fg, const double* vg, const double* gt,
                                int64_t chunk, double* phik, double* Z, double* M, double* out,
                                cudaStream_t st, int* blas_status);
+// Nuclear derivative of the Fock matrix (Sec. II.B) for the 3 n_atom directions a = 3 A + c:
+// caller-order inputs (direction arrays [a n + i], grad_rho_a [(a n + i) 3 + d], EUW_gr
+// [(q n + i) 3 n_atom + a]); seg = the host copy of the n_atom + 1 kept-point segment starts;
+// LR: 4 nk nbf doubles, K2: 2 nbf^2 doubles.
+struct FockDerivIn {
+    int32_t nbf;
+    const double *phi, *dphi, *hphi;  // n x nbf, n x nbf x 3, n x nbf x 3 x 3
+    const int32_t* bf_atom;           // nbf
+    const double *vrho, *vgamma;      // n
+    const double *f_rho_a, *f_gamma_a, *grad_rho_a, *w_a, *E_w, *U_w, *W_w, *EUW_gr;
+};
+cudaError_t launch_fock_derivative(const PointsDev& p, void* blas, const FockDerivIn& in,
+                                   const int64_t* seg, int64_t chunk, double* phik, double* Z,
+                                   double* M, double* LR, double* K2, double* out, cudaStream_t st,
+                                   int* blas_status);
 int ao_blas_create(void** blas);
 void ao_blas_destroy(void* blas);
 

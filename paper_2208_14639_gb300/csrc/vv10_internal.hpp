@@ -141,6 +141,7 @@ struct vv10_ctx {
     vv10::DevBuf wsplit;  // their TF32 hi / FP32 lo split (tensor-core path)
     vv10::DevBuf ehalf;   // per-CTA totals of the energy-only kernel
     vv10::DevBuf aophik, aoz, aom;  // AO assembly: gathered phi, Z, GEMM results
+    vv10::DevBuf aofa;              // nuclear derivative of F: basis-derivative factors, K^c
     vv10::DevBuf ngpart;            // per-block partials of the nuclear-gradient terms
     void* blas = nullptr;            // cuBLAS handle of the AO assembly (made on first use)
 

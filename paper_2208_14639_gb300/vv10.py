@@ -49,7 +49,7 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
            "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
            "vv10_weight_response", "vv10_energy", "vv10_fock_matrix",
-           "vv10_orbital_hessian", "vv10_nuclear_gradient")
+           "vv10_orbital_hessian", "vv10_nuclear_gradient", "vv10_fock_derivative")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
 VV10_N_PHASES = 16
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
         "vv10_fock_matrix": (st, [P, I32, P, P, P, P, P, P]),
         "vv10_nuclear_gradient": (st, [P, I32, P, P, P, P, P]),
         "vv10_orbital_hessian": (st, [P, I32, P, P, I32, P, P, P, P, P, P]),
+        "vv10_fock_derivative": (st, [P, I32] + [P] * 16),
         "vv10_weight_grad": (st, [P, P, P]),
         "vv10_sync": (st, [P, P]),
         "vv10_set_tiles": (st, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -260,6 +261,25 @@ def vv10_orbital_hessian(h, phi, grad_phi, f_rho_t, f_gamma_t, grad_rho_t, vgamm
         _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)), _dptr(vgamma, "vgamma", shape=(n,)),
         _dptr(G, "G", shape=(P, nbf, nbf)), _stream(stream))
     _check(h, st, "vv10_orbital_hessian")
+
+
+def vv10_fock_derivative(h, phi, grad_phi, hess_phi, bf_atom, vrho, vgamma, f_rho_a, f_gamma_a,
+                         grad_rho_a, w_a, E_w, U_w, W_w, EUW_gr, FA, stream=None) -> None:
+    n, nbf = phi.shape
+    P = int(FA.shape[0])
+    na = P // 3
+    dirs = dict(shape=(P, n))
+    st = load().vv10_fock_derivative(
+        h, int(nbf), _dptr(phi, "phi", shape=(n, nbf)), _dptr(grad_phi, "grad_phi", shape=(n, nbf, 3)),
+        _dptr(hess_phi, "hess_phi", shape=(n, nbf, 3, 3)),
+        _dptr(bf_atom, "bf_atom", torch.int32, shape=(nbf,)),
+        _dptr(vrho, "vrho", shape=(n,)), _dptr(vgamma, "vgamma", shape=(n,)),
+        _dptr(f_rho_a, "f_rho_a", **dirs), _dptr(f_gamma_a, "f_gamma_a", **dirs),
+        _dptr(grad_rho_a, "grad_rho_a", shape=(P, n, 3)), _dptr(w_a, "w_a", **dirs),
+        _dptr(E_w, "E_w", **dirs), _dptr(U_w, "U_w", **dirs), _dptr(W_w, "W_w", **dirs),
+        _dptr(EUW_gr, "EUW_gr", shape=(3, n, na, 3)), _dptr(FA, "FA", shape=(P, nbf, nbf)),
+        _stream(stream))
+    _check(h, st, "vv10_fock_derivative")
 
 
 def vv10_nuclear_gradient(h, out, rho_t=None, grad_rho_t=None, w_t=None, stream=None) -> None:
@@ -512,6 +532,17 @@ class VV10:
                         device=phi.device)
         vv10_orbital_hessian(self.h, phi, grad_phi, f_rho_t, f_gamma_t, grad_rho_t, vgamma, G, stream)
         return G
+
+    def fock_derivative(self, phi, grad_phi, hess_phi, bf_atom, vrho, vgamma, f_rho_a, f_gamma_a,
+                        grad_rho_a, w_a, E_w, U_w, W_w, EUW_gr, stream=None):
+        """F^A (3 n_atom x nbf x nbf), the nuclear derivative of the Fock matrix, from the
+        potential, the Hessian contraction with the nuclear trials, the weight-derivative and
+        the atom-resolved sums and the basis (values, gradients, Hessians) on the grid."""
+        FA = torch.empty(3 * self.n_atom, phi.shape[1], phi.shape[1], dtype=torch.float64,
+                         device=phi.device)
+        vv10_fock_derivative(self.h, phi, grad_phi, hess_phi, bf_atom, vrho, vgamma, f_rho_a,
+                             f_gamma_a, grad_rho_a, w_a, E_w, U_w, W_w, EUW_gr, FA, stream)
+        return FA
 
     def energy(self, prec=VV10_FP64, stream=None) -> float:
         """E alone, from the unordered pairs (half the pair evaluations)."""
