@@ -388,6 +388,40 @@ def time_ao_assembly(vv, h, pb, reps):
     return ev[0].elapsed_time(ev[1]) / reps, ev[2].elapsed_time(ev[3]) / reps, nbf
 
 
+def time_fock_derivative(vv, h, pb, prec, wdirs, reps):
+    """The nuclear derivative of the Fock matrix (vv10_fock_derivative) along the step's 3 N_atom
+    trial directions, with the weight-derivative sums along the Becke weight directions, the
+    step's atom-resolved sums and the synthetic Gaussian basis (values, gradients, Hessians) on
+    the grid: milliseconds per call (each call reads the atom segments back to the host)."""
+    import torch
+    from paper_2208_14639_gb300 import synth
+    o, d = pb.out, pb.d
+    if o["euw"] is None:
+        return None
+    basis = synth.ao_basis(pb.g.molecule)
+    xyz = pb.host["xyz"]
+    dev = d["xyz"].device
+    phi, dphi = (torch.from_numpy(x).to(dev) for x in synth.ao_values(basis, xyz))
+    d2phi = torch.from_numpy(synth.ao_second_derivatives(basis, xyz)).to(dev)
+    bf_atom = torch.from_numpy(basis.atom.astype(np.int32)).to(dev)
+    E, U, W = (torch.empty_like(wdirs) for _ in range(3))
+    vv.vv10_weight_response(h, prec, wdirs, E, U, W)
+    nbf = basis.nbf
+    FA = torch.empty(3 * pb.n_atom, nbf, nbf, dtype=torch.float64, device=dev)
+    args = (h, phi, dphi, d2phi, bf_atom, o["vrho"], o["vgamma"], o["frt"], o["fgt"], d["gt"],
+            wdirs, E, U, W, o["euw"], FA)
+    vv.vv10_fock_derivative(*args)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        vv.vv10_fock_derivative(*args)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps
+
+
 def time_e2e(vv, h, pb, prec, steps, warmup):
     """The same step with host inputs: every step copies all of its inputs from pinned host
     memory to the device and all of its outputs back, inside the timed region.  The copies
@@ -528,6 +562,7 @@ def gpu_arm(args):
         P_w = int(wdirs.shape[0])
         ms_wr = time_weight_response(vv, h, pb, prec, wdirs, 3)
         ms_fock, ms_gt, nbf = time_ao_assembly(vv, h, pb, 3)
+        ms_fa = time_fock_derivative(vv, h, pb, prec, wdirs, 3)
     alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
     breakdown = {
         # the two metric quantities, each timed as its own entry point (3 calls each)
@@ -553,6 +588,11 @@ def gpu_arm(args):
             "fock_matrix_call_ms": ms_fock,
             "orbital_hessian_call_ms": ms_gt,
             "orbital_hessian_fp64_tflops": 2.0 * nbf * nbf * nk * pb.P / (ms_gt / 1e3) / 1e12,
+            # nuclear derivative of the Fock matrix (3 N_atom directions): 2 nbf^2 flops per
+            # point and direction, plus 24 nbf^2 per point for the basis-function derivatives
+            "fock_derivative_call_ms": ms_fa,
+            "fock_derivative_fp64_tflops": (2.0 * nbf * nbf * nk * (3 * pb.n_atom + 12) / (ms_fa / 1e3) / 1e12
+                                            if ms_fa else None),
             # weight-derivative sums for the 3 N_atom Becke weight directions (not in the step)
             "weight_response_P": P_w,
             "weight_response_call_ms": ms_wr,
