@@ -46,13 +46,40 @@ def quantities():
                 weight_W=Ww[:, ROWS], nuclear_gradient=grad, nuclear_hessian=H)
 
 
+AO_NR, AO_NA, AO_SEED = 8, 14, 5
+AO_ROWS = [0, 4, 8, 12]
+
+
+def fock_quantities():
+    """The Fock matrix and its nuclear derivative for water with its AO basis (13 functions) on
+    the 8 x 14 grid per atom, the points with rho > 1e-6: rows AO_ROWS of F and of every F^a."""
+    mol = synth.water()
+    g, phi, dphi, d2phi, basis, _, _, rt, gt, W = synth.ao_moving_system(mol, AO_NR, AO_NA, seed=AO_SEED)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    P = 3 * mol.n_atom
+    _, vr, vg = oracle.potential(*args)
+    F = oracle.fock_matrix(g.weights, g.grad_rho, vr, vg, phi, dphi)
+    Ew, Uw, Ww = oracle.weight_response(*args, W)
+    Egr, Ugr, Wgr = (x.reshape(g.n, P).T for x in oracle.atom_resolved(*args, g.atom_of_point, mol.n_atom))
+    fr, fg = oracle.hessian_contract(*args, rt, gt)
+    pp = oracle.point_props(g.rho, g.grad_rho)
+    FA = oracle.fock_derivative(g.weights, g.rho, g.grad_rho, g.rho >= 1e-10, pp["kappa_rho"],
+                                pp["omega_rho"], pp["omega_gamma"], vr, vg, phi, dphi, d2phi,
+                                basis.atom, g.atom_of_point, gt, W, Ew, Uw, Ww, Egr, Ugr, Wgr, fr, fg)
+    return dict(fock_matrix=F[AO_ROWS], fock_derivative=FA[:, AO_ROWS])
+
+
 def main():
     q = quantities()
+    qf = fock_quantities()
     out = {"what": f"water, {NR}x{NA} points per atom, b=6, C=0.01, rho_cut=1e-10; Becke weight "
-                   "directions; rows " + str(ROWS) + " of the weight-derivative sums",
+                   "directions; rows " + str(ROWS) + " of the weight-derivative sums; the Fock "
+                   f"matrix and its nuclear derivative (rows {AO_ROWS}) on the {AO_NR}x{AO_NA} "
+                   f"grid's points with rho > 1e-6, AO basis, density matrix seed {AO_SEED}",
            "source": "oracle/ (FP64 CPU) via tests/golden/make_golden_nuclear.py",
-           "rows": ROWS}
+           "rows": ROWS, "ao_rows": AO_ROWS}
     out.update({k: np.asarray(v).tolist() for k, v in q.items()})
+    out.update({k: np.asarray(v).tolist() for k, v in qf.items()})
     with open(os.path.join(HERE, "water_780_nuclear.json"), "w") as f:
         json.dump(out, f, indent=1)
     print("nuclear gradient", q["nuclear_gradient"])

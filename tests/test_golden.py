@@ -33,7 +33,8 @@ def test_water_golden(oracle_mod):
 
 def test_water_nuclear_golden(oracle_mod):
     """The nuclear-derivative quantities (grid-grid Hessian blocks, weight-derivative sums, the
-    nuclear gradient and the nine-term nuclear Hessian) reproduce their stored values (written
+    nuclear gradient, the nine-term nuclear Hessian, the Fock matrix and its nuclear derivative)
+    reproduce their stored values (written
     by tests/golden/make_golden_nuclear.py, which calls only oracle/)."""
     import importlib.util
     spec = importlib.util.spec_from_file_location("make_golden_nuclear",
@@ -42,8 +43,9 @@ def test_water_nuclear_golden(oracle_mod):
     spec.loader.exec_module(mk)
     with open(os.path.join(HERE, "golden", "water_780_nuclear.json")) as f:
         gold = json.load(f)
-    assert gold["rows"] == mk.ROWS
+    assert gold["rows"] == mk.ROWS and gold["ao_rows"] == mk.AO_ROWS
     q = mk.quantities()
+    q.update(mk.fock_quantities())
     for key, val in q.items():
         ref = np.asarray(gold[key])
         np.testing.assert_allclose(val, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max(), err_msg=key)
