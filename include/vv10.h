@@ -267,7 +267,8 @@ vv10_status vv10_nuclear_gradient(vv10_handle h, int32_t P, const double* rho_t,
  *   E_w, U_w, W_w        3 n_atom x n device in: vv10_weight_response along w^a
  *   EUW_gr               3 x n x n_atom x 3 device in: vv10_coord_grad's atom-resolved sums
  *   FA                   3 n_atom x nbf x nbf device out (each symmetric)
- * Scratch: (4 n_kept + the per-direction operands of at most about 1 GB) nbf doubles.  Reads the
+ * Scratch: 5 n_kept nbf + 2 nbf^2 doubles, plus per-direction operands and products of about 1 GB
+ * at most (the directions are taken in chunks).  Reads the
  * n_atom + 1 atom segment starts back to the host (the call synchronises the stream and cannot
  * be captured in a CUDA graph).  Errors: INVALID_ARG, UNSUPPORTED (nbf too large), OOM, CUDA. */
 vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
