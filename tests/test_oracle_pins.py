@@ -631,7 +631,15 @@ def test_fock_derivative_from_its_three_terms(oracle_mod, name, make, nr, na, se
     g, phi, dphi, d2phi, basis, Pm, sel, rt, gt, W = synth.ao_moving_system(mol, nr, na, seed=seed)
     FA = _fock_derivative_terms(oracle_mod, g, phi, dphi, d2phi, basis, rt, gt, W)
     scale = np.abs(FA).max()
-    h = 1e-4
+    fd = _fock_differences(oracle_mod, mol, nr, na, Pm, sel)
+    assert np.abs(FA - fd).max() <= 1e-6 * scale
+    assert np.abs(FA - FA.transpose(0, 2, 1)).max() <= 1e-14 * scale
+    assert np.abs(FA.reshape(mol.n_atom, 3, *FA.shape[1:]).sum(axis=0)).max() <= 1e-8 * scale
+
+
+def _fock_differences(oracle_mod, mol, nr, na, Pm, sel, h=1e-4):
+    """Central differences of the oracle Fock matrix of the moving pipeline, (3 N_atom, nbf, nbf)."""
+    out = []
     for a in range(3 * mol.n_atom):
         Fs = []
         for sg in (1, -1):
@@ -641,6 +649,40 @@ def test_fock_derivative_from_its_three_terms(oracle_mod, name, make, nr, na, se
                                                  sel=sel)[:3]
             _, vr2, vg2 = oracle_mod.potential(g2.coords, g2.weights, g2.rho, g2.grad_rho)
             Fs.append(oracle_mod.fock_matrix(g2.weights, g2.grad_rho, vr2, vg2, f2, df2))
-        assert np.abs(FA[a] - (Fs[0] - Fs[1]) / (2 * h)).max() <= 1e-6 * scale
-    assert np.abs(FA - FA.transpose(0, 2, 1)).max() <= 1e-14 * scale
-    assert np.abs(FA.reshape(mol.n_atom, 3, *FA.shape[1:]).sum(axis=0)).max() <= 1e-8 * scale
+        out.append((Fs[0] - Fs[1]) / (2 * h))
+    return np.array(out)
+
+
+def test_fock_derivative_pin_catches_planted_mistakes(oracle_mod):
+    """Each plausible mistake planted in the oracle's assembly (one term dropped by zeroing its
+    input, or one half of the basis-function derivative dropped by relabelling the atoms) moves
+    F^A at least 100 times the pin's tolerance away from the central differences."""
+    mol, nr, na, seed = synth.water(), 8, 14, 5
+    g, phi, dphi, d2phi, basis, Pm, sel, rt, gt, W = synth.ao_moving_system(mol, nr, na, seed=seed)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    NA, P = mol.n_atom, 3 * mol.n_atom
+    _, vr, vg = oracle_mod.potential(*args)
+    Ew, Uw, Ww = oracle_mod.weight_response(*args, W)
+    Egr, Ugr, Wgr = (x.reshape(g.n, P).T for x in oracle_mod.atom_resolved(*args, g.atom_of_point, NA))
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    pp = oracle_mod.point_props(g.rho, g.grad_rho)
+    base = dict(vg=vg, d2phi=d2phi, bf_atom=basis.atom, own=g.atom_of_point, gt=gt, W=W, Ew=Ew,
+                Uw=Uw, Ww=Ww, Egr=Egr, Ugr=Ugr, Wgr=Wgr, fr=fr, fg=fg)
+
+    def assemble(**kw):
+        q = dict(base, **kw)
+        return oracle_mod.fock_derivative(g.weights, g.rho, g.grad_rho, g.rho >= 1e-10,
+                                          pp["kappa_rho"], pp["omega_rho"], pp["omega_gamma"], vr,
+                                          q["vg"], phi, dphi, q["d2phi"], q["bf_atom"], q["own"],
+                                          q["gt"], q["W"], q["Ew"], q["Uw"], q["Ww"], q["Egr"],
+                                          q["Ugr"], q["Wgr"], q["fr"], q["fg"])
+
+    fd = _fock_differences(oracle_mod, mol, nr, na, Pm, sel)
+    scale = np.abs(fd).max()
+    assert np.abs(assemble() - fd).max() <= 1e-6 * scale
+    planted = {k: {k: np.zeros_like(v)} for k, v in base.items()
+               if k in ("d2phi", "gt", "W", "Ew", "Uw", "Ww", "Egr", "Ugr", "Wgr", "fr", "fg")}
+    planted["owner half"] = {"own": np.full_like(g.atom_of_point, -1)}
+    planted["centre half"] = {"bf_atom": np.full_like(basis.atom, -1)}
+    for name, kw in planted.items():
+        assert np.abs(assemble(**kw) - fd).max() >= 1e-4 * scale, name
