@@ -596,6 +596,51 @@ def test_nuclear_hessian_from_its_nine_terms(oracle_mod, name, make, nr, na):
     assert np.abs(H.reshape(P, NA, 3).sum(axis=1)).max() <= 1e-6 * scale
 
 
+def test_nuclear_hessian_pin_catches_planted_mistakes(oracle_mod):
+    """Each input of the nine-term assembly zeroed in turn (a dropped term or pair sum: the
+    potential, E_i, rho^a, grad rho^a, their second derivatives, w^a, w^{ab}, the
+    weight-derivative and atom-resolved sums, the Hessian contraction, the grid-grid blocks)
+    moves the nuclear Hessian at least 100 times the pin's tolerance away from the central
+    differences of the gradient."""
+    mol, nr, na = synth.water(), 10, 26
+    g, rt, gt, W = _nuclear_case(mol, nr, na)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    kept = g.rho >= 1e-10
+    NA, P = mol.n_atom, 3 * mol.n_atom
+    _, vr, vg = oracle_mod.potential(*args)
+    pp = oracle_mod.point_props(g.rho, g.grad_rho)
+    r2, g2 = synth.nuclear_density_second_derivatives(mol, g.coords, g.atom_of_point)
+    Ew, Uw, Ww = oracle_mod.weight_response(*args, W)
+    Egr, Ugr, Wgr = (x.reshape(g.n, P).T for x in oracle_mod.atom_resolved(*args, g.atom_of_point, NA))
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    base = dict(vr=vr, vg=vg, E=oracle_mod.pair_sums(*args)["E"], rt=rt, gt=gt, r2=r2, g2=g2, W=W,
+                Wab=synth.weight_second_derivatives(mol, nr, na), Ew=Ew, Uw=Uw, Ww=Ww, Egr=Egr,
+                Ugr=Ugr, Wgr=Wgr, fr=fr, fg=fg,
+                Hgg=oracle_mod.coord_hessian(*args, g.atom_of_point, NA).transpose(0, 2, 1, 3).reshape(P, P))
+
+    def assemble(**kw):
+        q = dict(base, **kw)
+        return oracle_mod.nuclear_hessian(g.weights, g.rho, g.grad_rho, kept, pp["kappa_rho"],
+                                          pp["omega_rho"], pp["omega_gamma"], *(q[k] for k in (
+                                              "vr", "vg", "E", "rt", "gt", "r2", "g2", "W", "Wab",
+                                              "Ew", "Uw", "Ww", "Egr", "Ugr", "Wgr", "fr", "fg",
+                                              "Hgg")))
+
+    h = 1e-4
+    fd = np.zeros((P, P))
+    for b in range(P):
+        gs = []
+        for sg in (1, -1):
+            c = mol.coords.copy()
+            c[b // 3, b % 3] += sg * h
+            gs.append(_nuclear_gradient(oracle_mod, *_nuclear_case(synth.Molecule(mol.symbols, c), nr, na)))
+        fd[:, b] = (gs[0] - gs[1]) / (2 * h)
+    scale = np.abs(fd).max()
+    assert np.abs(assemble() - fd).max() <= 1e-6 * scale
+    for k, v in base.items():
+        assert np.abs(assemble(**{k: np.zeros_like(v)}) - fd).max() >= 1e-4 * scale, k
+
+
 # ------------------------------------------------------ nuclear derivative of the Fock matrix
 
 def _fock_derivative_terms(oracle_mod, g, phi, dphi, d2phi, basis, rt, gt, W):
