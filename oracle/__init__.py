@@ -12,6 +12,7 @@ is how large grids are checked on sampled outputs.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import platform
@@ -52,8 +53,39 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    path = build()
-    lib = ctypes.CDLL(path)
+    _lib = _configure(ctypes.CDLL(build()))
+    return _lib
+
+
+@contextlib.contextmanager
+def planted(old: str, new: str, tag: str):
+    """Test infrastructure for checking the pins themselves: inside the block every wrapper of
+    this module runs a copy of vv10_oracle.c in which the text ``old`` (which must occur exactly
+    once) is replaced by ``new``, i.e. with one planted mistake.  The copy is compiled with the
+    same flags under _build/."""
+    global _lib
+    with open(_SRC) as f:
+        src = f.read()
+    if src.count(old) != 1:
+        raise ValueError(f"planted mistake {tag!r}: the text to replace occurs {src.count(old)} times")
+    keep = _load()
+    os.makedirs(_BUILD, exist_ok=True)
+    csrc = os.path.join(_BUILD, f"planted_{tag}.c")
+    so = os.path.join(_BUILD, f"liborc_planted_{tag}_{platform.machine()}.so")
+    with open(csrc, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
+                    "-o", so, csrc, "-lm"], check=True)
+    with _lock:
+        _lib = _configure(ctypes.CDLL(so))
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = keep
+
+
+def _configure(lib):
     D = ctypes.c_double
     I64 = ctypes.c_int64
     I32 = ctypes.c_int32
@@ -80,7 +112,6 @@ def _load():
                  "orc_point_grad", "orc_atom_grad", "orc_atom_resolved", "orc_point_coord_hessian",
                  "orc_coord_hessian", "orc_weight_response"):
         getattr(lib, name).restype = ctypes.c_int
-    _lib = lib
     return lib
 
 
