@@ -1,12 +1,15 @@
 """The pins catch plausible mistakes in the oracle.
 
 Each case plants one mistake in a copy of the oracle's C source (a dropped term, a wrong sign
-or factor, a dropped self pair), compiles it, and runs the named pins of test_oracle_pins.py
-against it: every named pin must fail.  The unmodified oracle passes the same pins in that
-module.  Planting happens on the CPU only; nothing here touches the CUDA path.
+or factor, a dropped self pair) or of one of its numpy assemblies, and runs the named pins of
+test_oracle_pins.py against it: every named pin must fail.  The unmodified oracle passes the
+same pins in that module.  Planting happens on the CPU only; nothing here touches the CUDA path.
 """
+import contextlib
+import inspect
 import os
 import sys
+import textwrap
 
 import pytest
 
@@ -84,3 +87,67 @@ def test_planted_mistake_fails_its_pins(oracle_mod, tag, old, new, catch):
             except (AssertionError, FloatingPointError, ValueError):
                 continue
             pytest.fail(f"{name} passed with the planted mistake {tag}")
+
+
+def FOCK(o):
+    pins.test_fock_matrix_is_energy_derivative(o)
+
+
+def GT(o):
+    pins.test_orbital_hessian_is_fock_derivative(o)
+
+
+def FA(o):
+    pins.test_fock_derivative_from_its_three_terms(o, *pins.FOCK_NUCLEAR_CASES[0])
+
+
+def NH(o):
+    pins.test_nuclear_hessian_from_its_nine_terms(o, *pins.NUCLEAR_CASES[0])
+
+
+@contextlib.contextmanager
+def planted_py(module, name, old, new):
+    """The module's function `name` recompiled from its source with `old` (occurring once)
+    replaced by `new`, until the block exits."""
+    fn = getattr(module, name)
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, (name, old)
+    ns = dict(module.__dict__)
+    exec(compile(src.replace(old, new), f"<planted {name}>", "exec"), ns)
+    setattr(module, name, ns[name])
+    try:
+        yield
+    finally:
+        setattr(module, name, fn)
+
+
+# (tag, oracle function, text in its source, its planted replacement, pins that must fail)
+PY_MUTANTS = [
+    ("fock_drops_2_on_gamma_term", "fock_matrix", "v = 2.0 * (w * _f64(vgamma))[:, None]",
+     "v = (w * _f64(vgamma))[:, None]", [FOCK]),
+    ("fock_one_sided_gradient_term", "fock_matrix", "+ vdphi.T @ phi + phi.T @ vdphi",
+     "+ 2.0 * vdphi.T @ phi", [FOCK]),
+    ("orbital_hessian_drops_fgamma_grad_rho_t", "orbital_hessian",
+     "(fg[t][:, None] * g + vg[:, None] * gt[t])", "(fg[t][:, None] * g)", [GT]),
+    ("fock_derivative_drops_grad_rho_a_term", "fock_derivative",
+     "+ D(2.0 * (w * vg)[:, None] * ga[a])", "", [FA]),
+    ("fock_derivative_drops_basis_hessian_term", "fock_derivative",
+     "+ bga.T @ phi + pa.T @ bdphi", "+ pa.T @ bdphi", [FA]),
+    ("fock_derivative_drops_weight_derivative_term", "fock_derivative",
+     "Fw = (S(wa[a] * m * vr) + ", "Fw = (", [FA]),
+    ("nuclear_hessian_drops_a_transpose", "nuclear_hessian", "+ EGw + EGw.T +", "+ 2.0 * EGw +",
+     [NH]),
+    ("nuclear_hessian_gamma_ab_drops_first_product", "nuclear_hessian",
+     'np.einsum("and,bnd->abn", ga, ga) + ', "", [NH]),
+]
+
+
+@pytest.mark.parametrize("tag,name,old,new,catch", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_planted_mistake_in_an_assembly_fails_its_pins(oracle_mod, tag, name, old, new, catch):
+    with planted_py(oracle_mod, name, old, new):
+        for pin in catch:
+            try:
+                pin(oracle_mod)
+            except (AssertionError, FloatingPointError, ValueError):
+                continue
+            pytest.fail(f"{pin.__name__} passed with the planted mistake {tag}")
