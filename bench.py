@@ -3,16 +3,19 @@
 
 One step = one pass of the whole hot path over the workload's synthetic grid, through the
 C ABI: vv10_prepare_points -> vv10_evaluate (energy, potential, Hessian contraction with P
-trials, point gradient, atom sums, atom-resolved E/U/W^Bgr).  The step evaluates the three
-pair quantities of the separate entry points (energy/potential, Hessian, coordinate terms),
-N_kept^2 ordered pairs each, so
-    value = 3 * N_kept^2 * steps / (time of the timed steps)         [pair evals/s]
-with inputs resident in HBM when the timed region starts.  The same step in FP64 and
-per-call rates are reported beside it.  N > 1 (torchrun): every rank runs its own copy of
-the workload (independent problems, no data-path collective); value sums over ranks.
+trials, point gradient, atom sums; atom-resolved E/U/W^Bgr on the grids small enough to keep
+them).  Every quantity of the step is a sum over all N_kept^2 ordered pairs, so
+    value = N_kept^2 * steps / (time of the timed steps)             [pair evals/s]
+with inputs resident in HBM when the timed region starts.  The metric's two quantities are
+also timed on their own entry points (metric_parts: energy + potential, Hessian
+contraction), each beside its FP64 rate on the same GPU.  Default workload: the 60-atom CHON
+molecule (1,359,000 points, P = 180), mixed precision with the split-FP16 contraction.
+N > 1 (torchrun): every rank runs its own copy of the workload (independent problems, no
+data-path collective); value sums over ranks.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload hexamer|water|cluster24|chon60|batch] [--precision mixed|fp64]
+                       [--workload chon60|hexamer|water|cluster24|batch]
+                       [--precision f16x3|tf32x3|fp64]
 --workload batch runs the 64-molecule batch through vv10_batch_prepare + vv10_batch_run
 (energy, potential and Hessian contraction; 2 sum_m N_kept,m^2 pairs per step).
 """
@@ -35,6 +38,10 @@ if ROOT not in sys.path:
 
 METRIC = "VV10 pair evals/s: E+potential & Hessian contraction, mixed vs FP64 GPU"
 UNIT = "pair evals/s"
+DTYPES = {"f16x3": "f32 pair tiles, split-fp16 tensor-core contraction, f64 precompute/reductions",
+          "mixed": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions",
+          "tf32x3": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions",
+          "fp64": "f64"}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
@@ -178,20 +185,25 @@ def load_peaks():
 
 
 class Problem:
-    """A workload's inputs resident on the device plus preallocated outputs."""
+    """A workload's inputs resident on the device plus preallocated outputs.  Trial densities
+    are evaluated on the device (the same formulas as the host generator); `host` holds the
+    step's inputs in host memory (the trials copied back once, untimed) for the end-to-end
+    timing and the oracle."""
 
     def __init__(self, g, dev, resolved: bool = True):
         import torch
         from paper_2208_14639_gb300 import synth
         T = lambda a, dt=torch.float64: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dt)
-        rt, gt = synth.trial_densities(g.molecule, g.coords)
         self.g = g
         self.n = g.n
         self.n_atom = g.molecule.n_atom
-        self.P = rt.shape[0]
+        self.d = {"xyz": T(g.coords), "w": T(g.weights), "rho": T(g.rho), "grad": T(g.grad_rho),
+                  "atom": T(g.atom_of_point, torch.int32)}
+        self.d["rt"], self.d["gt"] = synth.trial_densities_torch(g.molecule, self.d["xyz"])
+        self.P = int(self.d["rt"].shape[0])
         self.host = {"xyz": g.coords, "w": g.weights, "rho": g.rho, "grad": g.grad_rho,
-                     "atom": g.atom_of_point.astype(np.int32), "rt": rt, "gt": gt}
-        self.d = {k: T(v, torch.int32 if k == "atom" else torch.float64) for k, v in self.host.items()}
+                     "atom": g.atom_of_point.astype(np.int32),
+                     "rt": self.d["rt"].cpu().numpy(), "gt": self.d["gt"].cpu().numpy()}
         f64 = dict(dtype=torch.float64, device=dev)
         self.out = {
             "vrho": torch.empty(self.n, **f64), "vgamma": torch.empty(self.n, **f64),
@@ -479,8 +491,18 @@ def time_e2e(vv, h, pb, prec, steps, warmup):
     return sec, nk, h2d, d2h
 
 
+def oracle_rows(args, rt, gt, rows):
+    """The oracle's whole path for a set of rows i (full j sums): potential, Hessian
+    contraction with every trial, point gradient."""
+    import oracle
+    oracle.potential(*args, rows=rows)
+    oracle.hessian_contract(*args, rt, gt, rows=rows)
+    oracle.point_grad(*args, rows=rows)
+
+
 def cpu_baseline(pb, budget_s: float):
-    """The FP64 oracle, as it stands, on a bounded row sample of the same workload."""
+    """The FP64 oracle, as it stands, on a bounded row sample of the same workload: each
+    sampled row runs the whole path over all j, so a row counts N_kept pairs."""
     import oracle
     g = pb.g
     args = (g.coords, g.weights, g.rho, g.grad_rho)
@@ -489,27 +511,49 @@ def cpu_baseline(pb, budget_s: float):
     cores = len(os.sched_getaffinity(0))
     oracle.set_num_threads(cores)
     # calibrate on a small sample, then size the sample to the budget
-    rows = kept[np.linspace(0, nk - 1, 64).astype(np.int64)]
+    rows = kept[np.linspace(0, nk - 1, 16).astype(np.int64)]
     t0 = time.perf_counter()
-    oracle.potential(*args, rows=rows)
-    oracle.hessian_contract(*args, pb.host["rt"], pb.host["gt"], rows=rows[:16])
-    oracle.point_grad(*args, rows=rows)
+    oracle_rows(args, pb.host["rt"], pb.host["gt"], rows)
     cal = time.perf_counter() - t0
-    scale = max(1.0, budget_s / max(cal, 1e-3))
-    n_rows = int(min(nk, 64 * scale))
-    n_hrows = int(min(nk, 16 * scale))
+    n_rows = int(min(nk, max(16, 16 * budget_s / max(cal, 1e-3))))
     rows = kept[np.linspace(0, nk - 1, n_rows).astype(np.int64)]
-    hrows = kept[np.linspace(0, nk - 1, n_hrows).astype(np.int64)]
     t0 = time.perf_counter()
-    oracle.potential(*args, rows=rows)
-    oracle.hessian_contract(*args, pb.host["rt"], pb.host["gt"], rows=hrows)
-    oracle.point_grad(*args, rows=rows)
+    oracle_rows(args, pb.host["rt"], pb.host["gt"], rows)
     sec = time.perf_counter() - t0
-    pairs = (2 * n_rows + n_hrows) * nk
-    return {"value": pairs / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": n_rows * nk / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
             "seconds": sec,
-            "sample": f"{n_rows} rows (energy/potential and point gradient) and {n_hrows} rows "
-                      f"(Hessian contraction, P={pb.P}) of {nk} kept points, full j sums"}
+            "sample": f"{n_rows} rows of {nk} kept points, each through the whole path "
+                      f"(potential, Hessian contraction with P={pb.P}, point gradient), full j sums"}
+
+
+def fp64_hessian_same_grid(vv, dev, prec):
+    """FP64 against mixed Hessian contraction on the water-hexamer grid (174,600 points,
+    P = 54): on the larger grids the FP64 contraction alone would take many minutes.  Each
+    call timed once after an untimed one; milliseconds and pairs per second."""
+    import torch
+    from paper_2208_14639_gb300 import synth
+    g = synth.config_water_hexamer()
+    pb = Problem(g, dev, resolved=False)
+    h = vv.vv10_create(dev.index or 0)
+    d, o = pb.d, pb.out
+    nk = vv.vv10_prepare_points(h, d["xyz"], d["w"], d["rho"], d["grad"], d["atom"], pb.n_atom)
+    out = {"workload": "water-hexamer-like cluster, 174,600 points, P=54", "n_kept": nk}
+    stream = torch.cuda.current_stream()
+    for name, p in (("mixed", prec), ("fp64", vv.VV10_FP64)):
+        vv.vv10_energy_potential(h, p, o["vrho"], o["vgamma"], want_energy=False)
+        vv.vv10_hessian_contract(h, p, d["rt"], d["gt"], o["frt"], o["fgt"])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        vv.vv10_hessian_contract(h, p, d["rt"], d["gt"], o["frt"], o["fgt"])
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        out[f"{name}_ms"] = ms
+        out[f"{name}_pair_evals_per_s"] = float(nk) * nk / (ms / 1e3)
+    out["speedup_mixed_vs_fp64"] = out["fp64_ms"] / out["mixed_ms"]
+    vv.vv10_destroy(h)
+    return out
 
 
 def gpu_arm(args):
@@ -530,6 +574,7 @@ def gpu_arm(args):
     h = vv.vv10_create(local)
     prec = vv.PRECISIONS[args.precision]
     peaks, peak_src = load_peaks()
+    large = pb.n > EXTRA_CALLS_MAX_POINTS
     # the step runs the Hessian after the energy: form A/B/C in the energy pass
     vv.vv10_set_options(h, vv.VV10_OPT_FUSE_HESSIAN_SUMS)
     if prec != vv.VV10_FP64:  # tile shapes tuned on first use, i.e. inside the warm-up steps
@@ -543,7 +588,9 @@ def gpu_arm(args):
     clocks = clk.summary()
     ms_max = max_over_ranks(ms, world)
     pairs_call = float(nk) * float(nk)
-    value = 3.0 * pairs_call * args.steps * world / (ms_max / 1e3)
+    # every quantity of the step is a sum over all N_kept^2 ordered pairs: value counts each
+    # pair once per step
+    value = pairs_call * args.steps * world / (ms_max / 1e3)
 
     K = args.steps
     per = {k: v[0] / K for k, v in prof.items()}
@@ -552,38 +599,28 @@ def gpu_arm(args):
     hess_flops = 8.0 * pairs_call * pb.P
     ms_ep, ms_hc = time_calls(vv, h, pb, prec, 3)
     ms_e = time_energy_only(vv, h, prec, 3)
-    ms_ch = time_coord_hessian(vv, h, pb, prec, 3)
-    pairs_ch = coord_hessian_pairs(pb)
-    # the calls beyond the step on grids whose host-side inputs stay small (the weight
-    # derivatives are 3 N_atom x N, the basis values and gradients 4 nbf x N doubles)
-    extras = pb.n <= EXTRA_CALLS_MAX_POINTS
-    if extras:
+    alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    breakdown = {
+        # the energy alone from the unordered pairs (vv10_energy; half the pair evaluations)
+        "energy_only_call_ms": ms_e,
+        "energy_only_pairs_per_s": pairs_call / (ms_e / 1e3),
+    }
+    if not large:  # the calls beyond the step, on grids whose host-side inputs stay small
+        ms_ch = time_coord_hessian(vv, h, pb, prec, 3)
+        pairs_ch = coord_hessian_pairs(pb)
         wdirs = pb.weight_dirs()
         P_w = int(wdirs.shape[0])
         ms_wr = time_weight_response(vv, h, pb, prec, wdirs, 3)
         ms_fock, ms_gt, nbf = time_ao_assembly(vv, h, pb, 3)
         ms_fa = time_fock_derivative(vv, h, pb, prec, wdirs, 3)
-    alu_peak_ops = N_SM * FP32_LANES_PER_SM * (clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    breakdown = {
-        # the two metric quantities, each timed as its own entry point (3 calls each)
-        "energy_potential_call_ms": ms_ep,
-        "energy_potential_pairs_per_s": pairs_call / (ms_ep / 1e3),
-        "energy_potential_alu_frac": ALU_OPS_PER_PAIR_EUW * pairs_call / (ms_ep / 1e3) / alu_peak_ops,
-        # the energy alone from the unordered pairs (vv10_energy; half the pair evaluations)
-        "energy_only_call_ms": ms_e,
-        "energy_only_pairs_per_s": pairs_call / (ms_e / 1e3),
-        "hessian_call_ms": ms_hc,
-        "hessian_pairs_per_s": pairs_call / (ms_hc / 1e3),
-        "hessian_P_pairs_per_s": pb.P * pairs_call / (ms_hc / 1e3),
-        "hessian_alg_tflops": hess_flops / (ms_hc / 1e3) / 1e12,
-        # the grid-grid nuclear Hessian block (not part of the step)
-        "coord_hessian_call_ms": ms_ch,
-        "coord_hessian_pairs": pairs_ch,
-        "coord_hessian_pairs_per_s": pairs_ch / (ms_ch / 1e3),
-        "coord_hessian_alu_frac": ALU_OPS_PER_PAIR_CH * pairs_ch / (ms_ch / 1e3) / alu_peak_ops,
-        **({
-            # AO-side assembly of the step's outputs (FP64 cuBLAS GEMM over the kept points;
-            # not part of the step): 2 nbf^2 flops per point and channel
+        breakdown.update({
+            # the grid-grid nuclear Hessian block (not part of the step)
+            "coord_hessian_call_ms": ms_ch,
+            "coord_hessian_pairs": pairs_ch,
+            "coord_hessian_pairs_per_s": pairs_ch / (ms_ch / 1e3),
+            "coord_hessian_alu_frac": ALU_OPS_PER_PAIR_CH * pairs_ch / (ms_ch / 1e3) / alu_peak_ops,
+            # AO-side assembly of the step's outputs (not part of the step): 2 nbf^2 flops per
+            # point and channel
             "ao_nbf": nbf,
             "fock_matrix_call_ms": ms_fock,
             "orbital_hessian_call_ms": ms_gt,
@@ -598,60 +635,74 @@ def gpu_arm(args):
             "weight_response_call_ms": ms_wr,
             "weight_response_pairs_per_s": pairs_call / (ms_wr / 1e3),
             **weight_response_roofline(prec, P_w, pairs_call, ms_wr, alu_peak_ops, peaks),
-        } if extras else {"calls_beyond_the_step": f"not timed above {EXTRA_CALLS_MAX_POINTS} points"}),
-        # the step's own phases
+        })
+    else:
+        breakdown["calls_beyond_the_step"] = f"not timed above {EXTRA_CALLS_MAX_POINTS} points"
+    breakdown.update({
         "step_pair_pass_pairs_per_s": pairs_call / (t_coord / 1e3) if t_coord else None,
         "phase_ms_per_step": {k: round(v, 4) for k, v in per.items() if v},
-        "note": "in the step one pass over the pairs (phase atom_resolved) forms the E/U/W and "
-                "A/B/C row sums, the atom-resolved terms and the point gradient; then the "
-                "contraction",
+        "note": "in the step one pass over the pairs forms the E/U/W and A/B/C row sums and the "
+                "point gradient (and, on the grids that keep them, the atom-resolved terms); "
+                "then the contraction",
+    })
+
+    # the metric's two quantities on their own (each its own entry point, 3 calls each)
+    parts = {
+        "energy_potential": {
+            "pair_evals_per_s": pairs_call / (ms_ep / 1e3), "ms_per_call": ms_ep,
+            "alu_frac": ALU_OPS_PER_PAIR_EUW * pairs_call / (ms_ep / 1e3) / alu_peak_ops},
+        "hessian_contraction": {
+            "pair_evals_per_s": pairs_call / (ms_hc / 1e3), "ms_per_call": ms_hc,
+            "P": pb.P, "P_pair_evals_per_s": pb.P * pairs_call / (ms_hc / 1e3),
+            "alg_tflops": hess_flops / (ms_hc / 1e3) / 1e12},
+        "counting": "ordered pairs sum N_kept^2 per call, independent of the kernels' "
+                    "symmetry shortcuts",
     }
 
     # roofline of the dominant kernel
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     dom = max(per, key=per.get)
-    roof = None
+    roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "kernel": dom}
     if dom == "contraction_tensor_core":
         t = per[dom] / 1e3
-        # trial groups of at most 192 (the contraction's default width) and their padded width
         groups = -(-pb.P // 192)
         ppad = max(32, 32 * -(-(-(-pb.P // groups)) // 32))
+        f16 = prec == vv.VV10_MIXED_F16X3
+        kernel = "k_hess_f16" if f16 else "k_hess_tc"
+        # the dense peak of the operand type: FP16 = the measured bf16 rate (same MMA rate);
+        # TF32 = half of it (the nominal ratio).  The contraction runs for seconds inside a
+        # long step: the sustained figure.
+        key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
+        peak = peaks[key] * (1.0 if f16 else 0.5) * 1e12
+        t_tensor = 3 * 8.0 * pairs_call * ppad * groups / peak
         ops_pair = tc_alu_ops_per_pair(ppad) * groups
-        tf32_peak = peaks["bf16_tflops"] * 0.5 * 1e12  # nominal tf32 : bf16 = 1 : 2
-        t_tensor = 3 * 8.0 * pairs_call * ppad * groups / tf32_peak
         alu_peak = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
-        t_alu = ops_pair * pairs_call / alu_peak
-        if t_alu >= t_tensor:
-            roof = {"bound": "alu", "achieved": ops_pair * pairs_call / t / 1e12,
-                    "peak": alu_peak / 1e12, "unit": "TFLOP/s (FP32 ops)",
-                    "frac": t_alu / t, "traffic": None, "kernel": "k_hess_tc",
-                    "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median under load)",
-                    "tensor_alt": {"achieved_alg_tflops": hess_flops / t / 1e12,
-                                   "tf32_peak_tflops": tf32_peak / 1e12,
-                                   "frac_of_split_peak": t_tensor / t}}
-        else:
-            roof = {"bound": "tensor", "achieved": hess_flops / t / 1e12, "peak": tf32_peak / 1e12,
-                    "unit": "TFLOP/s", "frac": hess_flops / t / tf32_peak,
-                    "traffic": PROFILED_TRAFFIC.get(("k_hess_tc", args.workload)),
-                    "kernel": "k_hess_tc",
-                    "peak_source": f"{peak_src} bf16 {peaks['bf16_tflops']} x 0.5 (tf32 dense)",
-                    "issued_mma_frac": t_tensor / t,
-                    "alu_alt": {"frac": t_alu / t, "ops_per_pair": ops_pair}}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "kernel": dom}
+        roof = {"bound": "tensor", "achieved": hess_flops / t / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": hess_flops / t / peak,
+                "traffic": PROFILED_TRAFFIC.get((kernel, args.workload)),
+                "kernel": kernel,
+                "peak_source": f"{peak_src} {key} {peaks[key]} x {1.0 if f16 else 0.5} "
+                               f"({'fp16' if f16 else 'tf32'} dense)",
+                "counting": "achieved = 8 P N_kept^2 algorithmic flops per launch / CUDA-event "
+                            "time; the 3-product split issues 3 x 8 Ppad N_kept^2",
+                "issued_mma_frac": t_tensor / t,
+                "alu_alt": {"frac": ops_pair * pairs_call / t / alu_peak, "ops_per_pair": ops_pair}}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions"
-                 if prec != vv.VV10_FP64 else "f64",
+        "dtype": DTYPES.get(args.precision, "f64"),
         "data": "synthetic (seeded molecule-shaped grids, Gaussian densities, analytic trials)",
         "config": {"workload": label, "n_points": pb.n, "n_kept": nk, "P": pb.P,
-                   "precision": args.precision, "pairs_per_call": pairs_call,
+                   "precision": args.precision, "pairs_per_step": pairs_call,
+                   "value_counts": "N_kept^2 ordered pairs per step: one pass of the whole path "
+                                   "(energy, potential, Hessian contraction with P trials, "
+                                   "point gradient) over every pair",
                    "l2": f"inputs larger than L2 ({pb.input_bytes() / 1e6:.0f} MB resident)",
                    "parallelism": f"replica x{world}"},
+        "metric_parts": parts,
         "roofline": roof,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -662,29 +713,37 @@ def gpu_arm(args):
 
     if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
         vv.vv10_set_autotune(h, 0)  # FP64 baseline at its default shapes
-        ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
-        per64 = {k: v[0] for k, v in prof64.items()}
-        ms_ep64, ms_hc64 = time_calls(vv, h, pb, vv.VV10_FP64, 1)
-        ms_ch64 = time_coord_hessian(vv, h, pb, vv.VV10_FP64, 1)
-        ms_wr64 = time_weight_response(vv, h, pb, vv.VV10_FP64, wdirs, 1) if extras else None
-        result["fp64"] = {
-            "value": 3.0 * pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
-            "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
-            "energy_potential_pairs_per_s": pairs_call / (ms_ep64 / 1e3),
-            "hessian_pairs_per_s": pairs_call / (ms_hc64 / 1e3),
-            "coord_hessian_pairs_per_s": pairs_ch / (ms_ch64 / 1e3),
-            "weight_response_pairs_per_s": pairs_call / (ms_wr64 / 1e3) if extras else None,
-            "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
-        }
-        result["speedup_mixed_vs_fp64_energy_potential"] = ms_ep64 / ms_ep
-        result["speedup_mixed_vs_fp64_hessian"] = ms_hc64 / ms_hc
-        result["speedup_mixed_vs_fp64_coord_hessian"] = ms_ch64 / ms_ch
-        if extras:
-            result["speedup_mixed_vs_fp64_weight_response"] = ms_wr64 / ms_wr
-        result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
+        if not large:
+            ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
+            per64 = {k: v[0] for k, v in prof64.items()}
+            ms_ep64, ms_hc64 = time_calls(vv, h, pb, vv.VV10_FP64, 1)
+            result["fp64"] = {
+                "value": pairs_call / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1, "warmup": 1,
+                "energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
+                "phase_ms": {k: round(v, 3) for k, v in per64.items() if v},
+            }
+            result["speedup_mixed_vs_fp64"] = value / world / result["fp64"]["value"]
+            parts["hessian_contraction"]["fp64_pair_evals_per_s"] = pairs_call / (ms_hc64 / 1e3)
+            parts["hessian_contraction"]["speedup_vs_fp64"] = ms_hc64 / ms_hc
+        else:
+            # the FP64 energy/potential call on this grid (one call); the FP64 contraction on
+            # the water-hexamer grid, mixed beside it
+            o = pb.out
+            vv.vv10_prepare_points(h, pb.d["xyz"], pb.d["w"], pb.d["rho"], pb.d["grad"], pb.d["atom"],
+                                   pb.n_atom)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e64 = vv.vv10_energy_potential(h, vv.VV10_FP64, o["vrho"], o["vgamma"], want_energy=True)
+            ms_ep64 = (time.perf_counter() - t0) * 1e3
+            result["fp64"] = {"energy": e64, "abs_energy_diff_mixed_vs_fp64": abs(e_mixed - e64),
+                              "energy_potential_ms": ms_ep64,
+                              "hessian_contraction_same_grid": fp64_hessian_same_grid(vv, dev, prec)}
+        parts["energy_potential"]["fp64_pair_evals_per_s"] = pairs_call / (ms_ep64 / 1e3)
+        parts["energy_potential"]["speedup_vs_fp64"] = ms_ep64 / ms_ep
 
-    sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, K, 1)
-    result["e2e"] = {"value": 3.0 * pairs_call * K / sec, "unit": UNIT,
+    e2e_steps = K if not large else max(1, min(K, 3))
+    sec, nk_e, h2d, d2h = time_e2e(vv, h, pb, prec, e2e_steps, 1)
+    result["e2e"] = {"value": pairs_call * e2e_steps / sec, "unit": UNIT, "steps": e2e_steps,
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1024,32 +1083,22 @@ def reference_arm(args):
     nk = kept.size
     cores = len(os.sched_getaffinity(0))
     oracle.set_num_threads(cores)
-    # each step: a bounded row sample of the same three calls (about 20 s per step)
-    rows = kept[np.linspace(0, nk - 1, 64).astype(np.int64)]
+    # each step: a bounded row sample, every row through the whole path (about 20 s per step)
+    rows = kept[np.linspace(0, nk - 1, 16).astype(np.int64)]
     t0 = time.perf_counter()
-    oracle.potential(*argsg, rows=rows)
-    oracle.hessian_contract(*argsg, rt, gt, rows=rows[:16])
-    oracle.point_grad(*argsg, rows=rows)
-    scale = max(1.0, min(20.0, 120.0 / (args.steps + args.warmup)) / max(time.perf_counter() - t0, 1e-3))
-    n_rows, n_hrows = int(min(nk, 64 * scale)), int(min(nk, 16 * scale))
+    oracle_rows(argsg, rt, gt, rows)
+    per_step = min(20.0, 120.0 / (args.steps + args.warmup))
+    n_rows = int(min(nk, max(16, 16 * per_step / max(time.perf_counter() - t0, 1e-3))))
     rows = kept[np.linspace(0, nk - 1, n_rows).astype(np.int64)]
-    hrows = kept[np.linspace(0, nk - 1, n_hrows).astype(np.int64)]
-
-    def step():
-        oracle.potential(*argsg, rows=rows)
-        oracle.hessian_contract(*argsg, rt, gt, rows=hrows)
-        oracle.point_grad(*argsg, rows=rows)
-
     for _ in range(args.warmup):
-        step()
+        oracle_rows(argsg, rt, gt, rows)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        oracle_rows(argsg, rt, gt, rows)
     sec = time.perf_counter() - t0
-    pairs = (2 * n_rows + n_hrows) * nk * args.steps
-    value = pairs / sec
-    sample = (f"{n_rows} rows (energy/potential, point gradient) and {n_hrows} rows (Hessian, "
-              f"P={rt.shape[0]}) of {nk} kept points per step, full j sums")
+    value = n_rows * nk * args.steps / sec
+    sample = (f"{n_rows} rows of {nk} kept points per step, each through the whole path "
+              f"(potential, Hessian contraction with P={rt.shape[0]}, point gradient), full j sums")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
@@ -1069,8 +1118,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("hexamer", "water", "cluster24", "chon60", "batch"),
-                    default="hexamer")
-    ap.add_argument("--precision", choices=("mixed", "tf32x3", "fp64"), default="mixed")
+                    default="chon60")
+    ap.add_argument("--precision", choices=("f16x3", "mixed", "tf32x3", "fp64"), default="f16x3")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

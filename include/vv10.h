@@ -49,7 +49,17 @@ typedef enum {
     VV10_MIXED_TF32X3 = 1,  /* FP32 pair tiles; Hessian contraction on tensor cores as split
                                TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate; FP64 point
                                precompute and FP64 cross-tile / final reductions            */
-    VV10_MIXED_BF16X3 = 2   /* as above with split BF16 operands for the contraction         */
+    VV10_MIXED_BF16X3 = 2,  /* as above with split BF16 operands for the contraction; not
+                               built for the contraction (UNSUPPORTED there): a two-piece
+                               bf16 split keeps ~16 bits, above the 1e-6 tolerance, and a
+                               three-piece split costs as many MMAs as split TF32.  Split
+                               TF32 or split FP16 stands in for it.                          */
+    VV10_MIXED_F16X3 = 3    /* FP32 pair tiles; Hessian contraction on tensor cores as split
+                               FP16 (hi*hi + hi*lo + lo*hi, K = 16 per MMA: half the MMA
+                               instructions of split TF32) with FP32 accumulate; every
+                               operand scaled by an exact power of two into FP16's range
+                               (per trial column; per row and 16-j stage for the kernel
+                               tiles); elsewhere as VV10_MIXED_TF32X3                       */
 } vv10_precision;
 
 /* VV10 parameters b and C (Sec. II.A) and the density cutoff below which a point is
@@ -279,17 +289,46 @@ vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
                                  const double* U_w, const double* W_w, const double* EUW_gr,
                                  double* FA, void* stream);
 
+/* The VV10 nuclear Hessian, all nine terms of Sec. II.B Eq. E_hess, a = 3 A + c:
+ *   E^{ab} = E_GG + E_ww + E_grgr + E_Gw + E_Gw^T + E_Ggr + E_Ggr^T + E_wgr + E_wgr^T
+ * with, over the kept points,
+ *   E_GG  = sum w [f^rho rho^{ab} + f^gamma gamma^{ab} + rho^a f^{rho,b} + gamma^a f^{gamma,b}]
+ *   E_ww  = sum w^{ab} rho (beta + E) + sum w^a rho E^{bw},   E_wgr = sum w^a rho E^{b,gr}
+ *   E_Gw  = sum w^b (f^rho rho^a + f^gamma gamma^a) + sum w rho^a [E^{bw} + rho (kappa' U^{bw}
+ *           + omega_rho W^{bw})] + sum w gamma^a rho omega_gamma W^{bw}
+ *   E_Ggr = the same two sums with E/U/W^{b,gr} in place of E/U/W^{bw}
+ *   E_grgr = E^{AB}_{gr,gr} (vv10_coord_hessian)
+ * gamma^a = 2 grad rho . grad rho^a and gamma^{ab} = 2 (grad rho^a . grad rho^b + grad rho .
+ * grad rho^{ab}) are full derivatives.  Every pair sum comes from this library in precision
+ * `prec` (the energy call, the Hessian contraction with the trials (rho^a, grad rho^a), the
+ * weight-derivative sums along w^a, the atom-resolved sums and the grid-grid blocks), the
+ * local derivatives kappa', omega_rho, omega_gamma from the prepared points; the assembly
+ * runs in FP64 with per-block partials summed in a fixed order.
+ *   rho_a, grad_rho_a     P x n, P x n x 3: the density's nuclear derivatives at the grid
+ *                         points moving with their atoms (P = 3 n_atom, caller order)
+ *   rho_ab, grad_rho_ab   P x P x n, P x P x n x 3: their second derivatives
+ *   w_a, w_ab             P x n, P x P x n: the quadrature weights' derivatives
+ *   H                     P x P device out
+ * Needs atom_of_point at prepare time.  Replaces the row sums cached by the last energy call
+ * with those of `prec`.  Errors: INVALID_ARG, UNSUPPORTED (3 n_atom > VV10_MAX_TRIALS), OOM,
+ * CUDA, TIMEOUT. */
+vv10_status vv10_nuclear_hessian(vv10_handle h, vv10_precision prec, const double* rho_a,
+                                 const double* grad_rho_a, const double* rho_ab,
+                                 const double* grad_rho_ab, const double* w_a, const double* w_ab,
+                                 double* H, void* stream);
+
 /* dE/dw_i = rho_i (beta + E_i) (the integrand of E^A_w, Sec. II.A) from the E_i cached
  * by the last vv10_energy_potential call.  dEdw: n device out. */
 vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
 
 /* Energy and potential for callers that cannot allocate device memory (the paper has no
- * counterpart).  Some callers are not allowed to call cudaMalloc at all: code recorded
- * into a CUDA graph, runtimes that grab (nearly) all device memory up front for their own
- * allocator, or plug-ins that are only ever handed buffers.  This entry point gives them
- * the same E, f^rho and f^gamma as vv10_energy_potential (same pair-sum kernel) without a
- * handle and without allocating: its scratch is one static device array of about 11 MB
- * that every GPU which loads this library holds until the process exits.
+ * counterpart).  Some callers may not call cudaMalloc at all: a host whose runtime took
+ * (nearly) all device memory up front for its own allocator, or a plug-in that is only
+ * ever handed buffers and has no allocator to call.  This entry point gives them the same
+ * E, f^rho and f^gamma as vv10_energy_potential (same pair-sum kernel) without a handle and
+ * without allocating: its scratch is one static device array of about 11 MB that every GPU
+ * which loads this library holds until the process exits, which caps n at
+ * VV10_NOALLOC_MAX_POINTS.
  *   n                  number of points, 1 <= n <= VV10_NOALLOC_MAX_POINTS
  *   xyz, w, rho, grad_rho   as for vv10_prepare_points (device pointers, FP64)
  *   prm, prec          as for vv10_prepare_points / vv10_energy_potential
@@ -298,12 +337,14 @@ vv10_status vv10_weight_grad(vv10_handle h, double* dEdw, void* stream);
  * It runs on the calling thread's current device and does not synchronise.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress, with that
  * device current): make that first call before any stream capture.  Every call shares
- * the one array and leaves its contents behind; calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialised by the caller.  Points
- * below rho_cut take part in no sum and get zero outputs, as elsewhere.
+ * the one array and leaves its contents behind (each call clears what it needs cleared);
+ * calls that overlap on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller.  Points below rho_cut take part in no sum and get zero
+ * outputs, as elsewhere.
  * Errors: INVALID_ARG (n < 1, bad pointer or parameter), UNSUPPORTED (n above the
- * maximum), CUDA.  Device-side conditions (non-finite values, a wait that gave up) are
- * not reported by this entry point. */
+ * maximum), CUDA.  Device-side failures are not returned (the call does not wait for the
+ * GPU): a non-finite input value or a bounded wait that gave up makes the call write NaN
+ * to *energy and to every vrho / vgamma value, so that no partial result passes as one. */
 #define VV10_NOALLOC_MAX_POINTS 32768
 vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xyz, const double* w,
                                           const double* rho, const double* grad_rho,

@@ -3,8 +3,7 @@
 Each .cu translation unit under csrc/ is compiled by nvcc in parallel, then linked into
 ``_build/libvv10_<arch>.so`` with the static CUDA runtime, so the library loads on a
 machine without a GPU driver (the driver is only needed once a CUDA call is made).  It links
-the toolkit's cuBLAS (for the FP64 GEMM of the AO-side assembly), found through an rpath to the
-toolkit's lib64.
+no other library: every kernel, the AO assembly's FP64 products included, is in csrc/.
 """
 from __future__ import annotations
 
@@ -70,9 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcublas",
-           "-Xlinker", f"-rpath={cuda_lib}"]
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

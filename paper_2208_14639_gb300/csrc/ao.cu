@@ -3,8 +3,9 @@
 //   M_mu_nu = sum_i w_i [s_i phi_mu phi_nu + 2 v_i . (phi_nu grad phi_mu + phi_mu grad phi_nu)]
 // with (s, v) = (f^rho, f^gamma grad rho) for F and (f^{rho,t}, f^{gamma,t} grad rho +
 // f^gamma grad rho^t) for G^t.  With Z_i,mu = w_i (s_i phi_i,mu / 2 + 2 v_i . grad phi_i,mu),
-// M = Phi^T Z + Z^T Phi: a plain FP64 GEMM over the kept points (cuBLAS; the channels of a
-// chunk side by side as the columns of one product), then the symmetrisation.
+// M = Phi^T Z + Z^T Phi: a plain FP64 GEMM over the kept points (this library's own split-K
+// kernel, gemm_f64.cu; the channels of a chunk side by side as the columns of one product),
+// then the symmetrisation.
 //
 // The nuclear derivative of the Fock matrix (Sec. II.B, F^a = F^a_G + F^a_gr + F^a_w, a = 3 A + c)
 // regroups the same terms in two parts.  (1) The terms whose basis products are not
@@ -21,8 +22,6 @@
 // and F^a += X + X^T.  K^c over the points of one atom is one GEMM over that atom's contiguous
 // range of kept points (the kept order groups the points by atom), the two factors of each
 // point side by side as two consecutive columns.
-#include <cublas_v2.h>
-
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -159,6 +158,16 @@ __global__ void k_fa_basis(int32_t nbf, int32_t A, const int32_t* __restrict__ b
 
 }  // namespace
 
+// Split-K scratch of the largest product an assembly makes: nbf x (chunk nbf) results per
+// split, at most ~4 CTAs per SM of 64 x 64 tiles, and never fewer than 64 splits of the
+// nbf x nbf products of the basis-function derivatives.
+size_t ao_gemm_work_elems(int32_t nbf, int64_t chunk, int n_sm) {
+    const size_t nn = static_cast<size_t>(nbf) * nbf;
+    const size_t big = nn * static_cast<size_t>(chunk) * static_cast<size_t>(gemm_abt_splits(nbf, static_cast<int>(chunk * nbf), int64_t(1) << 40, n_sm));
+    const size_t small = nn * 64;
+    return big > small ? big : small;
+}
+
 int64_t ao_channels_per_chunk(int64_t nk, int32_t nbf, int32_t n_ch, size_t max_bytes) {
     const size_t per = sizeof(double) * static_cast<size_t>(nk > 0 ? nk : 1) * static_cast<size_t>(nbf);
     int64_t c = static_cast<int64_t>(max_bytes / per);
@@ -168,29 +177,33 @@ int64_t ao_channels_per_chunk(int64_t nk, int32_t nbf, int32_t n_ch, size_t max_
 
 namespace {
 
+// Split count of one product, limited by the split-K scratch (work_elems doubles).
+int ao_splits(int M, int N, int64_t K, int n_sm, size_t work_elems) {
+    int s = gemm_abt_splits(M, N, K, n_sm);
+    const size_t per = static_cast<size_t>(M) * static_cast<size_t>(N);
+    const int cap = static_cast<int>(work_elems / (per > 0 ? per : 1));
+    return s < cap ? s : (cap > 0 ? cap : 1);
+}
+
 // The channel chunks of M = Phi^T Z + Z^T Phi: make_z(c0, nc) launches the kernel that writes Z
 // for channels c0 .. c0 + nc - 1; phik holds the gathered basis values.
 template <class MakeZ>
-cudaError_t assemble_chunks(const PointsDev& p, cublasHandle_t h, int32_t nbf, int32_t n_ch,
+cudaError_t assemble_chunks(const PointsDev& p, const AoGemm& g, int32_t nbf, int32_t n_ch,
                             int64_t chunk, const double* phik, double* Z, double* M, double* out,
-                            cudaStream_t st, int* blas_status, MakeZ make_z) {
+                            cudaStream_t st, MakeZ make_z) {
     const int64_t nn = static_cast<int64_t>(nbf) * nbf;
-    const double one = 1.0, zero = 0.0;
     for (int32_t c0 = 0; c0 < n_ch; c0 += static_cast<int32_t>(chunk)) {
         const int32_t nc = static_cast<int32_t>(n_ch - c0 < chunk ? n_ch - c0 : chunk);
         make_z(c0, nc);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        // one GEMM for the chunk: M (column-major nbf x nc nbf) = A B^T with A = phik viewed
-        // as nbf x nk and B = Z viewed as (nc nbf) x nk (both column-major); column c nbf + nu
-        // of M is column nu of M_c
-        const cublasStatus_t bs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nbf, nc * nbf,
-                                              static_cast<int>(p.nk), &one, phik, nbf, Z, nc * nbf,
-                                              &zero, M, nbf);
-        if (bs != CUBLAS_STATUS_SUCCESS) {
-            *blas_status = static_cast<int>(bs);
-            return cudaSuccess;
-        }
+        // one product for the chunk: M (column-major nbf x nc nbf) = A B^T with A = phik
+        // viewed as nbf x nk and B = Z viewed as (nc nbf) x nk (k slowest in both); column
+        // c nbf + nu of M is column nu of M_c
+        const int N = nc * nbf;
+        e = launch_gemm_abt(nbf, N, p.nk, phik, nbf, Z, N, M, nbf, g.work,
+                            ao_splits(nbf, N, p.nk, g.n_sm, g.work_elems), st);
+        if (e != cudaSuccess) return e;
         k_ao_sym<<<dim3(static_cast<unsigned>((nn + 255) / 256), static_cast<unsigned>(nc)), 256, 0, st>>>(
             nbf, M, out + c0 * nn);
         e = cudaGetLastError();
@@ -201,12 +214,11 @@ cudaError_t assemble_chunks(const PointsDev& p, cublasHandle_t h, int32_t nbf, i
 
 }  // namespace
 
-cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, const double* phi,
+cudaError_t launch_ao_assemble(const PointsDev& p, const AoGemm& g, int32_t nbf, const double* phi,
                                const double* dphi, int32_t n_ch, const double* s,
                                const double* fg, const double* vg, const double* gt,
                                int64_t chunk, double* phik, double* Z, double* M, double* out,
-                               cudaStream_t st, int* blas_status) {
-    *blas_status = 0;
+                               cudaStream_t st) {
     const int64_t nn = static_cast<int64_t>(nbf) * nbf;
     if (p.nk == 0) return cudaMemsetAsync(out, 0, sizeof(double) * nn * n_ch, st);
     const int64_t ne = p.nk * nbf;
@@ -214,23 +226,16 @@ cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, cons
     k_ao_gather<<<gx, 256, 0, st>>>(p, nbf, phi, phik);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cublasHandle_t h = static_cast<cublasHandle_t>(blas);
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) {
-        *blas_status = 1;
-        return cudaSuccess;
-    }
-    return assemble_chunks(p, h, nbf, n_ch, chunk, phik, Z, M, out, st, blas_status,
+    return assemble_chunks(p, g, nbf, n_ch, chunk, phik, Z, M, out, st,
                            [&](int32_t c0, int32_t nc) {
                                k_ao_z<<<dim3(gx, static_cast<unsigned>(nc)), 256, 0, st>>>(
                                    p, nbf, phi, dphi, s, fg, vg, gt, c0, Z);
                            });
 }
 
-cudaError_t launch_fock_derivative(const PointsDev& p, void* blas, const FockDerivIn& in,
+cudaError_t launch_fock_derivative(const PointsDev& p, const AoGemm& g, const FockDerivIn& in,
                                    const int64_t* seg, int64_t chunk, double* phik, double* Z,
-                                   double* M, double* LR, double* K2, double* out, cudaStream_t st,
-                                   int* blas_status) {
-    *blas_status = 0;
+                                   double* M, double* LR, double* K2, double* out, cudaStream_t st) {
     const int32_t nbf = in.nbf;
     const int32_t n_dir = 3 * p.n_atom;
     const int64_t nn = static_cast<int64_t>(nbf) * nbf;
@@ -241,17 +246,12 @@ cudaError_t launch_fock_derivative(const PointsDev& p, void* blas, const FockDer
     k_ao_gather<<<gx, 256, 0, st>>>(p, nbf, in.phi, phik);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cublasHandle_t h = static_cast<cublasHandle_t>(blas);
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) {
-        *blas_status = 1;
-        return cudaSuccess;
-    }
     // (1) the terms without derivatives of the basis functions (writes every out[a])
-    e = assemble_chunks(p, h, nbf, n_dir, chunk, phik, Z, M, out, st, blas_status,
+    e = assemble_chunks(p, g, nbf, n_dir, chunk, phik, Z, M, out, st,
                         [&](int32_t a0, int32_t nc) {
                             k_fa_z<<<dim3(gx, static_cast<unsigned>(nc)), 256, 0, st>>>(p, in, a0, Z);
                         });
-    if (e != cudaSuccess || *blas_status != 0) return e;
+    if (e != cudaSuccess) return e;
     // (2) the derivatives of the basis functions
     double* R = LR;
     double* L = LR + 2 * ne;
@@ -260,27 +260,19 @@ cudaError_t launch_fock_derivative(const PointsDev& p, void* blas, const FockDer
     k_fa_right<<<gx, 256, 0, st>>>(p, in, R);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const double one = 1.0, zero = 0.0;
     for (int c = 0; c < 3; ++c) {
         k_fa_left<<<gx, 256, 0, st>>>(p, in, c, L);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        cublasStatus_t bs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nbf, nbf,
-                                        static_cast<int>(2 * p.nk), &one, L, nbf, R, nbf, &zero,
-                                        Kall, nbf);
-        if (bs != CUBLAS_STATUS_SUCCESS) {
-            *blas_status = static_cast<int>(bs);
-            return cudaSuccess;
-        }
+        e = launch_gemm_abt(nbf, nbf, 2 * p.nk, L, nbf, R, nbf, Kall, nbf, g.work,
+                            ao_splits(nbf, nbf, 2 * p.nk, g.n_sm, g.work_elems), st);
+        if (e != cudaSuccess) return e;
         for (int32_t A = 0; A < p.n_atom; ++A) {
             const int64_t s0 = seg[A], na = seg[A + 1] - seg[A];
             if (na > 0) {
-                bs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nbf, nbf, static_cast<int>(2 * na),
-                                 &one, L + 2 * s0 * nbf, nbf, R + 2 * s0 * nbf, nbf, &zero, KA, nbf);
-                if (bs != CUBLAS_STATUS_SUCCESS) {
-                    *blas_status = static_cast<int>(bs);
-                    return cudaSuccess;
-                }
+                e = launch_gemm_abt(nbf, nbf, 2 * na, L + 2 * s0 * nbf, nbf, R + 2 * s0 * nbf, nbf,
+                                    KA, nbf, g.work, ao_splits(nbf, nbf, 2 * na, g.n_sm, g.work_elems), st);
+                if (e != cudaSuccess) return e;
             }
             k_fa_basis<<<gn, 256, 0, st>>>(nbf, A, in.bf_atom, Kall, na > 0 ? KA : nullptr,
                                           out + (3 * static_cast<int64_t>(A) + c) * nn);
@@ -289,18 +281,6 @@ cudaError_t launch_fock_derivative(const PointsDev& p, void* blas, const FockDer
         }
     }
     return cudaSuccess;
-}
-
-int ao_blas_create(void** blas) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return 1;
-    // the default (no atomics) keeps results bitwise reproducible
-    *blas = h;
-    return 0;
-}
-
-void ao_blas_destroy(void* blas) {
-    if (blas) cublasDestroy(static_cast<cublasHandle_t>(blas));
 }
 
 }  // namespace vv10

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aofa, &ngpart, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &tc16_bh, &tc16_bl, &tc16_small, &nhess, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aogw, &aofa, &ngpart, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -63,8 +63,6 @@ void vv10_ctx::release_all() {
     }
     if (h_pinned) cudaFreeHost(h_pinned);
     h_pinned = nullptr;
-    ao_blas_destroy(blas);
-    blas = nullptr;
     for (ProfRec& r : prof) {
         event_pool.push_back(r.a);
         event_pool.push_back(r.b);
@@ -411,13 +409,7 @@ vv10_status vv10_ctx::run_pairsum(int mode, bool fp64, cudaStream_t st, int* n_s
         cfg.stall = 1;
         debug_stall = 0;
     }
-    // normalise the split count the same way the launcher does
-    const int64_t ntile = P.nk_pad / kJTile;
-    int req = cfg.n_split < 1 ? 1 : cfg.n_split;
-    if (req > ntile) req = static_cast<int>(ntile > 0 ? ntile : 1);
-    const int64_t tps = ntile > 0 ? (ntile + req - 1) / req : 1;
-    const int ns = static_cast<int>(ntile > 0 ? (ntile + tps - 1) / tps : 1);
-    cfg.n_split = req;
+    const int ns = pairsum_split_count(P.nk_pad, cfg.n_split);  // the splits the launch uses
     VV10_TRY(ensure(part, sizeof(double) * nq * static_cast<size_t>(ns) * (P.nk_pad > 0 ? P.nk_pad : 1),
                     "pair-sum partials"));
     {
@@ -456,7 +448,7 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
     VV10_CHECK_HANDLE(h);
     h->set_error("");
     VV10_TRY(h->require_prepared());
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -584,6 +576,82 @@ vv10_status vv10_nuclear_gradient(vv10_handle h, int32_t P_dir, const double* rh
     return VV10_OK;
 }
 
+vv10_status vv10_nuclear_hessian(vv10_handle h, vv10_precision prec, const double* rho_a,
+                                 const double* grad_rho_a, const double* rho_ab,
+                                 const double* grad_rho_ab, const double* w_a, const double* w_ab,
+                                 double* H, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (!precision_known(prec)) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (h->P.n_atom < 1) {
+        h->set_error("the nuclear Hessian needs atom_of_point at prepare time");
+        return VV10_ERR_INVALID_ARG;
+    }
+    const int32_t np = 3 * h->P.n_atom;
+    if (np > VV10_MAX_TRIALS) {
+        h->set_error("3 n_atom must not exceed VV10_MAX_TRIALS");
+        return VV10_ERR_UNSUPPORTED;
+    }
+    VV10_TRY(h->bind());
+    const void* ptrs[] = {rho_a, grad_rho_a, rho_ab, grad_rho_ab, w_a, w_ab, H};
+    for (const void* q : ptrs)
+        if (!q || !device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+            h->set_error("every array must be an 8-byte aligned device pointer");
+            return VV10_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = h->P.n;
+    const size_t pn = static_cast<size_t>(np) * static_cast<size_t>(n > 0 ? n : 1);
+    const size_t na2 = static_cast<size_t>(h->P.n_atom) * h->P.n_atom * 9;
+    const size_t nparts = static_cast<size_t>(np) * np * nhess_blocks(h->P.nk);
+    // scratch: f^rho, f^gamma [n] | f^{rho,a}, f^{gamma,a}, E/U/W^{aw} [P][n] | E/U/W^{a,gr}
+    // [3][n][P] | E^{AB}_{gr,gr} | block partials
+    const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
+    const size_t total = 2 * nn + 5 * pn + 3 * pn + na2 + nparts;
+    VV10_TRY(h->ensure(h->nhess, sizeof(double) * total, "nuclear-Hessian scratch"));
+    double* base = static_cast<double*>(h->nhess.p);
+    double* vr = base;
+    double* vg = vr + nn;
+    double* fr = vg + nn;
+    double* fg = fr + pn;
+    double* Ew = fg + pn;
+    double* Uw = Ew + pn;
+    double* Ww = Uw + pn;
+    double* euw = Ww + pn;
+    double* Hgg = euw + 3 * pn;
+    double* part = Hgg + na2;
+    // the pair sums, each from this library's own entry point in the requested precision
+    VV10_TRY(vv10_energy_potential(h, prec, nullptr, vr, vg, stream));
+    VV10_TRY(vv10_hessian_contract(h, prec, np, rho_a, grad_rho_a, fr, fg, stream));
+    VV10_TRY(vv10_weight_response(h, prec, np, w_a, Ew, Uw, Ww, stream));
+    VV10_TRY(vv10_coord_grad(h, prec, nullptr, nullptr, euw, stream));
+    VV10_TRY(vv10_coord_hessian(h, prec, Hgg, nullptr, stream));
+    NucHessIn in;
+    in.P = np;
+    in.rho_a = rho_a;
+    in.grad_rho_a = grad_rho_a;
+    in.rho_ab = rho_ab;
+    in.grad_rho_ab = grad_rho_ab;
+    in.w_a = w_a;
+    in.w_ab = w_ab;
+    in.f_rho_a = fr;
+    in.f_gamma_a = fg;
+    in.E_w = Ew;
+    in.U_w = Uw;
+    in.W_w = Ww;
+    in.EUW_gr = euw;
+    in.vrho = vr;
+    in.vgamma = vg;
+    in.sumE = static_cast<const double*>(h->sumE.p);
+    PhaseScope ph(h, PH_NUCLEAR_GRADIENT, st, 2);
+    VV10_CUDA(h, launch_nuclear_hessian(h->P, in, Hgg, part, H, st), "nuclear Hessian assembly");
+    return VV10_OK;
+}
+
 vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P_trials,
                                   const double* rho_t, const double* grad_rho_t,
                                   double* f_rho_t, double* f_gamma_t, void* stream) {
@@ -598,7 +666,7 @@ vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P_
         h->set_error("P must be in [1, VV10_MAX_TRIALS]");
         return P_trials < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
     }
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -618,7 +686,7 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
     VV10_CHECK_HANDLE(h);
     h->set_error("");
     VV10_TRY(h->require_prepared());
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -679,7 +747,7 @@ vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grg
     VV10_CHECK_HANDLE(h);
     h->set_error("");
     VV10_TRY(h->require_prepared());
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -720,7 +788,7 @@ vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
     VV10_CHECK_HANDLE(h);
     h->set_error("");
     VV10_TRY(h->require_prepared());
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -777,7 +845,7 @@ vv10_status vv10_energy(vv10_handle h, vv10_precision prec, double* energy, void
     VV10_CHECK_HANDLE(h);
     h->set_error("");
     VV10_TRY(h->require_prepared());
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -824,26 +892,19 @@ static vv10_status ao_assemble(vv10_handle h, int32_t nbf, const double* phi, co
         return VV10_ERR_INVALID_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!h->blas && ao_blas_create(&h->blas) != 0) {
-        h->blas = nullptr;
-        h->set_error("cuBLAS handle creation failed");
-        return VV10_ERR_CUDA;
-    }
     const size_t nk = static_cast<size_t>(P.nk > 0 ? P.nk : 1);
     const int64_t chunk = ao_channels_per_chunk(P.nk, nbf, n_ch, size_t(1) << 30);
     VV10_TRY(h->ensure(h->aophik, sizeof(double) * nk * nbf, "gathered basis values"));
     VV10_TRY(h->ensure(h->aoz, sizeof(double) * nk * nbf * chunk, "assembly operand"));
     VV10_TRY(h->ensure(h->aom, sizeof(double) * static_cast<size_t>(nbf) * nbf * chunk, "assembly products"));
-    int bs = 0;
-    PhaseScope ph(h, PH_AO_ASSEMBLY, st, P.nk > 0 ? 1 + 2 * static_cast<int>((n_ch + chunk - 1) / chunk) : 0);
-    VV10_CUDA(h, launch_ao_assemble(P, h->blas, nbf, phi, dphi, n_ch, s, fg, vg, gt, chunk,
+    const size_t gw = ao_gemm_work_elems(nbf, chunk, h->n_sm);
+    VV10_TRY(h->ensure(h->aogw, sizeof(double) * gw, "assembly product partials"));
+    const AoGemm g{static_cast<double*>(h->aogw.p), gw, h->n_sm};
+    PhaseScope ph(h, PH_AO_ASSEMBLY, st, P.nk > 0 ? 1 + 4 * static_cast<int>((n_ch + chunk - 1) / chunk) : 0);
+    VV10_CUDA(h, launch_ao_assemble(P, g, nbf, phi, dphi, n_ch, s, fg, vg, gt, chunk,
                                     static_cast<double*>(h->aophik.p), static_cast<double*>(h->aoz.p),
-                                    static_cast<double*>(h->aom.p), out, st, &bs),
+                                    static_cast<double*>(h->aom.p), out, st),
               "AO assembly");
-    if (bs != 0) {
-        h->set_error("cuBLAS failed (status %d) in the AO assembly", bs);
-        return VV10_ERR_CUDA;
-    }
     return VV10_OK;
 }
 
@@ -912,11 +973,6 @@ vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
         h->set_error("vv10_fock_derivative reads the atom segments on the host and cannot be captured");
         return VV10_ERR_INVALID_ARG;
     }
-    if (!h->blas && ao_blas_create(&h->blas) != 0) {
-        h->blas = nullptr;
-        h->set_error("cuBLAS handle creation failed");
-        return VV10_ERR_CUDA;
-    }
     const int32_t n_dir = 3 * P.n_atom;
     const size_t nk = static_cast<size_t>(P.nk > 0 ? P.nk : 1);
     const size_t nn = static_cast<size_t>(nbf) * nbf;
@@ -925,6 +981,9 @@ vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
     VV10_TRY(h->ensure(h->aoz, sizeof(double) * nk * nbf * chunk, "assembly operand"));
     VV10_TRY(h->ensure(h->aom, sizeof(double) * nn * chunk, "assembly products"));
     VV10_TRY(h->ensure(h->aofa, sizeof(double) * (4 * nk * nbf + 2 * nn), "basis-derivative factors"));
+    const size_t gw = ao_gemm_work_elems(nbf, chunk, h->n_sm);
+    VV10_TRY(h->ensure(h->aogw, sizeof(double) * gw, "assembly product partials"));
+    const AoGemm g{static_cast<double*>(h->aogw.p), gw, h->n_sm};
     std::vector<int64_t> seg(static_cast<size_t>(P.n_atom) + 1);
     VV10_CUDA(h, cudaMemcpyAsync(seg.data(), P.seg, sizeof(int64_t) * seg.size(),
                                  cudaMemcpyDeviceToHost, st), "atom segments");
@@ -932,20 +991,18 @@ vv10_status vv10_fock_derivative(vv10_handle h, int32_t nbf, const double* phi,
     FockDerivIn in{nbf, phi, grad_phi, hess_phi, bf_atom, vrho, vgamma, f_rho_a, f_gamma_a,
                    grad_rho_a, w_a, E_w, U_w, W_w, EUW_gr};
     double* fa = static_cast<double*>(h->aofa.p);
+    // launches: gather, right factor, per chunk (Z, product, its split sum, symmetrisation),
+    // per direction c (left factor, product + split sum, per atom product + split sum and
+    // the basis-derivative update)
     const int n_launch =
-        P.nk > 0 ? 2 + 2 * static_cast<int>((n_dir + chunk - 1) / chunk) + 3 * (1 + P.n_atom) : 0;
-    int bs = 0;
+        P.nk > 0 ? 2 + 4 * static_cast<int>((n_dir + chunk - 1) / chunk) + 3 * (3 + 3 * P.n_atom) : 0;
     PhaseScope ph(h, PH_AO_ASSEMBLY, st, n_launch);
-    VV10_CUDA(h, launch_fock_derivative(P, h->blas, in, seg.data(), chunk,
+    VV10_CUDA(h, launch_fock_derivative(P, g, in, seg.data(), chunk,
                                         static_cast<double*>(h->aophik.p),
                                         static_cast<double*>(h->aoz.p),
                                         static_cast<double*>(h->aom.p), fa, fa + 4 * nk * nbf, FA,
-                                        st, &bs),
+                                        st),
               "nuclear derivative of the Fock matrix");
-    if (bs != 0) {
-        h->set_error("cuBLAS failed (status %d) in the nuclear derivative of the Fock matrix", bs);
-        return VV10_ERR_CUDA;
-    }
     return VV10_OK;
 }
 
@@ -1031,7 +1088,7 @@ vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
     VV10_CHECK_HANDLE(h);
     h->set_error("");
     VV10_TRY(h->require_prepared());
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3) {
+    if (!precision_known(prec)) {
         h->set_error("unknown precision %d", static_cast<int>(prec));
         return VV10_ERR_INVALID_ARG;
     }
@@ -1202,7 +1259,7 @@ vv10_status vv10_set_autotune(vv10_handle h, int flags) {
 vv10_status vv10_autotune(vv10_handle h, vv10_precision prec, int what, void* stream) {
     VV10_CHECK_HANDLE(h);
     h->set_error("");
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3)
+    if (!precision_known(prec))
         return VV10_ERR_INVALID_ARG;
     if (what & ~(VV10_TUNE_PAIRSUMS | VV10_TUNE_BATCH)) {
         h->set_error("vv10_autotune tunes VV10_TUNE_PAIRSUMS and VV10_TUNE_BATCH; the contraction "

@@ -620,7 +620,7 @@ vv10_status vv10_batch_energy_potential(vv10_handle h, vv10_precision prec, doub
         h->set_error("vv10_batch_prepare has not been called");
         return VV10_ERR_INVALID_ARG;
     }
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3)
+    if (!precision_known(prec))
         return VV10_ERR_INVALID_ARG;
     vv10_status s = h->bind();
     if (s != VV10_OK) return s;
@@ -644,6 +644,10 @@ vv10_status vv10_batch_hessian_contract(vv10_handle h, vv10_precision prec, cons
     }
     if (prec == VV10_MIXED_BF16X3) {
         h->set_error("the BF16x3 Hessian contraction is not available in this library");
+        return VV10_ERR_UNSUPPORTED;
+    }
+    if (prec == VV10_MIXED_F16X3) {
+        h->set_error("the batched contraction runs in FP64 or split TF32");
         return VV10_ERR_UNSUPPORTED;
     }
     if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3) return VV10_ERR_INVALID_ARG;
@@ -693,7 +697,7 @@ vv10_status vv10_batch_run(vv10_handle h, vv10_precision prec, const int32_t* P,
         h->set_error("energies / vrho / vgamma must be device pointers");
         return VV10_ERR_INVALID_ARG;
     }
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3)
+    if (!precision_known(prec))
         return VV10_ERR_INVALID_ARG;
     s = h->batch_ep(prec, energies, vrho, vgamma, true, st);  // A/B/C in the same pass
     if (s != VV10_OK) return s;

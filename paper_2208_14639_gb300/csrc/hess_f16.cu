@@ -1,0 +1,764 @@
+// K3 on tensor cores with FP16 operands: the pair part of Eq. frhot (Sec. II.B) as a product
+// of generated kernel tiles with the trial matrix, split FP16 (hi*hi + hi*lo + lo*hi) on
+// tcgen05 kind::f16 with FP32 accumulation (VV10_MIXED_F16X3).
+//
+// FP16 carries 11 significant bits, like TF32, but only 5 exponent bits, so every operand is
+// brought into its range by an exact power of two:
+//  * trials (B operand): one factor s_t per trial column t maps the column's largest |u'|,
+//    |c_y y'| into [2^14, 2^15) (u' = -3/2 u, y' = 3/2 y as for the TF32 kernel); c_y is one
+//    global power of two that balances y against u, and the kernel tiles that multiply y
+//    are divided by c_y instead;
+//  * kernel tiles (A operand): one factor r per row i and stage (32 j) maps the largest |T|
+//    of the row's two tiles in the stage into [2^14, 2^15).
+// A stage's accumulator then holds r_i s_t sum_j A_ij B_jt: the drain multiplies by 1/r_i
+// before its round-to-nearest FP32 register sum, the flush to FP64 by 1/s_t.  A value far
+// below its scale becomes subnormal and keeps an absolute error of at most 2^-25 of the scale
+// (2^-40 of the largest element sharing it); every other value is carried to ~22 bits as in
+// the TF32 split.  Per stage and output kind the MMA issues 12 instructions of K = 16 (four
+// K-steps: u and y of each 16-j half of the 128-byte trial rows; three products each), half
+// the instruction count of the TF32 split for the same j.
+//
+// Work unit: 128 rows i (TMEM lanes) x output kind (both kinds when Ppad <= 64) x the trials
+// of the launch (MMA N = Ppad).  The j range is cut into chunks whose trial tiles fit in L2;
+// the persistent CTAs walk the chunks in order and, inside a chunk, each CTA its fixed units
+// u = blockIdx.x + k gridDim.x, adding its FP32 register sums into the FP64 partial output at
+// the end of every unit-chunk.  All CTAs therefore stream the same chunk's trial tiles at
+// about the same time (they stay in L2 at any N), and every output row is updated by one
+// CTA only, in a fixed order (no atomics).
+//
+// 16 warps per CTA (4 per TMEM lane quadrant, 8 j each), every one of which, per stage:
+// evaluates its part of the two (or four) kernel tiles, exchanges the row maxima of the
+// stage with the quadrant's other warps through shared memory, scales, splits and stores
+// its operand columns into TMEM, then drains the previous stage's accumulator.  Two single
+// threads carry the other roles inside that loop, so that each warp keeps 128 registers
+// (four warps per SM sub-partition): lane 0 of warp 0 issues the stage's MMAs once every
+// warp's operands are in place, lane 0 of warp 1 keeps the ring of copies (j records by
+// 1-D bulk copy, the hi and lo trial tiles by 2-D tensor copies) kF16Ring - 1 stages ahead.
+// Every wait is bounded (kSpinCycles); a wait that gives up sets the TIMEOUT bit and an
+// abort flag that ends the other waits.
+#include <cstring>
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.hpp"
+#include "tc.cuh"
+
+namespace vv10 {
+
+constexpr int kF16Kj = 32;                      // j per stage
+constexpr int kF16Warps = 16;                   // every warp generates and drains
+constexpr int kF16ProducerWarp = 1;             // lane 0 also issues the copies
+constexpr int kF16MmaWarp = 0;                  // lane 0 also issues the MMAs; owns TMEM
+constexpr int kF16Threads = kF16Warps * 32;
+constexpr int kF16Ring = 4;                     // stages of trial tiles in flight
+constexpr int kF16MaxPpad = 192;
+constexpr uint32_t kF16TmemCols = 512;
+constexpr size_t kF16ChunkBytes = 48u << 20;    // trial-tile bytes of one j chunk (L2-resident)
+
+struct F16Layout {
+    uint32_t tile_bytes;  // one Ppad x 64-half trial tile (128-byte rows: 16 u, 16 y, 16 u, 16 y)
+    uint32_t slot_bytes;  // hi and lo tiles of one stage
+    uint32_t rec_off;     // j records, 1024 B per stage
+    uint32_t xm_off;      // row-maximum exchange [2][4 quads][NK][32 lanes][4 parts] floats
+    uint32_t bar_off;
+    uint32_t total;
+};
+__host__ __device__ inline F16Layout f16_layout(int ppad, int nk) {
+    F16Layout L;
+    L.tile_bytes = static_cast<uint32_t>(ppad) * 128u;
+    L.slot_bytes = 2u * L.tile_bytes;
+    L.rec_off = kF16Ring * L.slot_bytes;
+    L.xm_off = L.rec_off + kF16Ring * 1024u;
+    L.bar_off = L.xm_off + 2u * 4u * static_cast<uint32_t>(nk) * 32u * 16u;
+    L.total = L.bar_off + 512u + 1024u;  // barriers + slack for the 1024-B alignment
+    return L;
+}
+
+struct F16Args {
+    const float4* r32a;     // row records (x, y, z, c) and (omega, kappa, p, q)
+    const float4* r32b;
+    const float4* r32p;     // pair-packed column records
+    double* acc;            // [2][acc_P][nk_pad] FP64 partial output, zero on entry
+    const double* col_isc;  // [acc_P] 1/s_t per trial column
+    const float* params;    // [0] = 1/c_y
+    int64_t nk, nk_pad, acc_P;
+    int32_t Pn, t0;         // trials of this launch and the first one's row
+    int64_t n_units;
+    int32_t n_stage, chunk; // stages in all, stages per j chunk
+    int32_t flush;          // stages per FP64 flush inside a unit-chunk
+    int* err;
+};
+
+__device__ __forceinline__ bool f16_wait(uint64_t* bar, uint32_t parity, int* err,
+                                         volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kSpinCycles) {
+            atomicOr(err, DEVERR_TIMEOUT);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// The FP32 kernel tiles of two j at once against row i, from a pair-packed record
+// v0..v3 = {-x,-y}, {-z,om}, {ka,-p}, {-q,c} (two lanes each).  With inv = 1/(g g' s),
+// L = 1/s, G_i = 1/g, G_j = 1/g', M = 2/s^2 + 2/(g g'), nA = -rho a and rp = R^2 inv:
+//   T1c = inv (1 + nA_i (L+G_i) + nA_j (L+G_j) + nA_i nA_j M)   = T1 / (-3/2)
+//   T2c = rp (nA_i M + L + G_j)                                   = T2 / (+3/2)
+//   T3c = rp (nA_j M + L + G_i)                                   = T3 / (+3/2)
+//   T4c = rp R^2 M                                                = T4 / (-3/2)
+// (the factors -3/2, +3/2 travel with the trials).  NK = 2: t = {T1c, T2c, T3c, T4c};
+// NK = 1: the two tiles of output `kind`.
+struct RowF {
+    float x, y, z, om, ka, np, nq;  // row i values; np = -p_i, nq = -q_i
+};
+__device__ __forceinline__ float2 f16_dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 f16_lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 f16_hi2(float4 v) { return make_float2(v.z, v.w); }
+
+template <int NK>
+__device__ __forceinline__ void f16_tiles2(int kind, const RowF& r, const float4 v0,
+                                           const float4 v1, const float4 v2, const float4 v3,
+                                           float2 (&t)[2 * NK]) {
+    const float2 one = make_float2(1.0f, 1.0f), two = make_float2(2.0f, 2.0f);
+    const float2 dx = __fadd2_rn(f16_dup(r.x), f16_lo2(v0));
+    const float2 dy = __fadd2_rn(f16_dup(r.y), f16_hi2(v0));
+    const float2 dz = __fadd2_rn(f16_dup(r.z), f16_lo2(v1));
+    float2 r2 = __fmul2_rn(dx, dx);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dz, dz, r2);
+    const float2 g = __ffma2_rn(f16_dup(r.om), r2, f16_dup(r.ka));
+    const float2 gp = __ffma2_rn(f16_hi2(v1), r2, f16_lo2(v2));
+    const float2 s = __fadd2_rn(g, gp);
+    const float2 ggp = __fmul2_rn(g, gp);
+    const float2 den = __fmul2_rn(ggp, s);
+    float2 inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.x) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.y) : "f"(den.y));
+    const float2 L = __fmul2_rn(ggp, inv);
+    const float2 sinv = __fmul2_rn(s, inv);  // 1/(g g')
+    const float2 Gi = __fmul2_rn(gp, sinv);
+    const float2 Gj = __fmul2_rn(g, sinv);
+    const float2 M = __fmul2_rn(two, __ffma2_rn(L, L, sinv));
+    const float2 nAi = __ffma2_rn(f16_dup(r.nq), r2, f16_dup(r.np));
+    const float2 nAj = __ffma2_rn(f16_lo2(v3), r2, f16_hi2(v2));
+    const float2 rp = __fmul2_rn(r2, inv);
+    const float2 LGi = __fadd2_rn(L, Gi), LGj = __fadd2_rn(L, Gj);
+    if (NK == 2 || kind == 0) {
+        float2 br = __ffma2_rn(nAi, LGi, one);
+        br = __ffma2_rn(nAj, LGj, br);
+        br = __ffma2_rn(__fmul2_rn(nAi, nAj), M, br);
+        t[0] = __fmul2_rn(inv, br);                       // T1c
+        t[1] = __fmul2_rn(rp, __ffma2_rn(nAi, M, LGj));   // T2c
+    }
+    if (NK == 2 || kind == 1) {
+        t[2 * NK - 2] = __fmul2_rn(rp, __ffma2_rn(nAj, M, LGi));  // T3c
+        t[2 * NK - 1] = __fmul2_rn(__fmul2_rn(rp, r2), M);        // T4c
+    }
+}
+
+// Power-of-two factor that maps a maximum m >= 0 into [2^14, 2^15), and its inverse (both
+// normal FP32 numbers: the exponent is clamped to [-126, 126]).
+__device__ __forceinline__ void f16_scale(float m, float& sc, float& isc) {
+    const int eb = static_cast<int>((__float_as_uint(m) >> 23) & 0xFFu);
+    int se = 141 - eb;
+    se = se > 126 ? 126 : (se < -126 ? -126 : se);
+    sc = __uint_as_float(static_cast<uint32_t>(se + 127) << 23);
+    isc = __uint_as_float(static_cast<uint32_t>(127 - se) << 23);
+}
+
+// Two scaled values -> packed FP16 hi and lo words (lower j in the low half).
+__device__ __forceinline__ void f16_split2(float2 x, float sc, uint32_t& hi, uint32_t& lo) {
+    x = __fmul2_rn(x, make_float2(sc, sc));
+    const __half2 h = __floats2half2_rn(x.x, x.y);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x.x - hf.x, x.y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ float f16_absmax4(float2 a, float2 b) {
+    return fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y)));
+}
+
+// TMEM column map.  NK = 1 (Ppad <= 192): accumulator buffer b at Ppad b, operand buffer b
+// (4 tiles x 16 columns) at 2 Ppad + 64 b.  NK = 2 (Ppad <= 64): accumulator (kind k, buffer
+// b) at Ppad (2k + b), operand buffer b (2 kinds x 4 tiles x 16 columns) at 4 Ppad + 128 b.
+// An operand tile holds the stage's 32 j as 16 columns of two FP16 each.
+template <int NK, int PPAD>
+__device__ __forceinline__ uint32_t f16_dcol(int kind, int b) {
+    return NK == 1 ? static_cast<uint32_t>(PPAD * b) : static_cast<uint32_t>(PPAD * (2 * kind + b));
+}
+template <int NK, int PPAD>
+__device__ __forceinline__ uint32_t f16_acol(int b) {
+    return NK == 1 ? static_cast<uint32_t>(2 * PPAD + 64 * b) : static_cast<uint32_t>(4 * PPAD + 128 * b);
+}
+
+// Position in the CTA's walk over (j chunk, unit, stage): every role advances the same cursor.
+struct F16Cursor {
+    int c, s, s0, s1;
+    int64_t u;
+    bool done;
+};
+__device__ __forceinline__ void f16_cursor_init(F16Cursor& k, const F16Args& a) {
+    k.c = 0;
+    k.u = blockIdx.x;
+    k.s0 = 0;
+    k.s1 = min(a.n_stage, a.chunk);
+    k.s = 0;
+    k.done = (k.u >= a.n_units) || (a.n_stage <= 0);
+}
+__device__ __forceinline__ void f16_cursor_next(F16Cursor& k, const F16Args& a) {
+    if (++k.s < k.s1) return;
+    k.u += gridDim.x;
+    if (k.u >= a.n_units) {
+        k.u = blockIdx.x;
+        ++k.c;
+        k.s0 = k.c * a.chunk;
+        if (k.s0 >= a.n_stage) {
+            k.done = true;
+            return;
+        }
+        k.s1 = min(a.n_stage, k.s0 + a.chunk);
+    }
+    k.s = k.s0;
+}
+
+template <int PQ, int NK>  // PQ accumulator columns per thread and kind (= Ppad / 4)
+__global__ void __launch_bounds__(kF16Threads, 1)
+k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
+           F16Args args) {
+    constexpr int PPAD = 4 * PQ;
+    static_assert(NK == 1 || PPAD <= 64, "two kinds per tile need Ppad <= 64");
+    static_assert(NK == 2 || 2 * PPAD + 128 <= static_cast<int>(kF16TmemCols), "TMEM columns");
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const F16Layout L = f16_layout(PPAD, NK);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    uint64_t* b_full = bars;                          // [kF16Ring]
+    uint64_t* b_empty = bars + kF16Ring;              // [kF16Ring]
+    uint64_t* a_full = bars + 2 * kF16Ring;           // [2]
+    uint64_t* mma_done = bars + 2 * kF16Ring + 2;     // [2]
+    uint64_t* xbar = bars + 2 * kF16Ring + 4;         // [2 slots][4 quads]
+    uint64_t* fin = bars + 2 * kF16Ring + 12;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kF16Ring + 13);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kF16Ring + 14);
+    float* xm = reinterpret_cast<float*>(smem + L.xm_off);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quad = warp & 3, part = warp >> 2;
+    const bool is_producer = (warp == kF16ProducerWarp && lane == 0);
+    const bool is_mma = (warp == kF16MmaWarp && lane == 0);
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kF16Ring; ++b) {
+            mbar_init(&b_full[b], 1);
+            mbar_init(&b_empty[b], kF16Warps);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&a_full[b], kF16Warps);
+            mbar_init(&mma_done[b], 1);
+        }
+        for (int b = 0; b < 8; ++b) mbar_init(&xbar[b], 4);  // one arrival per warp of a quad
+        mbar_init(fin, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == kF16MmaWarp) tc::tmem_alloc(tmem_slot, kF16TmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // ---------------------------------------------------------------- producer cursor
+    // (lane 0 of kF16ProducerWarp) keeps the ring kF16Ring - 1 stages ahead of the walk
+    F16Cursor pk;
+    f16_cursor_init(pk, args);
+    int p_slot = 0;
+    uint32_t p_ph = 0;
+    int64_t issued = 0;
+    bool ok = true;
+    auto produce = [&]() -> bool {  // issue the next stage's copies, if any
+        if (pk.done) return true;
+        if (!f16_wait(&b_empty[p_slot], p_ph ^ 1u, args.err, abort_flag)) return false;
+        uint8_t* base = smem + p_slot * L.slot_bytes;
+        uint8_t* rec = smem + L.rec_off + p_slot * 1024;
+        mbar_expect_tx(&b_full[p_slot], L.slot_bytes + 1024u);
+        bulk_g2s(rec, args.r32p + 2 * kF16Kj * static_cast<int64_t>(pk.s), 1024u, &b_full[p_slot]);
+        tc::tma_load_2d(base, &tm_bh, 64 * pk.s, args.t0, &b_full[p_slot]);
+        tc::tma_load_2d(base + L.tile_bytes, &tm_bl, 64 * pk.s, args.t0, &b_full[p_slot]);
+        ++issued;
+        if (++p_slot == kF16Ring) {
+            p_slot = 0;
+            p_ph ^= 1u;
+        }
+        f16_cursor_next(pk, args);
+        return true;
+    };
+    if (is_producer) {
+        tc::prefetch_tmap(&tm_bh);
+        tc::prefetch_tmap(&tm_bl);
+        for (int k = 0; k < kF16Ring - 1 && ok; ++k) ok = produce();
+    }
+
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    const uint32_t idesc = tc::idesc_f16(128, PPAD);
+    const float inv_cy = args.params[0];
+    float acc[NK][PQ];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int c = 0; c < PQ; ++c) acc[k][c] = 0.0f;
+
+    // Drain a finished accumulator (every kind of the unit) into the FP32 registers, each
+    // value times the inverse row factor of its stage.
+    auto drain = [&](int db, uint32_t dphase, int kind0, const float (&iscp)[NK]) -> bool {
+        const bool got = f16_wait(&mma_done[db], dphase, args.err, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) return false;  // warp-uniform exit
+        tc::fence_after();
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const uint32_t col = tmem + lane_off + f16_dcol<NK, PPAD>(NK == 2 ? k : kind0, db) + part * PQ;
+            constexpr int kChunk = PQ % 16 == 0 ? 16 : 8;
+#pragma unroll
+            for (int c0 = 0; c0 < PQ; c0 += kChunk) {
+                uint32_t r[kChunk];
+#pragma unroll
+                for (int c = 0; c < kChunk; c += 8)
+                    tc::ld_x8(col + c0 + c, *reinterpret_cast<uint32_t(*)[8]>(&r[c]));
+                tc::wait_ld();
+#pragma unroll
+                for (int c = 0; c < kChunk; c += 2) {
+                    const float2 v = __ffma2_rn(make_float2(__uint_as_float(r[c]), __uint_as_float(r[c + 1])),
+                                                make_float2(iscp[k], iscp[k]),
+                                                make_float2(acc[k][c0 + c], acc[k][c0 + c + 1]));
+                    acc[k][c0 + c] = v.x;
+                    acc[k][c0 + c + 1] = v.y;
+                }
+            }
+        }
+        tc::fence_before();
+        return true;
+    };
+    // Add the registers into the FP64 partial output (times 1/s_t; the gamma accumulator
+    // holds -(T3 u + T4 y)) and clear them.
+    auto flush = [&](int kind0, int64_t i) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const int kind = NK == 2 ? k : kind0;
+#pragma unroll
+            for (int c = 0; c < PQ; ++c) {
+                const int t = part * PQ + c;
+                if (i < args.nk && t < args.Pn) {
+                    const int64_t tg = static_cast<int64_t>(args.t0) + t;
+                    double* o = args.acc + ((static_cast<int64_t>(kind) * args.acc_P + tg) * args.nk_pad + i);
+                    const double v = static_cast<double>(acc[k][c]) * args.col_isc[tg];
+                    *o += (kind == 0) ? v : -v;
+                }
+                acc[k][c] = 0.0f;
+            }
+        }
+    };
+
+    int slot = 0, ab = 0;
+    uint32_t ph = 0, aph = 0;
+    int pslot = 0, dbuf = 0;
+    uint32_t dph = 0;
+    uint32_t gs = 0;  // stages walked by this CTA (exchange slot and phase)
+    bool mma_any = false;
+    float isc_prev[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) isc_prev[k] = 1.0f;
+    F16Cursor wk;
+    f16_cursor_init(wk, args);
+    ok = __all_sync(0xffffffffu, ok);
+    while (!wk.done && ok) {
+        // ---- one unit-chunk: rows of `row_tile`, stages [s0, s1)
+        const int64_t row_tile = NK == 2 ? wk.u : (wk.u >> 1);
+        const int kind0 = NK == 2 ? 0 : static_cast<int>(wk.u & 1);
+        const int64_t i = row_tile * 128 + quad * 32 + lane;
+        const int s0 = wk.s0, s1 = wk.s1;
+        float xi = 0.f, yi = 0.f, zi = 0.f, oi = 1.f, ki = 1.f, pi_ = 0.f, qi = 0.f;
+        if (i < args.nk) {
+            const float4 a = args.r32a[i];
+            const float4 b = args.r32b[i];
+            xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y; pi_ = b.z; qi = b.w;
+        }
+        const RowF rc{xi, yi, zi, oi, ki, -pi_, -qi};
+        int until_flush = args.flush;
+        for (int s = s0; s < s1; ++s) {
+            // the operand buffer ab is free once the MMAs of the stage two back are done
+            bool got = f16_wait(&b_full[slot], ph, args.err, abort_flag);
+            got = got && f16_wait(&mma_done[ab], aph ^ 1u, args.err, abort_flag);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after();
+            // this warp's 8 j: pair-packed records 4 part .. 4 part + 3
+            const float4* rec = reinterpret_cast<const float4*>(smem + L.rec_off + slot * 1024);
+            float2 t[4][2 * NK];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float4* v = rec + 4 * (4 * part + h);
+                f16_tiles2<NK>(kind0, rc, v[0], v[1], v[2], v[3], t[h]);
+#pragma unroll
+                for (int k = 0; k < NK; ++k)  // the tiles that multiply y carry 1/c_y
+                    t[h][2 * k + 1] = __fmul2_rn(t[h][2 * k + 1], make_float2(inv_cy, inv_cy));
+            }
+            // the row's largest |T| over the stage: this thread's 4 j, then the quad's 4 parts
+            const int xs = static_cast<int>(gs & 1u);
+            float* xrow = xm + (static_cast<size_t>((xs * 4 + quad) * NK) * 32 + lane) * 4;
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+                xrow[k * 32 * 4 + part] = fmaxf(fmaxf(f16_absmax4(t[0][2 * k], t[1][2 * k]),
+                                                      f16_absmax4(t[2][2 * k], t[3][2 * k])),
+                                                fmaxf(f16_absmax4(t[0][2 * k + 1], t[1][2 * k + 1]),
+                                                      f16_absmax4(t[2][2 * k + 1], t[3][2 * k + 1])));
+            __syncwarp();  // the warp's 32 stores are ordered before lane 0's release
+            if (lane == 0) mbar_arrive(&xbar[xs * 4 + quad]);
+            got = f16_wait(&xbar[xs * 4 + quad], (gs >> 1) & 1u, args.err, abort_flag);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            float sc[NK], isc[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const float4 q = *reinterpret_cast<const float4*>(xrow + k * 32 * 4);
+                f16_scale(fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)), sc[k], isc[k]);
+            }
+            // scaled FP16 hi / lo operand tiles of kind k: [hi Ta | lo Ta | hi Tb | lo Tb], 16
+            // columns each; this warp's 8 j are columns 4 part .. 4 part + 3
+            const uint32_t a = tmem + lane_off + f16_acol<NK, PPAD>(ab) + 4 * part;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) f16_split2(t[h][2 * k + b], sc[k], hw[h], lw[h]);
+                    tc::st_x4(a + 64u * k + 32u * b, hw);
+                    tc::st_x4(a + 64u * k + 32u * b + 16u, lw);
+                }
+            }
+            tc::wait_st();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[ab]);  // this warp's operands are in place
+            // ---- MMA issue (one thread): this stage, once every warp's operands are in place
+            if (is_mma) {
+                bool go = f16_wait(&a_full[ab], aph, args.err, abort_flag);
+                go = go && f16_wait(&b_full[slot], ph, args.err, abort_flag);
+                if (go) {
+                    tc::fence_after();
+                    const uint32_t base = smem_u32(smem + slot * L.slot_bytes);
+                    const uint64_t bh = tc::sdesc_kmajor_sw128(base);
+                    const uint64_t bl = tc::sdesc_kmajor_sw128(base + L.tile_bytes);
+                    // trial rows: [u (16 j) | y (16 j)] for the stage's two halves, 32 B each;
+                    // a K-step moves the descriptor's address field by 32 B (2 units)
+#pragma unroll
+                    for (int k = 0; k < NK; ++k) {
+                        const uint32_t d = tmem + f16_dcol<NK, PPAD>(NK == 2 ? k : kind0, ab);
+                        const uint32_t aa = tmem + f16_acol<NK, PPAD>(ab) + 64u * k;
+                        // operand tiles: Ta hi | Ta lo | Tb hi | Tb lo, 16 columns each (8 per
+                        // 16-j half).  The small products first (the accumulator truncates its
+                        // adds), the four hi*hi last.
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const uint64_t ku = 4u * hh, ky = 4u * hh + 2u;
+                            tc::mma_f16_ts(d, aa + 0 + 8 * hh, bl + ku, idesc, hh);   // Ta_hi u_lo
+                            tc::mma_f16_ts(d, aa + 16 + 8 * hh, bh + ku, idesc, 1u);  // Ta_lo u_hi
+                            tc::mma_f16_ts(d, aa + 32 + 8 * hh, bl + ky, idesc, 1u);  // Tb_hi y_lo
+                            tc::mma_f16_ts(d, aa + 48 + 8 * hh, bh + ky, idesc, 1u);  // Tb_lo y_hi
+                        }
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const uint64_t ku = 4u * hh, ky = 4u * hh + 2u;
+                            tc::mma_f16_ts(d, aa + 0 + 8 * hh, bh + ku, idesc, 1u);   // Ta_hi u_hi
+                            tc::mma_f16_ts(d, aa + 32 + 8 * hh, bh + ky, idesc, 1u);  // Tb_hi y_hi
+                        }
+                    }
+                    tc::commit(&mma_done[ab]);  // the ring slot is released after the drains
+                    mma_any = true;
+                }
+            }
+            if (!__all_sync(0xffffffffu, !*abort_flag)) {
+                ok = false;
+                break;
+            }
+            // ---- drain the previous stage while this stage's MMAs run; then one more copy
+            // (one per drained stage: the ring slot it fills was drained a stage earlier)
+            if (s > s0) {
+                if (!drain(dbuf, dph, kind0, isc_prev)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) mbar_arrive(&b_empty[pslot]);
+                if (--until_flush == 0) {
+                    flush(kind0, i);
+                    until_flush = args.flush;
+                }
+                if (is_producer && !produce()) *abort_flag = 1;
+                if (!__all_sync(0xffffffffu, !*abort_flag)) {
+                    ok = false;
+                    break;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NK; ++k) isc_prev[k] = isc[k];
+            dbuf = ab;
+            dph = aph;
+            pslot = slot;
+            if (++slot == kF16Ring) {
+                slot = 0;
+                ph ^= 1u;
+            }
+            ab ^= 1;
+            if (ab == 0) aph ^= 1u;
+            ++gs;
+        }
+        if (!ok) break;
+        if (!drain(dbuf, dph, kind0, isc_prev)) {
+            ok = false;
+            break;
+        }
+        if (lane == 0) mbar_arrive(&b_empty[pslot]);
+        if (is_producer && !produce()) *abort_flag = 1;
+        flush(kind0, i);
+        if (!__all_sync(0xffffffffu, !*abort_flag)) break;
+        // next unit-chunk
+        wk.s = s1 - 1;
+        f16_cursor_next(wk, args);
+    }
+    tc::wait_st();  // nothing of ours is in flight to TMEM on any exit path
+    tc::wait_ld();
+    if (is_producer)  // copies in flight must land before the CTA exits
+        for (int64_t k = (issued > kF16Ring ? issued - kF16Ring : 0); k < issued; ++k)
+            mbar_wait(&b_full[k % kF16Ring], static_cast<uint32_t>((k / kF16Ring) & 1), args.err);
+    if (is_mma && mma_any) {  // every MMA finished before TMEM is released
+        tc::commit(fin);
+        mbar_wait(fin, 0, args.err);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == kF16MmaWarp) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kF16TmemCols);
+    }
+}
+
+// ---------------------------------------------------------------- trial split
+
+// Per trial column, the largest |u'| and |y'| (u' = -3/2 u, y' = 3/2 y, in FP32) as bit
+// patterns (non-negative floats order like unsigned integers); colmax zeroed before.
+__global__ void __launch_bounds__(256)
+k_f16_colmax(const double* __restrict__ u, const double* __restrict__ y, int64_t nk_pad,
+             unsigned int* __restrict__ colmax, int32_t P) {
+    const int t = blockIdx.y;
+    const double* ut = u + static_cast<int64_t>(t) * nk_pad;
+    const double* yt = y + static_cast<int64_t>(t) * nk_pad;
+    float mu = 0.f, my = 0.f;
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < nk_pad;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        mu = fmaxf(mu, fabsf(static_cast<float>(-1.5 * ut[j])));
+        my = fmaxf(my, fabsf(static_cast<float>(1.5 * yt[j])));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&colmax[t], __float_as_uint(mu));
+        atomicMax(&colmax[P + t], __float_as_uint(my));
+    }
+}
+
+// c_y (a power of two near max|u'| / max|y'| over all trials, clamped to 2^[-24, 24]) and the
+// column factors s_t (the column's max(|u'|, c_y |y'|) mapped into [2^14, 2^15)).
+// params[0] = 1/c_y, params[1] = c_y; scale[t] = s_t; col_isc[t] = 1/s_t.
+__global__ void __launch_bounds__(256)
+k_f16_scales(const unsigned int* __restrict__ colmax, int32_t P, float* __restrict__ params,
+             float* __restrict__ scale, double* __restrict__ col_isc) {
+    __shared__ float su[8], sy[8];
+    __shared__ float s_cy;
+    float mu = 0.f, my = 0.f;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        mu = fmaxf(mu, __uint_as_float(colmax[t]));
+        my = fmaxf(my, __uint_as_float(colmax[P + t]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        su[threadIdx.x >> 5] = mu;
+        sy[threadIdx.x >> 5] = my;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (blockDim.x >> 5); ++w) {
+            mu = fmaxf(mu, su[w]);
+            my = fmaxf(my, sy[w]);
+        }
+        int e = 0;
+        if (mu > 0.f && my > 0.f && isfinite(mu) && isfinite(my)) {
+            e = static_cast<int>((__float_as_uint(mu) >> 23) & 0xFFu) -
+                static_cast<int>((__float_as_uint(my) >> 23) & 0xFFu);
+            e = e > 24 ? 24 : (e < -24 ? -24 : e);
+        }
+        s_cy = ldexpf(1.0f, e);
+        params[0] = ldexpf(1.0f, -e);
+        params[1] = s_cy;
+    }
+    __syncthreads();
+    const float cy = s_cy;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        float sc, isc;
+        f16_scale(fmaxf(__uint_as_float(colmax[t]), cy * __uint_as_float(colmax[P + t])), sc, isc);
+        scale[t] = sc;
+        col_isc[t] = static_cast<double>(isc);
+    }
+}
+
+// FP16 hi / lo trial tiles: row t, stage s holds 32 halves, u' s_t for the stage's 16 j
+// then c_y y' s_t; rows t >= P are zero.
+__global__ void __launch_bounds__(256)
+k_f16_split(const double* __restrict__ u, const double* __restrict__ y, int32_t P,
+            int64_t nk_pad, const float* __restrict__ params, const float* __restrict__ scale,
+            __half* __restrict__ bh, __half* __restrict__ bl) {
+    const int t = blockIdx.y;
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= nk_pad) return;
+    float a = 0.f, b = 0.f;
+    if (t < P) {
+        const int64_t o = static_cast<int64_t>(t) * nk_pad + j;
+        const float st = scale[t];
+        a = static_cast<float>(-1.5 * u[o]) * st;            // exact power-of-two scalings
+        b = static_cast<float>(1.5 * y[o]) * (params[1] * st);
+    }
+    const __half ah = __float2half_rn(a), bhh = __float2half_rn(b);
+    const __half al = __float2half_rn(a - __half2float(ah)), bll = __float2half_rn(b - __half2float(bhh));
+    const int64_t off = static_cast<int64_t>(t) * (2 * nk_pad) + (j >> 4) * 32 + (j & 15);
+    bh[off] = ah;
+    bh[off + 16] = bhh;
+    bl[off] = al;
+    bl[off + 16] = bll;
+}
+
+cudaError_t launch_f16_trial_split(const double* u, const double* y, int32_t P, int32_t rows,
+                                   int64_t nk_pad, unsigned int* colmax, float* params,
+                                   float* scale, double* col_isc, void* bh, void* bl,
+                                   cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * 2 * static_cast<size_t>(P), st);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = (nk_pad + 255) / 256;
+    dim3 g1(static_cast<unsigned>(nb < 16 ? nb : 16), static_cast<unsigned>(P));
+    k_f16_colmax<<<g1, 256, 0, st>>>(u, y, nk_pad, colmax, P);
+    k_f16_scales<<<1, 256, 0, st>>>(colmax, P, params, scale, col_isc);
+    dim3 g2(static_cast<unsigned>(nb), static_cast<unsigned>(rows));
+    k_f16_split<<<g2, 256, 0, st>>>(u, y, P, nk_pad, params, scale, static_cast<__half*>(bh),
+                                    static_cast<__half*>(bl));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 f16_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D map over a [rows][2 nk_pad] FP16 array, box = 64 halves (one stage: 16 u, 16 y, 16 u,
+// 16 y) x ppad trials, 128-B swizzle.
+static bool f16_make_map(CUtensorMap* m, const void* base, int64_t nk_pad, int64_t rows, int ppad) {
+    auto fn = f16_encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(2 * nk_pad), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(2 * nk_pad) * sizeof(__half)};
+    cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(ppad)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int PQ, int NK>
+static cudaError_t launch_f16_t(const CUtensorMap* maps, const F16Args& a, int n_sm, cudaStream_t st) {
+    const F16Layout L = f16_layout(4 * PQ, NK);
+    cudaError_t e = cudaFuncSetAttribute(k_hess_f16<PQ, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(L.total));
+    if (e != cudaSuccess) return e;
+    const int grid = static_cast<int>(a.n_units < n_sm ? a.n_units : n_sm);
+    if (grid <= 0) return cudaSuccess;
+    k_hess_f16<PQ, NK><<<grid, kF16Threads, L.total, st>>>(maps[0], maps[1], a);
+    return cudaGetLastError();
+}
+
+int hess_f16_kinds_per_tile(int ppad) { return ppad <= 64 ? 2 : 1; }
+
+// Contract the trials [t0, t0 + Pn) (Pn <= 192) of one system; the split arrays have `rows`
+// rows; col_isc and params as written by launch_f16_trial_split.
+cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
+                            const void* bh, const void* bl, int64_t rows, const double* col_isc,
+                            const float* params, int n_sm, int flush, double* acc, int* err,
+                            cudaStream_t st) {
+    if (p.nk == 0) return cudaSuccess;
+    const int ppad = hess_tc_ppad(Pn);
+    if (ppad > kF16MaxPpad || t0 + ppad > rows) return cudaErrorInvalidValue;
+    CUtensorMap maps[2];
+    if (!f16_make_map(&maps[0], bh, p.nk_pad, rows, ppad) || !f16_make_map(&maps[1], bl, p.nk_pad, rows, ppad))
+        return cudaErrorInvalidValue;
+    const int nk_t = hess_f16_kinds_per_tile(ppad);
+    F16Args a;
+    a.r32a = p.r32a;
+    a.r32b = p.r32b;
+    a.r32p = p.r32p;
+    a.acc = acc;
+    a.col_isc = col_isc;
+    a.params = params;
+    a.nk = p.nk;
+    a.nk_pad = p.nk_pad;
+    a.acc_P = acc_P;
+    a.Pn = Pn;
+    a.t0 = t0;
+    a.n_units = (nk_t == 2 ? 1 : 2) * ((p.nk + 127) / 128);
+    a.n_stage = static_cast<int32_t>(p.nk_pad / kF16Kj);
+    const size_t stage_bytes = 2u * static_cast<size_t>(ppad) * 128u + 1024u;
+    int64_t chunk = static_cast<int64_t>(kF16ChunkBytes / stage_bytes);
+    if (chunk < 64) chunk = 64;
+    a.chunk = static_cast<int32_t>(chunk < a.n_stage ? chunk : a.n_stage);
+    a.flush = flush > 0 ? flush : 512;
+    a.err = err;
+    switch (ppad / 4) {
+        case 8: return launch_f16_t<8, 2>(maps, a, n_sm, st);
+        case 16: return launch_f16_t<16, 2>(maps, a, n_sm, st);
+        case 24: return launch_f16_t<24, 1>(maps, a, n_sm, st);
+        case 32: return launch_f16_t<32, 1>(maps, a, n_sm, st);
+        case 40: return launch_f16_t<40, 1>(maps, a, n_sm, st);
+        case 48: return launch_f16_t<48, 1>(maps, a, n_sm, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vv10

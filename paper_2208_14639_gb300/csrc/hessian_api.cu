@@ -91,8 +91,12 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
     if (!fp64) {
         // tensor-core path: trials in groups of at most `cap` (<= 192, the MMA N of one launch)
         int cap = tc_cap_for(Pn, P.nk);
-        if (autotune & VV10_TUNE_CONTRACTION) H_TRY(tune_tc_cap(Pn, st, &cap));
-        H_TRY(tc_contract(Pn, cap, st));
+        if (prec == VV10_MIXED_F16X3) {
+            H_TRY(f16_contract(Pn, cap, st));
+        } else {
+            if (autotune & VV10_TUNE_CONTRACTION) H_TRY(tune_tc_cap(Pn, st, &cap));
+            H_TRY(tc_contract(Pn, cap, st));
+        }
         tc_cap_last = cap;
         PhaseScope ph2(this, PH_HESS_EPILOGUE, st, 1);
         H_CUDA(launch_hess_epilogue(P, Pn, static_cast<double*>(hacc.p), 1, P.nk_pad,
@@ -159,6 +163,47 @@ vv10_status vv10_ctx::tc_contract(int32_t Pn, int cap, cudaStream_t st) {
                               static_cast<float*>(tc_yl.p), rows, n_sm, tc_flush,
                               static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
                "tensor-core contraction");
+    }
+    return VV10_OK;
+}
+
+// Split u, y (in tu, ty) into scaled FP16 hi / lo tiles and contract all Pn trials on the
+// tensor cores (kind::f16) in groups of at most `cap` trials into hacc [2][Pn][nk_pad].
+vv10_status vv10_ctx::f16_contract(int32_t Pn, int cap, cudaStream_t st) {
+    const int ng = (Pn + cap - 1) / cap;
+    const int pg = (Pn + ng - 1) / ng;
+    const int ppad = hess_tc_ppad(pg);
+    const int64_t rows = static_cast<int64_t>(ng - 1) * pg + ppad;
+    const size_t sb = 2 * sizeof(uint16_t) * static_cast<size_t>(rows) * P.nk_pad;
+    H_TRY(ensure(tc16_bh, sb, "FP16 trial tiles (hi)"));
+    H_TRY(ensure(tc16_bl, sb, "FP16 trial tiles (lo)"));
+    // colmax [2 Pn] words | params [4] floats | scale [Pn] floats | col_isc [Pn] doubles
+    const size_t o_par = ((2 * sizeof(unsigned int) * Pn + 15) / 16) * 16;
+    const size_t o_sc = o_par + 16;
+    const size_t o_isc = ((o_sc + sizeof(float) * Pn + 15) / 16) * 16;
+    H_TRY(ensure(tc16_small, o_isc + sizeof(double) * Pn, "FP16 trial factors"));
+    char* sm = static_cast<char*>(tc16_small.p);
+    float* params = reinterpret_cast<float*>(sm + o_par);
+    const double* col_isc = reinterpret_cast<const double*>(sm + o_isc);
+    {
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 3);
+        H_CUDA(launch_f16_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), Pn,
+                                      static_cast<int32_t>(rows), P.nk_pad,
+                                      reinterpret_cast<unsigned int*>(sm), params,
+                                      reinterpret_cast<float*>(sm + o_sc),
+                                      reinterpret_cast<double*>(sm + o_isc), tc16_bh.p, tc16_bl.p, st),
+               "FP16 trial split");
+    }
+    const size_t ab = sizeof(double) * 2 * static_cast<size_t>(Pn) * P.nk_pad;
+    H_TRY(ensure(hacc, ab, "contraction partials"));
+    H_CUDA(cudaMemsetAsync(hacc.p, 0, ab, st), "zero contraction partials");
+    PhaseScope ph(this, PH_CONTRACT_TC, st, ng);
+    for (int g = 0; g < ng; ++g) {
+        const int t0 = g * pg;
+        const int pn = (Pn - t0 < pg) ? Pn - t0 : pg;
+        H_CUDA(launch_hess_f16(P, pn, t0, Pn, tc16_bh.p, tc16_bl.p, rows, col_isc, params, n_sm,
+                               tc_flush, static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
+               "FP16 tensor-core contraction");
     }
     return VV10_OK;
 }

@@ -60,6 +60,10 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
                                    double4* r64a, double4* r64b, float4* r32a, float4* r32b,
                                    float4* r32p, cudaStream_t st);
 
+// Precisions the library knows (vv10_precision values); every mixed one runs the pair sums
+// in FP32 and differs only in the Hessian contraction's tensor-core operands.
+constexpr bool precision_known(int prec) { return prec >= 0 && prec <= 3; }
+
 // ---------------------------------------------------------------- pair sums (pairsum.cu)
 enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2, MODE_EUWABC = 3, MODE_EUWABCG = 4 };
 constexpr int kPairModes = 5;
@@ -71,7 +75,9 @@ struct PairLaunch {
     int n_split = 1;          // j-splits (partials reduced by the epilogue)
     int stall = 0;            // test hook: CTA (0,0) issues no copies, so its waits time out
 };
-// part: [nq][n_split][nk_pad] FP64 partial sums (quantity-major, nq = pair_mode_nq(mode)).
+// part: [nq][n_split][nk_pad] FP64 partial sums (quantity-major, nq = pair_mode_nq(mode)),
+// n_split = pairsum_split_count(nk_pad, cfg.n_split), the number of splits the launch uses.
+int pairsum_split_count(int64_t nk_pad, int requested_split);
 cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLaunch& cfg,
                            double* part, int* err, cudaStream_t st);
 int pairsum_default_split(const PointsDev& p, int mode, bool fp64, int rows_per_thread, int n_sm);
@@ -128,6 +134,22 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
                            const float* uh, const float* ul, const float* yh, const float* yl,
                            int64_t rows, int n_sm, int flush, double* acc, int* err,
                            cudaStream_t st);
+
+// Tensor-core split-FP16 contraction (hess_f16.cu).  launch_f16_trial_split turns u, y
+// (FP64 [P][nk_pad]) into scaled FP16 hi / lo tiles [rows][2 nk_pad] (per stage of 16 j: 16 u
+// then 16 y), the global y balance factor (params[0] = 1/c_y, params[1] = c_y) and per-trial
+// factors (scale[t] = s_t, col_isc[t] = 1/s_t; colmax: 2 P scratch words).  launch_hess_f16
+// contracts the trials [t0, t0 + Pn), Pn <= 192, into acc [2][acc_P][nk_pad] (zeroed by the
+// caller), already multiplied by 1/s_t.
+cudaError_t launch_f16_trial_split(const double* u, const double* y, int32_t P, int32_t rows,
+                                   int64_t nk_pad, unsigned int* colmax, float* params,
+                                   float* scale, double* col_isc, void* bh, void* bl,
+                                   cudaStream_t st);
+int hess_f16_kinds_per_tile(int ppad);
+cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
+                            const void* bh, const void* bl, int64_t rows, const double* col_isc,
+                            const float* params, int n_sm, int flush, double* acc, int* err,
+                            cudaStream_t st);
 
 // Batched tensor-core contraction (molecule and task tables in device memory; see
 // hess_tc.cu for the record layouts the fill helpers write).
@@ -206,16 +228,30 @@ int energy_half_grid(bool fp64, int n_sm);
 cudaError_t launch_energy_half(const PointsDev& p, bool fp64, int grid, double* cta_total,
                                double* energy, cudaStream_t st);
 
+// FP64 C = A B^T (gemm_f64.cu): A M x K, B N x K with k slowest (column k at A + k lda), C
+// M x N column-major; the K range split n_split ways (gemm_abt_splits), partials in work
+// (n_split x M x N doubles) summed in a fixed order.
+int gemm_abt_splits(int M, int N, int64_t K, int n_sm);
+cudaError_t launch_gemm_abt(int M, int N, int64_t K, const double* A, int64_t lda, const double* B,
+                            int64_t ldb, double* C, int64_t ldc, double* work, int n_split,
+                            cudaStream_t st);
+
 // AO-side assembly (Sec. II.A Fock matrix, Sec. II.B contracted orbital Hessian): out[c] =
 // M_c + M_c^T, M_c = Phi^T Z_c over the kept points, channels in chunks of `chunk`
-// (ao_channels_per_chunk).  blas: a cuBLAS handle (ao_blas_create).  Scratch: phik (nk x nbf),
-// Z (chunk x nk x nbf), M (chunk x nbf x nbf).  *blas_status != 0 reports a cuBLAS failure.
+// (ao_channels_per_chunk).  Scratch: phik (nk x nbf), Z (chunk x nk x nbf), M (chunk x nbf x
+// nbf) and the product's split-K partials (AoGemm: ao_gemm_work_elems doubles).
+struct AoGemm {
+    double* work;
+    size_t work_elems;
+    int n_sm;
+};
+size_t ao_gemm_work_elems(int32_t nbf, int64_t chunk, int n_sm);
 int64_t ao_channels_per_chunk(int64_t nk, int32_t nbf, int32_t n_ch, size_t max_bytes);
-cudaError_t launch_ao_assemble(const PointsDev& p, void* blas, int32_t nbf, const double* phi,
+cudaError_t launch_ao_assemble(const PointsDev& p, const AoGemm& g, int32_t nbf, const double* phi,
                                const double* dphi, int32_t n_ch, const double* s,
                                const double* fg, const double* vg, const double* gt,
                                int64_t chunk, double* phik, double* Z, double* M, double* out,
-                               cudaStream_t st, int* blas_status);
+                               cudaStream_t st);
 // Nuclear derivative of the Fock matrix (Sec. II.B) for the 3 n_atom directions a = 3 A + c:
 // caller-order inputs (direction arrays [a n + i], grad_rho_a [(a n + i) 3 + d], EUW_gr
 // [(q n + i) 3 n_atom + a]); seg = the host copy of the n_atom + 1 kept-point segment starts;
@@ -227,12 +263,9 @@ struct FockDerivIn {
     const double *vrho, *vgamma;      // n
     const double *f_rho_a, *f_gamma_a, *grad_rho_a, *w_a, *E_w, *U_w, *W_w, *EUW_gr;
 };
-cudaError_t launch_fock_derivative(const PointsDev& p, void* blas, const FockDerivIn& in,
+cudaError_t launch_fock_derivative(const PointsDev& p, const AoGemm& g, const FockDerivIn& in,
                                    const int64_t* seg, int64_t chunk, double* phik, double* Z,
-                                   double* M, double* LR, double* K2, double* out, cudaStream_t st,
-                                   int* blas_status);
-int ao_blas_create(void** blas);
-void ao_blas_destroy(void* blas);
+                                   double* M, double* LR, double* K2, double* out, cudaStream_t st);
 
 // E^A_G + E^A_w (Sec. II.A) for Pn directions from the cached row sums sE, sU, sW (kept
 // order); rt, gt (Pn x n, Pn x n x 3) and wt (Pn x n) in caller order, either pair may be
@@ -242,5 +275,31 @@ cudaError_t launch_nuclear_gradient(const PointsDev& p, const double* sE, const 
                                     const double* sW, int32_t Pn, const double* rt,
                                     const double* gt, const double* wt, double* partial,
                                     double* out, cudaStream_t st);
+
+// Inputs of the nine-term nuclear Hessian assembly (Sec. II.B, Eq. E_hess), P = 3 n_atom
+// directions a = 3 A + c, every array in caller point order unless stated:
+struct NucHessIn {
+    int32_t P;
+    const double* rho_a;        // [P][n]     rho^a at the points moving with their atoms
+    const double* grad_rho_a;   // [P][n][3]
+    const double* rho_ab;       // [P][P][n]  second derivatives
+    const double* grad_rho_ab;  // [P][P][n][3]
+    const double* w_a;          // [P][n]     weight derivatives
+    const double* w_ab;         // [P][P][n]
+    const double* f_rho_a;      // [P][n]     Hessian contraction with (rho^a, grad rho^a)
+    const double* f_gamma_a;    // [P][n]
+    const double* E_w;          // [P][n]     weight-derivative sums along w^a
+    const double* U_w;
+    const double* W_w;
+    const double* EUW_gr;       // [3][n][n_atom][3] atom-resolved sums
+    const double* vrho;         // [n] f^rho, f^gamma
+    const double* vgamma;
+    const double* sumE;         // [nk] row sums E_i (kept order)
+};
+// H (P x P, device) = the point sums of the integrand + Hgg (E^{AB}_{gr,gr}, n_atom x n_atom x
+// 3 x 3); partial: P^2 x nhess_blocks(nk) scratch.
+int nhess_blocks(int64_t nk);
+cudaError_t launch_nuclear_hessian(const PointsDev& p, const NucHessIn& in, const double* Hgg,
+                                   double* partial, double* H, cudaStream_t st);
 
 }  // namespace vv10

@@ -1,9 +1,11 @@
 // vv10_energy_potential_noalloc: the energy/potential path for callers that cannot
-// allocate device memory -- e.g. code running inside a CUDA-graph capture that must not
-// grow a pool, a host that gave all memory to another allocator (a JAX/XLA-style
-// preallocating runtime, a custom arena), or plugins that are only handed buffers.
+// allocate device memory -- a host that gave (nearly) all device memory to another
+// allocator up front (a preallocating array runtime, a custom arena), or a plug-in that is
+// only ever handed buffers and has no allocator of its own to call.
 // All of its scratch lives in the file-scope array below, which every GPU that loads
 // this library holds (about 11 MB) until the process exits; the call allocates nothing.
+// A device-side failure (a non-finite input, a bounded wait that gave up) leaves NaN in
+// the energy and in every potential value it writes, so it cannot pass for a result.
 //
 // It uses the same pair-sum kernel as vv10_energy_potential, but skips the compaction
 // step: every one of the n points is a row and a column, and points below the density
@@ -20,6 +22,9 @@ namespace vv10 {
 constexpr int64_t kNaMaxPoints = VV10_NOALLOC_MAX_POINTS;
 constexpr int kNaMaxSplit = 8;
 constexpr int64_t kNaPad = ((kNaMaxPoints + kJTile - 1) / kJTile) * kJTile;
+// The point and epilogue kernels run n_pad / 256 blocks of 256 threads and the energy has
+// n_pad / 256 block partials: whole blocks only while the j tile is a multiple of 256.
+static_assert(kJTile % 256 == 0, "n_pad must be a whole number of 256-thread blocks");
 
 // Scratch layout (bytes, every block 256-aligned):
 //   r64a, r64b   2 x 32 x kNaPad   FP64 pair records
@@ -85,10 +90,15 @@ k_na_points(int64_t n, int64_t n_pad, const double* __restrict__ xyz, const doub
             const double* __restrict__ rho, const double* __restrict__ grad, double b, double C,
             double rho_cut, const double* __restrict__ center, double4* __restrict__ r64a,
             double4* __restrict__ r64b, float4* __restrict__ r32a, float4* __restrict__ r32b,
-            double* __restrict__ soa, int64_t* __restrict__ orig) {
+            double* __restrict__ soa, int64_t* __restrict__ orig, int* __restrict__ err) {
     const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (p >= n_pad) return;
     double* f = soa;
+    if (p < n) {  // a non-finite input is an error, not a point below the cutoff
+        bool finite = isfinite(rho[p]) && isfinite(w[p]);
+        for (int d = 0; d < 3; ++d) finite = finite && isfinite(xyz[3 * p + d]) && isfinite(grad[3 * p + d]);
+        if (!finite) atomicOr(err, DEVERR_BAD_INPUT);
+    }
     const bool keep = p < n && rho[p] >= rho_cut;
     if (!keep) {
         const double x = p < n ? xyz[3 * p] : 0.0, y = p < n ? xyz[3 * p + 1] : 0.0,
@@ -130,13 +140,15 @@ k_na_points(int64_t n, int64_t n_pad, const double* __restrict__ xyz, const doub
     orig[p] = p;
 }
 
-// f^rho, f^gamma and energy block partials; rows below the cutoff get zeros.
+// f^rho, f^gamma and energy block partials; rows below the cutoff get zeros.  If an
+// earlier kernel of this call set the error word, every output is NaN instead.
 __global__ void __launch_bounds__(256)
 k_na_epilogue(int64_t n, int64_t n_pad, double beta, const double* __restrict__ part, int n_split,
-              const double* __restrict__ soa, double* __restrict__ vrho,
-              double* __restrict__ vgamma, double* __restrict__ eblk) {
+              const double* __restrict__ soa, const int* __restrict__ err,
+              double* __restrict__ vrho, double* __restrict__ vgamma, double* __restrict__ eblk) {
     __shared__ double sh[8];
     const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool failed = *err != 0;
     double ei = 0.0;
     if (p < n) {
         double e = 0.0, u = 0.0, wv = 0.0;
@@ -153,11 +165,12 @@ k_na_epilogue(int64_t n, int64_t n_pad, double beta, const double* __restrict__ 
             fg = r * soa[4 * n_pad + p] * wv;
             ei = soa[0 * n_pad + p] * r * (beta + 0.5 * e);
         }
+        if (failed) fr = fg = NAN;
         if (vrho) vrho[p] = fr;
         if (vgamma) vgamma[p] = fg;
     }
     const double s = block_sum(ei, sh);
-    if (threadIdx.x == 0) eblk[blockIdx.x] = s;
+    if (threadIdx.x == 0) eblk[blockIdx.x] = failed ? NAN : s;
 }
 
 // Per-device address of the scratch array, looked up once (with that device current).
@@ -199,7 +212,7 @@ extern "C" vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xy
                                                      void* stream) {
     if (n < 1) return VV10_ERR_INVALID_ARG;
     if (n > kNaMaxPoints) return VV10_ERR_UNSUPPORTED;
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_BF16X3)
+    if (!precision_known(prec))
         return VV10_ERR_INVALID_ARG;
     if (!(prm.b > 0.0) || !(prm.C >= 0.0) || !(prm.rho_cut > 0.0) || !std::isfinite(prm.b) ||
         !std::isfinite(prm.C) || !std::isfinite(prm.rho_cut))
@@ -246,7 +259,7 @@ extern "C" vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xy
     k_na_center<<<1, 1024, 0, st>>>(n, xyz, rho, prm.rho_cut, center);
     k_na_points<<<static_cast<unsigned>(n_pad / 256), 256, 0, st>>>(
         n, n_pad, xyz, w, rho, grad_rho, prm.b, prm.C, prm.rho_cut, center, r64a, r64b, r32a,
-        r32b, soa, orig);
+        r32b, soa, orig, err);
     PointsDev P;
     P.n = n;
     P.nk = n;
@@ -261,18 +274,16 @@ extern "C" vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xy
     cfg.rows_per_thread = fp64 ? 1 : 2;
     int ns = pairsum_default_split(P, MODE_EUW, fp64, cfg.rows_per_thread, n_sm);
     if (ns > kNaMaxSplit) ns = kNaMaxSplit;
-    // the launcher normalises the split count; recompute the count it will use
-    const int64_t ntile = n_pad / kJTile;
-    const int64_t tps = (ntile + ns - 1) / ns;
-    const int ns_used = static_cast<int>((ntile + tps - 1) / tps);
     cfg.n_split = ns;
+    const int ns_used = pairsum_split_count(n_pad, ns);  // the splits the launch uses
     e = launch_pairsum(P, MODE_EUW, fp64, cfg, part, err, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return VV10_ERR_CUDA;
     }
     const int nblk = static_cast<int>(n_pad / 256);
-    k_na_epilogue<<<nblk, 256, 0, st>>>(n, n_pad, P.beta, part, ns_used, soa, vrho, vgamma, eblk);
+    k_na_epilogue<<<nblk, 256, 0, st>>>(n, n_pad, P.beta, part, ns_used, soa, err, vrho, vgamma,
+                                        eblk);
     e = launch_sum_blocks(eblk, nblk, energy, st);
     if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
         cudaGetLastError();

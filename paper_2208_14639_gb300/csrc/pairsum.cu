@@ -158,6 +158,13 @@ static cudaError_t launch_mode(const PointsDev& p, bool fp64, const PairLaunch& 
     return launch_t<float, MODE, 1, 256>(p, p.r32a, p.r32b, cfg.n_split, cfg.stall, part, err, st);
 }
 
+int pairsum_split_count(int64_t nk_pad, int req) {
+    int64_t jps;
+    int ns;
+    split_geometry(nk_pad, req, jps, ns);
+    return ns;
+}
+
 cudaError_t launch_pairsum(const PointsDev& p, int mode, bool fp64, const PairLaunch& cfg,
                            double* part, int* err, cudaStream_t st) {
     if (p.nk == 0) return cudaSuccess;

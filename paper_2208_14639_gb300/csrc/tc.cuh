@@ -1,5 +1,6 @@
 // Thin inline-PTX wrappers for the sm_100-family tensor-core path: TMEM allocation,
-// tcgen05.mma (kind::tf32, A from tensor or shared memory, B from shared memory), commit, TMEM
+// tcgen05.mma (kind::tf32 and kind::f16, A from tensor or shared memory, B from shared
+// memory), commit, TMEM
 // loads/stores, tensor-map (TMA) loads and shared-memory matrix descriptors.
 #pragma once
 
@@ -45,6 +46,12 @@ __device__ __forceinline__ void st_x4(uint32_t taddr, const uint32_t (&r)[4]) {
                  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
                  : "memory");
 }
+// 2 consecutive 32-bit columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void st_x2(uint32_t taddr, uint32_t r0, uint32_t r1) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(r0),
+                 "r"(r1)
+                 : "memory");
+}
 // 8 consecutive 32-bit columns of this warp's 32 lanes.
 __device__ __forceinline__ void ld_x8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -77,12 +84,38 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
     d |= static_cast<uint64_t>(4) << 61;          // swizzle mode: 64 B
     return d;
 }
+// The same with the 128-byte swizzle: rows of 128 B (64 halves), 8-row atoms of 1024 B.  A
+// K-step inside a row advances the start address by its byte offset (16-byte units).
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1) << 16;          // leading-dimension offset (unused here)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;  // stride-dimension offset: 8 rows * 128 B
+    d |= static_cast<uint64_t>(1) << 46;          // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;          // swizzle mode: 128 B
+    return d;
+}
 // Instruction descriptor: D FP32, A and B TF32, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
            (static_cast<uint32_t>(m >> 4) << 24);
 }
 
+// Instruction descriptor: D FP32, A and B FP16, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+    return (1u << 4) | (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
+// D[tmem] (+)= A[tmem] * B[smem desc]^T with FP16 operands (K = 16 per instruction; A holds
+// two consecutive K elements per 32-bit TMEM column, the lower K in the low half), issued
+// by one thread.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // D[tmem] (+)= A[tmem] * B[smem desc]^T, issued by one thread.
 __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
                                             uint32_t idesc, uint32_t accumulate) {

@@ -133,6 +133,8 @@ struct vv10_ctx {
     // Hessian scratch
     vv10::DevBuf tu, ty, trt, tgt, hacc;
     vv10::DevBuf tc_uh, tc_ul, tc_yh, tc_yl;
+    vv10::DevBuf tc16_bh, tc16_bl;  // split-FP16 trial tiles [rows][2 nk_pad]
+    vv10::DevBuf tc16_small;        // their column maxima, factors and y balance
 
     // coordinate scratch
     vv10::DevBuf gk;
@@ -141,9 +143,10 @@ struct vv10_ctx {
     vv10::DevBuf wsplit;  // their TF32 hi / FP32 lo split (tensor-core path)
     vv10::DevBuf ehalf;   // per-CTA totals of the energy-only kernel
     vv10::DevBuf aophik, aoz, aom;  // AO assembly: gathered phi, Z, GEMM results
+    vv10::DevBuf aogw;              // AO assembly: split-K partials of its FP64 products
     vv10::DevBuf aofa;              // nuclear derivative of F: basis-derivative factors, K^c
     vv10::DevBuf ngpart;            // per-block partials of the nuclear-gradient terms
-    void* blas = nullptr;            // cuBLAS handle of the AO assembly (made on first use)
+    vv10::DevBuf nhess;             // nuclear Hessian: its pair sums and block partials
 
     // tile overrides (index = mode + kPairModes * fp64, modes MODE_EUW..MODE_EUWABCG), set by
     // vv10_set_tiles / the autotuner
@@ -197,6 +200,7 @@ struct vv10_ctx {
     vv10_status tune_batch(bool fp64, cudaStream_t st, bool force);
     int tc_cap_for(int32_t P, int64_t nk) const;
     vv10_status tc_contract(int32_t P, int cap, cudaStream_t st);
+    vv10_status f16_contract(int32_t P, int cap, cudaStream_t st);
     vv10_status tune_tc_cap(int32_t P, cudaStream_t st, int* cap);
     vv10_status hessian(vv10_precision prec, int32_t P, const double* rho_t,
                         const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,

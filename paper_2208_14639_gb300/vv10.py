@@ -26,8 +26,9 @@ VV10_ERR_UNSUPPORTED = 6
 VV10_FP64 = 0
 VV10_MIXED_TF32X3 = 1
 VV10_MIXED_BF16X3 = 2
+VV10_MIXED_F16X3 = 3
 PRECISIONS = {"fp64": VV10_FP64, "tf32x3": VV10_MIXED_TF32X3, "bf16x3": VV10_MIXED_BF16X3,
-              "mixed": VV10_MIXED_TF32X3}
+              "f16x3": VV10_MIXED_F16X3, "mixed": VV10_MIXED_TF32X3}
 
 VV10_OPT_FUSE_HESSIAN_SUMS = 1
 VV10_TUNE_PAIRSUMS = 1
@@ -49,7 +50,8 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_batch_run", "vv10_get_tiles", "vv10_autotune", "vv10_set_autotune",
            "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
            "vv10_weight_response", "vv10_energy", "vv10_fock_matrix",
-           "vv10_orbital_hessian", "vv10_nuclear_gradient", "vv10_fock_derivative")
+           "vv10_orbital_hessian", "vv10_nuclear_gradient", "vv10_fock_derivative",
+           "vv10_nuclear_hessian")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
 VV10_N_PHASES = 16
@@ -101,6 +103,7 @@ def load(build_if_missing: bool = False):
         "vv10_energy": (st, [P, st, ctypes.POINTER(D), P]),
         "vv10_fock_matrix": (st, [P, I32, P, P, P, P, P, P]),
         "vv10_nuclear_gradient": (st, [P, I32, P, P, P, P, P]),
+        "vv10_nuclear_hessian": (st, [P, st, P, P, P, P, P, P, P, P]),
         "vv10_orbital_hessian": (st, [P, I32, P, P, I32, P, P, P, P, P, P]),
         "vv10_fock_derivative": (st, [P, I32] + [P] * 16),
         "vv10_weight_grad": (st, [P, P, P]),
@@ -289,6 +292,18 @@ def vv10_nuclear_gradient(h, out, rho_t=None, grad_rho_t=None, w_t=None, stream=
         h, P, _dptr(rho_t, "rho_t", shape=(P, n)), _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)),
         _dptr(w_t, "w_t", shape=(P, n)), _dptr(out, "out", shape=(P,)), _stream(stream))
     _check(h, st, "vv10_nuclear_gradient")
+
+
+def vv10_nuclear_hessian(h, prec: int, rho_a, grad_rho_a, rho_ab, grad_rho_ab, w_a, w_ab, H,
+                         stream=None) -> None:
+    """The nine-term nuclear Hessian (P x P, P = 3 n_atom) from the prepared points."""
+    P, n = int(rho_a.shape[0]), int(rho_a.shape[1])
+    st = load().vv10_nuclear_hessian(
+        h, int(prec), _dptr(rho_a, "rho_a", shape=(P, n)),
+        _dptr(grad_rho_a, "grad_rho_a", shape=(P, n, 3)), _dptr(rho_ab, "rho_ab", shape=(P, P, n)),
+        _dptr(grad_rho_ab, "grad_rho_ab", shape=(P, P, n, 3)), _dptr(w_a, "w_a", shape=(P, n)),
+        _dptr(w_ab, "w_ab", shape=(P, P, n)), _dptr(H, "H", shape=(P, P)), _stream(stream))
+    _check(h, st, "vv10_nuclear_hessian")
 
 
 def vv10_weight_grad(h, dEdw, stream=None) -> None:
@@ -519,6 +534,15 @@ class VV10:
         out = torch.empty(ref.shape[0], dtype=torch.float64, device=ref.device)
         vv10_nuclear_gradient(self.h, out, rho_t, grad_rho_t, w_t, stream)
         return out
+
+    def nuclear_hessian(self, rho_a, grad_rho_a, rho_ab, grad_rho_ab, w_a, w_ab, prec=VV10_FP64,
+                        stream=None):
+        """The nine-term VV10 nuclear Hessian (3 n_atom x 3 n_atom)."""
+        P = rho_a.shape[0]
+        H = torch.empty(P, P, dtype=torch.float64, device=rho_a.device)
+        vv10_nuclear_hessian(self.h, prec, rho_a, grad_rho_a, rho_ab, grad_rho_ab, w_a, w_ab, H,
+                             stream)
+        return H
 
     def fock_matrix(self, phi, grad_phi, vrho, vgamma, stream=None):
         """The VV10 Fock matrix (nbf x nbf) from f^rho, f^gamma and the basis on the grid."""

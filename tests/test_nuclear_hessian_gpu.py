@@ -1,12 +1,12 @@
-"""The VV10 nuclear Hessian (Sec. II.B, Eq. E_hess) from the GPU's pair sums, through the C ABI:
-the Hessian contraction with the nuclear trials (vv10_hessian_contract), the weight-derivative
-sums (vv10_weight_response), the atom-resolved sums (vv10_coord_grad), the grid-grid blocks
-(vv10_coord_hessian), f^rho, f^gamma and E_i (vv10_energy_potential, vv10_weight_grad),
-combined with the local derivatives by the oracle's nine-term assembly.
+"""The VV10 nuclear Hessian (Sec. II.B, Eq. E_hess) on the GPU, through the C ABI:
+vv10_nuclear_hessian forms every pair sum with the library's own entry points (energy and
+potential, the Hessian contraction with the nuclear trials, the weight-derivative sums, the
+atom-resolved sums, the grid-grid blocks), takes the local derivatives (kappa', omega_rho,
+omega_gamma) from its prepared points, and assembles the nine terms on the device.
 
-Against the same assembly of the oracle's pair sums: FP64 <= 1e-10, mixed <= 1e-6 relative (max
-norm); against central differences of the nuclear gradient of the whole synthetic pipeline:
-1e-6.
+Against the oracle (its own pair sums through its numpy nine-term assembly): FP64 <= 1e-10,
+mixed <= 1e-6 relative (max norm); against central differences of the nuclear gradient of
+the whole synthetic pipeline: 1e-6.
 """
 import numpy as np
 import pytest
@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 FP64 = vv10.VV10_FP64
 MIXED = vv10.VV10_MIXED_TF32X3
+F16 = vv10.VV10_MIXED_F16X3
 
 
 @pytest.fixture(scope="module")
@@ -66,23 +67,14 @@ def oracle_hessian(oracle_mod, c):
 def gpu_hessian(oracle_mod, c, prec, dev):
     g = c["g"]
     NA = g.molecule.n_atom
-    P = 3 * NA
     eng = vv10.VV10(0)
     eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev),
                 T(g.atom_of_point, dev, torch.int32), NA)
-    _, vr, vg = eng.energy_potential(prec)
-    dEdw = eng.weight_grad().cpu().numpy()
-    kept = g.rho >= 1e-10
-    E = np.where(kept, dEdw / np.where(kept, g.rho, 1.0) - oracle_mod.beta(), 0.0)
-    Ew, Uw, Ww = (x.cpu().numpy() for x in eng.weight_response(T(c["W"], dev), prec))
-    _, _, euw = eng.coord_grad(prec, atoms=False, resolved=True)
-    Egr, Ugr, Wgr = (x.reshape(g.n, P).T for x in euw.cpu().numpy())
-    fr, fg = eng.hessian_contract(T(c["rt"], dev), T(c["gt"], dev), prec)
-    Hgg, _ = eng.coord_hessian(prec)
-    Hgg = Hgg.cpu().numpy().transpose(0, 2, 1, 3).reshape(P, P)
+    H = eng.nuclear_hessian(T(c["rt"], dev), T(c["gt"], dev), T(c["r2"], dev), T(c["g2"], dev),
+                            T(c["W"], dev), T(c["Wab"], dev), prec)
+    out = H.cpu().numpy()
     eng.close()
-    return assemble(oracle_mod, c, vr.cpu().numpy(), vg.cpu().numpy(), E, Ew, Uw, Ww, Egr, Ugr, Wgr,
-                    fr.cpu().numpy(), fg.cpu().numpy(), Hgg)
+    return out
 
 
 def rel_max(a, b):
@@ -94,7 +86,8 @@ def water_small():
     return case(synth.water(), 10, 26)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F16, 1e-6)],
+                         ids=["fp64", "tf32x3", "f16x3"])
 def test_water_against_oracle_terms(dev, oracle_mod, water_small, prec, tol):
     ref = oracle_hessian(oracle_mod, water_small)
     got = gpu_hessian(oracle_mod, water_small, prec, dev)
@@ -136,3 +129,29 @@ def test_larger_water_grid(dev, oracle_mod):
     ref = oracle_hessian(oracle_mod, c)
     assert rel_max(gpu_hessian(oracle_mod, c, FP64, dev), ref) <= 1e-10
     assert rel_max(gpu_hessian(oracle_mod, c, MIXED, dev), ref) <= 1e-6
+
+
+def test_symmetric_and_translation_invariant(dev, oracle_mod):
+    """A 4-atom CHON molecule: H = H^T, and every row sums to zero over the three
+    translations (a rigid shift of the whole system leaves the gradient unchanged)."""
+    c = case(synth.random_chon(np.random.default_rng(41), 4), 10, 26)
+    H = gpu_hessian(oracle_mod, c, FP64, dev)
+    scale = np.abs(H).max()
+    assert np.abs(H - H.T).max() <= 1e-7 * scale  # w^{ab} comes from central differences
+    na = c["g"].molecule.n_atom
+    shift = H.reshape(3 * na, na, 3).sum(axis=1)
+    assert np.abs(shift).max() <= 1e-6 * scale
+    ref = oracle_hessian(oracle_mod, c)
+    assert rel_max(H, ref) <= 1e-10
+
+
+def test_requires_atom_labels(dev):
+    g = synth.random_points(64, seed=3, n_atom=2)
+    eng = vv10.VV10(0)
+    eng.prepare(T(g.coords, dev), T(g.weights, dev), T(g.rho, dev), T(g.grad_rho, dev))
+    z = lambda *shape: torch.zeros(*shape, dtype=torch.float64, device=dev)
+    with pytest.raises(vv10.VV10Error) as ei:
+        eng.nuclear_hessian(z(6, g.n), z(6, g.n, 3), z(6, 6, g.n), z(6, 6, g.n, 3), z(6, g.n),
+                            z(6, 6, g.n))
+    assert ei.value.status == vv10.VV10_ERR_INVALID_ARG
+    eng.close()

@@ -5,6 +5,9 @@ Tolerances (each error against the FP64 oracle):
               <= 1e-10 relative (L2 / Frobenius over the whole output);
   mixed path: |dE| <= 1e-7 Eh; potential <= 1e-6 relative L2 (vrho and vgamma separately);
               coordinate gradient <= 1e-6 relative.
+Every output check also bounds each element, |d_i| <= el_tol (|ref_i| + rms(ref)) with
+el_tol = tol (FP64) or 10 tol (mixed; see parity_util), and reports
+the largest absolute error (parity_util.check).
 Small cases compare every output element; the full-size water-hexamer grid (174,600
 points) compares the energy in full and sampled output rows (full j sums) otherwise.
 """
@@ -15,18 +18,17 @@ import pytest
 import torch
 
 from paper_2208_14639_gb300 import synth, vv10
+from parity_util import check, rel
 
 pytestmark = pytest.mark.gpu
 
 FP64 = vv10.VV10_FP64
 MIXED = vv10.VV10_MIXED_TF32X3
+F16 = vv10.VV10_MIXED_F16X3
+# the two tensor-core contractions of the mixed path: split TF32 and scaled split FP16
+TC_PRECS = pytest.mark.parametrize("tcp", [MIXED, F16], ids=["tf32x3", "f16x3"])
 
 
-def rel(a, b):
-    a = np.asarray(a)
-    b = np.asarray(b)
-    nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
 @pytest.fixture(scope="module")
@@ -68,12 +70,12 @@ def test_energy_potential(dev, oracle_mod, name, g, prec):
     vr, vg = vr.cpu().numpy(), vg.cpu().numpy()
     if prec == FP64:
         assert abs(e - e_ref) <= 1e-11 * abs(e_ref)
-        assert rel(vr, vr_ref) <= 1e-10
-        assert rel(vg, vg_ref) <= 1e-10
+        check(vr, vr_ref, 1e-10)
+        check(vg, vg_ref, 1e-10)
     else:
         assert abs(e - e_ref) <= 1e-7
-        assert rel(vr, vr_ref) <= 1e-6
-        assert rel(vg, vg_ref) <= 1e-6
+        check(vr, vr_ref, 1e-6)
+        check(vg, vg_ref, 1e-6)
     kept = g.rho >= 1e-10
     assert np.all(vr[~kept] == 0.0) and np.all(vg[~kept] == 0.0)
     eng.close()
@@ -86,8 +88,8 @@ def test_hessian_contraction_fp64(dev, oracle_mod, name, g):
     eng = make_engine(g, dev)
     eng.energy_potential(FP64)
     fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
-    assert rel(fr.cpu().numpy(), fr_ref) <= 1e-10
-    assert rel(fg.cpu().numpy(), fg_ref) <= 1e-10
+    check(fr.cpu().numpy(), fr_ref, 1e-10)
+    check(fg.cpu().numpy(), fg_ref, 1e-10)
     eng.close()
 
 
@@ -101,8 +103,8 @@ def test_hessian_single_trial_and_odd_P(dev, oracle_mod):
         eng = make_engine(g, dev)
         eng.energy_potential(FP64)
         fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
-        assert rel(fr.cpu().numpy(), fr_ref) <= 1e-10
-        assert rel(fg.cpu().numpy(), fg_ref) <= 1e-10
+        check(fr.cpu().numpy(), fr_ref, 1e-10)
+        check(fg.cpu().numpy(), fg_ref, 1e-10)
         eng.close()
 
 
@@ -110,23 +112,27 @@ MIXED_HESS = [("water", synth.config_water()), ("rand255", synth.random_points(2
               ("rand700", synth.random_points(700, seed=7, n_atom=4))]
 
 
+@TC_PRECS
 @pytest.mark.parametrize("name,g", MIXED_HESS, ids=[s[0] for s in MIXED_HESS])
-def test_hessian_contraction_mixed(dev, oracle_mod, name, g):
-    """Split-TF32 tensor-core contraction: <= 1e-6 relative Frobenius per output."""
+def test_hessian_contraction_mixed(dev, oracle_mod, name, g, tcp):
+    """Split-TF32 and split-FP16 tensor-core contractions: <= 1e-6 relative Frobenius per
+    output, every element within 1e-6 (|ref| + rms)."""
     rt, gt = synth.trial_densities(g.molecule, g.coords)
     fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
     eng = make_engine(g, dev)
     eng.energy_potential(MIXED)
-    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), MIXED)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), tcp)
     vv10.vv10_sync(eng.h)
-    assert rel(fr.cpu().numpy(), fr_ref) <= 1e-6
-    assert rel(fg.cpu().numpy(), fg_ref) <= 1e-6
+    check(fr.cpu().numpy(), fr_ref, 1e-6)
+    check(fg.cpu().numpy(), fg_ref, 1e-6)
     eng.close()
 
 
-@pytest.mark.parametrize("P", [1, 33, 200])
-def test_hessian_mixed_trial_counts(dev, oracle_mod, P):
-    """Trial counts below one MMA tile, ragged, and above one launch's 192 (two groups)."""
+@TC_PRECS
+@pytest.mark.parametrize("P", [1, 33, 65, 97, 200])
+def test_hessian_mixed_trial_counts(dev, oracle_mod, P, tcp):
+    """Trial counts below one MMA tile, ragged, across the widths where both output kinds share
+    a tile (<= 64) or not, and above one launch's 192 (two groups)."""
     g = synth.random_points(300, seed=17, n_atom=3)
     rng = np.random.default_rng(P)
     rt = rng.normal(size=(P, g.n)) * g.rho
@@ -134,10 +140,10 @@ def test_hessian_mixed_trial_counts(dev, oracle_mod, P):
     fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
     eng = make_engine(g, dev)
     eng.energy_potential(MIXED)
-    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), MIXED)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), tcp)
     vv10.vv10_sync(eng.h)
-    assert rel(fr.cpu().numpy(), fr_ref) <= 1e-6
-    assert rel(fg.cpu().numpy(), fg_ref) <= 1e-6
+    check(fr.cpu().numpy(), fr_ref, 1e-6)
+    check(fg.cpu().numpy(), fg_ref, 1e-6)
     eng.close()
 
 
@@ -152,13 +158,13 @@ def test_coordinate_terms(dev, oracle_mod, prec):
     gp, ga, euw = eng.coord_grad(prec, atoms=True, resolved=True)
     gp, ga, euw = gp.cpu().numpy(), ga.cpu().numpy(), euw.cpu().numpy()
     tol = 1e-10 if prec == FP64 else 1e-6
-    assert rel(gp, pg_ref) <= tol
+    check(gp, pg_ref, tol)
     seg = np.array([pg_ref[g.atom_of_point == a].sum(axis=0) for a in range(3)])
-    assert rel(ga, seg) <= (1e-9 if prec == FP64 else 1e-5)
+    check(ga, seg, 1e-9 if prec == FP64 else 1e-5)
     # translational invariance: the atom terms sum to zero up to rounding
     assert np.abs(ga.sum(axis=0)).max() <= (1e-9 if prec == FP64 else 1e-6) * np.abs(ga).max()
     for q, ref in enumerate((oE, oU, oW)):
-        assert rel(euw[q][rows], ref) <= (1e-10 if prec == FP64 else 1e-5)
+        check(euw[q][rows], ref, 1e-10 if prec == FP64 else 1e-5)
     eng.close()
 
 
@@ -174,11 +180,11 @@ def test_atom_resolved_and_gradient_with_interleaved_atoms(dev, oracle_mod):
     oE, oU, oW = oracle_mod.atom_resolved(*args, h.atom_of_point, 4)
     eng = make_engine(h, dev)
     gp, ga, euw = eng.coord_grad(FP64, atoms=True, resolved=True)
-    assert rel(gp.cpu().numpy(), pg_ref) <= 1e-10
-    assert rel(ga.cpu().numpy(), ag_ref) <= 1e-10
+    check(gp.cpu().numpy(), pg_ref, 1e-10)
+    check(ga.cpu().numpy(), ag_ref, 1e-10)
     euw = euw.cpu().numpy()
     for q, ref in enumerate((oE, oU, oW)):
-        assert rel(euw[q], ref) <= 1e-10
+        check(euw[q], ref, 1e-10)
     eng.close()
 
 
@@ -195,7 +201,7 @@ def test_permutation_and_determinism(dev):
     e2, vr2, _ = eng2.energy_potential(FP64)
     e3, vr3, _ = eng.energy_potential(FP64)
     assert abs(e2 - e3) <= 1e-13 * abs(e3)
-    assert rel(vr2.cpu().numpy(), vr3.cpu().numpy()[perm]) <= 1e-12
+    check(vr2.cpu().numpy(), vr3.cpu().numpy()[perm], 1e-12)
     eng.close()
     eng2.close()
 
@@ -206,7 +212,7 @@ def test_weight_gradient(dev, oracle_mod):
     ref = g.rho * (oracle_mod.beta() + E)
     eng = make_engine(g, dev)
     eng.energy_potential(FP64)
-    assert rel(eng.weight_grad().cpu().numpy(), ref) <= 1e-10
+    check(eng.weight_grad().cpu().numpy(), ref, 1e-10)
     eng.close()
 
 
@@ -228,10 +234,12 @@ def test_full_size_hexamer_energy_potential(dev, oracle_mod, hexamer):
         vr, vg = vr.cpu().numpy()[rows], vg.cpu().numpy()[rows]
         if prec == FP64:
             assert abs(e - e_ref) <= 1e-11 * abs(e_ref)
-            assert rel(vr, vr_ref) <= 1e-10 and rel(vg, vg_ref) <= 1e-10
+            check(vr, vr_ref, 1e-10)
+            check(vg, vg_ref, 1e-10)
         else:
             assert abs(e - e_ref) <= 1e-7
-            assert rel(vr, vr_ref) <= 1e-6 and rel(vg, vg_ref) <= 1e-6
+            check(vr, vr_ref, 1e-6)
+            check(vg, vg_ref, 1e-6)
     eng.close()
 
 
@@ -244,14 +252,15 @@ def test_full_size_hexamer_hessian_sampled(dev, oracle_mod, hexamer):
     eng = make_engine(g, dev)
     rtd, gtd = T(rt, dev), T(gt, dev)
     eng.energy_potential(MIXED)
-    fr, fg = eng.hessian_contract(rtd, gtd, MIXED)
-    vv10.vv10_sync(eng.h)
-    assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-6
-    assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-6
+    for tcp in (MIXED, F16):
+        fr, fg = eng.hessian_contract(rtd, gtd, tcp)
+        vv10.vv10_sync(eng.h)
+        check(fr.cpu().numpy()[:, rows], fr_ref, 1e-6, what=f"f_rho_t prec {tcp}")
+        check(fg.cpu().numpy()[:, rows], fg_ref, 1e-6, what=f"f_gamma_t prec {tcp}")
     eng.energy_potential(FP64)
     fr, fg = eng.hessian_contract(rtd, gtd, FP64)
-    assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-10
-    assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-10
+    check(fr.cpu().numpy()[:, rows], fr_ref, 1e-10)
+    check(fg.cpu().numpy()[:, rows], fg_ref, 1e-10)
     eng.close()
 
 
@@ -309,29 +318,58 @@ def test_error_paths(dev):
 
 # ----------------------------------------------------------------- 60-atom CHON, 1.36 M points
 
+def chon60_rows(g, oracle_mod, n_spread=128, n_tail=64, n_omg=64):
+    """Rows of the 60-atom grid checked against the oracle: n_spread kept points spread over
+    the grid, the n_tail kept points of lowest density and the n_omg kept points of largest
+    |omega_gamma| (where the FP32 pair arithmetic is most fragile: rho^4 small, omega_gamma
+    up to ~1e10)."""
+    kept = np.flatnonzero(g.rho >= 1e-10)
+    spread = kept[np.linspace(0, kept.size - 1, n_spread).astype(np.int64)]
+    tail = kept[np.argsort(g.rho[kept], kind="stable")[:n_tail]]
+    om_g = np.abs(oracle_mod.point_props(g.rho[kept], g.grad_rho[kept])["omega_gamma"])
+    big = kept[np.argsort(-om_g, kind="stable")[:n_omg]]
+    rows = np.unique(np.concatenate([spread, tail, big]))
+    return rows, tail, big
+
+
 def test_full_size_chon60_mixed(dev, oracle_mod):
     """60-atom CHON molecule, 75 x 302 points per atom (1,359,000 points), P = 180, mixed
-    precision: the energy against the FP64 GPU path (|dE| <= 1e-7 Eh), sampled rows of the
-    potential, the Hessian contraction and the point gradient against the oracle (full j
-    sums)."""
+    precision, against the oracle on >= 256 rows (full j sums): spread rows, the 64 kept
+    points of lowest density and the 64 of largest |omega_gamma|.  Potential, Hessian
+    contraction, point gradient and the per-row energy terms dE/dw_i = rho_i (beta + E_i)
+    (their weighted sum over the rows is the rows' share of the energy) each per element;
+    the energy against the FP64 GPU path (|dE| <= 1e-7 Eh)."""
     g = synth.config_chon60()
     eng = make_engine(g, dev)
     xyz = T(g.coords, dev)
     rt, gt = synth.trial_densities_torch(g.molecule, xyz)
     assert rt.shape == (180, g.n)
     e_mixed, vr, vg = eng.energy_potential(MIXED)
+    dedw = eng.weight_grad()
     fr, fg = eng.hessian_contract(rt, gt, MIXED)
     gp, _, _ = eng.coord_grad(MIXED, atoms=False)
     vv10.vv10_sync(eng.h)
-    rows = np.linspace(0, g.n - 1, 16).astype(np.int64)
+    rows, tail, big = chon60_rows(g, oracle_mod)
+    assert rows.size >= 250 and tail.size == 64 and big.size == 64
     args = (g.coords, g.weights, g.rho, g.grad_rho)
     _, vr_ref, vg_ref = oracle_mod.potential(*args, rows=rows)
-    assert rel(vr.cpu().numpy()[rows], vr_ref) <= 1e-6
-    assert rel(vg.cpu().numpy()[rows], vg_ref) <= 1e-6
+    check(vr.cpu().numpy()[rows], vr_ref, 1e-6, what="vrho")
+    check(vg.cpu().numpy()[rows], vg_ref, 1e-6, what="vgamma")
+    E_ref = oracle_mod.pair_sums(*args, rows=rows)["E"]
+    dedw_ref = g.rho[rows] * (oracle_mod.beta() + E_ref)
+    dedw = dedw.cpu().numpy()[rows]
+    check(dedw, dedw_ref, 1e-6, what="dE/dw")
+    # the rows' share of E = sum_i w_i rho_i (beta + E_i / 2)
+    share = lambda d: float(np.sum(g.weights[rows] * (0.5 * d + 0.5 * g.rho[rows] * oracle_mod.beta())))
+    assert abs(share(dedw) - share(dedw_ref)) <= 1e-8
     fr_ref, fg_ref = oracle_mod.hessian_contract(*args, rt.cpu().numpy(), gt.cpu().numpy(), rows=rows)
-    assert rel(fr.cpu().numpy()[:, rows], fr_ref) <= 1e-6
-    assert rel(fg.cpu().numpy()[:, rows], fg_ref) <= 1e-6
-    assert rel(gp.cpu().numpy()[rows], oracle_mod.point_grad(*args, rows=rows)) <= 1e-6
+    check(fr.cpu().numpy()[:, rows], fr_ref, 1e-6, what="f_rho_t")
+    check(fg.cpu().numpy()[:, rows], fg_ref, 1e-6, what="f_gamma_t")
+    fr, fg = eng.hessian_contract(rt, gt, F16)  # the split-FP16 contraction, same rows
+    vv10.vv10_sync(eng.h)
+    check(fr.cpu().numpy()[:, rows], fr_ref, 1e-6, what="f_rho_t (f16x3)")
+    check(fg.cpu().numpy()[:, rows], fg_ref, 1e-6, what="f_gamma_t (f16x3)")
+    check(gp.cpu().numpy()[rows], oracle_mod.point_grad(*args, rows=rows), 1e-6, what="grad")
     e_fp64, _, _ = eng.energy_potential(FP64, want_energy=True)
     assert abs(e_mixed - e_fp64) <= 1e-7
     eng.close()
@@ -339,7 +377,8 @@ def test_full_size_chon60_mixed(dev, oracle_mod):
 
 # ----------------------------------------------------------------- limits and degenerate inputs
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F16, 1e-6)],
+                         ids=["fp64", "tf32x3", "f16x3"])
 def test_hessian_maximum_trial_count(dev, oracle_mod, prec, tol):
     """P = VV10_MAX_TRIALS (4096): 22 tensor-core groups of 187 trials, or 128 FP64 chunks."""
     g = synth.random_points(96, seed=23, n_atom=2)
@@ -352,8 +391,8 @@ def test_hessian_maximum_trial_count(dev, oracle_mod, prec, tol):
     eng.energy_potential(prec)
     fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), prec)
     vv10.vv10_sync(eng.h)
-    assert rel(fr.cpu().numpy(), fr_ref) <= tol
-    assert rel(fg.cpu().numpy(), fg_ref) <= tol
+    check(fr.cpu().numpy(), fr_ref, tol)
+    check(fg.cpu().numpy(), fg_ref, tol)
     with pytest.raises(vv10.VV10Error):  # one more is refused
         eng.hessian_contract(T(np.zeros((P + 1, g.n)), dev), T(np.zeros((P + 1, g.n, 3)), dev), prec)
     eng.close()
