@@ -907,31 +907,28 @@ def batch_cpu_sample(bp, budget_s: float):
                       f"P={[bp.P[m] for m in picks]})"}
 
 
-def gpu_batch_arm(args):
+def batch_record(args, dev, world, rank, steps, warmup, prec_name, with_fp64=True, with_cpu=True,
+                 label_note=None):
+    """The 64-molecule batch through vv10_batch_prepare + vv10_batch_run: the timed steps,
+    its roofline, the FP64 comparison on a subset, the end-to-end timing and (optionally) the
+    oracle sample.  Returns the record (a dict)."""
     import torch
     from paper_2208_14639_gb300 import vv10 as vv
-
-    rank, world, local = rank_info()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    vv.load(build_if_missing=True)
+    local = dev.index or 0
     bp = BatchProblem(dev, workers=max(1, len(os.sched_getaffinity(0))))
     h = vv.vv10_create(local)
-    prec = vv.PRECISIONS[args.precision]
+    prec = vv.PRECISIONS[prec_name]
     peaks, peak_src = load_peaks()
     if prec != vv.VV10_FP64:  # batched pair-sum tiles tuned on first use (warm-up)
         vv.vv10_set_autotune(h, vv.VV10_TUNE_BATCH)
 
     with ClockSampler(local) as clk:
-        ms, nk, prof = time_batch(vv, h, bp, prec, args.steps, args.warmup, world)
+        ms, nk, prof = time_batch(vv, h, bp, prec, steps, warmup, world)
     clocks = clk.summary()
     ms_max = max_over_ranks(ms, world)
     nk = np.asarray(nk, dtype=np.float64)
     pairs_step = float((nk * nk).sum())
-    K = args.steps
+    K = steps
     value = 2.0 * pairs_step * K * world / (ms_max / 1e3)
     per = {k: v[0] / K for k, v in prof.items()}
     launches = sum(v[1] for v in prof.values())
@@ -947,30 +944,27 @@ def gpu_batch_arm(args):
             "traffic": None, "kernel": dom}
     if dom == "contraction_tensor_core":
         t = per[dom] / 1e3
-        tf32_peak = peaks["bf16_tflops"] * 0.5 * 1e12
-        t_tensor = 3 * 8.0 * float((nk2 * ppad * np.array(groups)).sum()) / tf32_peak
-        alu_peak = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
-        alu_ops = float(sum(nk2[m] * groups[m] * tc_alu_ops_per_pair(int(ppad[m])) for m in range(len(nk))))
-        roof = {"bound": "alu", "achieved": alu_ops / t / 1e12, "peak": alu_peak / 1e12,
-                "unit": "TFLOP/s (FP32 ops)", "frac": alu_ops / t / alu_peak, "traffic": None,
-                "kernel": "k_hess_tc (batched)",
-                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median under load)",
-                "tensor_alt": {"achieved_alg_tflops": hess_flops / t / 1e12,
-                               "tf32_peak_tflops": tf32_peak / 1e12,
-                               "frac_of_split_peak": t_tensor / t}}
+        f16 = prec == vv.VV10_MIXED_F16X3
+        key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
+        peak = peaks[key] * (1.0 if f16 else 0.5) * 1e12
+        t_tensor = 3 * 8.0 * float((nk2 * ppad * np.array(groups)).sum()) / peak
+        roof = {"bound": "tensor", "achieved": hess_flops / t / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": hess_flops / t / peak, "traffic": None,
+                "kernel": "k_hess_f16 (batched)" if f16 else "k_hess_tc (batched)",
+                "peak_source": f"{peak_src} {key} {peaks[key]} x {1.0 if f16 else 0.5}",
+                "issued_mma_frac": t_tensor / t}
     t_ep = per["pair_sums_EUW"] + per["energy_epilogue"]
     t_hess = (per["pair_sums_ABC"] + per["trial_prep"] + per["contraction_tensor_core"] +
               per["contraction_fp64"] + per["hessian_epilogue"])
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+        "warmup": warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions"
-                 if prec != vv.VV10_FP64 else "f64",
+        "dtype": DTYPES.get(prec_name, "f64"),
         "data": "synthetic (seeded CHON molecules, Gaussian densities, analytic trials)",
         "config": {"workload": BATCH_LABEL, "n_molecules": len(bp.sys), "n_points": int(bp.off[-1]),
                    "n_kept": int(nk.sum()), "pairs_per_step": 2.0 * pairs_step,
-                   "trials_total": int(sum(bp.P)), "precision": args.precision,
+                   "trials_total": int(sum(bp.P)), "precision": prec_name,
                    "l2": f"inputs larger than L2 ({bp.input_bytes() / 1e9:.1f} GB resident)",
                    "parallelism": f"replica x{world}",
                    "pair_count": "2 sum_m N_kept,m^2 (energy/potential + Hessian contraction)"},
@@ -982,7 +976,9 @@ def gpu_batch_arm(args):
                       "phase_ms_per_step": {k: round(v, 3) for k, v in per.items() if v}},
         "energies_first4": [float(x) for x in bp.out["E"][:4].cpu()],
     }
-    if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
+    if label_note:
+        result["note"] = label_note
+    if rank == 0 and with_fp64 and prec != vv.VV10_FP64:
         # FP64 baseline on the eight smallest molecules (the whole batch would take minutes)
         vv.vv10_set_autotune(h, 0)
         order = np.argsort(bp.n, kind="stable")[:8]
@@ -1003,12 +999,29 @@ def gpu_batch_arm(args):
         }
         del sub
         run_batch_step(vv, h, bp, prec)  # back to the full batch (the handle holds one batch)
-    sec, h2d, d2h = time_batch_e2e(vv, h, bp, prec, max(1, min(K, 2)), 1)
-    result["e2e"] = {"value": 2.0 * pairs_step * max(1, min(K, 2)) / sec, "unit": UNIT,
+    e2e_steps = max(1, min(K, 2))
+    sec, h2d, d2h = time_batch_e2e(vv, h, bp, prec, e2e_steps, 1)
+    result["e2e"] = {"value": 2.0 * pairs_step * e2e_steps / sec, "unit": UNIT, "steps": e2e_steps,
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and with_cpu:
         result["cpu_baseline"] = batch_cpu_sample(bp, args.cpu_seconds)
     vv.vv10_destroy(h)
+    del bp
+    return result
+
+
+def gpu_batch_arm(args):
+    import torch
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2208_14639_gb300 import vv10 as vv
+    vv.load(build_if_missing=True)
+    result = batch_record(args, dev, world, rank, args.steps, args.warmup, args.precision,
+                          with_fp64=not args.no_fp64_arm, with_cpu=not args.no_cpu_baseline)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

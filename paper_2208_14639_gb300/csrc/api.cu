@@ -1202,7 +1202,8 @@ vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_s
             return VV10_ERR_INVALID_ARG;
         }
         h->tc_cap_manual = rows_per_thread;
-        h->batch.tc_classes.clear();  // rebuild the batch layout with the new width
+        h->batch.tc_classes.clear();  // rebuild the batch layouts with the new width
+        h->batch.f16_classes.clear();
         h->batch_drop_graph();
         return VV10_OK;
     }

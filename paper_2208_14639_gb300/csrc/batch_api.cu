@@ -50,7 +50,8 @@ void vv10_ctx::batch_release() {
     batch_drop_graph();
     BatchState& B = batch;
     DevBuf* bufs[] = {&B.scratch, &B.small, &B.arena, &B.sums, &B.part, &B.eblk, &B.pair_tab,
-                      &B.counter, &B.rtgt, &B.splits, &B.acc, &B.maps, &B.tc_tab};
+                      &B.counter, &B.rtgt, &B.splits, &B.acc, &B.maps, &B.tc_tab,
+                      &B.f16small, &B.f16tab, &B.f16counter};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -279,6 +280,8 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
         return VV10_OK;
     }
 
+    if (prec == VV10_MIXED_F16X3) return batch_hess_f16(same_P, Pt, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st);
+
     // tensor-core path.  Layout (rebuilt when the trial counts change): per molecule the
     // trial values at kept points, four FP32 trial splits of `rows` rows, the FP64 partial
     // output, four tensor maps; per padded group width one molecule-group table and one
@@ -372,6 +375,7 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
             B_CUDA(cudaMemcpy(B.tc_tab.p, tab.data(), tab.size(), cudaMemcpyHostToDevice),
                    "upload tensor-core tables");
         B.hess_P.assign(Pt, Pt + n_mol);
+        B.f16_classes.clear();  // the split-FP16 layout shares the arenas: rebuild it when used
     }
 
     // trial values and splits, molecule by molecule
@@ -398,6 +402,162 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
                                         static_cast<char*>(B.tc_tab.p) + c.tasks, c.n_tasks, c.ppad,
                                         n_sm, tc_flush, err, st),
                    "batched tensor-core contraction");
+    }
+    PhaseScope ph(this, PH_HESS_EPILOGUE, st, static_cast<int>(n_mol));
+    for (size_t m = 0; m < n_mol; ++m) {
+        BatchMol& M = B.mol[m];
+        if (M.nk == 0) continue;
+        double* s = at<double>(B.sums, M.sums);
+        B_CUDA(launch_hess_epilogue(M.P, M.n_t, at<double>(B.acc, M.acc), 1, M.nk_pad, s + M.cap,
+                                    s + 2 * M.cap, s + 3 * M.cap, s + 4 * M.cap, s + 5 * M.cap,
+                                    at<double>(B.rtgt, M.rt), at<double>(B.rtgt, M.gt),
+                                    f_rho_t + M.toff, f_gamma_t + M.toff, err, st),
+               "Hessian epilogue");
+    }
+    return VV10_OK;
+}
+
+// The split-FP16 contraction of the batch.  Layout (rebuilt when the trial counts change):
+// per molecule the trial values at kept points, its FP16 hi / lo trial tiles [rows][2 nk_pad],
+// its column factors, the FP64 partial output and two tensor maps; per padded width one
+// molecule-group table and one task table (row tile x output kind), largest molecules first,
+// taken by the persistent CTAs from an atomic counter.
+vv10_status vv10_ctx::batch_hess_f16(bool same_P, const int32_t* Pt, const double* rho_t,
+                                     const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
+                                     cudaStream_t st) {
+    BatchState& B = batch;
+    const size_t n_mol = B.mol.size();
+    int* err = static_cast<int*>(dev_err.p);
+    if (!same_P || B.f16_classes.empty()) {
+        batch_drop_graph();
+        size_t rtgt = 0, split = 0, small = 0, acc = 0, umax = 0;
+        for (size_t m = 0; m < n_mol; ++m) {
+            BatchMol& M = B.mol[m];
+            const int cap = tc_cap_for(M.n_t, M.nk);
+            M.ng = (M.n_t + cap - 1) / cap;
+            M.pg = (M.n_t + M.ng - 1) / M.ng;
+            M.ppad = hess_tc_ppad(M.pg);
+            M.rows = static_cast<int64_t>(M.ng - 1) * M.pg + M.ppad;
+            const size_t nk1 = M.nk > 0 ? M.nk : 1;
+            M.rt = rtgt;
+            rtgt += a256(sizeof(double) * M.n_t * nk1);
+            M.gt = rtgt;
+            rtgt += a256(sizeof(double) * M.n_t * nk1);
+            M.split = split;  // hi then lo, [rows][2 nk_pad] FP16 each
+            split += 2 * a256(sizeof(uint16_t) * 2 * M.rows * M.nk_pad);
+            M.f16small = small;  // colmax [2 n_t] | params [4] | scale [n_t] | col_isc [n_t]
+            small += a256(sizeof(unsigned int) * 2 * M.n_t) + 256 + a256(sizeof(float) * M.n_t) +
+                     a256(sizeof(double) * M.n_t);
+            M.acc = acc;
+            acc += a256(sizeof(double) * 2 * M.n_t * M.nk_pad);
+            umax = std::max(umax, sizeof(double) * M.n_t * M.nk_pad);
+        }
+        B_TRY(ensure(B.rtgt, rtgt, "batch trial values"));
+        B_TRY(ensure(B.splits, split > 0 ? split : 256, "batch FP16 trial tiles"));
+        B_TRY(ensure(B.f16small, small > 0 ? small : 256, "batch FP16 trial factors"));
+        B_TRY(ensure(B.acc, acc > 0 ? acc : 256, "batch contraction partials"));
+        B_TRY(ensure(tu, umax > 0 ? umax : 256, "trial u"));
+        B_TRY(ensure(ty, umax > 0 ? umax : 256, "trial y"));
+        std::vector<unsigned char> maps(256 * n_mol, 0);
+        for (size_t m = 0; m < n_mol; ++m) {
+            BatchMol& M = B.mol[m];
+            if (M.nk_pad == 0) continue;
+            char* sp = at<char>(B.splits, M.split);
+            const size_t half = a256(sizeof(uint16_t) * 2 * M.rows * M.nk_pad);
+            if (!hess_f16_make_maps(maps.data() + 256 * m, sp, sp + half, M.nk_pad, M.rows, M.ppad)) {
+                set_error("tensor map encoding failed");
+                return VV10_ERR_CUDA;
+            }
+        }
+        B_TRY(ensure(B.maps, maps.size(), "batch tensor maps"));
+        B_CUDA(cudaMemcpy(B.maps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice),
+               "upload tensor maps");
+        std::vector<int> widths;
+        for (const BatchMol& M : B.mol)
+            if (M.nk > 0 && std::find(widths.begin(), widths.end(), M.ppad) == widths.end())
+                widths.push_back(M.ppad);
+        std::sort(widths.begin(), widths.end());
+        std::vector<unsigned char> tab;
+        B.f16_classes.clear();
+        for (int ppad : widths) {
+            TcClass c;
+            c.ppad = ppad;
+            std::vector<std::pair<int, int>> groups;  // (molecule, group), largest molecules first
+            for (int m : B.order)
+                if (B.mol[m].ppad == ppad && B.mol[m].nk > 0)
+                    for (int g = 0; g < B.mol[m].ng; ++g) groups.push_back({m, g});
+            c.mols = a256(tab.size());
+            tab.resize(c.mols + hess_f16_mol_bytes() * groups.size());
+            for (size_t k = 0; k < groups.size(); ++k) {
+                const BatchMol& M = B.mol[groups[k].first];
+                const int t0 = groups[k].second * M.pg;
+                const int pn = std::min(M.pg, M.n_t - t0);
+                char* sm = at<char>(B.f16small, M.f16small);
+                const size_t o_par = a256(sizeof(unsigned int) * 2 * M.n_t);
+                const size_t o_isc = o_par + 256 + a256(sizeof(float) * M.n_t);
+                hess_f16_fill_mol(tab.data() + c.mols + hess_f16_mol_bytes() * k, M.P.r32a, M.P.r32b,
+                                  M.P.r32p, static_cast<char*>(B.maps.p) + 256 * groups[k].first,
+                                  at<double>(B.acc, M.acc), reinterpret_cast<const double*>(sm + o_isc),
+                                  reinterpret_cast<const float*>(sm + o_par), M.nk, M.nk_pad, M.n_t, pn, t0);
+            }
+            const int kinds = hess_f16_kinds_per_tile(ppad) == 2 ? 1 : 2;
+            std::vector<unsigned char> tk;
+            int64_t nt = 0;
+            for (size_t k = 0; k < groups.size(); ++k) {
+                const int64_t rt = (B.mol[groups[k].first].nk + 127) / 128;
+                for (int64_t r = 0; r < rt; ++r)
+                    for (int kind = 0; kind < kinds; ++kind) {
+                        tk.resize(tk.size() + hess_f16_task_bytes());
+                        hess_f16_fill_task(tk.data() + hess_f16_task_bytes() * nt, static_cast<int32_t>(k),
+                                           static_cast<int32_t>(r), kind);
+                        ++nt;
+                    }
+            }
+            c.tasks = a256(tab.size());
+            tab.resize(c.tasks + tk.size());
+            std::memcpy(tab.data() + c.tasks, tk.data(), tk.size());
+            c.n_tasks = nt;
+            B.f16_classes.push_back(c);
+        }
+        B_TRY(ensure(B.f16tab, tab.size() + 256, "batch split-FP16 tables"));
+        if (!tab.empty())
+            B_CUDA(cudaMemcpy(B.f16tab.p, tab.data(), tab.size(), cudaMemcpyHostToDevice),
+                   "upload split-FP16 tables");
+        B_TRY(ensure(B.f16counter, 256, "batch task counter"));
+        B.hess_P.assign(Pt, Pt + n_mol);
+        B.tc_classes.clear();  // the split-TF32 layout shares the arenas: rebuild it when used
+    }
+
+    // trial values, factors and FP16 tiles, molecule by molecule
+    for (size_t m = 0; m < n_mol; ++m) {
+        BatchMol& M = B.mol[m];
+        if (M.nk == 0) continue;
+        char* sp = at<char>(B.splits, M.split);
+        const size_t half = a256(sizeof(uint16_t) * 2 * M.rows * M.nk_pad);
+        char* sm = at<char>(B.f16small, M.f16small);
+        const size_t o_par = a256(sizeof(unsigned int) * 2 * M.n_t);
+        const size_t o_sc = o_par + 256;
+        const size_t o_isc = o_sc + a256(sizeof(float) * M.n_t);
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 4);
+        B_CUDA(launch_trial_prep(M.P, M.n_t, rho_t + M.toff, grad_rho_t + 3 * M.toff,
+                                 static_cast<double*>(tu.p), static_cast<double*>(ty.p),
+                                 at<double>(B.rtgt, M.rt), at<double>(B.rtgt, M.gt), st),
+               "trial prep");
+        B_CUDA(launch_f16_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), M.n_t,
+                                      static_cast<int32_t>(M.rows), M.nk_pad,
+                                      reinterpret_cast<unsigned int*>(sm), reinterpret_cast<float*>(sm + o_par),
+                                      reinterpret_cast<float*>(sm + o_sc), reinterpret_cast<double*>(sm + o_isc),
+                                      sp, sp + half, st),
+               "FP16 trial split");
+    }
+    B_CUDA(cudaMemsetAsync(B.acc.p, 0, B.acc.bytes, st), "zero contraction partials");
+    {
+        PhaseScope ph(this, PH_CONTRACT_TC, st, 2 * static_cast<int>(B.f16_classes.size()));
+        for (const TcClass& c : B.f16_classes)
+            B_CUDA(launch_hess_f16_batch(static_cast<char*>(B.f16tab.p) + c.mols,
+                                         static_cast<char*>(B.f16tab.p) + c.tasks, c.n_tasks, c.ppad,
+                                         static_cast<int*>(B.f16counter.p), n_sm, tc_flush, err, st),
+                   "batched split-FP16 contraction");
     }
     PhaseScope ph(this, PH_HESS_EPILOGUE, st, static_cast<int>(n_mol));
     for (size_t m = 0; m < n_mol; ++m) {
@@ -465,6 +625,7 @@ vv10_status vv10_batch_prepare(vv10_handle h, int32_t n_mol, const int64_t* offs
     B.prepared = B.have_euw = B.have_abc = false;
     B.pair_tab_fp64 = -1;
     B.tc_classes.clear();
+    B.f16_classes.clear();
     B.hess_P.clear();
     B.mol.assign(n_mol, BatchMol());
     B.n_total = offsets[n_mol];
@@ -646,11 +807,8 @@ vv10_status vv10_batch_hessian_contract(vv10_handle h, vv10_precision prec, cons
         h->set_error("the BF16x3 Hessian contraction is not available in this library");
         return VV10_ERR_UNSUPPORTED;
     }
-    if (prec == VV10_MIXED_F16X3) {
-        h->set_error("the batched contraction runs in FP64 or split TF32");
-        return VV10_ERR_UNSUPPORTED;
-    }
-    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3) return VV10_ERR_INVALID_ARG;
+    if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_F16X3)
+        return VV10_ERR_INVALID_ARG;
     if (!P) return VV10_ERR_INVALID_ARG;
     for (size_t m = 0; m < h->batch.mol.size(); ++m)
         if (P[m] < 1 || P[m] > VV10_MAX_TRIALS) {

@@ -62,6 +62,7 @@ struct F16Layout {
     uint32_t slot_bytes;  // hi and lo tiles of one stage
     uint32_t rec_off;     // j records, 1024 B per stage
     uint32_t xm_off;      // row-maximum exchange [2][4 quads][NK][32 lanes][4 parts] floats
+    uint32_t prod_off;    // the producer thread's state
     uint32_t bar_off;
     uint32_t total;
 };
@@ -71,25 +72,44 @@ __host__ __device__ inline F16Layout f16_layout(int ppad, int nk) {
     L.slot_bytes = 2u * L.tile_bytes;
     L.rec_off = kF16Ring * L.slot_bytes;
     L.xm_off = L.rec_off + kF16Ring * 1024u;
-    L.bar_off = L.xm_off + 2u * 4u * static_cast<uint32_t>(nk) * 32u * 16u;
+    L.prod_off = L.xm_off + 2u * 4u * static_cast<uint32_t>(nk) * 32u * 16u;
+    L.bar_off = L.prod_off + 128u;
     L.total = L.bar_off + 512u + 1024u;  // barriers + slack for the 1024-B alignment
     return L;
 }
 
-struct F16Args {
-    const float4* r32a;     // row records (x, y, z, c) and (omega, kappa, p, q)
+// One system (molecule) of a launch: its records, trial tiles, factors and output.
+struct F16Mol {
+    const float4* r32a;        // row records (x, y, z, c) and (omega, kappa, p, q)
     const float4* r32b;
-    const float4* r32p;     // pair-packed column records
-    double* acc;            // [2][acc_P][nk_pad] FP64 partial output, zero on entry
-    const double* col_isc;  // [acc_P] 1/s_t per trial column
-    const float* params;    // [0] = 1/c_y
+    const float4* r32p;        // pair-packed column records
+    const CUtensorMap* maps;   // batch: its hi and lo tile maps (device memory); single: unused
+    double* acc;               // [2][acc_P][nk_pad] FP64 partial output, zero on entry
+    const double* col_isc;     // [acc_P] 1/s_t per trial column
+    const float* params;       // [0] = 1/c_y
     int64_t nk, nk_pad, acc_P;
-    int32_t Pn, t0;         // trials of this launch and the first one's row
-    int64_t n_units;
-    int32_t n_stage, chunk; // stages in all, stages per j chunk
-    int32_t flush;          // stages per FP64 flush inside a unit-chunk
+    int32_t Pn, t0;            // trials of this launch and the first one's row
+};
+// One unit of a batched launch: 128 rows of molecule `mol` x output kind.
+struct F16Task {
+    int32_t mol, row_tile, kind, pad;
+};
+struct F16Args {
+    F16Mol single;             // the system of a single-system launch
+    const F16Mol* mols;        // batch: molecule table (null for a single system)
+    const F16Task* tasks;      // batch: units, largest molecules first
+    int* counter;              // batch: next unit to take (zero on entry)
+    int64_t n_units;           // single: row tiles x kinds per tile's pass; batch: tasks
+    int32_t n_stage, chunk;    // single: stages in all, stages per j chunk
+    int32_t flush;             // stages per FP64 flush inside a unit-chunk
     int* err;
 };
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(m))
+                 : "memory");
+}
 
 __device__ __forceinline__ bool f16_wait(uint64_t* bar, uint32_t parity, int* err,
                                          volatile int* abort_flag) {
@@ -178,7 +198,8 @@ __device__ __forceinline__ void f16_split2(float2 x, float sc, uint32_t& hi, uin
     x = __fmul2_rn(x, make_float2(sc, sc));
     const __half2 h = __floats2half2_rn(x.x, x.y);
     const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(x.x - hf.x, x.y - hf.y);
+    const float2 r = __ffma2_rn(hf, make_float2(-1.0f, -1.0f), x);  // x - hi, exact
+    const __half2 l = __floats2half2_rn(r.x, r.y);
     hi = *reinterpret_cast<const uint32_t*>(&h);
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
@@ -200,22 +221,67 @@ __device__ __forceinline__ uint32_t f16_acol(int b) {
     return NK == 1 ? static_cast<uint32_t>(2 * PPAD + 64 * b) : static_cast<uint32_t>(4 * PPAD + 128 * b);
 }
 
-// Position in the CTA's walk over (j chunk, unit, stage): every role advances the same cursor.
+// Stage metadata the producer writes next to every stage it loads (the walk's single source
+// of truth: the other roles follow it).
+enum : int32_t { F16_FIRST = 1, F16_LAST = 2, F16_END = 4 };
+struct F16Meta {
+    int32_t mol, row_tile, kind, flags;
+};
+
+// The producer's position in the walk.  Single system: (j chunk c, unit u, stage s), units
+// u = blockIdx.x + k gridDim.x inside every chunk.  Batch: (task q, stage s), tasks taken
+// from an atomic counter, largest molecules first.
 struct F16Cursor {
     int c, s, s0, s1;
     int64_t u;
+    int32_t mol, row_tile, kind;
     bool done;
 };
+// The producer thread's state (shared memory).
+struct F16Prod {
+    F16Cursor k;
+    int64_t issued;
+    int32_t slot, mol;
+    uint32_t ph, end;
+};
+
+// Batch: the next task from the CTAs' shared counter (false once every task is taken).
+__device__ __forceinline__ bool f16_next_task(F16Cursor& k, const F16Args& a) {
+    const int64_t q = atomicAdd(a.counter, 1);
+    if (q >= a.n_units) return false;
+    const F16Task t = a.tasks[q];
+    k.u = q;
+    k.mol = t.mol;
+    k.row_tile = t.row_tile;
+    k.kind = t.kind;
+    k.s0 = 0;
+    k.s1 = static_cast<int>(a.mols[t.mol].nk_pad / kF16Kj);  // tasks exist for kept points only
+    k.s = 0;
+    return true;
+}
+template <int NK>
 __device__ __forceinline__ void f16_cursor_init(F16Cursor& k, const F16Args& a) {
     k.c = 0;
+    k.mol = 0;
+    if (a.mols) {
+        k.done = !f16_next_task(k, a);
+        return;
+    }
     k.u = blockIdx.x;
+    k.row_tile = static_cast<int32_t>(NK == 2 ? k.u : (k.u >> 1));
+    k.kind = NK == 2 ? 0 : static_cast<int32_t>(k.u & 1);
     k.s0 = 0;
     k.s1 = min(a.n_stage, a.chunk);
     k.s = 0;
     k.done = (k.u >= a.n_units) || (a.n_stage <= 0);
 }
+template <int NK>
 __device__ __forceinline__ void f16_cursor_next(F16Cursor& k, const F16Args& a) {
     if (++k.s < k.s1) return;
+    if (a.mols) {
+        k.done = !f16_next_task(k, a);
+        return;
+    }
     k.u += gridDim.x;
     if (k.u >= a.n_units) {
         k.u = blockIdx.x;
@@ -227,6 +293,8 @@ __device__ __forceinline__ void f16_cursor_next(F16Cursor& k, const F16Args& a) 
         }
         k.s1 = min(a.n_stage, k.s0 + a.chunk);
     }
+    k.row_tile = static_cast<int32_t>(NK == 2 ? k.u : (k.u >> 1));
+    k.kind = NK == 2 ? 0 : static_cast<int32_t>(k.u & 1);
     k.s = k.s0;
 }
 
@@ -250,6 +318,7 @@ k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CU
     uint64_t* fin = bars + 2 * kF16Ring + 12;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kF16Ring + 13);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kF16Ring + 14);
+    F16Meta* meta = reinterpret_cast<F16Meta*>(bars + 2 * kF16Ring + 16);  // [kF16Ring]
     float* xm = reinterpret_cast<float*>(smem + L.xm_off);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -277,40 +346,72 @@ k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CU
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // ---------------------------------------------------------------- producer cursor
-    // (lane 0 of kF16ProducerWarp) keeps the ring kF16Ring - 1 stages ahead of the walk
-    F16Cursor pk;
-    f16_cursor_init(pk, args);
-    int p_slot = 0;
-    uint32_t p_ph = 0;
-    int64_t issued = 0;
+    // ---------------------------------------------------------------- producer (one thread)
+    // keeps the ring kF16Ring - 1 stages ahead of the walk; every stage's copies complete on
+    // its b_full barrier together with the producer's arrival, which releases the metadata.
+    // Its state lives in shared memory (only one thread touches it), not in every thread's
+    // registers.
+    F16Prod* pr = reinterpret_cast<F16Prod*>(smem + L.prod_off);
     bool ok = true;
-    auto produce = [&]() -> bool {  // issue the next stage's copies, if any
-        if (pk.done) return true;
-        if (!f16_wait(&b_empty[p_slot], p_ph ^ 1u, args.err, abort_flag)) return false;
-        uint8_t* base = smem + p_slot * L.slot_bytes;
-        uint8_t* rec = smem + L.rec_off + p_slot * 1024;
-        mbar_expect_tx(&b_full[p_slot], L.slot_bytes + 1024u);
-        bulk_g2s(rec, args.r32p + 2 * kF16Kj * static_cast<int64_t>(pk.s), 1024u, &b_full[p_slot]);
-        tc::tma_load_2d(base, &tm_bh, 64 * pk.s, args.t0, &b_full[p_slot]);
-        tc::tma_load_2d(base + L.tile_bytes, &tm_bl, 64 * pk.s, args.t0, &b_full[p_slot]);
-        ++issued;
-        if (++p_slot == kF16Ring) {
-            p_slot = 0;
-            p_ph ^= 1u;
+    auto produce = [&]() -> bool {
+        F16Prod& P = *pr;
+        if (P.end) return true;
+        if (!f16_wait(&b_empty[P.slot], P.ph ^ 1u, args.err, abort_flag)) return false;
+        if (P.k.done) {  // the end of the walk takes one slot, with no copies
+            meta[P.slot] = F16Meta{0, 0, 0, F16_END};
+            mbar_arrive(&b_full[P.slot]);
+            P.end = 1;
+            return true;
         }
-        f16_cursor_next(pk, args);
+        const F16Mol& M = args.mols ? args.mols[P.k.mol] : args.single;
+        const CUtensorMap* mh = &tm_bh;
+        const CUtensorMap* ml = &tm_bl;
+        if (args.mols) {
+            mh = M.maps;
+            ml = M.maps + 1;
+            if (P.k.mol != P.mol) {  // a new molecule's tensor maps
+                P.mol = P.k.mol;
+                tmap_acquire(mh);
+                tmap_acquire(ml);
+                tc::prefetch_tmap(mh);
+                tc::prefetch_tmap(ml);
+            }
+        }
+        const int s = P.k.s;
+        meta[P.slot] = F16Meta{P.k.mol, P.k.row_tile, P.k.kind,
+                               (s == P.k.s0 ? F16_FIRST : 0) | (s == P.k.s1 - 1 ? F16_LAST : 0)};
+        uint8_t* base = smem + P.slot * L.slot_bytes;
+        uint8_t* rec = smem + L.rec_off + P.slot * 1024;
+        mbar_expect_tx(&b_full[P.slot], L.slot_bytes + 1024u);
+        bulk_g2s(rec, M.r32p + 2 * kF16Kj * static_cast<int64_t>(s), 1024u, &b_full[P.slot]);
+        tc::tma_load_2d(base, mh, 64 * s, M.t0, &b_full[P.slot]);
+        tc::tma_load_2d(base + L.tile_bytes, ml, 64 * s, M.t0, &b_full[P.slot]);
+        ++P.issued;
+        if (++P.slot == kF16Ring) {
+            P.slot = 0;
+            P.ph ^= 1u;
+        }
+        f16_cursor_next<NK>(P.k, args);
         return true;
     };
     if (is_producer) {
-        tc::prefetch_tmap(&tm_bh);
-        tc::prefetch_tmap(&tm_bl);
+        F16Prod& P = *pr;
+        P.slot = 0;
+        P.ph = 0;
+        P.end = 0;
+        P.mol = -1;
+        P.issued = 0;
+        f16_cursor_init<NK>(P.k, args);
+        if (!args.mols) {
+            tc::prefetch_tmap(&tm_bh);
+            tc::prefetch_tmap(&tm_bl);
+        }
         for (int k = 0; k < kF16Ring - 1 && ok; ++k) ok = produce();
+        if (!ok) *abort_flag = 1;
     }
 
     const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
     const uint32_t idesc = tc::idesc_f16(128, PPAD);
-    const float inv_cy = args.params[0];
     float acc[NK][PQ];
 #pragma unroll
     for (int k = 0; k < NK; ++k)
@@ -347,19 +448,20 @@ k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CU
         tc::fence_before();
         return true;
     };
-    // Add the registers into the FP64 partial output (times 1/s_t; the gamma accumulator
-    // holds -(T3 u + T4 y)) and clear them.
-    auto flush = [&](int kind0, int64_t i) {
+    // Add the registers into the molecule's FP64 partial output (times 1/s_t; the gamma
+    // accumulator holds -(T3 u + T4 y)) and clear them.
+    auto flush = [&](int mol, int kind0, int64_t i) {
+        const F16Mol& M = args.mols ? args.mols[mol] : args.single;
 #pragma unroll
         for (int k = 0; k < NK; ++k) {
             const int kind = NK == 2 ? k : kind0;
 #pragma unroll
             for (int c = 0; c < PQ; ++c) {
                 const int t = part * PQ + c;
-                if (i < args.nk && t < args.Pn) {
-                    const int64_t tg = static_cast<int64_t>(args.t0) + t;
-                    double* o = args.acc + ((static_cast<int64_t>(kind) * args.acc_P + tg) * args.nk_pad + i);
-                    const double v = static_cast<double>(acc[k][c]) * args.col_isc[tg];
+                if (i < M.nk && t < M.Pn) {
+                    const int64_t tg = static_cast<int64_t>(M.t0) + t;
+                    double* o = M.acc + ((static_cast<int64_t>(kind) * M.acc_P + tg) * M.nk_pad + i);
+                    const double v = static_cast<double>(acc[k][c]) * M.col_isc[tg];
                     *o += (kind == 0) ? v : -v;
                 }
                 acc[k][c] = 0.0f;
@@ -376,173 +478,162 @@ k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CU
     float isc_prev[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) isc_prev[k] = 1.0f;
-    F16Cursor wk;
-    f16_cursor_init(wk, args);
-    ok = __all_sync(0xffffffffu, ok);
-    while (!wk.done && ok) {
-        // ---- one unit-chunk: rows of `row_tile`, stages [s0, s1)
-        const int64_t row_tile = NK == 2 ? wk.u : (wk.u >> 1);
-        const int kind0 = NK == 2 ? 0 : static_cast<int>(wk.u & 1);
-        const int64_t i = row_tile * 128 + quad * 32 + lane;
-        const int s0 = wk.s0, s1 = wk.s1;
-        float xi = 0.f, yi = 0.f, zi = 0.f, oi = 1.f, ki = 1.f, pi_ = 0.f, qi = 0.f;
-        if (i < args.nk) {
-            const float4 a = args.r32a[i];
-            const float4 b = args.r32b[i];
-            xi = a.x; yi = a.y; zi = a.z; oi = b.x; ki = b.y; pi_ = b.z; qi = b.w;
+    // the current unit: molecule, output kind, row, row data, 1/c_y
+    int mol = 0, kind0 = 0, until_flush = args.flush;
+    int64_t i = 0;
+    float inv_cy = 1.f;
+    RowF rc{0.f, 0.f, 0.f, 1.f, 1.f, 0.f, 0.f};
+    ok = __all_sync(0xffffffffu, !*abort_flag);
+    while (ok) {
+        // the operand buffer ab is free once the MMAs of the stage two back are done
+        bool got = f16_wait(&b_full[slot], ph, args.err, abort_flag);
+        got = got && f16_wait(&mma_done[ab], aph ^ 1u, args.err, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) break;
+        tc::fence_after();
+        const F16Meta m = meta[slot];
+        if (m.flags & F16_END) break;
+        if (m.flags & F16_FIRST) {  // a new unit: its rows and molecule
+            mol = m.mol;
+            kind0 = NK == 2 ? 0 : m.kind;
+            const F16Mol& M = args.mols ? args.mols[mol] : args.single;
+            i = static_cast<int64_t>(m.row_tile) * 128 + quad * 32 + lane;
+            float xi = 0.f, yi = 0.f, zi = 0.f, oi = 1.f, ki = 1.f, pi_ = 0.f, qi = 0.f;
+            if (i < M.nk) {
+                const float4 a4 = M.r32a[i];
+                const float4 b4 = M.r32b[i];
+                xi = a4.x; yi = a4.y; zi = a4.z; oi = b4.x; ki = b4.y; pi_ = b4.z; qi = b4.w;
+            }
+            rc = RowF{xi, yi, zi, oi, ki, -pi_, -qi};
+            inv_cy = M.params[0];
+            until_flush = args.flush;
         }
-        const RowF rc{xi, yi, zi, oi, ki, -pi_, -qi};
-        int until_flush = args.flush;
-        for (int s = s0; s < s1; ++s) {
-            // the operand buffer ab is free once the MMAs of the stage two back are done
-            bool got = f16_wait(&b_full[slot], ph, args.err, abort_flag);
-            got = got && f16_wait(&mma_done[ab], aph ^ 1u, args.err, abort_flag);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
+        // this warp's 8 j: pair-packed records 4 part .. 4 part + 3
+        const float4* rec = reinterpret_cast<const float4*>(smem + L.rec_off + slot * 1024);
+        float2 t[4][2 * NK];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float4* v = rec + 4 * (4 * part + h);
+            f16_tiles2<NK>(kind0, rc, v[0], v[1], v[2], v[3], t[h]);
+#pragma unroll
+            for (int k = 0; k < NK; ++k)  // the tiles that multiply y carry 1/c_y
+                t[h][2 * k + 1] = __fmul2_rn(t[h][2 * k + 1], make_float2(inv_cy, inv_cy));
+        }
+        // the row's largest |T| over the stage: this thread's 8 j, then the quad's 4 parts
+        const int xs = static_cast<int>(gs & 1u);
+        float* xrow = xm + (static_cast<size_t>((xs * 4 + quad) * NK) * 32 + lane) * 4;
+#pragma unroll
+        for (int k = 0; k < NK; ++k)
+            xrow[k * 32 * 4 + part] = fmaxf(fmaxf(f16_absmax4(t[0][2 * k], t[1][2 * k]),
+                                                  f16_absmax4(t[2][2 * k], t[3][2 * k])),
+                                            fmaxf(f16_absmax4(t[0][2 * k + 1], t[1][2 * k + 1]),
+                                                  f16_absmax4(t[2][2 * k + 1], t[3][2 * k + 1])));
+        __syncwarp();  // the warp's 32 stores are ordered before lane 0's release
+        if (lane == 0) mbar_arrive(&xbar[xs * 4 + quad]);
+        got = f16_wait(&xbar[xs * 4 + quad], (gs >> 1) & 1u, args.err, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) break;
+        float sc[NK], isc[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const float4 q = *reinterpret_cast<const float4*>(xrow + k * 32 * 4);
+            f16_scale(fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)), sc[k], isc[k]);
+        }
+        // scaled FP16 hi / lo operand tiles of kind k: [hi Ta | lo Ta | hi Tb | lo Tb], 16
+        // columns each; this warp's 8 j are columns 4 part .. 4 part + 3
+        const uint32_t a = tmem + lane_off + f16_acol<NK, PPAD>(ab) + 4 * part;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) f16_split2(t[h][2 * k + b], sc[k], hw[h], lw[h]);
+                tc::st_x4(a + 64u * k + 32u * b, hw);
+                tc::st_x4(a + 64u * k + 32u * b + 16u, lw);
             }
-            tc::fence_after();
-            // this warp's 8 j: pair-packed records 4 part .. 4 part + 3
-            const float4* rec = reinterpret_cast<const float4*>(smem + L.rec_off + slot * 1024);
-            float2 t[4][2 * NK];
+        }
+        tc::wait_st();
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[ab]);  // this warp's operands are in place
+        // ---- MMA issue (one thread): this stage, once every warp's operands are in place
+        if (is_mma) {
+            bool go = f16_wait(&a_full[ab], aph, args.err, abort_flag);
+            if (go) {
+                tc::fence_after();
+                const uint32_t base = smem_u32(smem + slot * L.slot_bytes);
+                const uint64_t bh = tc::sdesc_kmajor_sw128(base);
+                const uint64_t bl = tc::sdesc_kmajor_sw128(base + L.tile_bytes);
+                // trial rows: [u (16 j) | y (16 j)] for the stage's two halves, 32 B each; a
+                // K-step moves the descriptor's address field by 32 B (2 units)
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float4* v = rec + 4 * (4 * part + h);
-                f16_tiles2<NK>(kind0, rc, v[0], v[1], v[2], v[3], t[h]);
+                for (int k = 0; k < NK; ++k) {
+                    const uint32_t d = tmem + f16_dcol<NK, PPAD>(NK == 2 ? k : kind0, ab);
+                    const uint32_t aa = tmem + f16_acol<NK, PPAD>(ab) + 64u * k;
+                    // operand tiles: Ta hi | Ta lo | Tb hi | Tb lo, 16 columns each (8 per
+                    // 16-j half).  The small products first (the accumulator truncates its
+                    // adds), the four hi*hi last.
 #pragma unroll
-                for (int k = 0; k < NK; ++k)  // the tiles that multiply y carry 1/c_y
-                    t[h][2 * k + 1] = __fmul2_rn(t[h][2 * k + 1], make_float2(inv_cy, inv_cy));
-            }
-            // the row's largest |T| over the stage: this thread's 4 j, then the quad's 4 parts
-            const int xs = static_cast<int>(gs & 1u);
-            float* xrow = xm + (static_cast<size_t>((xs * 4 + quad) * NK) * 32 + lane) * 4;
-#pragma unroll
-            for (int k = 0; k < NK; ++k)
-                xrow[k * 32 * 4 + part] = fmaxf(fmaxf(f16_absmax4(t[0][2 * k], t[1][2 * k]),
-                                                      f16_absmax4(t[2][2 * k], t[3][2 * k])),
-                                                fmaxf(f16_absmax4(t[0][2 * k + 1], t[1][2 * k + 1]),
-                                                      f16_absmax4(t[2][2 * k + 1], t[3][2 * k + 1])));
-            __syncwarp();  // the warp's 32 stores are ordered before lane 0's release
-            if (lane == 0) mbar_arrive(&xbar[xs * 4 + quad]);
-            got = f16_wait(&xbar[xs * 4 + quad], (gs >> 1) & 1u, args.err, abort_flag);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
-            }
-            float sc[NK], isc[NK];
-#pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                const float4 q = *reinterpret_cast<const float4*>(xrow + k * 32 * 4);
-                f16_scale(fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)), sc[k], isc[k]);
-            }
-            // scaled FP16 hi / lo operand tiles of kind k: [hi Ta | lo Ta | hi Tb | lo Tb], 16
-            // columns each; this warp's 8 j are columns 4 part .. 4 part + 3
-            const uint32_t a = tmem + lane_off + f16_acol<NK, PPAD>(ab) + 4 * part;
-#pragma unroll
-            for (int k = 0; k < NK; ++k) {
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    uint32_t hw[4], lw[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) f16_split2(t[h][2 * k + b], sc[k], hw[h], lw[h]);
-                    tc::st_x4(a + 64u * k + 32u * b, hw);
-                    tc::st_x4(a + 64u * k + 32u * b + 16u, lw);
-                }
-            }
-            tc::wait_st();
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[ab]);  // this warp's operands are in place
-            // ---- MMA issue (one thread): this stage, once every warp's operands are in place
-            if (is_mma) {
-                bool go = f16_wait(&a_full[ab], aph, args.err, abort_flag);
-                go = go && f16_wait(&b_full[slot], ph, args.err, abort_flag);
-                if (go) {
-                    tc::fence_after();
-                    const uint32_t base = smem_u32(smem + slot * L.slot_bytes);
-                    const uint64_t bh = tc::sdesc_kmajor_sw128(base);
-                    const uint64_t bl = tc::sdesc_kmajor_sw128(base + L.tile_bytes);
-                    // trial rows: [u (16 j) | y (16 j)] for the stage's two halves, 32 B each;
-                    // a K-step moves the descriptor's address field by 32 B (2 units)
-#pragma unroll
-                    for (int k = 0; k < NK; ++k) {
-                        const uint32_t d = tmem + f16_dcol<NK, PPAD>(NK == 2 ? k : kind0, ab);
-                        const uint32_t aa = tmem + f16_acol<NK, PPAD>(ab) + 64u * k;
-                        // operand tiles: Ta hi | Ta lo | Tb hi | Tb lo, 16 columns each (8 per
-                        // 16-j half).  The small products first (the accumulator truncates its
-                        // adds), the four hi*hi last.
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const uint64_t ku = 4u * hh, ky = 4u * hh + 2u;
-                            tc::mma_f16_ts(d, aa + 0 + 8 * hh, bl + ku, idesc, hh);   // Ta_hi u_lo
-                            tc::mma_f16_ts(d, aa + 16 + 8 * hh, bh + ku, idesc, 1u);  // Ta_lo u_hi
-                            tc::mma_f16_ts(d, aa + 32 + 8 * hh, bl + ky, idesc, 1u);  // Tb_hi y_lo
-                            tc::mma_f16_ts(d, aa + 48 + 8 * hh, bh + ky, idesc, 1u);  // Tb_lo y_hi
-                        }
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const uint64_t ku = 4u * hh, ky = 4u * hh + 2u;
-                            tc::mma_f16_ts(d, aa + 0 + 8 * hh, bh + ku, idesc, 1u);   // Ta_hi u_hi
-                            tc::mma_f16_ts(d, aa + 32 + 8 * hh, bh + ky, idesc, 1u);  // Tb_hi y_hi
-                        }
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint64_t ku = 4u * hh, ky = 4u * hh + 2u;
+                        tc::mma_f16_ts(d, aa + 0 + 8 * hh, bl + ku, idesc, hh);   // Ta_hi u_lo
+                        tc::mma_f16_ts(d, aa + 16 + 8 * hh, bh + ku, idesc, 1u);  // Ta_lo u_hi
+                        tc::mma_f16_ts(d, aa + 32 + 8 * hh, bl + ky, idesc, 1u);  // Tb_hi y_lo
+                        tc::mma_f16_ts(d, aa + 48 + 8 * hh, bh + ky, idesc, 1u);  // Tb_lo y_hi
                     }
-                    tc::commit(&mma_done[ab]);  // the ring slot is released after the drains
-                    mma_any = true;
-                }
-            }
-            if (!__all_sync(0xffffffffu, !*abort_flag)) {
-                ok = false;
-                break;
-            }
-            // ---- drain the previous stage while this stage's MMAs run; then one more copy
-            // (one per drained stage: the ring slot it fills was drained a stage earlier)
-            if (s > s0) {
-                if (!drain(dbuf, dph, kind0, isc_prev)) {
-                    ok = false;
-                    break;
-                }
-                if (lane == 0) mbar_arrive(&b_empty[pslot]);
-                if (--until_flush == 0) {
-                    flush(kind0, i);
-                    until_flush = args.flush;
-                }
-                if (is_producer && !produce()) *abort_flag = 1;
-                if (!__all_sync(0xffffffffu, !*abort_flag)) {
-                    ok = false;
-                    break;
-                }
-            }
 #pragma unroll
-            for (int k = 0; k < NK; ++k) isc_prev[k] = isc[k];
-            dbuf = ab;
-            dph = aph;
-            pslot = slot;
-            if (++slot == kF16Ring) {
-                slot = 0;
-                ph ^= 1u;
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint64_t ku = 4u * hh, ky = 4u * hh + 2u;
+                        tc::mma_f16_ts(d, aa + 0 + 8 * hh, bh + ku, idesc, 1u);   // Ta_hi u_hi
+                        tc::mma_f16_ts(d, aa + 32 + 8 * hh, bh + ky, idesc, 1u);  // Tb_hi y_hi
+                    }
+                }
+                tc::commit(&mma_done[ab]);  // the ring slot is released after the drains
+                mma_any = true;
             }
-            ab ^= 1;
-            if (ab == 0) aph ^= 1u;
-            ++gs;
         }
-        if (!ok) break;
-        if (!drain(dbuf, dph, kind0, isc_prev)) {
-            ok = false;
-            break;
-        }
-        if (lane == 0) mbar_arrive(&b_empty[pslot]);
-        if (is_producer && !produce()) *abort_flag = 1;
-        flush(kind0, i);
         if (!__all_sync(0xffffffffu, !*abort_flag)) break;
-        // next unit-chunk
-        wk.s = s1 - 1;
-        f16_cursor_next(wk, args);
+        // ---- drain the previous stage of this unit while this stage's MMAs run; then one
+        // more copy (one per drained stage: the slot it fills was drained a stage earlier)
+        if (!(m.flags & F16_FIRST)) {
+            if (!drain(dbuf, dph, kind0, isc_prev)) break;
+            if (lane == 0) mbar_arrive(&b_empty[pslot]);
+            if (--until_flush == 0) {
+                flush(mol, kind0, i);
+                until_flush = args.flush;
+            }
+            if (is_producer && !produce()) *abort_flag = 1;
+            if (!__all_sync(0xffffffffu, !*abort_flag)) break;
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) isc_prev[k] = isc[k];
+        dbuf = ab;
+        dph = aph;
+        pslot = slot;
+        if (++slot == kF16Ring) {
+            slot = 0;
+            ph ^= 1u;
+        }
+        ab ^= 1;
+        if (ab == 0) aph ^= 1u;
+        ++gs;
+        if (m.flags & F16_LAST) {  // the unit's last stage: drain it and write the rows out
+            if (!drain(dbuf, dph, kind0, isc_prev)) break;
+            if (lane == 0) mbar_arrive(&b_empty[pslot]);
+            if (is_producer && !produce()) *abort_flag = 1;
+            flush(mol, kind0, i);
+            if (!__all_sync(0xffffffffu, !*abort_flag)) break;
+        }
     }
     tc::wait_st();  // nothing of ours is in flight to TMEM on any exit path
     tc::wait_ld();
-    if (is_producer)  // copies in flight must land before the CTA exits
-        for (int64_t k = (issued > kF16Ring ? issued - kF16Ring : 0); k < issued; ++k)
+    if (is_producer) {  // copies in flight must land before the CTA exits
+        // (after the end marker, its slot's previous stage was drained before it was written,
+        // and that slot's parity has moved on: wait for the other ring slots only)
+        const int64_t issued = pr->issued;
+        const int64_t back = pr->end ? kF16Ring - 1 : kF16Ring;
+        for (int64_t k = (issued > back ? issued - back : 0); k < issued; ++k)
             mbar_wait(&b_full[k % kF16Ring], static_cast<uint32_t>((k / kF16Ring) & 1), args.err);
+    }
     if (is_mma && mma_any) {  // every MMA finished before TMEM is released
         tc::commit(fin);
         mbar_wait(fin, 0, args.err);
@@ -715,6 +806,19 @@ static cudaError_t launch_f16_t(const CUtensorMap* maps, const F16Args& a, int n
     return cudaGetLastError();
 }
 
+static cudaError_t launch_f16_dispatch(int ppad, const CUtensorMap* maps, const F16Args& a, int n_sm,
+                                       cudaStream_t st) {
+    switch (ppad / 4) {
+        case 8: return launch_f16_t<8, 2>(maps, a, n_sm, st);
+        case 16: return launch_f16_t<16, 2>(maps, a, n_sm, st);
+        case 24: return launch_f16_t<24, 1>(maps, a, n_sm, st);
+        case 32: return launch_f16_t<32, 1>(maps, a, n_sm, st);
+        case 40: return launch_f16_t<40, 1>(maps, a, n_sm, st);
+        case 48: return launch_f16_t<48, 1>(maps, a, n_sm, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 int hess_f16_kinds_per_tile(int ppad) { return ppad <= 64 ? 2 : 1; }
 
 // Contract the trials [t0, t0 + Pn) (Pn <= 192) of one system; the split arrays have `rows`
@@ -731,17 +835,8 @@ cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t 
         return cudaErrorInvalidValue;
     const int nk_t = hess_f16_kinds_per_tile(ppad);
     F16Args a;
-    a.r32a = p.r32a;
-    a.r32b = p.r32b;
-    a.r32p = p.r32p;
-    a.acc = acc;
-    a.col_isc = col_isc;
-    a.params = params;
-    a.nk = p.nk;
-    a.nk_pad = p.nk_pad;
-    a.acc_P = acc_P;
-    a.Pn = Pn;
-    a.t0 = t0;
+    memset(&a, 0, sizeof(a));
+    a.single = F16Mol{p.r32a, p.r32b, p.r32p, nullptr, acc, col_isc, params, p.nk, p.nk_pad, acc_P, Pn, t0};
     a.n_units = (nk_t == 2 ? 1 : 2) * ((p.nk + 127) / 128);
     a.n_stage = static_cast<int32_t>(p.nk_pad / kF16Kj);
     const size_t stage_bytes = 2u * static_cast<size_t>(ppad) * 128u + 1024u;
@@ -750,15 +845,53 @@ cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t 
     a.chunk = static_cast<int32_t>(chunk < a.n_stage ? chunk : a.n_stage);
     a.flush = flush > 0 ? flush : 512;
     a.err = err;
-    switch (ppad / 4) {
-        case 8: return launch_f16_t<8, 2>(maps, a, n_sm, st);
-        case 16: return launch_f16_t<16, 2>(maps, a, n_sm, st);
-        case 24: return launch_f16_t<24, 1>(maps, a, n_sm, st);
-        case 32: return launch_f16_t<32, 1>(maps, a, n_sm, st);
-        case 40: return launch_f16_t<40, 1>(maps, a, n_sm, st);
-        case 48: return launch_f16_t<48, 1>(maps, a, n_sm, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_f16_dispatch(ppad, maps, a, n_sm, st);
+}
+
+// ---------------------------------------------------------------- batched launches
+
+size_t hess_f16_mol_bytes() { return sizeof(F16Mol); }
+size_t hess_f16_task_bytes() { return sizeof(F16Task); }
+
+// Tensor maps of one molecule (hi, lo: 2 consecutive CUtensorMap).
+bool hess_f16_make_maps(void* out2, const void* bh, const void* bl, int64_t nk_pad, int64_t rows,
+                        int ppad) {
+    CUtensorMap* m = static_cast<CUtensorMap*>(out2);
+    return f16_make_map(&m[0], bh, nk_pad, rows, ppad) && f16_make_map(&m[1], bl, nk_pad, rows, ppad);
+}
+
+void hess_f16_fill_mol(void* dst, const float4* r32a, const float4* r32b, const float4* r32p,
+                       const void* maps_dev, double* acc, const double* col_isc,
+                       const float* params, int64_t nk, int64_t nk_pad, int64_t acc_P, int32_t Pn,
+                       int32_t t0) {
+    const F16Mol m{r32a, r32b, r32p, static_cast<const CUtensorMap*>(maps_dev), acc, col_isc, params,
+                   nk, nk_pad, acc_P, Pn, t0};
+    memcpy(dst, &m, sizeof(m));
+}
+
+void hess_f16_fill_task(void* dst, int32_t mol, int32_t row_tile, int32_t kind) {
+    const F16Task t{mol, row_tile, kind, 0};
+    memcpy(dst, &t, sizeof(t));
+}
+
+// Batched contraction: every task of the table shares `ppad`; molecules, tasks and tensor
+// maps live in device memory (written before the launch); counter: one int, zeroed here.
+cudaError_t launch_hess_f16_batch(const void* mols, const void* tasks, int64_t n_tasks, int ppad,
+                                  int* counter, int n_sm, int flush, int* err, cudaStream_t st) {
+    if (n_tasks <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    CUtensorMap unused[2];
+    memset(unused, 0, sizeof(unused));
+    F16Args a;
+    memset(&a, 0, sizeof(a));
+    a.mols = static_cast<const F16Mol*>(mols);
+    a.tasks = static_cast<const F16Task*>(tasks);
+    a.counter = counter;
+    a.n_units = n_tasks;
+    a.flush = flush > 0 ? flush : 512;
+    a.err = err;
+    return launch_f16_dispatch(ppad, unused, a, n_sm, st);
 }
 
 }  // namespace vv10

@@ -146,6 +146,19 @@ cudaError_t launch_f16_trial_split(const double* u, const double* y, int32_t P, 
                                    float* scale, double* col_isc, void* bh, void* bl,
                                    cudaStream_t st);
 int hess_f16_kinds_per_tile(int ppad);
+// Batched split-FP16 contraction over a task table (one launch per padded width): tasks
+// (molecule, 128-row tile, kind) largest molecules first, taken from an atomic counter.
+size_t hess_f16_mol_bytes();
+size_t hess_f16_task_bytes();
+bool hess_f16_make_maps(void* out2 /* 2 CUtensorMap */, const void* bh, const void* bl,
+                        int64_t nk_pad, int64_t rows, int ppad);
+void hess_f16_fill_mol(void* dst, const float4* r32a, const float4* r32b, const float4* r32p,
+                       const void* maps_dev, double* acc, const double* col_isc,
+                       const float* params, int64_t nk, int64_t nk_pad, int64_t acc_P, int32_t Pn,
+                       int32_t t0);
+void hess_f16_fill_task(void* dst, int32_t mol, int32_t row_tile, int32_t kind);
+cudaError_t launch_hess_f16_batch(const void* mols, const void* tasks, int64_t n_tasks, int ppad,
+                                  int* counter, int n_sm, int flush, int* err, cudaStream_t st);
 cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
                             const void* bh, const void* bl, int64_t rows, const double* col_isc,
                             const float* params, int n_sm, int flush, double* acc, int* err,

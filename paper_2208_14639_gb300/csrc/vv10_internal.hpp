@@ -69,7 +69,9 @@ struct BatchMol {
     int ng = 1, pg = 0, ppad = 0;  // tensor-core groups of <= 192 trials, padded group width
     int64_t rows = 0;            // rows of each trial split ((ng - 1) pg + ppad)
     size_t rt = 0, gt = 0;       // rho^t, gamma^t at kept points (n_t x nk doubles each)
-    size_t split = 0;            // four FP32 [rows][nk_pad] trial splits
+    size_t split = 0;            // four FP32 [rows][nk_pad] trial splits (split TF32), or the
+                                 // FP16 hi / lo tiles [rows][2 nk_pad] (split FP16)
+    size_t f16small = 0;         // split FP16: column maxima, factors, y balance
     size_t acc = 0;              // FP64 [2][n_t][nk_pad] contraction partials
 };
 
@@ -93,6 +95,8 @@ struct BatchState {
     std::vector<int32_t> hess_P;
     DevBuf rtgt, splits, acc, maps, tc_tab;
     std::vector<TcClass> tc_classes;
+    DevBuf f16small, f16tab, f16counter;  // split-FP16 layout (shares rtgt, splits, acc, maps)
+    std::vector<TcClass> f16_classes;
     // graph of a whole batched pass, and what it was captured for
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
@@ -178,6 +182,9 @@ struct vv10_ctx {
     vv10_status batch_hess(vv10_precision prec, const int32_t* P, const double* rho_t,
                            const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
                            cudaStream_t st);
+    vv10_status batch_hess_f16(bool same_P, const int32_t* P, const double* rho_t,
+                               const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
+                               cudaStream_t st);
     void batch_release();
     void batch_drop_graph();
 

@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 
 FP64 = vv10.VV10_FP64
 MIXED = vv10.VV10_MIXED_TF32X3
-TOL = {FP64: (1e-11, 1e-10), MIXED: (1e-7, 1e-6)}  # (energy, arrays)
+F16 = vv10.VV10_MIXED_F16X3
+TOL = {FP64: (1e-11, 1e-10), MIXED: (1e-7, 1e-6), F16: (1e-7, 1e-6)}  # (energy, arrays)
+PRECS = pytest.mark.parametrize("prec", [FP64, MIXED, F16], ids=["fp64", "tf32x3", "f16x3"])
 
 
 def rel(a, b):
@@ -115,7 +117,7 @@ def oracle_refs(oracle_mod):
     return refs
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+@PRECS
 def test_batch_matches_oracle(dev, oracle_refs, prec):
     systems, Ps = small_batch()
     b = Batch(systems, Ps, dev)
@@ -140,7 +142,7 @@ def test_batch_matches_oracle(dev, oracle_refs, prec):
         vv10.vv10_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+@PRECS
 def test_batch_matches_single_system_path(dev, prec):
     systems, Ps = small_batch()
     b = Batch(systems, Ps, dev, seed=3)
@@ -174,7 +176,7 @@ def test_batch_matches_single_system_path(dev, prec):
         vv10.vv10_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+@PRECS
 def test_batch_run_graph_replay(dev, prec):
     """vv10_batch_run: the first call runs eagerly and records a graph; replays read the
     current contents of the same buffers (the contraction is linear in the trials)."""
@@ -260,7 +262,8 @@ def test_batch_without_atom_labels(dev, oracle_refs):
 
 def test_batch_64_molecules_sampled_rows(dev, oracle_mod):
     """The batch of 64 molecules (3-30 atoms, 50 x 194 points per atom, 9.7k-291k points,
-    P = 3 N_atom), mixed precision through one recorded graph, as timed by the benchmark;
+    P = 3 N_atom), mixed precision (split TF32 and split FP16) through recorded graphs, as
+    timed by the benchmark;
     energies of the four smallest molecules in full and 16 sampled rows of the potential
     and of the Hessian contraction of the smallest, a middle and the largest molecule
     against the oracle."""
@@ -294,6 +297,15 @@ def test_batch_64_molecules_sampled_rows(dev, oracle_mod):
         for _ in range(2):  # record, then replay
             vv10.vv10_batch_run(h, MIXED, Ps, rt, gt, E, vr, vg, fr, fg)
         vv10.vv10_sync(h)
+        # the split-FP16 contraction of the same batch (its own recorded graph) against the
+        # split-TF32 one, every molecule and element (both within 1e-6 of the oracle)
+        fr16 = torch.empty_like(fr)
+        fg16 = torch.empty_like(fg)
+        for _ in range(2):
+            vv10.vv10_batch_run(h, F16, Ps, rt, gt, E, vr, vg, fr16, fg16)
+        vv10.vv10_sync(h)
+        assert rel(fr16.cpu().numpy(), fr.cpu().numpy()) <= 1e-6
+        assert rel(fg16.cpu().numpy(), fg.cpu().numpy()) <= 1e-6
         order = np.argsort(n, kind="stable")
         for m in order[:4]:
             g = systems[m]
@@ -311,7 +323,8 @@ def test_batch_64_molecules_sampled_rows(dev, oracle_mod):
             rt_m = rt[s:e].view(Ps[m], n[m]).cpu().numpy()
             gt_m = gt[s:e].view(Ps[m], n[m], 3).cpu().numpy()
             r_fr, r_fg = oracle_mod.hessian_contract(*args, rt_m, gt_m, rows=rows)
-            assert rel(fr[s:e].view(Ps[m], n[m])[:, rows].cpu().numpy(), r_fr) <= 1e-6
-            assert rel(fg[s:e].view(Ps[m], n[m])[:, rows].cpu().numpy(), r_fg) <= 1e-6
+            for f_r, f_g in ((fr, fg), (fr16, fg16)):
+                assert rel(f_r[s:e].view(Ps[m], n[m])[:, rows].cpu().numpy(), r_fr) <= 1e-6
+                assert rel(f_g[s:e].view(Ps[m], n[m])[:, rows].cpu().numpy(), r_fg) <= 1e-6
     finally:
         vv10.vv10_destroy(h)

@@ -321,15 +321,17 @@ def test_error_paths(dev):
 def chon60_rows(g, oracle_mod, n_spread=128, n_tail=64, n_omg=64):
     """Rows of the 60-atom grid checked against the oracle: n_spread kept points spread over
     the grid, the n_tail kept points of lowest density and the n_omg kept points of largest
-    |omega_gamma| (where the FP32 pair arithmetic is most fragile: rho^4 small, omega_gamma
-    up to ~1e10)."""
+    |omega_gamma| not already chosen (where the FP32 pair arithmetic is most fragile: rho^4
+    small, omega_gamma up to ~1e10; the two sets overlap, so the second takes the next
+    largest)."""
     kept = np.flatnonzero(g.rho >= 1e-10)
     spread = kept[np.linspace(0, kept.size - 1, n_spread).astype(np.int64)]
     tail = kept[np.argsort(g.rho[kept], kind="stable")[:n_tail]]
     om_g = np.abs(oracle_mod.point_props(g.rho[kept], g.grad_rho[kept])["omega_gamma"])
-    big = kept[np.argsort(-om_g, kind="stable")[:n_omg]]
-    rows = np.unique(np.concatenate([spread, tail, big]))
-    return rows, tail, big
+    chosen = set(spread.tolist()) | set(tail.tolist())
+    big = [int(i) for i in kept[np.argsort(-om_g, kind="stable")] if int(i) not in chosen][:n_omg]
+    rows = np.unique(np.concatenate([spread, tail, np.array(big, dtype=np.int64)]))
+    return rows, tail, np.array(big, dtype=np.int64)
 
 
 def test_full_size_chon60_mixed(dev, oracle_mod):
@@ -350,7 +352,7 @@ def test_full_size_chon60_mixed(dev, oracle_mod):
     gp, _, _ = eng.coord_grad(MIXED, atoms=False)
     vv10.vv10_sync(eng.h)
     rows, tail, big = chon60_rows(g, oracle_mod)
-    assert rows.size >= 250 and tail.size == 64 and big.size == 64
+    assert rows.size >= 250 and tail.size == 64 and big.size == 64  # overlap of spread and tail only
     args = (g.coords, g.weights, g.rho, g.grad_rho)
     _, vr_ref, vg_ref = oracle_mod.potential(*args, rows=rows)
     check(vr.cpu().numpy()[rows], vr_ref, 1e-6, what="vrho")
