@@ -17,7 +17,9 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
                        [--workload chon60|hexamer|water|cluster24|batch]
                        [--precision f16x3|tf32x3|fp64]
 --workload batch runs the 64-molecule batch through vv10_batch_prepare + vv10_batch_run
-(energy, potential and Hessian contraction; 2 sum_m N_kept,m^2 pairs per step).
+(energy, potential and Hessian contraction; 2 sum_m N_kept,m^2 pairs per step); the default
+run adds the same batch as a second record ("batch": 3 timed steps, split TF32, its own
+roofline, FP64 comparison on a subset and end-to-end timing).
 """
 from __future__ import annotations
 
@@ -63,9 +65,9 @@ ALU_OPS_PER_PAIR_CH = 38
 #   weight-derivative sums: 19 to form 1/(g g' s), 1/s + 1/g and the three kernel values,
 #   then 3 FMAs per direction
 ALU_OPS_PER_PAIR_WR = 19
-# DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel
-# (profiles/k_hess_tc_water_hexamer.md), keyed by workload; absent -> traffic null.
-PROFILED_TRAFFIC = {("k_hess_tc", "hexamer"): 1.2312e9}
+# DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel on
+# the full-size launch, keyed by (kernel, workload); absent -> traffic null.
+PROFILED_TRAFFIC = {}
 
 
 def workloads():
@@ -750,6 +752,14 @@ def gpu_arm(args):
         result["cpu_baseline"] = cpu_baseline(pb, args.cpu_seconds)
 
     vv.vv10_destroy(h)
+    if args.with_batch:
+        # the 64-molecule batch (many molecules of uneven size in persistent launches and a
+        # recorded graph) as a second timed record of the same run, on a freed device
+        del pb
+        torch.cuda.empty_cache()
+        result["batch"] = batch_record(args, dev, world, rank, max(1, min(K, 3)), 2,
+                                       args.batch_precision, with_fp64=not args.no_fp64_arm,
+                                       with_cpu=False)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -1134,6 +1144,11 @@ def main(argv=None):
                     default="chon60")
     ap.add_argument("--precision", choices=("f16x3", "mixed", "tf32x3", "fp64"), default="f16x3")
     ap.add_argument("--no-fp64-arm", action="store_true")
+    ap.add_argument("--no-batch", dest="with_batch", action="store_false",
+                    help="leave out the 64-molecule batch record of the single-system runs")
+    ap.add_argument("--batch-precision", choices=("f16x3", "mixed", "tf32x3", "fp64"), default="tf32x3",
+                    help="the batch record's precision (split TF32: its trial groups are at most "
+                         "96 wide, where the split-FP16 kernel is not the faster one)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args(argv)
