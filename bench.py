@@ -529,9 +529,10 @@ def cpu_baseline(pb, budget_s: float):
 
 
 def fp64_hessian_same_grid(vv, dev, prec):
-    """FP64 against mixed Hessian contraction on the water-hexamer grid (174,600 points,
-    P = 54): on the larger grids the FP64 contraction alone would take many minutes.  Each
-    call timed once after an untimed one; milliseconds and pairs per second."""
+    """FP64 (SIMT and tensor-core integer slices) against mixed Hessian contraction on the
+    water-hexamer grid (174,600 points, P = 54): on the larger grids the FP64 SIMT contraction
+    alone would take many minutes.  Each call timed once after an untimed one; milliseconds,
+    pairs per second and the distance of each result to the FP64 SIMT one."""
     import torch
     from paper_2208_14639_gb300 import synth
     g = synth.config_water_hexamer()
@@ -541,7 +542,8 @@ def fp64_hessian_same_grid(vv, dev, prec):
     nk = vv.vv10_prepare_points(h, d["xyz"], d["w"], d["rho"], d["grad"], d["atom"], pb.n_atom)
     out = {"workload": "water-hexamer-like cluster, 174,600 points, P=54", "n_kept": nk}
     stream = torch.cuda.current_stream()
-    for name, p in (("mixed", prec), ("fp64", vv.VV10_FP64)):
+    res = {}
+    for name, p in (("mixed", prec), ("fp64", vv.VV10_FP64), ("fp64tc", vv.VV10_FP64_TC)):
         vv.vv10_energy_potential(h, p, o["vrho"], o["vgamma"], want_energy=False)
         vv.vv10_hessian_contract(h, p, d["rt"], d["gt"], o["frt"], o["fgt"])
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -553,7 +555,13 @@ def fp64_hessian_same_grid(vv, dev, prec):
         ms = ev[0].elapsed_time(ev[1])
         out[f"{name}_ms"] = ms
         out[f"{name}_pair_evals_per_s"] = float(nk) * nk / (ms / 1e3)
+        res[name] = (o["frt"].clone(), o["fgt"].clone())
     out["speedup_mixed_vs_fp64"] = out["fp64_ms"] / out["mixed_ms"]
+    out["speedup_fp64tc_vs_fp64"] = out["fp64_ms"] / out["fp64tc_ms"]
+    for name in ("mixed", "fp64tc"):  # relative Frobenius distance to the FP64 SIMT result
+        out[f"{name}_rel_diff_vs_fp64"] = max(
+            float(torch.linalg.norm(res[name][k] - res["fp64"][k]) / torch.linalg.norm(res["fp64"][k]))
+            for k in range(2))
     vv.vv10_destroy(h)
     return out
 

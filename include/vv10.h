@@ -54,12 +54,19 @@ typedef enum {
                                bf16 split keeps ~16 bits, above the 1e-6 tolerance, and a
                                three-piece split costs as many MMAs as split TF32.  Split
                                TF32 or split FP16 stands in for it.                          */
-    VV10_MIXED_F16X3 = 3    /* FP32 pair tiles; Hessian contraction on tensor cores as split
+    VV10_MIXED_F16X3 = 3,   /* FP32 pair tiles; Hessian contraction on tensor cores as split
                                FP16 (hi*hi + hi*lo + lo*hi, K = 16 per MMA: half the MMA
                                instructions of split TF32) with FP32 accumulate; every
                                operand scaled by an exact power of two into FP16's range
-                               (per trial column; per row and 16-j stage for the kernel
+                               (per trial column; per row and 32-j stage for the kernel
                                tiles); elsewhere as VV10_MIXED_TF32X3                       */
+    VV10_FP64_TC = 4        /* as VV10_FP64, except the pair part of the Hessian contraction:
+                               kernel tiles generated in FP64 and the trials are cut into five
+                               8-bit integer slices each (FP16-exact), whose 15 leading
+                               products the tensor cores sum exactly in FP32 (about 40 bits
+                               of each tile and trial kept); results agree with VV10_FP64 to
+                               ~1e-11 relative.  Single systems only: the batched
+                               contraction returns VV10_ERR_UNSUPPORTED for it.            */
 } vv10_precision;
 
 /* VV10 parameters b and C (Sec. II.A) and the density cutoff below which a point is

@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &tc16_bh, &tc16_bl, &tc16_small, &nhess, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aogw, &aofa, &ngpart, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &tc16_bh, &tc16_bl, &tc16_small, &o64_sl, &o64_small, &o64_rec, &nhess, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aogw, &aofa, &ngpart, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -459,7 +459,7 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
         return VV10_ERR_INVALID_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     PointsDev& P = h->P;
     const size_t nkb = sizeof(double) * static_cast<size_t>(h->soa_ld);
     VV10_TRY(h->ensure(h->sumE, nkb, "E_i"));
@@ -702,7 +702,7 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
             return VV10_ERR_INVALID_ARG;
         }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     PointsDev& P = h->P;
     if (grad_points) VV10_CUDA(h, cudaMemsetAsync(grad_points, 0, sizeof(double) * 3 * P.n, st), "memset");
     if (grad_atoms) VV10_CUDA(h, cudaMemsetAsync(grad_atoms, 0, sizeof(double) * 3 * P.n_atom, st), "memset");
@@ -764,7 +764,7 @@ vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grg
         }
     if (!E_grgr && !D_points) return VV10_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     PointsDev& P = h->P;
     const size_t na = static_cast<size_t>(P.n_atom);
     // chunk offsets, per-task partials, then room for the blocks when only D_i^B is asked for
@@ -817,7 +817,7 @@ vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
     VV10_TRY(h->ensure(h->wdir, sizeof(double) * static_cast<size_t>(P) * Pd.nk_pad,
                        "weight directions"));
     double* yk = static_cast<double*>(h->wdir.p);
-    if (prec != VV10_FP64 && P > 4) {
+    if (!precision_fp64(prec) && P > 4) {
         // tensor cores (below 5 directions a 32-wide MMA is mostly padding)
         int ng = 0, ppad = 0;
         weight_tc_groups(P, &ng, &ppad);
@@ -836,7 +836,7 @@ vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
     }
     PhaseScope ph(h, PH_WEIGHT_RESPONSE, st, 2);
     VV10_CUDA(h, launch_weight_dirs(Pd, P, w_t, yk, st), "weight directions");
-    VV10_CUDA(h, launch_weight_response(Pd, prec == VV10_FP64, P, yk, E_t, U_t, W_t, st),
+    VV10_CUDA(h, launch_weight_response(Pd, precision_fp64(prec), P, yk, E_t, U_t, W_t, st),
               "weight-derivative sums");
     return VV10_OK;
 }
@@ -855,7 +855,7 @@ vv10_status vv10_energy(vv10_handle h, vv10_precision prec, double* energy, void
     }
     VV10_TRY(h->bind());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     const int grid = energy_half_grid(fp64, h->n_sm);
     VV10_TRY(h->ensure(h->ehalf, sizeof(double) * (static_cast<size_t>(grid) + 8), "energy partials"));
     double* dev_e = static_cast<double*>(h->ehalf.p) + grid;  // after the per-CTA totals
@@ -1120,7 +1120,7 @@ vv10_status vv10_evaluate(vv10_handle h, vv10_precision prec, int32_t P_trials,
             }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     if (EUW_Bgr || grad_points || grad_atoms) {
         VV10_TRY(evaluate_single_pass(h, fp64, vrho, vgamma, grad_points, grad_atoms, EUW_Bgr, st));
         if (P_trials > 0) VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, f_rho_t, f_gamma_t, st));
@@ -1273,7 +1273,7 @@ vv10_status vv10_autotune(vv10_handle h, vv10_precision prec, int what, void* st
         h->set_error("vv10_autotune cannot run while the stream is being captured");
         return VV10_ERR_INVALID_ARG;
     }
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     if (what & VV10_TUNE_PAIRSUMS) {
         VV10_TRY(h->require_prepared());
         for (int mode = 0; mode < 3; ++mode) VV10_TRY(h->tune_pairsum(mode, fp64, st, true));

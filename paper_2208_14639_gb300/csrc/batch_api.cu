@@ -151,7 +151,7 @@ vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt, int split_tiles) {
 vv10_status vv10_ctx::batch_ep(vv10_precision prec, double* energies, double* vrho,
                                double* vgamma, bool with_abc, cudaStream_t st) {
     BatchState& B = batch;
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     if (autotune & VV10_TUNE_BATCH) B_TRY(tune_batch(fp64, st, false));
     int rpt, split_tiles;
     batch_tiles(fp64, &rpt, &split_tiles);
@@ -198,7 +198,7 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
                                  const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
                                  cudaStream_t st) {
     BatchState& B = batch;
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     const size_t n_mol = B.mol.size();
     int* err = static_cast<int*>(dev_err.p);
     // trial offsets in the caller's concatenated arrays, and output clearing
@@ -805,6 +805,11 @@ vv10_status vv10_batch_hessian_contract(vv10_handle h, vv10_precision prec, cons
     }
     if (prec == VV10_MIXED_BF16X3) {
         h->set_error("the BF16x3 Hessian contraction is not available in this library");
+        return VV10_ERR_UNSUPPORTED;
+    }
+    if (prec == VV10_FP64_TC) {
+        h->set_error("the FP64 tensor-core contraction is built for single systems "
+                     "(vv10_hessian_contract); a batch takes VV10_FP64");
         return VV10_ERR_UNSUPPORTED;
     }
     if (prec != VV10_FP64 && prec != VV10_MIXED_TF32X3 && prec != VV10_MIXED_F16X3)

@@ -35,7 +35,7 @@ int vv10::hess_f64_trials_per_cta(int32_t P) {
 vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho_t,
                               const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
                               cudaStream_t st) {
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     const size_t out_bytes = sizeof(double) * static_cast<size_t>(Pn) * P.n;
     H_CUDA(cudaMemsetAsync(f_rho_t, 0, out_bytes, st), "memset f_rho_t");
     H_CUDA(cudaMemsetAsync(f_gamma_t, 0, out_bytes, st), "memset f_gamma_t");
@@ -109,6 +109,18 @@ vv10_status vv10_ctx::hessian(vv10_precision prec, int32_t Pn, const double* rho
         return VV10_OK;
     }
 
+    if (prec == VV10_FP64_TC) {  // FP64 accuracy on the tensor cores (integer slices)
+        H_TRY(o64_contract(Pn, st));
+        PhaseScope ph2(this, PH_HESS_EPILOGUE, st, 1);
+        H_CUDA(launch_hess_epilogue(P, Pn, static_cast<double*>(hacc.p), 1, P.nk_pad,
+                                    static_cast<double*>(sumU.p), static_cast<double*>(sumW.p),
+                                    static_cast<double*>(sumA.p), static_cast<double*>(sumB.p),
+                                    static_cast<double*>(sumC.p), static_cast<double*>(trt.p),
+                                    static_cast<double*>(tgt.p), f_rho_t, f_gamma_t,
+                                    static_cast<int*>(dev_err.p), st),
+               "Hessian epilogue");
+        return VV10_OK;
+    }
     HessLaunch cfg;
     cfg.trials_per_cta = hess_f64_trials_per_cta(Pn);
     cfg.n_split = hess_f64_default_split(P, Pn, cfg.trials_per_cta, n_sm);
@@ -204,6 +216,47 @@ vv10_status vv10_ctx::f16_contract(int32_t Pn, int cap, cudaStream_t st) {
         H_CUDA(launch_hess_f16(P, pn, t0, Pn, tc16_bh.p, tc16_bl.p, rows, col_isc, params, n_sm,
                                tc_flush, static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
                "FP16 tensor-core contraction");
+    }
+    return VV10_OK;
+}
+
+// Cut u, y (in tu, ty) into FP16 integer slices and contract all Pn trials with FP64
+// accuracy on the tensor cores, in groups of at most 32 trials, into hacc [2][Pn][nk_pad].
+vv10_status vv10_ctx::o64_contract(int32_t Pn, cudaStream_t st) {
+    const int cap = hess_o64_max_group();
+    const int ng = (Pn + cap - 1) / cap;
+    const int pg = (Pn + ng - 1) / ng;
+    const int64_t rows = static_cast<int64_t>(ng - 1) * pg + cap;
+    const int64_t stride = 2 * static_cast<int64_t>(rows) * P.nk_pad;  // halves per slice array
+    H_TRY(ensure(o64_sl, hess_o64_slices() * sizeof(uint16_t) * static_cast<size_t>(stride),
+                 "FP64 trial slices"));
+    H_TRY(ensure(o64_rec, 64 * static_cast<size_t>(P.nk_pad), "FP32-pair point records"));
+    // colmax [2] words | params [2] doubles | civ [ng][nk_pad / 16][32] floats
+    const int64_t civ_n = hess_o64_civ_floats(Pn, pg, P.nk_pad);
+    H_TRY(ensure(o64_small, 32 + sizeof(float) * static_cast<size_t>(civ_n), "FP64 trial factors"));
+    char* sm = static_cast<char*>(o64_small.p);
+    double* params = reinterpret_cast<double*>(sm + 16);
+    float* civ = reinterpret_cast<float*>(sm + 32);
+    {
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 5);
+        H_CUDA(launch_o64_prep(P, static_cast<double*>(tu.p), static_cast<double*>(ty.p), Pn,
+                               static_cast<int32_t>(rows), pg, o64_rec.p,
+                               reinterpret_cast<unsigned long long*>(sm), params, o64_sl.p, stride,
+                               civ, st),
+               "FP64 trial slices");
+    }
+    const size_t ab = sizeof(double) * 2 * static_cast<size_t>(Pn) * P.nk_pad;
+    H_TRY(ensure(hacc, ab, "contraction partials"));
+    H_CUDA(cudaMemsetAsync(hacc.p, 0, ab, st), "zero contraction partials");
+    const int64_t civ_group = civ_n / ng;
+    PhaseScope ph(this, PH_CONTRACT_TC, st, ng);
+    for (int g = 0; g < ng; ++g) {
+        const int t0 = g * pg;
+        const int pn = (Pn - t0 < pg) ? Pn - t0 : pg;
+        H_CUDA(launch_hess_o64(P, pn, t0, Pn, o64_rec.p, o64_sl.p, stride, rows, civ + g * civ_group,
+                               params, n_sm, tc_flush, static_cast<double*>(hacc.p),
+                               static_cast<int*>(dev_err.p), st),
+               "FP64 tensor-core contraction");
     }
     return VV10_OK;
 }

@@ -62,7 +62,10 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
 
 // Precisions the library knows (vv10_precision values); every mixed one runs the pair sums
 // in FP32 and differs only in the Hessian contraction's tensor-core operands.
-constexpr bool precision_known(int prec) { return prec >= 0 && prec <= 3; }
+constexpr bool precision_known(int prec) { return prec >= 0 && prec <= 4; }
+// FP64 pair arithmetic and sums (VV10_FP64 and VV10_FP64_TC, which differ in the
+// Hessian contraction only).
+constexpr bool precision_fp64(int prec) { return prec == 0 || prec == 4; }
 
 // ---------------------------------------------------------------- pair sums (pairsum.cu)
 enum PairMode : int { MODE_EUW = 0, MODE_ABC = 1, MODE_GRAD = 2, MODE_EUWABC = 3, MODE_EUWABCG = 4 };
@@ -163,6 +166,27 @@ cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t 
                             const void* bh, const void* bl, int64_t rows, const double* col_isc,
                             const float* params, int n_sm, int flush, double* acc, int* err,
                             cudaStream_t st);
+
+// Tensor-core contraction with FP64 accuracy (hess_o64.cu).  launch_o64_prep writes the
+// kept points' column records (`rec`, 64 B per point, nk_pad of them), cuts u, y (FP64
+// [P][nk_pad]) into hess_o64_slices() FP16 integer slice arrays [rows][2 nk_pad]
+// (`slice_stride` halves apart; per 16-j block 16 u' then 16 c_y y', scaled per trial and
+// block) with params[0] = 1/c_y, params[1] = c_y (colmax: 2 scratch words), and the factors'
+// inverses civ [group][nk_pad / 16][32] for trial groups of pg <= hess_o64_max_group()
+// (hess_o64_civ_floats floats).  launch_hess_o64 contracts the trials [t0, t0 + Pn), Pn <= pg,
+// with `civ` pointing at their group's block, into acc [2][acc_P][nk_pad] (zeroed by the
+// caller).
+int hess_o64_max_group();
+int hess_o64_slices();
+int64_t hess_o64_civ_floats(int32_t P, int32_t pg, int64_t nk_pad);
+cudaError_t launch_o64_prep(const PointsDev& p, const double* u, const double* y, int32_t P,
+                            int32_t rows, int32_t pg, void* rec, unsigned long long* colmax,
+                            double* params, void* slices, int64_t slice_stride, float* civ,
+                            cudaStream_t st);
+cudaError_t launch_hess_o64(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
+                            const void* rec, const void* slices, int64_t slice_stride,
+                            int64_t rows, const float* civ, const double* params, int n_sm,
+                            int flush, double* acc, int* err, cudaStream_t st);
 
 // Batched tensor-core contraction (molecule and task tables in device memory; see
 // hess_tc.cu for the record layouts the fill helpers write).

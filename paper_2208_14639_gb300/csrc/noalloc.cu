@@ -238,7 +238,7 @@ extern "C" vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xy
         return VV10_ERR_CUDA;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool fp64 = (prec == VV10_FP64);
+    const bool fp64 = precision_fp64(prec);
     const int64_t n_pad = ((n + kJTile - 1) / kJTile) * kJTile;
     double4* r64a = reinterpret_cast<double4*>(base + kNaOffR64a);
     double4* r64b = reinterpret_cast<double4*>(base + kNaOffR64b);

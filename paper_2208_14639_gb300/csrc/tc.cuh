@@ -60,6 +60,13 @@ __device__ __forceinline__ void ld_x8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "r"(taddr)
                  : "memory");
 }
+// 4 consecutive 32-bit columns of this warp's 32 lanes.
+__device__ __forceinline__ void ld_x4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
 // 16 consecutive 32-bit columns of this warp's 32 lanes.
 __device__ __forceinline__ void ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(

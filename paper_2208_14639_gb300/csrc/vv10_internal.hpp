@@ -139,6 +139,9 @@ struct vv10_ctx {
     vv10::DevBuf tc_uh, tc_ul, tc_yh, tc_yl;
     vv10::DevBuf tc16_bh, tc16_bl;  // split-FP16 trial tiles [rows][2 nk_pad]
     vv10::DevBuf tc16_small;        // their column maxima, factors and y balance
+    vv10::DevBuf o64_sl;            // FP64-accurate contraction: FP16 trial slice arrays
+    vv10::DevBuf o64_small;         // their factors and y balance
+    vv10::DevBuf o64_rec;           // and the points' FP32-pair column records
 
     // coordinate scratch
     vv10::DevBuf gk;
@@ -208,6 +211,7 @@ struct vv10_ctx {
     int tc_cap_for(int32_t P, int64_t nk) const;
     vv10_status tc_contract(int32_t P, int cap, cudaStream_t st);
     vv10_status f16_contract(int32_t P, int cap, cudaStream_t st);
+    vv10_status o64_contract(int32_t P, cudaStream_t st);
     vv10_status tune_tc_cap(int32_t P, cudaStream_t st, int* cap);
     vv10_status hessian(vv10_precision prec, int32_t P, const double* rho_t,
                         const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,

@@ -27,8 +27,9 @@ VV10_FP64 = 0
 VV10_MIXED_TF32X3 = 1
 VV10_MIXED_BF16X3 = 2
 VV10_MIXED_F16X3 = 3
+VV10_FP64_TC = 4
 PRECISIONS = {"fp64": VV10_FP64, "tf32x3": VV10_MIXED_TF32X3, "bf16x3": VV10_MIXED_BF16X3,
-              "f16x3": VV10_MIXED_F16X3, "mixed": VV10_MIXED_TF32X3}
+              "f16x3": VV10_MIXED_F16X3, "fp64tc": VV10_FP64_TC, "mixed": VV10_MIXED_TF32X3}
 
 VV10_OPT_FUSE_HESSIAN_SUMS = 1
 VV10_TUNE_PAIRSUMS = 1

@@ -25,6 +25,9 @@ pytestmark = pytest.mark.gpu
 FP64 = vv10.VV10_FP64
 MIXED = vv10.VV10_MIXED_TF32X3
 F16 = vv10.VV10_MIXED_F16X3
+F64TC = vv10.VV10_FP64_TC
+# the two FP64 contractions: FP64 SIMT and five-slice integer products on the tensor cores
+F64_PRECS = pytest.mark.parametrize("fp", [FP64, F64TC], ids=["fp64", "fp64tc"])
 # the two tensor-core contractions of the mixed path: split TF32 and scaled split FP16
 TC_PRECS = pytest.mark.parametrize("tcp", [MIXED, F16], ids=["tf32x3", "f16x3"])
 
@@ -81,28 +84,30 @@ def test_energy_potential(dev, oracle_mod, name, g, prec):
     eng.close()
 
 
+@F64_PRECS
 @pytest.mark.parametrize("name,g", SMALL[:1] + SMALL[3:], ids=[s[0] for s in SMALL[:1] + SMALL[3:]])
-def test_hessian_contraction_fp64(dev, oracle_mod, name, g):
+def test_hessian_contraction_fp64(dev, oracle_mod, name, g, fp):
     rt, gt = synth.trial_densities(g.molecule, g.coords)
     fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
     eng = make_engine(g, dev)
     eng.energy_potential(FP64)
-    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), fp)
     check(fr.cpu().numpy(), fr_ref, 1e-10)
     check(fg.cpu().numpy(), fg_ref, 1e-10)
     eng.close()
 
 
-def test_hessian_single_trial_and_odd_P(dev, oracle_mod):
+@F64_PRECS
+def test_hessian_single_trial_and_odd_P(dev, oracle_mod, fp):
     g = synth.random_points(300, seed=11, n_atom=3)
     rng = np.random.default_rng(1)
-    for P in (1, 5, 33):
+    for P in (1, 5, 33, 65, 130):
         rt = rng.normal(size=(P, g.n)) * g.rho
         gt = rng.normal(size=(P, g.n, 3)) * np.abs(g.grad_rho)[None]
         fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
         eng = make_engine(g, dev)
         eng.energy_potential(FP64)
-        fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), FP64)
+        fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), fp)
         check(fr.cpu().numpy(), fr_ref, 1e-10)
         check(fg.cpu().numpy(), fg_ref, 1e-10)
         eng.close()
@@ -144,6 +149,58 @@ def test_hessian_mixed_trial_counts(dev, oracle_mod, P, tcp):
     vv10.vv10_sync(eng.h)
     check(fr.cpu().numpy(), fr_ref, 1e-6)
     check(fg.cpu().numpy(), fg_ref, 1e-6)
+    eng.close()
+
+
+def test_fp64tc_trial_scales(dev, oracle_mod):
+    """Trials 20 orders of magnitude apart, one zero trial and one with zero u or y part:
+    each column has its own power-of-two factor, so every trial keeps FP64 accuracy relative
+    to itself (checked trial by trial, not over the whole output)."""
+    g = synth.random_points(400, seed=31, n_atom=3)
+    rng = np.random.default_rng(9)
+    P = 6
+    rt = rng.normal(size=(P, g.n)) * g.rho
+    gt = rng.normal(size=(P, g.n, 3)) * np.abs(g.grad_rho)[None]
+    rt[1] *= 1e-12
+    gt[1] *= 1e-12
+    rt[2] *= 1e8
+    gt[2] *= 1e8
+    rt[3] = 0.0
+    gt[3] = 0.0
+    gt[4] = 0.0          # no gradient part: y' = 0 in this column
+    rt[5] = 0.0          # no density part: u' = 0 in this column
+    fr_ref, fg_ref = oracle_mod.hessian_contract(g.coords, g.weights, g.rho, g.grad_rho, rt, gt)
+    eng = make_engine(g, dev)
+    eng.energy_potential(FP64)
+    fr, fg = eng.hessian_contract(T(rt, dev), T(gt, dev), F64TC)
+    vv10.vv10_sync(eng.h)
+    fr, fg = fr.cpu().numpy(), fg.cpu().numpy()
+    for t in range(P):
+        if t == 3:
+            assert not fr[t].any() and not fg[t].any()
+            continue
+        check(fr[t], fr_ref[t], 1e-10, what=f"f_rho_t trial {t}")
+        check(fg[t], fg_ref[t], 1e-10, what=f"f_gamma_t trial {t}")
+    eng.close()
+
+
+def test_fp64tc_matches_fp64_simt(dev):
+    """The two FP64 contractions on the same GPU inputs (a 4-atom CHON system of 26,400
+    points, 54 random trials as for the water hexamer): agreement to 1e-11 relative, element
+    by element against |ref_i| + rms."""
+    g = synth.make_system(synth.random_chon(np.random.default_rng(3), 4), 60, 110)
+    rng = np.random.default_rng(54)
+    rt = rng.normal(size=(54, g.n)) * g.rho
+    gt = rng.normal(size=(54, g.n, 3)) * np.abs(g.grad_rho)[None]
+    eng = make_engine(g, dev)
+    eng.energy_potential(FP64)
+    rtd, gtd = T(rt, dev), T(gt, dev)
+    fr0, fg0 = eng.hessian_contract(rtd, gtd, FP64)
+    fr0, fg0 = fr0.cpu().numpy(), fg0.cpu().numpy()
+    fr1, fg1 = eng.hessian_contract(rtd, gtd, F64TC)
+    vv10.vv10_sync(eng.h)
+    check(fr1.cpu().numpy(), fr0, 1e-11, what="f_rho_t")
+    check(fg1.cpu().numpy(), fg0, 1e-11, what="f_gamma_t")
     eng.close()
 
 
@@ -258,9 +315,11 @@ def test_full_size_hexamer_hessian_sampled(dev, oracle_mod, hexamer):
         check(fr.cpu().numpy()[:, rows], fr_ref, 1e-6, what=f"f_rho_t prec {tcp}")
         check(fg.cpu().numpy()[:, rows], fg_ref, 1e-6, what=f"f_gamma_t prec {tcp}")
     eng.energy_potential(FP64)
-    fr, fg = eng.hessian_contract(rtd, gtd, FP64)
-    check(fr.cpu().numpy()[:, rows], fr_ref, 1e-10)
-    check(fg.cpu().numpy()[:, rows], fg_ref, 1e-10)
+    for fp in (FP64, F64TC):
+        fr, fg = eng.hessian_contract(rtd, gtd, fp)
+        vv10.vv10_sync(eng.h)
+        check(fr.cpu().numpy()[:, rows], fr_ref, 1e-10, what=f"f_rho_t prec {fp}")
+        check(fg.cpu().numpy()[:, rows], fg_ref, 1e-10, what=f"f_gamma_t prec {fp}")
     eng.close()
 
 
@@ -379,10 +438,11 @@ def test_full_size_chon60_mixed(dev, oracle_mod):
 
 # ----------------------------------------------------------------- limits and degenerate inputs
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F16, 1e-6)],
-                         ids=["fp64", "tf32x3", "f16x3"])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F16, 1e-6), (F64TC, 1e-10)],
+                         ids=["fp64", "tf32x3", "f16x3", "fp64tc"])
 def test_hessian_maximum_trial_count(dev, oracle_mod, prec, tol):
-    """P = VV10_MAX_TRIALS (4096): 22 tensor-core groups of 187 trials, or 128 FP64 chunks."""
+    """P = VV10_MAX_TRIALS (4096): 22 tensor-core groups of 187 trials, 64 groups of 64 on the
+    FP64 tensor-core path, or 128 FP64 chunks."""
     g = synth.random_points(96, seed=23, n_atom=2)
     P = 4096
     rng = np.random.default_rng(5)
@@ -400,7 +460,7 @@ def test_hessian_maximum_trial_count(dev, oracle_mod, prec, tol):
     eng.close()
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec", [FP64, MIXED, F64TC], ids=["fp64", "mixed", "fp64tc"])
 def test_all_points_below_cutoff(dev, prec):
     """Every point below rho_cut: no kept point, zero energy and zero outputs everywhere."""
     g0 = synth.random_points(50, seed=29, n_atom=2)

@@ -136,3 +136,148 @@ def test_scaling_mistakes_are_caught(oracle_mod):
     assert np.abs(np.log2(np.abs(u).max() / np.abs(y).max())) > 1  # c_y is not 1 here
     for planted in (dict(undo_row=False), dict(undo_col=False), dict(fold_cy=False)):
         assert err(**planted) > 1e-2, planted
+
+
+# ------------------------------------------------------------ FP64 accuracy from integer slices
+#
+# The FP64 tensor-core contraction: kernel tiles as FP32 pairs (hi, lo) cut into seven 8-bit
+# integer slices in FP32 arithmetic, trials cut into seven slices in FP64; per 16-j stage one
+# factor per tile row and one per trial column (powers of two into [2^6, 2^7)); the 28
+# products with p + q <= 6 summed per level.
+
+F32 = np.float32
+
+
+def two_sum32(a, b):
+    s = (a + b).astype(F32)
+    bp = (s - a).astype(F32)
+    return s, ((a - (s - bp)).astype(F32) + (b - bp).astype(F32)).astype(F32)
+
+
+def tile_slices7(hi, lo, carry=True):
+    """Seven slices of x = hi + lo (|x| < 2^7) in FP32: three from hi, whose remainder joins lo
+    in an error-free sum w + e (dropped with carry=False), three from w, the last from what is
+    left and e."""
+    hi, lo = np.asarray(hi, F32), np.asarray(lo, F32)
+    s0 = np.rint(hi)
+    r0 = (hi - s0) * F32(256)
+    s1 = np.rint(r0)
+    r1 = (r0 - s1) * F32(256)
+    s2 = np.rint(r1)
+    w, e = two_sum32(((r1 - s2) * F32(2.0 ** -16)).astype(F32) if carry else np.zeros_like(lo), lo)
+    u3 = (w * F32(2.0 ** 24)).astype(F32)
+    s3 = np.rint(u3)
+    u4 = ((u3 - s3) * F32(256)).astype(F32)
+    s4 = np.rint(u4)
+    u5 = ((u4 - s4) * F32(256)).astype(F32)
+    s5 = np.rint(u5)
+    s6 = np.rint((e.astype(np.float64) * 2.0 ** 48 + (u5 - s5).astype(np.float64) * 256).astype(F32))
+    return [s.astype(np.float64) for s in (s0, s1, s2, s3, s4, s5, s6)]
+
+
+def pair32(x):
+    hi = np.asarray(x).astype(F32)
+    return hi, (np.asarray(x) - hi.astype(np.float64)).astype(F32)
+
+
+def trial_slices7(x):
+    out, r = [], np.asarray(x, dtype=np.float64).copy()
+    for _ in range(7):
+        s = np.rint(r)
+        out.append(s)
+        r = (r - s) * 256.0
+    return out
+
+
+def pow2_into(m, lo_exp):
+    e = np.floor(np.log2(np.where(m > 0, m, 1.0)))
+    return np.where(m > 0, 2.0 ** (lo_exp - e), 1.0)
+
+
+def contract_o64(Ta, Tb, u, y, J=16, levels=7, carry=True, weight=8, col_per_stage=True):
+    """The seven-slice product; level sums asserted to be integers below 2^23 (exact in the
+    tensor cores' FP32 accumulation).  The flags plant mistakes."""
+    cy = 2.0 ** np.round(np.log2(np.abs(u).max() / np.abs(y).max()))
+    Tb = Tb / cy
+    s_all = pow2_into(np.maximum(np.abs(u).max(1), cy * np.abs(y).max(1)), 6)
+    out = np.zeros((Ta.shape[0], u.shape[0]))
+    for j0 in range(0, Ta.shape[1], J):
+        sl = slice(j0, j0 + J)
+        a, b, us, ys = Ta[:, sl], Tb[:, sl], u[:, sl], cy * y[:, sl]
+        s_t = pow2_into(np.maximum(np.abs(us).max(1), np.abs(ys).max(1)), 6) if col_per_stage \
+            else s_all
+        U, Y = trial_slices7(us * s_t[:, None]), trial_slices7(ys * s_t[:, None])
+        r = pow2_into(np.maximum(np.abs(a).max(1), np.abs(b).max(1)), 6)
+        A = tile_slices7(*pair32(a * r[:, None]), carry=carry)
+        B = tile_slices7(*pair32(b * r[:, None]), carry=carry)
+        st = np.zeros_like(out)
+        for lev in range(levels):
+            L = sum(A[p] @ U[lev - p].T + B[p] @ Y[lev - p].T for p in range(lev + 1))
+            assert np.all(L == np.rint(L)) and np.abs(L).max() < 2.0 ** 23
+            st += L * 2.0 ** (-weight * lev)
+        out += st / r[:, None] / s_t[None, :]
+    return out
+
+
+def test_seven_slices_reconstruct():
+    """Tile slices are integers of at most 8 bits (|s3|, |s6| <= 192), exact in FP16, and
+    rebuild the FP32 pair hi + lo to within 2^-49 for |x| < 2^7 across the whole range (the
+    pair itself carries x to 2^-48 relative); trial slices rebuild an FP64 value to within
+    2^-49, exactly when all its bits lie above 2^-48 (|x| >= 2^4)."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-128, 128, 20000),
+                        rng.uniform(-1, 1, 20000) * 10.0 ** rng.uniform(-15, 2, 20000),
+                        [0.0, 127.99999999, -127.99999999, 2.0 ** -20, 3.0 ** -15]])
+    hi, lo = pair32(x)
+    s = tile_slices7(hi, lo)
+    for k, sk in enumerate(s):
+        assert np.all(sk == np.rint(sk)) and np.all(np.abs(sk) <= (192 if k in (3, 6) else 128))
+        assert np.all(sk.astype(np.float16).astype(np.float64) == sk)
+    pair = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.abs(sum(sk * 2.0 ** (-8 * k) for k, sk in enumerate(s)) - pair).max() <= 2.0 ** -49
+    t = trial_slices7(x)
+    assert all(np.abs(tk).max() <= 128 for tk in t)
+    rebuilt = sum(tk * 2.0 ** (-8 * k) for k, tk in enumerate(t))
+    assert np.abs(rebuilt - x).max() <= 2.0 ** -49
+    big = np.abs(x) >= 16.0  # all 53 bits above 2^-48: exact
+    assert np.array_equal(rebuilt[big], x[big])
+    # without the third slice's remainder carried into the low half, the bits of hi between
+    # 2^-16 and 2^-24 of the scale are lost
+    s_nc = tile_slices7(hi, lo, carry=False)
+    assert np.abs(sum(sk * 2.0 ** (-8 * k) for k, sk in enumerate(s_nc)) - pair).max() > 2.0 ** -25
+
+
+SLICE_CASES = [("water_small", lambda: synth.config_water(n_rad=16, n_ang=38)),
+               ("chon4", lambda: synth.make_system(synth.random_chon(np.random.default_rng(7), 4), 12, 38)),
+               ("rand255", lambda: synth.random_points(255, seed=4, n_atom=3))]
+
+
+@pytest.mark.parametrize("case,make", SLICE_CASES, ids=[c[0] for c in SLICE_CASES])
+def test_seven_slice_product_fp64_accuracy(oracle_mod, case, make):
+    """Relative Frobenius error <= 1e-12 and every element within 1e-11 (|ref| + rms): inside
+    the 1e-10 bound the GPU parity tests apply to the FP64 paths.  Random points (no shell
+    structure) give the largest ranges inside a stage."""
+    T, u, y = tiles_and_trials(make(), oracle_mod)
+    for Ta, Tb in ((T[0], T[1]), (T[2], T[3])):
+        exact = Ta @ u.T + Tb @ y.T
+        nrm = np.linalg.norm(exact)
+        got = contract_o64(Ta, Tb, u, y)
+        assert np.linalg.norm(got - exact) / nrm <= 1e-12
+        assert np.all(np.abs(got - exact) <= 1e-11 * (np.abs(exact) + np.sqrt(np.mean(exact ** 2))))
+
+
+def test_seven_slice_mistakes_are_caught(oracle_mod):
+    """A dropped level, the remainder carry left out or a wrong level weight each move the
+    product well past the bounds above; one column factor for all of j (instead of one per
+    stage) at least doubles the error."""
+    T, u, y = tiles_and_trials(synth.random_points(255, seed=4, n_atom=3), oracle_mod)
+    Ta, Tb = T[2], T[3]
+    exact = Ta @ u.T + Tb @ y.T
+    nrm = np.linalg.norm(exact)
+    err = lambda **kw: np.linalg.norm(contract_o64(Ta, Tb, u, y, **kw) - exact) / nrm
+    base = err()
+    assert base <= 1e-12
+    assert err(levels=6) > 1e-11
+    assert err(carry=False) > 1e-11
+    assert err(weight=7) > 1e-3
+    assert err(col_per_stage=False) > 2 * base
