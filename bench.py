@@ -43,7 +43,9 @@ UNIT = "pair evals/s"
 DTYPES = {"f16x3": "f32 pair tiles, split-fp16 tensor-core contraction, f64 precompute/reductions",
           "mixed": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions",
           "tf32x3": "f32 pair tiles, split-tf32 tensor-core contraction, f64 precompute/reductions",
-          "fp64": "f64"}
+          "fp64": "f64",
+          "fp64tc": "f64 pair sums; Hessian contraction from double-fp32 tiles cut into 8-bit "
+                    "integer slices, exact fp32 tensor-core level sums"}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
@@ -65,6 +67,12 @@ ALU_OPS_PER_PAIR_CH = 38
 #   weight-derivative sums: 19 to form 1/(g g' s), 1/s + 1/g and the three kernel values,
 #   then 3 FMAs per direction
 ALU_OPS_PER_PAIR_WR = 19
+#   FP64 tensor-core contraction, per pair, trial group of 32 and output kind: 33 for the
+#   exact coordinate differences and r^2, about 250 for the double-FP32 kernel tiles (17
+#   additions of 11 operations, 24 products of 7, a reciprocal of 12), 2 x 30 for the seven
+#   slices of the two tiles, and 8 x 40 / 4 for the level drains of the row's outputs
+#   (shared by the 4 j a thread generates per stage); both output kinds
+O64_ALU_OPS_PER_PAIR = 2 * (33 + 250 + 60 + 80)
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel on
 # the full-size launch, keyed by (kernel, workload); absent -> traffic null.
 PROFILED_TRAFFIC = {}
@@ -80,6 +88,9 @@ def workloads():
                       synth.config_cluster24),
         "chon60": ("60-atom CHON molecule, 75x302 points per atom (1,359,000 points), P=180",
                    synth.config_chon60),
+        # the same molecule on a coarser grid: P = 180 at a device footprint of a few GB
+        "chon60s": ("60-atom CHON molecule, 40x110 points per atom (264,000 points), P=180",
+                    lambda: synth.config_chon60(n_rad=40, n_ang=110)),
     }
 
 
@@ -89,7 +100,7 @@ EXTRA_CALLS_MAX_POINTS = 400_000
 
 # Radial x angular points per atom of each workload's grid (for its weight derivatives).
 GRID_SHAPES = {"water": (30, 110), "hexamer": (50, 194), "cluster24": (30, 139),
-               "chon60": (75, 302)}
+               "chon60": (75, 302), "chon60s": (40, 110)}
 
 
 # ------------------------------------------------------------------ host-side rank logic
@@ -579,7 +590,7 @@ def gpu_arm(args):
     vv.load(build_if_missing=True)
     label, make = workloads()[args.workload]
     g = make()
-    pb = Problem(g, dev, resolved=(args.workload != "chon60"))
+    pb = Problem(g, dev, resolved=not args.workload.startswith("chon60"))
     pb.grid_shape = GRID_SHAPES[args.workload]
     h = vv.vv10_create(local)
     prec = vv.PRECISIONS[args.precision]
@@ -587,7 +598,7 @@ def gpu_arm(args):
     large = pb.n > EXTRA_CALLS_MAX_POINTS
     # the step runs the Hessian after the energy: form A/B/C in the energy pass
     vv.vv10_set_options(h, vv.VV10_OPT_FUSE_HESSIAN_SUMS)
-    if prec != vv.VV10_FP64:  # tile shapes tuned on first use, i.e. inside the warm-up steps
+    if prec not in (vv.VV10_FP64, vv.VV10_FP64_TC):  # tile shapes tuned on first use (warm-up)
         vv.vv10_set_autotune(h, vv.VV10_TUNE_PAIRSUMS | vv.VV10_TUNE_CONTRACTION)
 
     with ClockSampler(local) as clk:
@@ -674,7 +685,19 @@ def gpu_arm(args):
     dom = max(per, key=per.get)
     roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None, "kernel": dom}
-    if dom == "contraction_tensor_core":
+    if dom == "contraction_tensor_core" and prec == vv.VV10_FP64_TC:
+        # FP32 ALU-bound: double-FP32 tile generation, slicing and level drains
+        t = per[dom] / 1e3
+        groups = -(-pb.P // 32)
+        alu_peak = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
+        ops = O64_ALU_OPS_PER_PAIR * groups * pairs_call
+        roof = {"bound": "alu", "achieved": ops / t / 1e12, "peak": alu_peak / 1e12,
+                "unit": "Tops/s (FP32)", "frac": ops / t / alu_peak, "traffic": None,
+                "kernel": "k_hess_o64",
+                "peak_source": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
+                "counting": f"{O64_ALU_OPS_PER_PAIR} FP32 operations per pair and trial group of 32 "
+                            "(both output kinds)"}
+    elif dom == "contraction_tensor_core":
         t = per[dom] / 1e3
         groups = -(-pb.P // 192)
         ppad = max(32, 32 * -(-(-(-pb.P // groups)) // 32))
@@ -721,7 +744,7 @@ def gpu_arm(args):
         "energy": e_mixed,
     }
 
-    if rank == 0 and not args.no_fp64_arm and prec != vv.VV10_FP64:
+    if rank == 0 and not args.no_fp64_arm and prec not in (vv.VV10_FP64, vv.VV10_FP64_TC):
         vv.vv10_set_autotune(h, 0)  # FP64 baseline at its default shapes
         if not large:
             ms64, nk64, e64, prof64 = time_steps(vv, h, pb, vv.VV10_FP64, 1, 1, 1)
@@ -1148,9 +1171,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hexamer", "water", "cluster24", "chon60", "batch"),
+    ap.add_argument("--workload", choices=("hexamer", "water", "cluster24", "chon60", "chon60s", "batch"),
                     default="chon60")
-    ap.add_argument("--precision", choices=("f16x3", "mixed", "tf32x3", "fp64"), default="f16x3")
+    ap.add_argument("--precision", choices=("f16x3", "mixed", "tf32x3", "fp64", "fp64tc"),
+                    default="f16x3")
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-batch", dest="with_batch", action="store_false",
                     help="leave out the 64-molecule batch record of the single-system runs")

@@ -27,12 +27,17 @@ import torch
 
 from . import vv10 as _vv
 
-_PREC = {"fp64": _vv.VV10_FP64, "mixed": _vv.VV10_MIXED_TF32X3, "tf32x3": _vv.VV10_MIXED_TF32X3}
+_PREC = {"fp64": _vv.VV10_FP64, "mixed": _vv.VV10_MIXED_TF32X3, "tf32x3": _vv.VV10_MIXED_TF32X3,
+         "f16x3": _vv.VV10_MIXED_F16X3, "fp64tc": _vv.VV10_FP64_TC}
 
 
 class _DeviceHandle:
     """One library handle per device, shared by all energies evaluated on it; the handle's
-    prepared point set belongs to the most recent _State that (re)prepared it."""
+    prepared point set belongs to the most recent _State that (re)prepared it.  Each slot
+    carries a re-entrant lock: re-preparing the handle and the library calls that read the
+    prepared points happen under it, so energies and Hessian-vector products taken from
+    several threads on one device do not interleave (their work is queued in that order on
+    the calling threads' streams)."""
 
     _lock = threading.Lock()
     _handles = {}
@@ -43,7 +48,8 @@ class _DeviceHandle:
             h = cls._handles.get(device)
             if h is None:
                 _vv.load(build_if_missing=True)
-                h = cls._handles[device] = {"h": _vv.vv10_create(device), "owner": None}
+                h = cls._handles[device] = {"h": _vv.vv10_create(device), "owner": None,
+                                            "lock": threading.RLock()}
             return h
 
 
@@ -77,12 +83,18 @@ class _State:
         self.vrho, self.vgamma = vrho, vgamma
         self.slot["owner"] = self
 
+    @property
+    def lock(self):
+        return self.slot["lock"]
+
     def hessian(self, a_rho, a_grad):
         """(w f^{rho,t}, 2 w (f^{gamma,t} grad rho + f^gamma d grad rho)) for trials (P, n)."""
-        self.ensure()
         fr = torch.empty_like(a_rho)
         fg = torch.empty_like(a_rho)
-        _vv.vv10_hessian_contract(self.h, self.prec, a_rho.contiguous(), a_grad.contiguous(), fr, fg)
+        with self.lock:
+            self.ensure()
+            _vv.vv10_hessian_contract(self.h, self.prec, a_rho.contiguous(), a_grad.contiguous(),
+                                      fr, fg)
         w = self.weights
         d_rho = w * fr
         d_grad = 2.0 * w[:, None] * (fg[..., None] * self.grad_rho + self.vgamma[:, None] * a_grad)
@@ -108,17 +120,18 @@ class _FirstDerivs(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, state, want_coords, want_w, rho, grad_rho, coords, weights):
-        state.ensure()
+        n = state.weights.shape[0]
+        g_coords = torch.zeros(n, 3, dtype=torch.float64, device=state.weights.device)
+        g_w = torch.zeros(n, dtype=torch.float64, device=state.weights.device)
+        with state.lock:
+            state.ensure()
+            if want_coords:
+                _vv.vv10_coord_grad(state.h, state.prec, g_coords)
+            if want_w:
+                _vv.vv10_weight_grad(state.h, g_w)
         w = state.weights
         g_rho = w * state.vrho
         g_grad = 2.0 * (w * state.vgamma)[:, None] * state.grad_rho
-        n = w.shape[0]
-        g_coords = torch.zeros(n, 3, dtype=torch.float64, device=w.device)
-        g_w = torch.zeros(n, dtype=torch.float64, device=w.device)
-        if want_coords:
-            _vv.vv10_coord_grad(state.h, state.prec, g_coords)
-        if want_w:
-            _vv.vv10_weight_grad(state.h, g_w)
         ctx.state = state
         ctx.set_materialize_grads(False)
         return g_rho, g_grad, g_coords, g_w
@@ -147,7 +160,8 @@ class _FirstDerivs(torch.autograd.Function):
 class _Energy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rho, grad_rho, coords, weights, state):
-        state.ensure()
+        with state.lock:
+            state.ensure()
         ctx.state = state
         ctx.save_for_backward(rho, grad_rho, coords, weights)
         return torch.tensor(state.energy, dtype=torch.float64, device=rho.device)

@@ -51,7 +51,7 @@ void vv10_ctx::batch_release() {
     BatchState& B = batch;
     DevBuf* bufs[] = {&B.scratch, &B.small, &B.arena, &B.sums, &B.part, &B.eblk, &B.pair_tab,
                       &B.counter, &B.rtgt, &B.splits, &B.acc, &B.maps, &B.tc_tab,
-                      &B.f16small, &B.f16tab, &B.f16counter};
+                      &B.f16small, &B.f16tab, &B.f16counter, &B.epi, &B.prep_tab};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -145,6 +145,69 @@ vv10_status vv10_ctx::batch_pair_tables(bool fp64, int rpt, int split_tiles) {
     B.pair_tab_fp64 = fp64 ? 1 : 0;
     B.pair_tab_rpt = rpt;
     B.pair_tab_split_tiles = split_tiles;
+    return batch_epi_tables();
+}
+
+// The molecule table of the batched per-point kernels and each launch's block prefix sums
+// (rebuilt with the pair-sum tables and with the tensor-core Hessian layout, outside any
+// stream capture).
+vv10_status vv10_ctx::batch_epi_tables() {
+    BatchState& B = batch;
+    const int n_mol = static_cast<int>(B.mol.size());
+    const bool tc = !B.tc_classes.empty();    // the split-TF32 Hessian layout
+    const bool f16 = !B.f16_classes.empty();  // the split-FP16 one (they share the arenas)
+    std::vector<EpiMol> t(n_mol);
+    std::vector<int64_t> pe(n_mol + 1, 0), pt(n_mol + 1, 0), pm(n_mol + 1, 0), ph(n_mol + 1, 0);
+    for (int m = 0; m < n_mol; ++m) {
+        const BatchMol& M = B.mol[m];
+        EpiMol& e = t[m];
+        e.P = M.P;
+        e.part = at<double>(B.part, M.part);
+        e.sums = at<double>(B.sums, M.sums);
+        e.eblk = at<double>(B.eblk, M.eblk);
+        e.cap = M.cap;
+        e.off = M.off;
+        e.n_split = M.n_split;
+        e.nblk = M.nblk;
+        pe[m + 1] = pe[m] + M.nblk;
+        int64_t ntr = 0, nmx = 0, nhs = 0;
+        if ((tc || f16) && M.nk > 0) {
+            e.rt = at<double>(B.rtgt, M.rt);
+            e.gt = at<double>(B.rtgt, M.gt);
+            e.split = at<char>(B.splits, M.split);
+            e.split_step = tc ? static_cast<int64_t>(a256(sizeof(float) * M.rows * M.nk_pad) / sizeof(float))
+                              : static_cast<int64_t>(a256(sizeof(uint16_t) * 2 * M.rows * M.nk_pad) / sizeof(uint16_t));
+            if (f16) e.f16small = at<char>(B.f16small, M.f16small);
+            e.acc = at<double>(B.acc, M.acc);
+            e.toff = M.toff;
+            e.n_t = M.n_t;
+            e.rows = static_cast<int32_t>(M.rows);
+            ntr = (M.nk_pad / 256) * M.rows;
+            nmx = f16 ? (M.nk_pad / 256) * M.n_t : 0;
+            nhs = ((M.nk + 255) / 256) * M.n_t;
+        }
+        pt[m + 1] = pt[m] + ntr;
+        pm[m + 1] = pm[m] + nmx;
+        ph[m + 1] = ph[m] + nhs;
+    }
+    const size_t pre_bytes = sizeof(int64_t) * (n_mol + 1);
+    B.epi_pre_ep = a256(sizeof(EpiMol) * n_mol);
+    B.epi_pre_tr = B.epi_pre_ep + a256(pre_bytes);
+    B.epi_pre_mx = B.epi_pre_tr + a256(pre_bytes);
+    B.epi_pre_hs = B.epi_pre_mx + a256(pre_bytes);
+    B_TRY(ensure(B.epi, B.epi_pre_hs + a256(pre_bytes), "batch molecule table"));
+    std::vector<unsigned char> buf(B.epi_pre_hs + pre_bytes, 0);
+    std::memcpy(buf.data(), t.data(), sizeof(EpiMol) * n_mol);
+    std::memcpy(buf.data() + B.epi_pre_ep, pe.data(), pre_bytes);
+    std::memcpy(buf.data() + B.epi_pre_tr, pt.data(), pre_bytes);
+    std::memcpy(buf.data() + B.epi_pre_mx, pm.data(), pre_bytes);
+    std::memcpy(buf.data() + B.epi_pre_hs, ph.data(), pre_bytes);
+    B_CUDA(cudaMemcpy(B.epi.p, buf.data(), buf.size(), cudaMemcpyHostToDevice),
+           "upload batch molecule table");
+    B.epi_n_ep = pe[n_mol];
+    B.epi_n_tr = pt[n_mol];
+    B.epi_n_mx = pm[n_mol];
+    B.epi_n_hs = ph[n_mol];
     return VV10_OK;
 }
 
@@ -167,27 +230,18 @@ vv10_status vv10_ctx::batch_ep(vv10_precision prec, double* energies, double* vr
                                     fp64, rpt, n_sm, err, st),
                "batched pair sums");
     }
+    const int n_mol = static_cast<int>(B.mol.size());
+    const EpiMol* mt = at<EpiMol>(B.epi, 0);
     if (with_abc) {  // A_i, B_i, C_i: quantities 3..5 of each molecule's partial buffer
-        PhaseScope ph(this, PH_PAIR_ABC, st, static_cast<int>(B.mol.size()));
-        for (size_t m = 0; m < B.mol.size(); ++m) {
-            BatchMol& M = B.mol[m];
-            double* s = at<double>(B.sums, M.sums);
-            B_CUDA(launch_abc_epilogue(M.P, at<double>(B.part, M.part) + 3 * static_cast<size_t>(M.n_split) * M.nk_pad,
-                                       M.n_split, s + 3 * M.cap, s + 4 * M.cap, s + 5 * M.cap, st),
-                   "batched A/B/C epilogue");
-        }
+        PhaseScope ph(this, PH_PAIR_ABC, st, 1);
+        B_CUDA(launch_abc_epilogue_batch(mt, at<int64_t>(B.epi, B.epi_pre_ep), n_mol, B.epi_n_ep, st),
+               "batched A/B/C epilogue");
     }
-    PhaseScope ph(this, PH_EP_EPILOGUE, st, 2 * static_cast<int>(B.mol.size()));
-    for (size_t m = 0; m < B.mol.size(); ++m) {
-        BatchMol& M = B.mol[m];
-        double* s = at<double>(B.sums, M.sums);
-        B_CUDA(launch_ep_epilogue(M.P, at<double>(B.part, M.part), M.n_split, s, s + M.cap,
-                                  s + 2 * M.cap, vrho ? vrho + M.off : nullptr,
-                                  vgamma ? vgamma + M.off : nullptr, at<double>(B.eblk, M.eblk), err, st),
-               "batched energy epilogue");
-        B_CUDA(launch_sum_blocks(at<double>(B.eblk, M.eblk), M.nblk, energies + m, st),
-               "batched energy sum");
-    }
+    PhaseScope ph(this, PH_EP_EPILOGUE, st, 2);
+    B_CUDA(launch_ep_epilogue_batch(mt, at<int64_t>(B.epi, B.epi_pre_ep), n_mol, B.epi_n_ep, vrho,
+                                    vgamma, err, st),
+           "batched energy epilogue");
+    B_CUDA(launch_sum_blocks_batch(mt, n_mol, energies, st), "batched energy sums");
     B.have_euw = true;
     B.have_abc = with_abc;
     B.abc_fp64 = fp64;
@@ -226,6 +280,7 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
                                         err, st),
                    "batched A/B/C sums");
         }
+        // MODE_ABC writes A/B/C as quantities 0..2 of each molecule's partials
         PhaseScope ph(this, PH_PAIR_ABC, st, static_cast<int>(n_mol));
         for (size_t m = 0; m < n_mol; ++m) {
             BatchMol& M = B.mol[m];
@@ -288,7 +343,7 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
     // task table (row tile x output kind), largest molecules first.
     if (!same_P || B.tc_classes.empty()) {
         batch_drop_graph();
-        size_t rtgt = 0, split = 0, acc = 0, umax = 0;
+        size_t rtgt = 0, split = 0, acc = 0;
         for (size_t m = 0; m < n_mol; ++m) {
             BatchMol& M = B.mol[m];
             const int cap = tc_cap_for(M.n_t, M.nk);
@@ -305,13 +360,10 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
             split += 4 * a256(sizeof(float) * M.rows * M.nk_pad);
             M.acc = acc;
             acc += a256(sizeof(double) * 2 * M.n_t * M.nk_pad);
-            umax = std::max(umax, sizeof(double) * M.n_t * M.nk_pad);
         }
         B_TRY(ensure(B.rtgt, rtgt, "batch trial values"));
         B_TRY(ensure(B.splits, split > 0 ? split : 256, "batch trial splits"));
         B_TRY(ensure(B.acc, acc > 0 ? acc : 256, "batch contraction partials"));
-        B_TRY(ensure(tu, umax > 0 ? umax : 256, "trial u"));
-        B_TRY(ensure(ty, umax > 0 ? umax : 256, "trial y"));
         std::vector<unsigned char> maps(512 * n_mol, 0);
         for (size_t m = 0; m < n_mol; ++m) {
             BatchMol& M = B.mol[m];
@@ -376,23 +428,16 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
                    "upload tensor-core tables");
         B.hess_P.assign(Pt, Pt + n_mol);
         B.f16_classes.clear();  // the split-FP16 layout shares the arenas: rebuild it when used
+        B_TRY(batch_epi_tables());
     }
 
-    // trial values and splits, molecule by molecule
-    for (size_t m = 0; m < n_mol; ++m) {
-        BatchMol& M = B.mol[m];
-        if (M.nk == 0) continue;
-        float* sp = at<float>(B.splits, M.split);
-        const size_t step = a256(sizeof(float) * M.rows * M.nk_pad) / sizeof(float);
-        PhaseScope ph(this, PH_TRIAL_PREP, st, 2);
-        B_CUDA(launch_trial_prep(M.P, M.n_t, rho_t + M.toff, grad_rho_t + 3 * M.toff,
-                                 static_cast<double*>(tu.p), static_cast<double*>(ty.p),
-                                 at<double>(B.rtgt, M.rt), at<double>(B.rtgt, M.gt), st),
-               "trial prep");
-        B_CUDA(launch_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), M.n_t,
-                                  static_cast<int32_t>(M.rows), M.nk_pad, false, sp, sp + step,
-                                  sp + 2 * step, sp + 3 * step, st),
-               "trial split");
+    // trial values and their split-TF32 cut, every molecule in one launch
+    const EpiMol* mt = at<EpiMol>(B.epi, 0);
+    {
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 1);
+        B_CUDA(launch_trial_tc_batch(mt, at<int64_t>(B.epi, B.epi_pre_tr), static_cast<int>(n_mol),
+                                     B.epi_n_tr, rho_t, grad_rho_t, st),
+               "batched trial values and split");
     }
     B_CUDA(cudaMemsetAsync(B.acc.p, 0, B.acc.bytes, st), "zero contraction partials");
     {
@@ -403,17 +448,10 @@ vv10_status vv10_ctx::batch_hess(vv10_precision prec, const int32_t* Pt, const d
                                         n_sm, tc_flush, err, st),
                    "batched tensor-core contraction");
     }
-    PhaseScope ph(this, PH_HESS_EPILOGUE, st, static_cast<int>(n_mol));
-    for (size_t m = 0; m < n_mol; ++m) {
-        BatchMol& M = B.mol[m];
-        if (M.nk == 0) continue;
-        double* s = at<double>(B.sums, M.sums);
-        B_CUDA(launch_hess_epilogue(M.P, M.n_t, at<double>(B.acc, M.acc), 1, M.nk_pad, s + M.cap,
-                                    s + 2 * M.cap, s + 3 * M.cap, s + 4 * M.cap, s + 5 * M.cap,
-                                    at<double>(B.rtgt, M.rt), at<double>(B.rtgt, M.gt),
-                                    f_rho_t + M.toff, f_gamma_t + M.toff, err, st),
-               "Hessian epilogue");
-    }
+    PhaseScope ph(this, PH_HESS_EPILOGUE, st, 1);
+    B_CUDA(launch_hess_epilogue_batch(mt, at<int64_t>(B.epi, B.epi_pre_hs), static_cast<int>(n_mol),
+                                      B.epi_n_hs, f_rho_t, f_gamma_t, err, st),
+           "batched Hessian epilogue");
     return VV10_OK;
 }
 
@@ -430,7 +468,7 @@ vv10_status vv10_ctx::batch_hess_f16(bool same_P, const int32_t* Pt, const doubl
     int* err = static_cast<int*>(dev_err.p);
     if (!same_P || B.f16_classes.empty()) {
         batch_drop_graph();
-        size_t rtgt = 0, split = 0, small = 0, acc = 0, umax = 0;
+        size_t rtgt = 0, split = 0, small = 0, acc = 0;
         for (size_t m = 0; m < n_mol; ++m) {
             BatchMol& M = B.mol[m];
             const int cap = tc_cap_for(M.n_t, M.nk);
@@ -450,14 +488,11 @@ vv10_status vv10_ctx::batch_hess_f16(bool same_P, const int32_t* Pt, const doubl
                      a256(sizeof(double) * M.n_t);
             M.acc = acc;
             acc += a256(sizeof(double) * 2 * M.n_t * M.nk_pad);
-            umax = std::max(umax, sizeof(double) * M.n_t * M.nk_pad);
         }
         B_TRY(ensure(B.rtgt, rtgt, "batch trial values"));
         B_TRY(ensure(B.splits, split > 0 ? split : 256, "batch FP16 trial tiles"));
         B_TRY(ensure(B.f16small, small > 0 ? small : 256, "batch FP16 trial factors"));
         B_TRY(ensure(B.acc, acc > 0 ? acc : 256, "batch contraction partials"));
-        B_TRY(ensure(tu, umax > 0 ? umax : 256, "trial u"));
-        B_TRY(ensure(ty, umax > 0 ? umax : 256, "trial y"));
         std::vector<unsigned char> maps(256 * n_mol, 0);
         for (size_t m = 0; m < n_mol; ++m) {
             BatchMol& M = B.mol[m];
@@ -526,29 +561,17 @@ vv10_status vv10_ctx::batch_hess_f16(bool same_P, const int32_t* Pt, const doubl
         B_TRY(ensure(B.f16counter, 256, "batch task counter"));
         B.hess_P.assign(Pt, Pt + n_mol);
         B.tc_classes.clear();  // the split-TF32 layout shares the arenas: rebuild it when used
+        B_TRY(batch_epi_tables());
     }
 
-    // trial values, factors and FP16 tiles, molecule by molecule
-    for (size_t m = 0; m < n_mol; ++m) {
-        BatchMol& M = B.mol[m];
-        if (M.nk == 0) continue;
-        char* sp = at<char>(B.splits, M.split);
-        const size_t half = a256(sizeof(uint16_t) * 2 * M.rows * M.nk_pad);
-        char* sm = at<char>(B.f16small, M.f16small);
-        const size_t o_par = a256(sizeof(unsigned int) * 2 * M.n_t);
-        const size_t o_sc = o_par + 256;
-        const size_t o_isc = o_sc + a256(sizeof(float) * M.n_t);
-        PhaseScope ph(this, PH_TRIAL_PREP, st, 4);
-        B_CUDA(launch_trial_prep(M.P, M.n_t, rho_t + M.toff, grad_rho_t + 3 * M.toff,
-                                 static_cast<double*>(tu.p), static_cast<double*>(ty.p),
-                                 at<double>(B.rtgt, M.rt), at<double>(B.rtgt, M.gt), st),
-               "trial prep");
-        B_CUDA(launch_f16_trial_split(static_cast<double*>(tu.p), static_cast<double*>(ty.p), M.n_t,
-                                      static_cast<int32_t>(M.rows), M.nk_pad,
-                                      reinterpret_cast<unsigned int*>(sm), reinterpret_cast<float*>(sm + o_par),
-                                      reinterpret_cast<float*>(sm + o_sc), reinterpret_cast<double*>(sm + o_isc),
-                                      sp, sp + half, st),
-               "FP16 trial split");
+    // trial values, column maxima, factors and FP16 tiles of every molecule in three launches
+    B_CUDA(cudaMemsetAsync(B.f16small.p, 0, B.f16small.bytes, st), "zero trial column maxima");
+    {
+        PhaseScope ph(this, PH_TRIAL_PREP, st, 3);
+        B_CUDA(launch_f16_trial_batch(at<EpiMol>(B.epi, 0), at<int64_t>(B.epi, B.epi_pre_mx),
+                                      at<int64_t>(B.epi, B.epi_pre_tr), static_cast<int>(n_mol),
+                                      B.epi_n_mx, B.epi_n_tr, rho_t, grad_rho_t, st),
+               "batched FP16 trial tiles");
     }
     B_CUDA(cudaMemsetAsync(B.acc.p, 0, B.acc.bytes, st), "zero contraction partials");
     {
@@ -559,17 +582,10 @@ vv10_status vv10_ctx::batch_hess_f16(bool same_P, const int32_t* Pt, const doubl
                                          static_cast<int*>(B.f16counter.p), n_sm, tc_flush, err, st),
                    "batched split-FP16 contraction");
     }
-    PhaseScope ph(this, PH_HESS_EPILOGUE, st, static_cast<int>(n_mol));
-    for (size_t m = 0; m < n_mol; ++m) {
-        BatchMol& M = B.mol[m];
-        if (M.nk == 0) continue;
-        double* s = at<double>(B.sums, M.sums);
-        B_CUDA(launch_hess_epilogue(M.P, M.n_t, at<double>(B.acc, M.acc), 1, M.nk_pad, s + M.cap,
-                                    s + 2 * M.cap, s + 3 * M.cap, s + 4 * M.cap, s + 5 * M.cap,
-                                    at<double>(B.rtgt, M.rt), at<double>(B.rtgt, M.gt),
-                                    f_rho_t + M.toff, f_gamma_t + M.toff, err, st),
-               "Hessian epilogue");
-    }
+    PhaseScope ph(this, PH_HESS_EPILOGUE, st, 1);
+    B_CUDA(launch_hess_epilogue_batch(at<EpiMol>(B.epi, 0), at<int64_t>(B.epi, B.epi_pre_hs),
+                                      static_cast<int>(n_mol), B.epi_n_hs, f_rho_t, f_gamma_t, err, st),
+           "batched Hessian epilogue");
     return VV10_OK;
 }
 
@@ -659,28 +675,54 @@ vv10_status vv10_batch_prepare(vv10_handle h, int32_t n_mol, const int64_t* offs
         }
         B.h_small_bytes = 64 * static_cast<size_t>(n_mol);
     }
-    std::vector<PrepareScratch> ps(n_mol);
     int* err = static_cast<int*>(h->dev_err.p);
+    // one table of every molecule's pointers, and the block prefix sums of both phases
+    std::vector<PrepMol> pm(n_mol);
+    std::vector<int64_t> pre_blk(n_mol + 1, 0), pre_pts(n_mol + 1, 0);
+    int max_keys = 1;
     for (int32_t m = 0; m < n_mol; ++m) {
         BatchMol& M = B.mol[m];
+        PrepMol& q = pm[m];
         const int nblk = prepare_nblk(M.n);
         const int n_keys = (M.n_atom > 0 ? M.n_atom : 1) + 1;
         const size_t Mk = static_cast<size_t>(n_keys) * nblk;
         char* base = static_cast<char*>(B.scratch.p) + sc_off[m];
-        ps[m].hist = reinterpret_cast<int32_t*>(base);
-        ps[m].offs = reinterpret_cast<int64_t*>(base + a256(4 * Mk));
-        ps[m].bbox_part = reinterpret_cast<double*>(base + a256(4 * Mk) + a256(8 * (Mk + n_keys + 1)));
-        ps[m].center = reinterpret_cast<double*>(static_cast<char*>(B.small.p) + 64 * m);
-        ps[m].nk_dev = reinterpret_cast<int64_t*>(static_cast<char*>(B.small.p) + 64 * m + 32);
+        q.n = M.n;
+        q.xyz = xyz + 3 * M.off;
+        q.w = w + M.off;
+        q.rho = rho + M.off;
+        q.grad = grad_rho + 3 * M.off;
+        q.atom = atom_of_point ? atom_of_point + M.off : nullptr;
+        q.n_atom = M.n_atom;
+        q.n_keys = n_keys;
+        q.nblk = nblk;
+        q.hist = reinterpret_cast<int32_t*>(base);
+        q.offs = reinterpret_cast<int64_t*>(base + a256(4 * Mk));
+        q.bbox_part = reinterpret_cast<double*>(base + a256(4 * Mk) + a256(8 * (Mk + n_keys + 1)));
+        q.center = reinterpret_cast<double*>(static_cast<char*>(B.small.p) + 64 * m);
+        q.nk_dev = reinterpret_cast<int64_t*>(static_cast<char*>(B.small.p) + 64 * m + 32);
+        pre_blk[m + 1] = pre_blk[m] + (M.n > 0 ? nblk : 0);
+        max_keys = std::max(max_keys, n_keys);
+    }
+    const size_t tab_bytes = a256(sizeof(PrepMol) * n_mol);
+    const size_t pre_bytes = sizeof(int64_t) * (n_mol + 1);
+    s = h->ensure(B.prep_tab, tab_bytes + 2 * a256(pre_bytes), "batch prepare table");
+    if (s != VV10_OK) return s;
+    PrepMol* d_pm = static_cast<PrepMol*>(B.prep_tab.p);
+    int64_t* d_pre_blk = reinterpret_cast<int64_t*>(static_cast<char*>(B.prep_tab.p) + tab_bytes);
+    int64_t* d_pre_pts = reinterpret_cast<int64_t*>(static_cast<char*>(B.prep_tab.p) + tab_bytes + a256(pre_bytes));
+    cudaError_t e = cudaMemcpy(d_pm, pm.data(), sizeof(PrepMol) * n_mol, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_pre_blk, pre_blk.data(), pre_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return h->cuda_fail(e, "upload batch prepare table");
+    {
         PhaseScope ph(h, PH_PREPARE, st, 2);
-        cudaError_t e = launch_prepare_count(M.n, xyz + 3 * M.off, w + M.off, rho + M.off,
-                                             grad_rho + 3 * M.off,
-                                             atom_of_point ? atom_of_point + M.off : nullptr,
-                                             M.n_atom, prm.rho_cut, ps[m], err, st);
+        e = launch_prepare_count_batch(d_pm, d_pre_blk, n_mol, pre_blk[n_mol], max_keys,
+                                       prm.rho_cut, err, st);
         if (e != cudaSuccess) return h->cuda_fail(e, "batch prepare count");
     }
-    cudaError_t e = cudaMemcpyAsync(B.h_small, B.small.p, 64 * static_cast<size_t>(n_mol),
-                                    cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(B.h_small, B.small.p, 64 * static_cast<size_t>(n_mol),
+                        cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return h->cuda_fail(e, "read kept counts");
     s = h->check_device_errors(st);  // synchronises
     if (s != VV10_OK) return s;
@@ -727,12 +769,19 @@ vv10_status vv10_batch_prepare(vv10_handle h, int32_t n_mol, const int64_t* offs
         float4* r32b = reinterpret_cast<float4*>(p);
         p += a256(16 * M.cap);
         float4* r32p = reinterpret_cast<float4*>(p);
-        PhaseScope ph(h, PH_PREPARE, st, M.nk_pad > 0 ? 2 : 1);
-        e = launch_prepare_scatter(M.n, xyz + 3 * M.off, w + M.off, rho + M.off, grad_rho + 3 * M.off,
-                                   atom_of_point ? atom_of_point + M.off : nullptr, M.n_atom,
-                                   prm.rho_cut, prm.b, prm.C, ps[m], M.nk, M.nk_pad, orig, seg,
-                                   atom_k, soa, r64a, r64b, r32a, r32b, r32p, st);
-        if (e != cudaSuccess) return h->cuda_fail(e, "batch prepare scatter");
+        PrepMol& q = pm[m];
+        q.nk = M.nk;
+        q.nk_pad = M.nk_pad;
+        q.orig = orig;
+        q.seg = seg;
+        q.atom_k = atom_k;
+        q.soa = soa;
+        q.r64a = r64a;
+        q.r64b = r64b;
+        q.r32a = r32a;
+        q.r32b = r32b;
+        q.r32p = r32p;
+        pre_pts[m + 1] = pre_pts[m] + M.nk_pad / 256;
         PointsDev& P = M.P;
         P.n = M.n;
         P.nk = M.nk;
@@ -764,6 +813,16 @@ vv10_status vv10_batch_prepare(vv10_handle h, int32_t n_mol, const int64_t* offs
         P.r32b = r32b;
         P.r32p = r32p;
         n_kept[m] = M.nk;
+    }
+    e = cudaMemcpy(d_pm, pm.data(), sizeof(PrepMol) * n_mol, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_pre_pts, pre_pts.data(), pre_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return h->cuda_fail(e, "upload batch prepare table");
+    {
+        PhaseScope ph(h, PH_PREPARE, st, 2);
+        e = launch_prepare_scatter_batch(d_pm, d_pre_blk, d_pre_pts, n_mol, pre_blk[n_mol],
+                                         pre_pts[n_mol], max_keys, prm.rho_cut, prm.b, prm.C, st);
+        if (e != cudaSuccess) return h->cuda_fail(e, "batch prepare scatter");
     }
     B.order.resize(n_mol);
     std::iota(B.order.begin(), B.order.end(), 0);

@@ -116,6 +116,21 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // Error-free transformation of a sum (Knuth's TwoSum): s + e == a + b exactly.
+// The molecule whose block range [pre[m], pre[m + 1]) holds launch block k (pre: n_mol + 1
+// prefix sums, pre[0] = 0 <= k < pre[n_mol]; molecules with no blocks are skipped), and the
+// block's index inside it.
+__device__ __forceinline__ int batch_block_mol(const int64_t* __restrict__ pre, int n_mol,
+                                               int64_t k, int64_t& local) {
+    int lo = 0, hi = n_mol;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    local = k - pre[lo];
+    return lo;
+}
+
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
     s = a + b;
     const double bp = s - a;

@@ -14,10 +14,11 @@
 // diagonal terms are the delta_ij / w_i parts of the four printed coefficients.
 #include "common.cuh"
 #include "kernels.hpp"
+#include "tc.cuh"
 
 namespace vv10 {
 
-static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __global__ void __launch_bounds__(256)
 k_trial_prep(PointsDev P, int32_t Pn, const double* __restrict__ rho_t,
@@ -42,6 +43,42 @@ k_trial_prep(PointsDev P, int32_t Pn, const double* __restrict__ rho_t,
     y[o] = 2.0 * w * (P.rho[p] * P.om_g[p]) * gt;
     rt_k[static_cast<int64_t>(t) * P.nk + p] = rt;
     gt_k[static_cast<int64_t>(t) * P.nk + p] = gt;
+}
+
+// Batched: trial values and their split-TF32 cut in one pass (the same values as
+// k_trial_prep followed by the tensor-core path's trial split).  Rows t >= n_t are zero.
+__global__ void __launch_bounds__(256)
+k_trial_tc_batch(const EpiMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                 const double* __restrict__ rho_t, const double* __restrict__ grad_rho_t) {
+    int64_t blk;
+    const EpiMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    const int64_t nb = M.P.nk_pad / 256;
+    const int t = static_cast<int>(blk / nb);
+    const int64_t p = (blk - t * nb) * 256 + threadIdx.x;
+    float a = 0.f, c = 0.f;
+    if (t < M.n_t && p < M.P.nk) {
+        double u, y, rt, gt;
+        trial_values(M.P, rho_t + M.toff, grad_rho_t + 3 * M.toff, t, p, u, y, rt, gt);
+        M.rt[static_cast<int64_t>(t) * M.P.nk + p] = rt;
+        M.gt[static_cast<int64_t>(t) * M.P.nk + p] = gt;
+        a = static_cast<float>(-1.5 * u);  // the kernel tiles omit the -3/2 of Phi and the sign of T2
+        c = static_cast<float>(1.5 * y);
+    }
+    const float ah = __uint_as_float(tc::to_tf32(a)), ch = __uint_as_float(tc::to_tf32(c));
+    const int64_t o = static_cast<int64_t>(t) * M.P.nk_pad + p;
+    float* sp = static_cast<float*>(M.split);
+    sp[o] = ah;
+    sp[M.split_step + o] = a - ah;
+    sp[2 * M.split_step + o] = ch;
+    sp[3 * M.split_step + o] = c - ch;
+}
+
+cudaError_t launch_trial_tc_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                  const double* rho_t, const double* grad_rho_t, cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    k_trial_tc_batch<<<static_cast<unsigned>(n_blocks), 256, 0, st>>>(mols, pre, n_mol, rho_t,
+                                                                      grad_rho_t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trial_prep(const PointsDev& p, int32_t P, const double* rho_t,
@@ -179,15 +216,12 @@ cudaError_t launch_hess_f64(const PointsDev& p, int32_t P, const double* u, cons
 }
 
 // ------------------------------------------------------------------ epilogue
-__global__ void __launch_bounds__(256)
-k_hess_epilogue(PointsDev P, int32_t Pn, const double* __restrict__ acc, int n_split,
-                int64_t acc_ld, const double* __restrict__ U, const double* __restrict__ W,
-                const double* __restrict__ A, const double* __restrict__ B,
-                const double* __restrict__ C, const double* __restrict__ rt_k,
-                const double* __restrict__ gt_k, double* __restrict__ f_rho_t,
-                double* __restrict__ f_gamma_t, int* err) {
-    const int t = blockIdx.y;
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void hess_epilogue_point(
+    const PointsDev& P, int32_t Pn, const double* __restrict__ acc, int n_split, int64_t acc_ld,
+    const double* __restrict__ U, const double* __restrict__ W, const double* __restrict__ A,
+    const double* __restrict__ B, const double* __restrict__ C, const double* __restrict__ rt_k,
+    const double* __restrict__ gt_k, double* __restrict__ f_rho_t, double* __restrict__ f_gamma_t,
+    int* err, int t, int64_t p) {
     if (p >= P.nk) return;
     double ar = 0.0, ag = 0.0;
     for (int k = 0; k < n_split; ++k) {
@@ -211,6 +245,42 @@ k_hess_epilogue(PointsDev P, int32_t Pn, const double* __restrict__ acc, int n_s
     f_rho_t[o] = fr;
     f_gamma_t[o] = fg;
     if (!isfinite(fr) || !isfinite(fg)) atomicOr(err, DEVERR_NONFINITE);
+}
+
+__global__ void __launch_bounds__(256)
+k_hess_epilogue(PointsDev P, int32_t Pn, const double* __restrict__ acc, int n_split,
+                int64_t acc_ld, const double* __restrict__ U, const double* __restrict__ W,
+                const double* __restrict__ A, const double* __restrict__ B,
+                const double* __restrict__ C, const double* __restrict__ rt_k,
+                const double* __restrict__ gt_k, double* __restrict__ f_rho_t,
+                double* __restrict__ f_gamma_t, int* err) {
+    hess_epilogue_point(P, Pn, acc, n_split, acc_ld, U, W, A, B, C, rt_k, gt_k, f_rho_t, f_gamma_t,
+                        err, blockIdx.y, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+// Block k of molecule m: trial t = k / nb, kept points 256 (k mod nb) .., nb = ceil(nk / 256);
+// one split (the tensor-core partials), row sums E..C at sums + k cap.
+__global__ void __launch_bounds__(256)
+k_hess_epilogue_batch(const EpiMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                      double* __restrict__ f_rho_t, double* __restrict__ f_gamma_t, int* err) {
+    int64_t blk;
+    const EpiMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    const int64_t nb = cdiv64(M.P.nk, 256);
+    const int t = static_cast<int>(blk / nb);
+    const int64_t p = (blk - t * nb) * 256 + threadIdx.x;
+    const double* s = M.sums;
+    hess_epilogue_point(M.P, M.n_t, M.acc, 1, M.P.nk_pad, s + M.cap, s + 2 * M.cap, s + 3 * M.cap,
+                        s + 4 * M.cap, s + 5 * M.cap, M.rt, M.gt, f_rho_t + M.toff,
+                        f_gamma_t + M.toff, err, t, p);
+}
+
+cudaError_t launch_hess_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                       double* f_rho_t, double* f_gamma_t, int* err,
+                                       cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    k_hess_epilogue_batch<<<static_cast<unsigned>(n_blocks), 256, 0, st>>>(mols, pre, n_mol, f_rho_t,
+                                                                           f_gamma_t, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hess_epilogue(const PointsDev& p, int32_t P, const double* acc, int n_split,

@@ -676,9 +676,10 @@ k_f16_colmax(const double* __restrict__ u, const double* __restrict__ y, int64_t
 // c_y (a power of two near max|u'| / max|y'| over all trials, clamped to 2^[-24, 24]) and the
 // column factors s_t (the column's max(|u'|, c_y |y'|) mapped into [2^14, 2^15)).
 // params[0] = 1/c_y, params[1] = c_y; scale[t] = s_t; col_isc[t] = 1/s_t.
-__global__ void __launch_bounds__(256)
-k_f16_scales(const unsigned int* __restrict__ colmax, int32_t P, float* __restrict__ params,
-             float* __restrict__ scale, double* __restrict__ col_isc) {
+__device__ __forceinline__ void f16_scales_block(const unsigned int* __restrict__ colmax, int32_t P,
+                                                 float* __restrict__ params,
+                                                 float* __restrict__ scale,
+                                                 double* __restrict__ col_isc) {
     __shared__ float su[8], sy[8];
     __shared__ float s_cy;
     float mu = 0.f, my = 0.f;
@@ -721,21 +722,24 @@ k_f16_scales(const unsigned int* __restrict__ colmax, int32_t P, float* __restri
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_f16_scales(const unsigned int* __restrict__ colmax, int32_t P, float* __restrict__ params,
+             float* __restrict__ scale, double* __restrict__ col_isc) {
+    f16_scales_block(colmax, P, params, scale, col_isc);
+}
+
 // FP16 hi / lo trial tiles: row t, stage s holds 32 halves, u' s_t for the stage's 16 j
 // then c_y y' s_t; rows t >= P are zero.
-__global__ void __launch_bounds__(256)
-k_f16_split(const double* __restrict__ u, const double* __restrict__ y, int32_t P,
-            int64_t nk_pad, const float* __restrict__ params, const float* __restrict__ scale,
-            __half* __restrict__ bh, __half* __restrict__ bl) {
-    const int t = blockIdx.y;
-    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j >= nk_pad) return;
+// Row t, point j of the FP16 hi / lo trial tiles from u, y (zero where t or j is padding).
+__device__ __forceinline__ void f16_split_point(double u, double y, bool real, int t, int64_t j,
+                                                int64_t nk_pad, const float* __restrict__ params,
+                                                const float* __restrict__ scale,
+                                                __half* __restrict__ bh, __half* __restrict__ bl) {
     float a = 0.f, b = 0.f;
-    if (t < P) {
-        const int64_t o = static_cast<int64_t>(t) * nk_pad + j;
+    if (real) {
         const float st = scale[t];
-        a = static_cast<float>(-1.5 * u[o]) * st;            // exact power-of-two scalings
-        b = static_cast<float>(1.5 * y[o]) * (params[1] * st);
+        a = static_cast<float>(-1.5 * u) * st;            // exact power-of-two scalings
+        b = static_cast<float>(1.5 * y) * (params[1] * st);
     }
     const __half ah = __float2half_rn(a), bhh = __float2half_rn(b);
     const __half al = __float2half_rn(a - __half2float(ah)), bll = __float2half_rn(b - __half2float(bhh));
@@ -744,6 +748,108 @@ k_f16_split(const double* __restrict__ u, const double* __restrict__ y, int32_t 
     bh[off + 16] = bhh;
     bl[off] = al;
     bl[off + 16] = bll;
+}
+
+__global__ void __launch_bounds__(256)
+k_f16_split(const double* __restrict__ u, const double* __restrict__ y, int32_t P,
+            int64_t nk_pad, const float* __restrict__ params, const float* __restrict__ scale,
+            __half* __restrict__ bh, __half* __restrict__ bl) {
+    const int t = blockIdx.y;
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= nk_pad) return;
+    const int64_t o = static_cast<int64_t>(t) * nk_pad + j;
+    f16_split_point(t < P ? u[o] : 0.0, t < P ? y[o] : 0.0, t < P, t, j, nk_pad, params, scale, bh, bl);
+}
+
+// ---- the batch: every molecule's trial values, column maxima, factors and FP16 tiles in three
+// launches (the molecule table's f16 area: colmax [2 n_t] words (zeroed by the caller) |
+// params at o_par | scale [n_t] floats at o_sc | col_isc [n_t] doubles at o_isc).
+struct F16Small {
+    unsigned int* colmax;
+    float* params;
+    float* scale;
+    double* col_isc;
+};
+__device__ __forceinline__ F16Small f16_small(const EpiMol& M) {
+    char* sm = static_cast<char*>(M.f16small);
+    const size_t o_par = ((sizeof(unsigned int) * 2 * M.n_t + 255) / 256) * 256;
+    const size_t o_sc = o_par + 256;
+    const size_t o_isc = o_sc + ((sizeof(float) * M.n_t + 255) / 256) * 256;
+    return F16Small{reinterpret_cast<unsigned int*>(sm), reinterpret_cast<float*>(sm + o_par),
+                    reinterpret_cast<float*>(sm + o_sc), reinterpret_cast<double*>(sm + o_isc)};
+}
+
+// Block k of molecule m: trial t = k / nb, kept points 256 (k mod nb) .., nb = nk_pad / 256:
+// rho^t and gamma^t at the kept points, and the trial's largest |u'|, |y'|.
+__global__ void __launch_bounds__(256)
+k_f16_trial_max_batch(const EpiMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                      const double* __restrict__ rho_t, const double* __restrict__ grad_rho_t) {
+    int64_t blk;
+    const EpiMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    const int64_t nb = M.P.nk_pad / 256;
+    const int t = static_cast<int>(blk / nb);
+    const int64_t p = (blk - t * nb) * 256 + threadIdx.x;
+    float mu = 0.f, my = 0.f;
+    if (p < M.P.nk) {
+        double u, y, rt, gt;
+        trial_values(M.P, rho_t + M.toff, grad_rho_t + 3 * M.toff, t, p, u, y, rt, gt);
+        M.rt[static_cast<int64_t>(t) * M.P.nk + p] = rt;
+        M.gt[static_cast<int64_t>(t) * M.P.nk + p] = gt;
+        mu = fabsf(static_cast<float>(-1.5 * u));
+        my = fabsf(static_cast<float>(1.5 * y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const F16Small f = f16_small(M);
+        atomicMax(&f.colmax[t], __float_as_uint(mu));
+        atomicMax(&f.colmax[M.n_t + t], __float_as_uint(my));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_f16_scales_batch(const EpiMol* __restrict__ mols) {
+    const EpiMol& M = mols[blockIdx.x];
+    if (M.P.nk == 0 || M.n_t == 0) return;
+    const F16Small f = f16_small(M);
+    f16_scales_block(f.colmax, M.n_t, f.params, f.scale, f.col_isc);
+}
+
+// Block k of molecule m: row t = k / nb of its FP16 tiles (rows >= n_t zero), points
+// 256 (k mod nb) ..; hi tiles at M.split, lo tiles M.split_step halves further.
+__global__ void __launch_bounds__(256)
+k_f16_split_batch(const EpiMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                  const double* __restrict__ rho_t, const double* __restrict__ grad_rho_t) {
+    int64_t blk;
+    const EpiMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    const int64_t nb = M.P.nk_pad / 256;
+    const int t = static_cast<int>(blk / nb);
+    const int64_t p = (blk - t * nb) * 256 + threadIdx.x;
+    const bool real = t < M.n_t && p < M.P.nk;
+    double u = 0.0, y = 0.0;
+    if (real) {
+        double rt, gt;
+        trial_values(M.P, rho_t + M.toff, grad_rho_t + 3 * M.toff, t, p, u, y, rt, gt);
+    }
+    const F16Small f = f16_small(M);
+    __half* bh = reinterpret_cast<__half*>(M.split);
+    f16_split_point(u, y, real, t, p, M.P.nk_pad, f.params, f.scale, bh, bh + M.split_step);
+}
+
+cudaError_t launch_f16_trial_batch(const EpiMol* mols, const int64_t* pre_max,
+                                   const int64_t* pre_split, int n_mol, int64_t n_max_blocks,
+                                   int64_t n_split_blocks, const double* rho_t,
+                                   const double* grad_rho_t, cudaStream_t st) {
+    if (n_max_blocks > 0)
+        k_f16_trial_max_batch<<<static_cast<unsigned>(n_max_blocks), 256, 0, st>>>(mols, pre_max, n_mol,
+                                                                                 rho_t, grad_rho_t);
+    k_f16_scales_batch<<<n_mol, 256, 0, st>>>(mols);
+    if (n_split_blocks > 0)
+        k_f16_split_batch<<<static_cast<unsigned>(n_split_blocks), 256, 0, st>>>(mols, pre_split, n_mol,
+                                                                               rho_t, grad_rho_t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_f16_trial_split(const double* u, const double* y, int32_t P, int32_t rows,

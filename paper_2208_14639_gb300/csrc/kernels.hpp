@@ -33,6 +33,46 @@ struct PointsDev {
     const float4* r32p;
 };
 
+// One molecule of a batch, as the batched per-point kernels read it (a device table, one
+// entry per molecule).  A launch over many molecules takes the prefix sums `pre` (n_mol + 1
+// entries) of the blocks each molecule's own grid has: block k of the launch plays block
+// k - pre[m] of molecule m, pre[m] <= k < pre[m + 1].
+struct EpiMol {
+    PointsDev P;
+    const double* part = nullptr;  // pair-sum partials [q][n_split][nk_pad]
+    double* sums = nullptr;        // E, U, W, A, B, C at sums + k cap
+    double* eblk = nullptr;        // energy block partials (nblk)
+    double* rt = nullptr;          // rho^t, gamma^t at kept points [n_t][nk]
+    double* gt = nullptr;
+    void* split = nullptr;         // split TF32: four FP32 arrays uh, ul, yh, yl, split_step
+                                   // floats apart; split FP16: hi, lo tiles split_step halves apart
+    void* f16small = nullptr;      // split FP16: column maxima, factors and y balance
+    double* acc = nullptr;         // contraction partials [2][n_t][nk_pad]
+    int64_t cap = 0;               // row-sum stride
+    int64_t off = 0;               // first caller point
+    int64_t toff = 0;              // first trial value in the caller's concatenated arrays
+    int64_t split_step = 0;
+    int32_t n_split = 1, nblk = 0;  // pair-sum splits; energy blocks
+    int32_t n_t = 0, rows = 0;      // trials; rows of each trial split
+};
+#ifdef __CUDACC__
+// Trial values of row t at kept point p: u = w rho^t and y = 2 w sigma gamma^t (zero at padding
+// points), and rho^t, gamma^t for the epilogue.
+__device__ __forceinline__ void trial_values(const PointsDev& P, const double* __restrict__ rho_t,
+                                             const double* __restrict__ grad_rho_t, int t, int64_t p,
+                                             double& u, double& y, double& rt, double& gt) {
+    const int64_t i = P.orig[p];
+    const int64_t src = static_cast<int64_t>(t) * P.n + i;
+    rt = rho_t[src];
+    const double* g = grad_rho_t + 3 * src;
+    gt = P.gx[p] * g[0] + P.gy[p] * g[1] + P.gz[p] * g[2];  // gamma^t
+    const double w = P.w[p];
+    u = w * rt;
+    y = 2.0 * w * (P.rho[p] * P.om_g[p]) * gt;
+}
+
+#endif
+
 // SoA field order inside the FP64 per-point arena (each field nk_pad long).
 enum SoaField : int {
     F_W = 0, F_RHO, F_GX, F_GY, F_GZ, F_OM, F_KA, F_OMR, F_OMG, F_KAR, F_OMRR, F_OMRG, F_OMGG,
@@ -48,6 +88,36 @@ struct PrepareScratch {
     int64_t* nk_dev;    // 1
 };
 int prepare_nblk(int64_t n);
+// One molecule of a batched prepare (device table).  Phase 1 (count + scan) reads the caller
+// arrays and writes hist / offs / bbox_part / center / nk_dev; phase 2 (scatter + points, once
+// nk is known) writes the molecule's point block.
+struct PrepMol {
+    int64_t n = 0;
+    const double *xyz = nullptr, *w = nullptr, *rho = nullptr, *grad = nullptr;
+    const int32_t* atom = nullptr;
+    int32_t n_atom = 0, n_keys = 0, nblk = 0, pad = 0;
+    int32_t* hist = nullptr;
+    int64_t* offs = nullptr;      // n_keys nblk offsets, then the segment starts
+    double* bbox_part = nullptr;
+    double* center = nullptr;
+    int64_t* nk_dev = nullptr;
+    int64_t nk = 0, nk_pad = 0;
+    int64_t *orig = nullptr, *seg = nullptr;
+    int32_t* atom_k = nullptr;
+    double* soa = nullptr;
+    double4 *r64a = nullptr, *r64b = nullptr;
+    float4 *r32a = nullptr, *r32b = nullptr, *r32p = nullptr;
+};
+// Batched prepare: the count blocks (pre: prefix sums of nblk) and one scan CTA per
+// molecule; then the scatter blocks (pre_blk) and the point blocks (pre_pts: prefix sums of
+// nk_pad / 256).  max_keys: the largest n_keys.
+cudaError_t launch_prepare_count_batch(const PrepMol* mols, const int64_t* pre, int n_mol,
+                                       int64_t n_blocks, int max_keys, double rho_cut, int* err,
+                                       cudaStream_t st);
+cudaError_t launch_prepare_scatter_batch(const PrepMol* mols, const int64_t* pre_blk,
+                                         const int64_t* pre_pts, int n_mol, int64_t n_blocks,
+                                         int64_t n_point_blocks, int max_keys, double rho_cut,
+                                         double b, double C, cudaStream_t st);
 cudaError_t launch_prepare_count(int64_t n, const double* xyz, const double* w, const double* rho,
                                  const double* grad, const int32_t* atom, int32_t n_atom,
                                  double rho_cut, const PrepareScratch& s, int* err,
@@ -114,6 +184,16 @@ cudaError_t launch_ep_epilogue(const PointsDev& p, const double* part, int n_spl
 cudaError_t launch_sum_blocks(const double* eblk, int nblk, double* out, cudaStream_t st);
 cudaError_t launch_abc_epilogue(const PointsDev& p, const double* part, int n_split, double* A,
                                 double* B, double* C, cudaStream_t st);
+// Batched forms over a molecule table `mols` (device) and block prefix sums `pre` (device,
+// n_mol + 1 entries, pre[n_mol] blocks in all): the energy/potential epilogue (blocks of 256 kept points; vrho/vgamma at the
+// molecule's caller offset, may be NULL), the A/B/C epilogue (partials from quantity 3 of
+// each molecule's buffer), the energy block sums (one block per molecule, into energies[m]).
+cudaError_t launch_ep_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                     double* vrho, double* vgamma, int* err, cudaStream_t st);
+cudaError_t launch_abc_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                      cudaStream_t st);
+cudaError_t launch_sum_blocks_batch(const EpiMol* mols, int n_mol, double* energies,
+                                    cudaStream_t st);
 cudaError_t launch_weight_grad(const PointsDev& p, const double* E, double* dEdw,
                                cudaStream_t st);
 
@@ -128,6 +208,19 @@ cudaError_t launch_trial_prep(const PointsDev& p, int32_t P, const double* rho_t
 cudaError_t launch_trial_split(const double* u, const double* y, int32_t P, int32_t Prows,
                                int64_t nk_pad, bool bf16, float* uh, float* ul, float* yh,
                                float* yl, cudaStream_t st);
+// Batched split-FP16 trial preparation (hess_f16.cu): rho^t, gamma^t and every trial's column
+// maxima (blocks of nk_pad / 256 x n_t per molecule, pre_max; the f16 areas' maxima zeroed by
+// the caller), the factors (one CTA per molecule), the FP16 hi / lo tiles (blocks of
+// nk_pad / 256 x rows, pre_split).
+cudaError_t launch_f16_trial_batch(const EpiMol* mols, const int64_t* pre_max,
+                                   const int64_t* pre_split, int n_mol, int64_t n_max_blocks,
+                                   int64_t n_split_blocks, const double* rho_t,
+                                   const double* grad_rho_t, cudaStream_t st);
+// Batched trial preparation fused with the split-TF32 cut (the results of launch_trial_prep
+// followed by launch_trial_split, without the FP64 u, y in between): block k of molecule m
+// covers points 256 (k mod nb) .. of row t = k / nb of its splits, nb = nk_pad / 256.
+cudaError_t launch_trial_tc_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                  const double* rho_t, const double* grad_rho_t, cudaStream_t st);
 
 // Tensor-core (split-TF32) contraction of trials [t0, t0 + Pn), Pn <= 192, into the FP64
 // partial output acc [2][acc_P][nk_pad] (zeroed by the caller).  uh/ul/yh/yl: FP32
@@ -171,8 +264,8 @@ cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t 
 // kept points' column records (`rec`, 64 B per point, nk_pad of them), cuts u, y (FP64
 // [P][nk_pad]) into hess_o64_slices() FP16 integer slice arrays [rows][2 nk_pad]
 // (`slice_stride` halves apart; per 16-j block 16 u' then 16 c_y y', scaled per trial and
-// block) with params[0] = 1/c_y, params[1] = c_y (colmax: 2 scratch words), and the factors'
-// inverses civ [group][nk_pad / 16][32] for trial groups of pg <= hess_o64_max_group()
+// 32-j stage) with params[0] = 1/c_y, params[1] = c_y (colmax: 2 scratch words), and the factors'
+// inverses civ [group][nk_pad / 32][32] for trial groups of pg <= hess_o64_max_group()
 // (hess_o64_civ_floats floats).  launch_hess_o64 contracts the trials [t0, t0 + Pn), Pn <= pg,
 // with `civ` pointing at their group's block, into acc [2][acc_P][nk_pad] (zeroed by the
 // caller).
@@ -216,6 +309,11 @@ cudaError_t launch_hess_epilogue(const PointsDev& p, int32_t P, const double* ac
                                  const double* A, const double* B, const double* C,
                                  const double* rt_k, const double* gt_k, double* f_rho_t,
                                  double* f_gamma_t, int* err, cudaStream_t st);
+// Batched Hessian epilogue: block k of molecule m covers kept points 256 (k mod nb) .. of
+// trial t = k / nb, nb = ceil(nk / 256); outputs at the molecule's trial offset.
+cudaError_t launch_hess_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                       double* f_rho_t, double* f_gamma_t, int* err,
+                                       cudaStream_t st);
 
 // ---------------------------------------------------------------- coordinates (coord.cu)
 cudaError_t launch_grad_epilogue(const PointsDev& p, const double* part, int n_split,

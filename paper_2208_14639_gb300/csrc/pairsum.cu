@@ -188,12 +188,16 @@ __device__ __forceinline__ double sum_splits(const double* part, int q, int n_sp
     return s;
 }
 
-__global__ void __launch_bounds__(kEpThreads)
-k_ep_epilogue(PointsDev P, const double* __restrict__ part, int n_split, double* __restrict__ E,
-              double* __restrict__ U, double* __restrict__ W, double* __restrict__ vrho,
-              double* __restrict__ vgamma, double* __restrict__ eblk, int* err) {
+// One block of the energy/potential epilogue: kept points 256 blk .. (block sums into
+// eblk[blk]).
+__device__ __forceinline__ void ep_epilogue_block(const PointsDev& P, const double* __restrict__ part,
+                                                  int n_split, double* __restrict__ E,
+                                                  double* __restrict__ U, double* __restrict__ W,
+                                                  double* __restrict__ vrho,
+                                                  double* __restrict__ vgamma,
+                                                  double* __restrict__ eblk, int* err, int64_t blk) {
     __shared__ double sh[kEpThreads / 32];
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t p = blk * kEpThreads + threadIdx.x;
     double ei = 0.0;
     if (p < P.nk) {
         const double e = sum_splits(part, 0, n_split, P.nk_pad, p);
@@ -212,7 +216,32 @@ k_ep_epilogue(PointsDev P, const double* __restrict__ part, int n_split, double*
         ei = P.w[p] * r * (P.beta + 0.5 * e);
     }
     const double s = block_sum(ei, sh);
-    if (threadIdx.x == 0) eblk[blockIdx.x] = s;
+    if (threadIdx.x == 0) eblk[blk] = s;
+}
+
+__global__ void __launch_bounds__(kEpThreads)
+k_ep_epilogue(PointsDev P, const double* __restrict__ part, int n_split, double* __restrict__ E,
+              double* __restrict__ U, double* __restrict__ W, double* __restrict__ vrho,
+              double* __restrict__ vgamma, double* __restrict__ eblk, int* err) {
+    ep_epilogue_block(P, part, n_split, E, U, W, vrho, vgamma, eblk, err, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kEpThreads)
+k_ep_epilogue_batch(const EpiMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                    double* __restrict__ vrho, double* __restrict__ vgamma, int* err) {
+    int64_t blk;
+    const EpiMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    ep_epilogue_block(M.P, M.part, M.n_split, M.sums, M.sums + M.cap, M.sums + 2 * M.cap,
+                      vrho ? vrho + M.off : nullptr, vgamma ? vgamma + M.off : nullptr, M.eblk,
+                      err, blk);
+}
+
+cudaError_t launch_ep_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                     double* vrho, double* vgamma, int* err, cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    k_ep_epilogue_batch<<<static_cast<unsigned>(n_blocks), kEpThreads, 0, st>>>(mols, pre, n_mol,
+                                                                                vrho, vgamma, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ep_epilogue(const PointsDev& p, const double* part, int n_split, double* E,
@@ -224,8 +253,8 @@ cudaError_t launch_ep_epilogue(const PointsDev& p, const double* part, int n_spl
 }
 
 // Compensated (Neumaier per thread, TwoSum tree across threads) sum of block partials.
-__global__ void __launch_bounds__(256) k_sum_blocks(const double* __restrict__ v, int n,
-                                                    double* __restrict__ out) {
+__device__ __forceinline__ void sum_blocks_body(const double* __restrict__ v, int n,
+                                                double* __restrict__ out) {
     __shared__ double ss[256], sc[256];
     double s = 0.0, c = 0.0;
     for (int k = threadIdx.x; k < n; k += 256) {
@@ -249,19 +278,61 @@ __global__ void __launch_bounds__(256) k_sum_blocks(const double* __restrict__ v
     if (threadIdx.x == 0) out[0] = ss[0] + sc[0];
 }
 
+__global__ void __launch_bounds__(256) k_sum_blocks(const double* __restrict__ v, int n,
+                                                    double* __restrict__ out) {
+    sum_blocks_body(v, n, out);
+}
+
+// One block per molecule: its energy from its block partials.
+__global__ void __launch_bounds__(256) k_sum_blocks_batch(const EpiMol* __restrict__ mols,
+                                                          double* __restrict__ energies) {
+    const EpiMol& M = mols[blockIdx.x];
+    sum_blocks_body(M.eblk, M.nblk, energies + blockIdx.x);
+}
+
+cudaError_t launch_sum_blocks_batch(const EpiMol* mols, int n_mol, double* energies,
+                                    cudaStream_t st) {
+    if (n_mol <= 0) return cudaSuccess;
+    k_sum_blocks_batch<<<n_mol, 256, 0, st>>>(mols, energies);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum_blocks(const double* eblk, int nblk, double* out, cudaStream_t st) {
     k_sum_blocks<<<1, 256, 0, st>>>(eblk, nblk, out);
     return cudaGetLastError();
 }
 
-__global__ void k_abc_epilogue(PointsDev P, const double* __restrict__ part, int n_split,
-                               double* __restrict__ A, double* __restrict__ B,
-                               double* __restrict__ C) {
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void abc_epilogue_row(const PointsDev& P, const double* __restrict__ part,
+                                                 int n_split, double* __restrict__ A,
+                                                 double* __restrict__ B, double* __restrict__ C,
+                                                 int64_t p) {
     if (p >= P.nk) return;
     A[p] = 2.0 * sum_splits(part, 0, n_split, P.nk_pad, p);
     B[p] = 2.0 * sum_splits(part, 1, n_split, P.nk_pad, p);
     C[p] = 2.0 * sum_splits(part, 2, n_split, P.nk_pad, p);
+}
+
+__global__ void k_abc_epilogue(PointsDev P, const double* __restrict__ part, int n_split,
+                               double* __restrict__ A, double* __restrict__ B,
+                               double* __restrict__ C) {
+    abc_epilogue_row(P, part, n_split, A, B, C, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+// A/B/C from quantities 3..5 of each molecule's EUWABC partials.
+__global__ void __launch_bounds__(kEpThreads)
+k_abc_epilogue_batch(const EpiMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol) {
+    int64_t blk;
+    const EpiMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    abc_epilogue_row(M.P, M.part + 3 * static_cast<int64_t>(M.n_split) * M.P.nk_pad, M.n_split,
+                     M.sums + 3 * M.cap, M.sums + 4 * M.cap, M.sums + 5 * M.cap,
+                     blk * kEpThreads + threadIdx.x);
+}
+
+cudaError_t launch_abc_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,
+                                      cudaStream_t st) {
+    if (n_blocks <= 0) return cudaSuccess;
+    k_abc_epilogue_batch<<<static_cast<unsigned>(n_blocks), kEpThreads, 0, st>>>(mols, pre, n_mol);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_abc_epilogue(const PointsDev& p, const double* part, int n_split, double* A,

@@ -37,17 +37,22 @@ __device__ __forceinline__ int point_key(int64_t i, const double* rho, const int
     return (a >= 0 && a < n_atom) ? a : 0;
 }
 
-__global__ void __launch_bounds__(kPrepThreads)
-k_prep_count(int64_t n, const double* __restrict__ xyz, const double* __restrict__ w,
-             const double* __restrict__ rho, const double* __restrict__ grad,
-             const int32_t* __restrict__ atom, int32_t n_atom, double rho_cut, int n_keys,
-             int nblk, int32_t* __restrict__ hist, double* __restrict__ bbox_part, int* err) {
+// One count block (caller points kPB blk ..): key histogram and kept bounding box.
+__device__ __forceinline__ void prep_count_block(int64_t n, const double* __restrict__ xyz,
+                                                 const double* __restrict__ w,
+                                                 const double* __restrict__ rho,
+                                                 const double* __restrict__ grad,
+                                                 const int32_t* __restrict__ atom, int32_t n_atom,
+                                                 double rho_cut, int n_keys, int nblk,
+                                                 int32_t* __restrict__ hist,
+                                                 double* __restrict__ bbox_part, int* err,
+                                                 int64_t blk) {
     extern __shared__ int sh_hist[];
     __shared__ double sh_red[6][kPrepThreads / 32];
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x) sh_hist[k] = 0;
     __syncthreads();
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * kPB;
+    const int64_t base = blk * kPB;
     const int64_t end = min(n, base + kPB);
     int bad = 0;
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
@@ -67,7 +72,7 @@ k_prep_count(int64_t n, const double* __restrict__ xyz, const double* __restrict
     if (bad) atomicOr(err, bad);
     __syncthreads();
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x)
-        hist[static_cast<int64_t>(k) * nblk + blockIdx.x] = sh_hist[k];
+        hist[static_cast<int64_t>(k) * nblk + blk] = sh_hist[k];
     // block min / max of the kept coordinates (exact operations: order independent)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -85,15 +90,35 @@ k_prep_count(int64_t n, const double* __restrict__ xyz, const double* __restrict
         double v = sh_red[threadIdx.x][0];
         for (int q = 1; q < kPrepThreads / 32; ++q)
             v = threadIdx.x < 3 ? fmin(v, sh_red[threadIdx.x][q]) : fmax(v, sh_red[threadIdx.x][q]);
-        bbox_part[blockIdx.x * 6 + threadIdx.x] = v;
+        bbox_part[blk * 6 + threadIdx.x] = v;
     }
 }
 
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep_count(int64_t n, const double* __restrict__ xyz, const double* __restrict__ w,
+             const double* __restrict__ rho, const double* __restrict__ grad,
+             const int32_t* __restrict__ atom, int32_t n_atom, double rho_cut, int n_keys,
+             int nblk, int32_t* __restrict__ hist, double* __restrict__ bbox_part, int* err) {
+    prep_count_block(n, xyz, w, rho, grad, atom, n_atom, rho_cut, n_keys, nblk, hist, bbox_part,
+                     err, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep_count_batch(const PrepMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                   double rho_cut, int* err) {
+    int64_t blk;
+    const PrepMol& M = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    prep_count_block(M.n, M.xyz, M.w, M.rho, M.grad, M.atom, M.n_atom, rho_cut, M.n_keys, M.nblk,
+                     M.hist, M.bbox_part, err, blk);
+}
+
 // One CTA of 1024 threads: exclusive scan of M = n_keys*nblk counts.
-__global__ void __launch_bounds__(1024)
-k_prep_scan(const int32_t* __restrict__ hist, int64_t M, int64_t* __restrict__ offs, int n_keys,
-            int nblk, int32_t n_atom, const double* __restrict__ bbox_part,
-            double* __restrict__ center, int64_t* __restrict__ nk_out, int64_t* __restrict__ seg) {
+__device__ __forceinline__ void prep_scan_block(const int32_t* __restrict__ hist, int64_t M,
+                                                int64_t* __restrict__ offs, int n_keys, int nblk,
+                                                int32_t n_atom, const double* __restrict__ bbox_part,
+                                                double* __restrict__ center,
+                                                int64_t* __restrict__ nk_out,
+                                                int64_t* __restrict__ seg) {
     __shared__ int64_t sh[1024];
     __shared__ double shb[6];
     const int t = threadIdx.x;
@@ -130,17 +155,33 @@ k_prep_scan(const int32_t* __restrict__ hist, int64_t M, int64_t* __restrict__ o
     if (t == 0) seg[n_seg] = nk;
 }
 
-__global__ void __launch_bounds__(kPrepThreads)
-k_prep_scatter(int64_t n, const double* __restrict__ rho, const int32_t* __restrict__ atom,
-               int32_t n_atom, double rho_cut, int n_keys, int nblk,
-               const int64_t* __restrict__ offs, int64_t* __restrict__ orig) {
+__global__ void __launch_bounds__(1024)
+k_prep_scan(const int32_t* __restrict__ hist, int64_t M, int64_t* __restrict__ offs, int n_keys,
+            int nblk, int32_t n_atom, const double* __restrict__ bbox_part,
+            double* __restrict__ center, int64_t* __restrict__ nk_out, int64_t* __restrict__ seg) {
+    prep_scan_block(hist, M, offs, n_keys, nblk, n_atom, bbox_part, center, nk_out, seg);
+}
+
+// One CTA per molecule; the segment starts go into the slots after its offsets.
+__global__ void __launch_bounds__(1024) k_prep_scan_batch(const PrepMol* __restrict__ mols) {
+    const PrepMol& P = mols[blockIdx.x];
+    const int64_t M = static_cast<int64_t>(P.n_keys) * P.nblk;
+    prep_scan_block(P.hist, M, P.offs, P.n_keys, P.nblk, P.n_atom, P.bbox_part, P.center, P.nk_dev,
+                    P.offs + M);
+}
+
+__device__ __forceinline__ void prep_scatter_block(int64_t n, const double* __restrict__ rho,
+                                                   const int32_t* __restrict__ atom, int32_t n_atom,
+                                                   double rho_cut, int n_keys, int nblk,
+                                                   const int64_t* __restrict__ offs,
+                                                   int64_t* __restrict__ orig, int64_t blk) {
     extern __shared__ int64_t sh_cnt[];  // n_keys running destinations
     __shared__ int sh_key[kPB];
     __shared__ int64_t sh_pos[kPB];
-    const int64_t base = static_cast<int64_t>(blockIdx.x) * kPB;
+    const int64_t base = blk * kPB;
     const int cnt = static_cast<int>(n - base < kPB ? n - base : kPB);
     for (int k = threadIdx.x; k < n_keys; k += blockDim.x)
-        sh_cnt[k] = offs[static_cast<int64_t>(k) * nblk + blockIdx.x];
+        sh_cnt[k] = offs[static_cast<int64_t>(k) * nblk + blk];
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
         bool keep;
         sh_key[q] = point_key(base + q, rho, atom, n_atom, rho_cut, n_keys, keep);
@@ -154,15 +195,38 @@ k_prep_scatter(int64_t n, const double* __restrict__ rho, const int32_t* __restr
         if (sh_key[q] != n_keys - 1) orig[sh_pos[q]] = base + q;
 }
 
-__global__ void __launch_bounds__(256)
-k_prep_points(int64_t nk, int64_t nk_pad, const int64_t* __restrict__ orig,
-              const double* __restrict__ xyz, const double* __restrict__ w,
-              const double* __restrict__ rho, const double* __restrict__ grad,
-              const int32_t* __restrict__ atom, double b, double C,
-              const double* __restrict__ center, int32_t* __restrict__ atom_k,
-              double* __restrict__ soa, double4* __restrict__ r64a, double4* __restrict__ r64b,
-              float4* __restrict__ r32a, float4* __restrict__ r32b, float4* __restrict__ r32p) {
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep_scatter(int64_t n, const double* __restrict__ rho, const int32_t* __restrict__ atom,
+               int32_t n_atom, double rho_cut, int n_keys, int nblk,
+               const int64_t* __restrict__ offs, int64_t* __restrict__ orig) {
+    prep_scatter_block(n, rho, atom, n_atom, rho_cut, n_keys, nblk, offs, orig, blockIdx.x);
+}
+
+// Also copies each molecule's segment starts (block 0 of the molecule).
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep_scatter_batch(const PrepMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                     double rho_cut) {
+    int64_t blk;
+    const PrepMol& P = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    if (blk == 0) {
+        const int64_t M = static_cast<int64_t>(P.n_keys) * P.nblk;
+        const int n_seg = (P.n_atom > 0 ? P.n_atom : 1) + 1;
+        for (int a = threadIdx.x; a < n_seg; a += blockDim.x) P.seg[a] = P.offs[M + a];
+    }
+    prep_scatter_block(P.n, P.rho, P.atom, P.n_atom, rho_cut, P.n_keys, P.nblk, P.offs, P.orig, blk);
+}
+
+__device__ __forceinline__ void prep_point(int64_t nk, int64_t nk_pad, const int64_t* __restrict__ orig,
+                                           const double* __restrict__ xyz,
+                                           const double* __restrict__ w,
+                                           const double* __restrict__ rho,
+                                           const double* __restrict__ grad,
+                                           const int32_t* __restrict__ atom, double b, double C,
+                                           const double* __restrict__ center,
+                                           int32_t* __restrict__ atom_k, double* __restrict__ soa,
+                                           double4* __restrict__ r64a, double4* __restrict__ r64b,
+                                           float4* __restrict__ r32a, float4* __restrict__ r32b,
+                                           float4* __restrict__ r32p, int64_t p) {
     if (p >= nk_pad) return;
     // pair-packed record slots of this point: pair m = p / 2, component h = p % 2
     float* pk = reinterpret_cast<float*>(r32p) + (p >> 1) * 16 + (p & 1);
@@ -228,6 +292,27 @@ k_prep_points(int64_t nk, int64_t nk_pad, const int64_t* __restrict__ orig,
     atom_k[p] = atom ? atom[i] : 0;
 }
 
+__global__ void __launch_bounds__(256)
+k_prep_points(int64_t nk, int64_t nk_pad, const int64_t* __restrict__ orig,
+              const double* __restrict__ xyz, const double* __restrict__ w,
+              const double* __restrict__ rho, const double* __restrict__ grad,
+              const int32_t* __restrict__ atom, double b, double C,
+              const double* __restrict__ center, int32_t* __restrict__ atom_k,
+              double* __restrict__ soa, double4* __restrict__ r64a, double4* __restrict__ r64b,
+              float4* __restrict__ r32a, float4* __restrict__ r32b, float4* __restrict__ r32p) {
+    prep_point(nk, nk_pad, orig, xyz, w, rho, grad, atom, b, C, center, atom_k, soa, r64a, r64b,
+               r32a, r32b, r32p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_prep_points_batch(const PrepMol* __restrict__ mols, const int64_t* __restrict__ pre, int n_mol,
+                    double b, double C) {
+    int64_t blk;
+    const PrepMol& P = mols[batch_block_mol(pre, n_mol, blockIdx.x, blk)];
+    prep_point(P.nk, P.nk_pad, P.orig, P.xyz, P.w, P.rho, P.grad, P.atom, b, C, P.center, P.atom_k,
+               P.soa, P.r64a, P.r64b, P.r32a, P.r32b, P.r32p, blk * 256 + threadIdx.x);
+}
+
 cudaError_t launch_prepare_count(int64_t n, const double* xyz, const double* w, const double* rho,
                                  const double* grad, const int32_t* atom, int32_t n_atom,
                                  double rho_cut, const PrepareScratch& s, int* err,
@@ -270,6 +355,38 @@ cudaError_t launch_prepare_scatter(int64_t n, const double* xyz, const double* w
         e = cudaGetLastError();
     }
     return e;
+}
+
+cudaError_t launch_prepare_count_batch(const PrepMol* mols, const int64_t* pre, int n_mol,
+                                       int64_t n_blocks, int max_keys, double rho_cut, int* err,
+                                       cudaStream_t st) {
+    if (n_mol <= 0) return cudaSuccess;
+    if (n_blocks > 0) {
+        k_prep_count_batch<<<static_cast<unsigned>(n_blocks), kPrepThreads, max_keys * sizeof(int), st>>>(
+            mols, pre, n_mol, rho_cut, err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_prep_scan_batch<<<n_mol, 1024, 0, st>>>(mols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_scatter_batch(const PrepMol* mols, const int64_t* pre_blk,
+                                         const int64_t* pre_pts, int n_mol, int64_t n_blocks,
+                                         int64_t n_point_blocks, int max_keys, double rho_cut,
+                                         double b, double C, cudaStream_t st) {
+    if (n_blocks > 0) {
+        k_prep_scatter_batch<<<static_cast<unsigned>(n_blocks), kPrepThreads, max_keys * sizeof(int64_t), st>>>(
+            mols, pre_blk, n_mol, rho_cut);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_point_blocks > 0) {
+        k_prep_points_batch<<<static_cast<unsigned>(n_point_blocks), 256, 0, st>>>(mols, pre_pts,
+                                                                                n_mol, b, C);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
 }
 
 }  // namespace vv10

@@ -96,6 +96,11 @@ struct BatchState {
     DevBuf rtgt, splits, acc, maps, tc_tab;
     std::vector<TcClass> tc_classes;
     DevBuf f16small, f16tab, f16counter;  // split-FP16 layout (shares rtgt, splits, acc, maps)
+    // batched per-point kernels: molecule table and block prefix sums (energy / A,B,C
+    // epilogues; trial values + split TF32; Hessian epilogue); hess parts valid with tc_classes
+    DevBuf epi, prep_tab;
+    size_t epi_pre_ep = 0, epi_pre_tr = 0, epi_pre_mx = 0, epi_pre_hs = 0;
+    int64_t epi_n_ep = 0, epi_n_tr = 0, epi_n_mx = 0, epi_n_hs = 0;
     std::vector<TcClass> f16_classes;
     // graph of a whole batched pass, and what it was captured for
     cudaGraphExec_t graph = nullptr;
@@ -212,6 +217,7 @@ struct vv10_ctx {
     vv10_status tc_contract(int32_t P, int cap, cudaStream_t st);
     vv10_status f16_contract(int32_t P, int cap, cudaStream_t st);
     vv10_status o64_contract(int32_t P, cudaStream_t st);
+    vv10_status batch_epi_tables();
     vv10_status tune_tc_cap(int32_t P, cudaStream_t st, int* cap);
     vv10_status hessian(vv10_precision prec, int32_t P, const double* rho_t,
                         const double* grad_rho_t, double* f_rho_t, double* f_gamma_t,
