@@ -65,8 +65,9 @@ typedef enum {
                                8-bit integer slices each (FP16-exact), whose 15 leading
                                products the tensor cores sum exactly in FP32 (about 40 bits
                                of each tile and trial kept); results agree with VV10_FP64 to
-                               ~1e-11 relative.  Single systems only: the batched
-                               contraction returns VV10_ERR_UNSUPPORTED for it.            */
+                               ~1e-11 relative in norm, each element to ~1e-10 of its size
+                               (the double-FP32 tiles carry ~46 bits).  Single systems only:
+                               the batched contraction returns VV10_ERR_UNSUPPORTED.       */
 } vv10_precision;
 
 /* VV10 parameters b and C (Sec. II.A) and the density cutoff below which a point is

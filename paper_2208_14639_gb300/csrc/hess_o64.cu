@@ -12,24 +12,24 @@
 // Slices.  A value scaled by a power of two into |x| < 2^7 is written as
 //   x = s0 + s1 2^-8 + s2 2^-16 + s3 2^-24 + s4 2^-32 + s5 2^-40 + s6 2^-48 + e,
 // every s an integer of at most 8 bits (|s3|, |s6| <= 192), exactly representable in FP16.
-// Kernel tiles take one factor per row and 32-j stage (the row's largest |T| in the stage into
-// [2^6, 2^7)); trials one per column and 32-j stage (the largest of |u'| and c_y |y'| in the
+// Kernel tiles take one factor per row and 16-j stage (the row's largest |T| in the stage into
+// [2^6, 2^7)); trials one per column and 16-j stage (the largest of |u'| and c_y |y'| in the
 // block, with one global y balance c_y), so that a small value far below its row's or
 // column's maximum keeps its own precision.  The product of slices p and q carries the weight
 // 2^-8(p+q); the 28 pairs with p + q <= 6 are formed, the rest are below 2^-56 of the stage's
 // scale.  Each level l = p + q has its own TMEM accumulator, and a level's sum over one stage
-// is a sum of at most 7 x 64 products of integers below 2^14.6: below 2^23.4, so FP32 holds it
+// is a sum of at most 7 x 32 products of integers below 2^14.6: below 2^22.4, so FP32 holds it
 // exactly, whatever order and truncation the tensor core uses.  The drain combines the seven
 // levels of a stage into an unevaluated FP32 pair, multiplies it by the row and column
 // factors' inverses (powers of two) and adds it into a double-FP32 register sum per output;
 // the flush adds that sum in FP64 to the partial output.
 //
 // Work unit: 128 rows x one output kind x the trials of the launch (MMA N = Ppad = 32; TMEM
-// holds 7 x 32 accumulator and 7 x 32 operand columns).  The j range is walked in L2-sized
+// holds 7 x 32 accumulator and 7 x 16 operand columns).  The j range is walked in L2-sized
 // chunks as in the split-FP16 kernel (each CTA its fixed units in every chunk).  16 warps (4
-// per TMEM lane quadrant, 8 j each): generate the two tiles of the row, exchange the stage's
+// per TMEM lane quadrant, 4 j each): generate the two tiles of the row, exchange the stage's
 // row maxima, wait for the previous stage's MMAs and drain them, slice and store the operands
-// into TMEM; lane 0 of warp 0 issues the 112 MMAs of a stage, lane 0 of warp 1 keeps the copy
+// into TMEM; lane 0 of warp 0 issues the 56 MMAs of a stage, lane 0 of warp 1 keeps the copy
 // ring kO64Ring - 1 stages ahead.  Every wait is bounded (kSpinCycles).
 #include <cstring>
 #include <cuda.h>
@@ -42,7 +42,7 @@
 
 namespace vv10 {
 
-constexpr int kO64Kj = 32;          // j per stage (two K = 16 MMA steps per tile)
+constexpr int kO64Kj = 16;          // j per stage (one K = 16 MMA step per tile)
 constexpr int kO64Warps = 16;
 constexpr int kO64Threads = kO64Warps * 32;
 constexpr int kO64Ring = 4;         // stages of copies in flight
@@ -55,7 +55,7 @@ constexpr size_t kO64ChunkBytes = 48u << 20;
 constexpr uint32_t kO64RecBytes = 64;  // one column record (FP32 pairs)
 
 struct O64Layout {
-    uint32_t tile_bytes;  // one Ppad x 64-half slice tile (128-byte rows: per 16 j, 16 u' then 16 c_y y')
+    uint32_t tile_bytes;  // one Ppad x 32-half slice tile (64-byte rows: 16 u', 16 c_y y')
     uint32_t slot_bytes;  // the seven slice tiles of one stage
     uint32_t civ_off;     // the stage's column-factor inverses [Ppad] floats, per ring slot
     uint32_t rec_off;     // the stage's 16 column records, per ring slot
@@ -66,7 +66,7 @@ struct O64Layout {
 };
 __host__ __device__ constexpr O64Layout o64_layout() {
     O64Layout L{};
-    L.tile_bytes = kO64Ppad * 128u;
+    L.tile_bytes = kO64Ppad * 64u;
     L.slot_bytes = kO64Slices * L.tile_bytes;
     L.civ_off = kO64Ring * L.slot_bytes;
     L.rec_off = L.civ_off + kO64Ring * kO64Ppad * 4u;
@@ -278,12 +278,12 @@ __device__ __forceinline__ void o64_slices(float hi, float lo, float (&s)[kO64Sl
 }
 
 // TMEM columns: level l accumulator at 32 l (l = 0..6); operand slices at 224: slice p, tile
-// b (0: Ta, 1: Tb) at 224 + 32 p + 16 b, 16 columns (32 j, two FP16 each).
+// b (0: Ta, 1: Tb) at 224 + 16 p + 8 b, 8 columns (16 j, two FP16 each).
 __device__ __forceinline__ uint32_t o64_dcol(int l) { return static_cast<uint32_t>(kO64Ppad * l); }
 __device__ __forceinline__ uint32_t o64_acol(int p, int b) {
-    return static_cast<uint32_t>(kO64Levels * kO64Ppad + 32 * p + 16 * b);
+    return static_cast<uint32_t>(kO64Levels * kO64Ppad + 16 * p + 8 * b);
 }
-static_assert(kO64Levels * kO64Ppad + 32 * kO64Slices <= static_cast<int>(kO64TmemCols), "TMEM");
+static_assert(kO64Levels * kO64Ppad + 16 * kO64Slices <= static_cast<int>(kO64TmemCols), "TMEM");
 
 __global__ void __launch_bounds__(kO64Threads, 1)
 k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
@@ -355,7 +355,7 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
                  civ_bytes, &b_full[P.slot]);
         uint8_t* base = smem + P.slot * L.slot_bytes;
         for (int q = 0; q < kO64Slices; ++q)
-            tc::tma_load_2d(base + q * L.tile_bytes, maps[q], 64 * s, args.t0, &b_full[P.slot]);
+            tc::tma_load_2d(base + q * L.tile_bytes, maps[q], 32 * s, args.t0, &b_full[P.slot]);
         ++P.issued;
         if (++P.slot == kO64Ring) {
             P.slot = 0;
@@ -460,13 +460,13 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
             rc.nq = DF{-R.d.x, -R.d.y};
             until_flush = args.flush;
         }
-        // tiles of this warp's 8 j (records 8 part .. 8 part + 7)
+        // tiles of this warp's 4 j (records 4 part .. 4 part + 3)
         const O64Rec* rs = reinterpret_cast<const O64Rec*>(smem + L.rec_off + slot * kO64Kj * kO64RecBytes);
-        DF ta[8], tb[8];
+        DF ta[4], tb[4];
         float mx = 0.0f;
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            o64_tiles(kind0, rc, rs[8 * part + h], ta[h], tb[h]);
+        for (int h = 0; h < 4; ++h) {
+            o64_tiles(kind0, rc, rs[4 * part + h], ta[h], tb[h]);
             tb[h] = df_scale(tb[h], inv_cy);  // the tile that multiplies y carries 1/c_y
             mx = fmaxf(mx, fmaxf(fabsf(ta[h].h), fabsf(tb[h].h)));
         }
@@ -497,26 +497,24 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
             if (is_producer && !pr->end && !produce()) *abort_flag = 1;
             pending = false;
         }
-        // slices of the scaled tiles: this warp's 8 j are columns 4 part .. 4 part + 3 of each
-        // 16-column operand
-        const uint32_t a = tmem + lane_off + 4 * part;
+        // slices of the scaled tiles: this warp's 4 j are columns 2 part, 2 part + 1 of each
+        // 8-column operand
+        const uint32_t a = tmem + lane_off + 2 * part;
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const DF* t = b == 0 ? ta : tb;
-            uint32_t w[kO64Slices][4];
+            float s0[kO64Slices], s1[kO64Slices], s2[kO64Slices], s3[kO64Slices];
+            o64_slices(t[0].h * sc, t[0].l * sc, s0);
+            o64_slices(t[1].h * sc, t[1].l * sc, s1);
+            o64_slices(t[2].h * sc, t[2].l * sc, s2);
+            o64_slices(t[3].h * sc, t[3].l * sc, s3);
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                float s0[kO64Slices], s1[kO64Slices];
-                o64_slices(t[2 * h].h * sc, t[2 * h].l * sc, s0);
-                o64_slices(t[2 * h + 1].h * sc, t[2 * h + 1].l * sc, s1);
-#pragma unroll
-                for (int p = 0; p < kO64Slices; ++p) {
-                    const __half2 x = __floats2half2_rn(s0[p], s1[p]);
-                    w[p][h] = *reinterpret_cast<const uint32_t*>(&x);
-                }
+            for (int p = 0; p < kO64Slices; ++p) {
+                const __half2 x = __floats2half2_rn(s0[p], s1[p]);
+                const __half2 y = __floats2half2_rn(s2[p], s3[p]);
+                tc::st_x2(a + o64_acol(p, b), *reinterpret_cast<const uint32_t*>(&x),
+                          *reinterpret_cast<const uint32_t*>(&y));
             }
-#pragma unroll
-            for (int p = 0; p < kO64Slices; ++p) tc::st_x4(a + o64_acol(p, b), w[p]);
         }
         tc::wait_st();
         tc::fence_before();
@@ -527,20 +525,15 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
                 tc::fence_after();
                 const uint32_t base = smem_u32(smem + slot * L.slot_bytes);
                 // level l = p + q: slices p of the tiles (TMEM) x slices q of the trials (smem);
-                // trial rows: per 16-j half hh, [u' (16 j) | c_y y' (16 j)], 32 B each; a K-step
-                // moves the descriptor's address by 32 B (2 units)
+                // trial rows: [u' (16 j) | c_y y' (16 j)], 32 B each (2 descriptor units)
 #pragma unroll
                 for (int l = 0; l < kO64Levels; ++l) {
                     const uint32_t d = tmem + o64_dcol(l);
 #pragma unroll
                     for (int p = 0; p <= l; ++p) {
-                        const uint64_t bd = tc::sdesc_kmajor_sw128(base + (l - p) * L.tile_bytes);
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            tc::mma_f16_ts(d, tmem + o64_acol(p, 0) + 8 * hh, bd + 4u * hh, idesc,
-                                           (p == 0 && hh == 0) ? 0u : 1u);
-                            tc::mma_f16_ts(d, tmem + o64_acol(p, 1) + 8 * hh, bd + 4u * hh + 2u, idesc, 1u);
-                        }
+                        const uint64_t bd = tc::sdesc_kmajor_sw64(base + (l - p) * L.tile_bytes);
+                        tc::mma_f16_ts(d, tmem + o64_acol(p, 0), bd, idesc, p == 0 ? 0u : 1u);
+                        tc::mma_f16_ts(d, tmem + o64_acol(p, 1), bd + 2u, idesc, 1u);
                     }
                 }
                 tc::commit(mma_done);
@@ -655,9 +648,9 @@ __global__ void k_o64_balance(const unsigned long long* __restrict__ colmax,
 }
 
 // The seven FP16 slice arrays [rows][2 nk_pad] (per 16-j block: 16 u' then 16 c_y y', scaled by
-// the column factor of its 32-j stage; slices exact in FP64) and the factors' inverses
-// civ[group][n_stage][32] for trial groups [g pg, g pg + pg): one warp per (trial, 32-j
-// stage).  Rows t >= P are zero.
+// the block's column factor; slices exact in FP64) and the factors' inverses
+// civ[group][n_stage][32] for trial groups [g pg, g pg + pg): one half-warp per (trial, 16-j
+// block).  Rows t >= P are zero.
 __global__ void __launch_bounds__(256)
 k_o64_split(const double* __restrict__ u, const double* __restrict__ y, int32_t P, int32_t pg,
             int64_t nk_pad, const double* __restrict__ params, __half* __restrict__ out,
@@ -674,7 +667,7 @@ k_o64_split(const double* __restrict__ u, const double* __restrict__ y, int32_t 
     // which keeps the scaled values below 2^7)
     float m = static_cast<float>(fmax(fabs(a), fabs(b)));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     float sc, isc;
     o64_scale_f(m, sc, isc);
     double ra = a * sc, rb = b * sc;
@@ -687,10 +680,10 @@ k_o64_split(const double* __restrict__ u, const double* __restrict__ y, int32_t 
         ra = (ra - sa) * 256.0;
         rb = (rb - sb) * 256.0;
     }
-    if (t < P && (j & 31) == 0) {
+    if (t < P && (j & 15) == 0) {
         const int g = t / pg, c = t - g * pg;
         const int64_t n_stage = nk_pad / kO64Kj;
-        civ[(static_cast<int64_t>(g) * n_stage + (j >> 5)) * kO64Ppad + c] = isc;
+        civ[(static_cast<int64_t>(g) * n_stage + (j >> 4)) * kO64Ppad + c] = isc;
     }
 }
 
@@ -711,16 +704,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 o64_encode_fn() {
     return fn;
 }
 
-// [rows][2 nk_pad] halves; box 64 halves (one stage: 2 x (16 u', 16 c_y y')) x 32 rows, 128-byte swizzle.
+// [rows][2 nk_pad] halves; box 32 halves (one stage: 16 u', 16 c_y y') x 32 rows, 64-byte swizzle.
 static bool o64_make_map(CUtensorMap* m, const void* base, int64_t nk_pad, int64_t rows) {
     auto fn = o64_encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(2 * nk_pad), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(2 * nk_pad) * sizeof(__half)};
-    cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(kO64Ppad)};
+    cuuint32_t box[2] = {32u, static_cast<cuuint32_t>(kO64Ppad)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }

@@ -231,7 +231,7 @@ vv10_status vv10_ctx::o64_contract(int32_t Pn, cudaStream_t st) {
     H_TRY(ensure(o64_sl, hess_o64_slices() * sizeof(uint16_t) * static_cast<size_t>(stride),
                  "FP64 trial slices"));
     H_TRY(ensure(o64_rec, 64 * static_cast<size_t>(P.nk_pad), "FP32-pair point records"));
-    // colmax [2] words | params [2] doubles | civ [ng][nk_pad / 32][32] floats
+    // colmax [2] words | params [2] doubles | civ [ng][nk_pad / 16][32] floats
     const int64_t civ_n = hess_o64_civ_floats(Pn, pg, P.nk_pad);
     H_TRY(ensure(o64_small, 32 + sizeof(float) * static_cast<size_t>(civ_n), "FP64 trial factors"));
     char* sm = static_cast<char*>(o64_small.p);

@@ -264,8 +264,8 @@ cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t 
 // kept points' column records (`rec`, 64 B per point, nk_pad of them), cuts u, y (FP64
 // [P][nk_pad]) into hess_o64_slices() FP16 integer slice arrays [rows][2 nk_pad]
 // (`slice_stride` halves apart; per 16-j block 16 u' then 16 c_y y', scaled per trial and
-// 32-j stage) with params[0] = 1/c_y, params[1] = c_y (colmax: 2 scratch words), and the factors'
-// inverses civ [group][nk_pad / 32][32] for trial groups of pg <= hess_o64_max_group()
+// block) with params[0] = 1/c_y, params[1] = c_y (colmax: 2 scratch words), and the factors'
+// inverses civ [group][nk_pad / 16][32] for trial groups of pg <= hess_o64_max_group()
 // (hess_o64_civ_floats floats).  launch_hess_o64 contracts the trials [t0, t0 + Pn), Pn <= pg,
 // with `civ` pointing at their group's block, into acc [2][acc_P][nk_pad] (zeroed by the
 // caller).

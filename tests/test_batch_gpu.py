@@ -237,6 +237,12 @@ def test_batch_errors(dev):
             vv10.vv10_batch_hessian_contract(h, vv10.VV10_MIXED_BF16X3, b.P, b.d_rt, b.d_gt,
                                              b.fr, b.fg)
         assert ei.value.status == vv10.VV10_ERR_UNSUPPORTED
+        with pytest.raises(vv10.VV10Error) as ei:  # the FP64 tensor-core path: single systems only
+            vv10.vv10_batch_hessian_contract(h, vv10.VV10_FP64_TC, b.P, b.d_rt, b.d_gt, b.fr, b.fg)
+        assert ei.value.status == vv10.VV10_ERR_UNSUPPORTED
+        with pytest.raises(vv10.VV10Error) as ei:  # an unknown precision
+            vv10.vv10_batch_hessian_contract(h, 7, b.P, b.d_rt, b.d_gt, b.fr, b.fg)
+        assert ei.value.status == vv10.VV10_ERR_INVALID_ARG
         with pytest.raises(vv10.VV10Error):  # P = 0
             vv10.vv10_batch_hessian_contract(h, MIXED, [0] + b.P[1:], b.d_rt, b.d_gt, b.fr, b.fg)
         vv10.vv10_sync(h)

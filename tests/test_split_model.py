@@ -141,7 +141,7 @@ def test_scaling_mistakes_are_caught(oracle_mod):
 # ------------------------------------------------------------ FP64 accuracy from integer slices
 #
 # The FP64 tensor-core contraction: kernel tiles as FP32 pairs (hi, lo) cut into seven 8-bit
-# integer slices in FP32 arithmetic, trials cut into seven slices in FP64; per 32-j stage one
+# integer slices in FP32 arithmetic, trials cut into seven slices in FP64; per 16-j stage one
 # factor per tile row and one per trial column (powers of two into [2^6, 2^7)); the 28
 # products with p + q <= 6 summed per level.
 
@@ -194,9 +194,9 @@ def pow2_into(m, lo_exp):
     return np.where(m > 0, 2.0 ** (lo_exp - e), 1.0)
 
 
-def contract_o64(Ta, Tb, u, y, J=32, levels=7, carry=True, weight=8, col_per_stage=True):
-    """The seven-slice product over 32-j stages; level sums asserted to be integers below 2^24
-    (exact in the tensor cores' FP32 accumulation; the bound is 7 x 64 x 2^14.6 = 2^23.4).  The
+def contract_o64(Ta, Tb, u, y, J=16, levels=7, carry=True, weight=8, col_per_stage=True):
+    """The seven-slice product over 16-j stages; level sums asserted to be integers below 2^23
+    (exact in the tensor cores' FP32 accumulation; the bound is 7 x 32 x 2^14.6 = 2^22.4).  The
     flags plant mistakes."""
     cy = 2.0 ** np.round(np.log2(np.abs(u).max() / np.abs(y).max()))
     Tb = Tb / cy
@@ -214,7 +214,7 @@ def contract_o64(Ta, Tb, u, y, J=32, levels=7, carry=True, weight=8, col_per_sta
         st = np.zeros_like(out)
         for lev in range(levels):
             L = sum(A[p] @ U[lev - p].T + B[p] @ Y[lev - p].T for p in range(lev + 1))
-            assert np.all(L == np.rint(L)) and np.abs(L).max() < 2.0 ** 24
+            assert np.all(L == np.rint(L)) and np.abs(L).max() < 2.0 ** 23
             st += L * 2.0 ** (-weight * lev)
         out += st / r[:, None] / s_t[None, :]
     return out
