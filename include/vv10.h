@@ -165,6 +165,19 @@ vv10_status vv10_hessian_contract(vv10_handle h, vv10_precision prec, int32_t P,
                                   const double* rho_t, const double* grad_rho_t,
                                   double* f_rho_t, double* f_gamma_t, void* stream);
 
+/* Second derivatives of E along P directions (rho^t, grad rho^t) at once: with dE/d rho_i =
+ * w_i f^rho_i and dE/d grad rho_i = 2 w_i f^gamma_i grad rho_i (Sec. II.A), their directional
+ * derivatives from the contraction above (Sec. II.B, Eq. frhot):
+ *   hv_rho[t][i]     = w_i f^{rho,t}_i
+ *   hv_grad[t][i][c] = 2 w_i (f^{gamma,t}_i d_c rho_i + f^gamma_i d_c rho^t_i)
+ * (a Hessian-vector product of E in the variables (rho, grad rho); zero at dropped points).
+ *   P, rho_t, grad_rho_t   as for vv10_hessian_contract
+ *   hv_rho     P x n device out;  hv_grad  P x n x 3 device out
+ * Uses handle scratch of 2 P n doubles.  Errors: as vv10_hessian_contract. */
+vv10_status vv10_hessian_vector_product(vv10_handle h, vv10_precision prec, int32_t P,
+                                        const double* rho_t, const double* grad_rho_t,
+                                        double* hv_rho, double* hv_grad, void* stream);
+
 /* Grid-position derivative terms (Sec. II.A Eq. grad_gr, first form; Sec. II.B Eq. EiBgr):
  *   grad_points  n x 3 out (may be NULL): dE/dr_i with rho, grad rho and w held fixed,
  *                = -2 w_i rho_i sum_j w_j rho_j Phi_ij D_ij (r_i - r_j),

@@ -88,16 +88,14 @@ class _State:
         return self.slot["lock"]
 
     def hessian(self, a_rho, a_grad):
-        """(w f^{rho,t}, 2 w (f^{gamma,t} grad rho + f^gamma d grad rho)) for trials (P, n)."""
-        fr = torch.empty_like(a_rho)
-        fg = torch.empty_like(a_rho)
+        """(w f^{rho,t}, 2 w (f^{gamma,t} grad rho + f^gamma d grad rho)) for trials (P, n),
+        both formed by the library (vv10_hessian_vector_product)."""
+        d_rho = torch.empty_like(a_rho)
+        d_grad = torch.empty_like(a_grad)
         with self.lock:
             self.ensure()
-            _vv.vv10_hessian_contract(self.h, self.prec, a_rho.contiguous(), a_grad.contiguous(),
-                                      fr, fg)
-        w = self.weights
-        d_rho = w * fr
-        d_grad = 2.0 * w[:, None] * (fg[..., None] * self.grad_rho + self.vgamma[:, None] * a_grad)
+            _vv.vv10_hessian_vector_product(self.h, self.prec, a_rho.contiguous(),
+                                            a_grad.contiguous(), d_rho, d_grad)
         return d_rho, d_grad
 
 

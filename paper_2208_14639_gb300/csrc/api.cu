@@ -55,7 +55,7 @@ void vv10_ctx::release_all() {
     DevBuf* bufs[] = {&prep_hist, &prep_offs, &prep_bbox, &prep_small, &orig, &seg, &atom_k,
                       &soa, &r64a, &r64b, &r32a, &r32b, &r32p, &sumE, &sumU, &sumW, &sumA, &sumB,
                       &sumC, &part, &eblk, &scal, &tu, &ty, &trt, &tgt, &hacc, &gk,
-                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &tc16_bh, &tc16_bl, &tc16_small, &o64_sl, &o64_small, &o64_rec, &nhess, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aogw, &aofa, &ngpart, &dev_err};
+                      &tc_uh, &tc_ul, &tc_yh, &tc_yl, &tc16_bh, &tc16_bl, &tc16_small, &o64_sl, &o64_small, &o64_rec, &hvp_fr, &hvp_fg, &nhess, &chpart, &wdir, &wsplit, &ehalf, &aophik, &aoz, &aom, &aogw, &aofa, &ngpart, &dev_err};
     for (DevBuf* b : bufs) {
         if (b->p) cudaFree(b->p);
         b->p = nullptr;
@@ -649,6 +649,47 @@ vv10_status vv10_nuclear_hessian(vv10_handle h, vv10_precision prec, const doubl
     in.sumE = static_cast<const double*>(h->sumE.p);
     PhaseScope ph(h, PH_NUCLEAR_GRADIENT, st, 2);
     VV10_CUDA(h, launch_nuclear_hessian(h->P, in, Hgg, part, H, st), "nuclear Hessian assembly");
+    return VV10_OK;
+}
+
+vv10_status vv10_hessian_vector_product(vv10_handle h, vv10_precision prec, int32_t P_trials,
+                                        const double* rho_t, const double* grad_rho_t,
+                                        double* hv_rho, double* hv_grad, void* stream) {
+    VV10_CHECK_HANDLE(h);
+    h->set_error("");
+    VV10_TRY(h->require_prepared());
+    if (!h->have_euw) {
+        h->set_error("vv10_energy_potential must be called first (it provides U_i, W_i)");
+        return VV10_ERR_INVALID_ARG;
+    }
+    if (P_trials < 1 || P_trials > VV10_MAX_TRIALS) {
+        h->set_error("P must be in [1, VV10_MAX_TRIALS]");
+        return P_trials < 1 ? VV10_ERR_INVALID_ARG : VV10_ERR_UNSUPPORTED;
+    }
+    if (!precision_known(prec)) {
+        h->set_error("unknown precision %d", static_cast<int>(prec));
+        return VV10_ERR_INVALID_ARG;
+    }
+    VV10_TRY(h->bind());
+    const void* ptrs[] = {rho_t, grad_rho_t, hv_rho, hv_grad};
+    for (const void* q : ptrs)
+        if (!device_ptr_ok(q, h->device) || !aligned(q, 8)) {
+            h->set_error("trial and output arrays must be 8-byte aligned device pointers");
+            return VV10_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t pn = static_cast<size_t>(P_trials) * static_cast<size_t>(h->P.n);
+    VV10_TRY(h->ensure(h->hvp_fr, sizeof(double) * pn, "Hessian-vector product scratch"));
+    VV10_TRY(h->ensure(h->hvp_fg, sizeof(double) * pn, "Hessian-vector product scratch"));
+    double* fr = static_cast<double*>(h->hvp_fr.p);
+    double* fg = static_cast<double*>(h->hvp_fg.p);
+    VV10_TRY(h->hessian(prec, P_trials, rho_t, grad_rho_t, fr, fg, st));
+    VV10_CUDA(h, cudaMemsetAsync(hv_rho, 0, sizeof(double) * pn, st), "memset hv_rho");
+    VV10_CUDA(h, cudaMemsetAsync(hv_grad, 0, 3 * sizeof(double) * pn, st), "memset hv_grad");
+    PhaseScope ph(h, PH_HESS_EPILOGUE, st, 1);
+    VV10_CUDA(h, launch_hvp_assemble(h->P, P_trials, static_cast<double*>(h->sumW.p), fr, fg,
+                                     grad_rho_t, hv_rho, hv_grad, st),
+              "Hessian-vector product");
     return VV10_OK;
 }
 

@@ -295,4 +295,39 @@ cudaError_t launch_hess_epilogue(const PointsDev& p, int32_t P, const double* ac
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ Hessian-vector product
+// Second derivatives of E along trial directions (Sec. II.B, Eq. frhot with dE/d rho_i =
+// w_i f^rho_i and dE/d grad rho_i = 2 w_i f^gamma_i grad rho_i, Sec. II.A):
+//   hv_rho[t][i]     = w_i f^{rho,t}_i
+//   hv_grad[t][i][c] = 2 w_i (f^{gamma,t}_i d_c rho_i + f^gamma_i d_c rho^t_i),
+// f^gamma_i = rho_i omega_gamma,i W_i; kept points only (the caller zeroes the rest).
+__global__ void __launch_bounds__(256)
+k_hvp_assemble(PointsDev P, int32_t Pn, const double* __restrict__ W,
+               const double* __restrict__ f_rho_t, const double* __restrict__ f_gamma_t,
+               const double* __restrict__ grad_rho_t, double* __restrict__ hv_rho,
+               double* __restrict__ hv_grad) {
+    const int t = blockIdx.y;
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= P.nk) return;
+    const int64_t i = P.orig[p];
+    const int64_t o = static_cast<int64_t>(t) * P.n + i;
+    const double w = P.w[p];
+    const double fg = P.rho[p] * P.om_g[p] * W[p];
+    const double ft = f_gamma_t[o];
+    hv_rho[o] = w * f_rho_t[o];
+    const double* gt = grad_rho_t + 3 * o;
+    hv_grad[3 * o + 0] = 2.0 * w * (ft * P.gx[p] + fg * gt[0]);
+    hv_grad[3 * o + 1] = 2.0 * w * (ft * P.gy[p] + fg * gt[1]);
+    hv_grad[3 * o + 2] = 2.0 * w * (ft * P.gz[p] + fg * gt[2]);
+}
+
+cudaError_t launch_hvp_assemble(const PointsDev& p, int32_t P, const double* W, const double* f_rho_t,
+                                const double* f_gamma_t, const double* grad_rho_t, double* hv_rho,
+                                double* hv_grad, cudaStream_t st) {
+    if (p.nk == 0) return cudaSuccess;
+    dim3 grid(static_cast<unsigned>(cdiv64(p.nk, 256)), static_cast<unsigned>(P));
+    k_hvp_assemble<<<grid, 256, 0, st>>>(p, P, W, f_rho_t, f_gamma_t, grad_rho_t, hv_rho, hv_grad);
+    return cudaGetLastError();
+}
+
 }  // namespace vv10

@@ -77,18 +77,18 @@ __host__ __device__ constexpr O64Layout o64_layout() {
     return L;
 }
 
-// Column (and row) record: every quantity as an FP32 pair (hi, lo), hi = fl32(v), lo =
-// fl32(v - hi): x, y, z, omega, kappa, p = rho kappa_rho, q = rho omega_rho.
+// Records of two consecutive points j0 = 2m, j1 = 2m + 1: every quantity v as an FP32 pair
+// (hi = fl32(v), lo = fl32(v - hi)), stored as {hi0, hi1, lo0, lo1} so that the two points' his
+// and los are ready-made operands of packed FP32x2 instructions: x, y, z, omega, kappa,
+// p = rho kappa_rho, q = rho omega_rho (and one unused float4).
 struct __align__(16) O64Rec {
-    float4 a;  // x.hi x.lo y.hi y.lo
-    float4 b;  // z.hi z.lo omega.hi omega.lo
-    float4 c;  // kappa.hi kappa.lo p.hi p.lo
-    float4 d;  // q.hi q.lo 0 0
+    float4 v[8];
 };
-static_assert(sizeof(O64Rec) == kO64RecBytes, "record size");
+static_assert(sizeof(O64Rec) == 2 * kO64RecBytes, "record size");
+enum : int { R_X = 0, R_Y, R_Z, R_OM, R_KA, R_P, R_Q };
 
 struct O64Args {
-    const O64Rec* rec;       // [nk_pad] records of the kept points
+    const O64Rec* rec;       // [nk_pad / 2] pair records of the kept points
     double* acc;             // [2][acc_P][nk_pad] FP64 partial output, zero on entry
     const float* civ;        // [n_stage][Ppad] column-factor inverses of this launch's group
     const double* params;    // [0] = 1/c_y
@@ -203,6 +203,60 @@ __device__ __forceinline__ DF df_rcp(DF x) {
 __device__ __forceinline__ DF df_neg(DF x) { return DF{-x.h, -x.l}; }
 __device__ __forceinline__ DF df_scale(DF x, float f) { return DF{x.h * f, x.l * f}; }  // f = 2^k
 
+// The same operations on two independent values at once (packed FP32x2 instructions: one
+// issue slot for two lanes, each lane rounded to nearest as the scalar forms).
+struct DF2 {
+    float2 h, l;
+};
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ DF2 df2_two_sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bp = sub2(s, a);
+    return DF2{s, add2(sub2(a, sub2(s, bp)), sub2(b, bp))};
+}
+__device__ __forceinline__ DF2 df2_fast(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return DF2{s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ DF2 df2_add(DF2 x, DF2 y) {
+    const DF2 s = df2_two_sum(x.h, y.h);
+    return df2_fast(s.h, add2(s.l, add2(x.l, y.l)));
+}
+__device__ __forceinline__ DF2 df2_mul(DF2 x, DF2 y) {
+    const float2 p = mul2(x.h, y.h);
+    float2 e = fma2(x.h, y.h, mul2(p, f2(-1.0f)));  // the product's rounding error, exactly
+    e = fma2(x.h, y.l, e);
+    e = fma2(x.l, y.h, e);
+    return df2_fast(p, e);
+}
+__device__ __forceinline__ DF2 df2_sqr(DF2 x) {
+    const float2 p = mul2(x.h, x.h);
+    float2 e = fma2(x.h, x.h, mul2(p, f2(-1.0f)));
+    e = fma2(add2(x.h, x.h), x.l, e);
+    return df2_fast(p, e);
+}
+__device__ __forceinline__ DF2 df2_rcp(DF2 x) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(x.h.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(x.h.y));
+    const float2 nxh = mul2(x.h, f2(-1.0f));
+    r = fma2(r, fma2(nxh, r, f2(1.0f)), r);
+    const float2 p = mul2(x.h, r);
+    const float2 pe = fma2(x.h, r, mul2(p, f2(-1.0f)));  // x.h r = p + pe
+    float2 res = sub2(sub2(f2(1.0f), p), pe);            // 1 - p is exact
+    res = fma2(mul2(x.l, f2(-1.0f)), r, res);
+    return df2_fast(r, mul2(r, res));
+}
+__device__ __forceinline__ DF2 df2_neg(DF2 x) { return DF2{mul2(x.h, f2(-1.0f)), mul2(x.l, f2(-1.0f))}; }
+__device__ __forceinline__ DF2 df2_dup(DF x) { return DF2{f2(x.h), f2(x.l)}; }
+__device__ __forceinline__ DF2 df2_rec(const float4& v) {
+    return DF2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
 // Exact difference of two coordinates held as FP32 pairs, rounded to a pair.
 __device__ __forceinline__ DF df_diff(float ah, float al, float bh, float bl) {
     const DF s = df_two_sum(ah, -bh);
@@ -215,36 +269,42 @@ struct RowDF {
     DF om, ka, np, nq;
 };
 
-// The two kernel tiles of output `kind` for row r against the column record c (the
-// quantities and signs of the FP32 generator of the split kernels): kind 0 -> (T1c, T2c),
-// kind 1 -> (T3c, T4c).
-__device__ __forceinline__ void o64_tiles(int kind, const RowDF& r, const O64Rec& c, DF& ta, DF& tb) {
-    const DF dx = df_diff(r.xh, r.xl, c.a.x, c.a.y);
-    const DF dy = df_diff(r.yh, r.yl, c.a.z, c.a.w);
-    const DF dz = df_diff(r.zh, r.zl, c.b.x, c.b.y);
-    const DF r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
-    const DF g = df_add(df_mul(r.om, r2), r.ka);
-    const DF gp = df_add(df_mul(DF{c.b.z, c.b.w}, r2), DF{c.c.x, c.c.y});
-    const DF s = df_add(g, gp);
-    const DF ggp = df_mul(g, gp);
-    const DF inv = df_rcp(df_mul(ggp, s));
-    const DF L = df_mul(ggp, inv);
-    const DF sinv = df_mul(s, inv);  // 1/(g g')
-    const DF M = df_scale(df_add(df_sqr(L), sinv), 2.0f);
-    const DF nAi = df_add(df_mul(r.nq, r2), r.np);
-    const DF nAj = df_neg(df_add(df_mul(DF{c.d.x, c.d.y}, r2), DF{c.c.z, c.c.w}));
-    const DF rp = df_mul(r2, inv);
+// The two kernel tiles of output `kind` for row r against the two columns of pair record c
+// (lane 0: j0, lane 1: j1; the quantities and signs of the FP32 generator of the split
+// kernels): kind 0 -> (T1c, T2c), kind 1 -> (T3c, T4c).
+__device__ __forceinline__ void o64_tiles2(int kind, const RowDF& r, const O64Rec& c, DF2& ta, DF2& tb) {
+    // exact coordinate differences (TwoSum of the high parts), rounded to pairs
+    auto diff = [&](float ah, float al, const float4& b) {
+        const DF2 t = df2_two_sum(f2(ah), mul2(make_float2(b.x, b.y), f2(-1.0f)));
+        return df2_fast(t.h, add2(t.l, sub2(f2(al), make_float2(b.z, b.w))));
+    };
+    const DF2 dx = diff(r.xh, r.xl, c.v[R_X]);
+    const DF2 dy = diff(r.yh, r.yl, c.v[R_Y]);
+    const DF2 dz = diff(r.zh, r.zl, c.v[R_Z]);
+    const DF2 r2 = df2_add(df2_add(df2_sqr(dx), df2_sqr(dy)), df2_sqr(dz));
+    const DF2 g = df2_add(df2_mul(df2_dup(r.om), r2), df2_dup(r.ka));
+    const DF2 gp = df2_add(df2_mul(df2_rec(c.v[R_OM]), r2), df2_rec(c.v[R_KA]));
+    const DF2 s = df2_add(g, gp);
+    const DF2 ggp = df2_mul(g, gp);
+    const DF2 inv = df2_rcp(df2_mul(ggp, s));
+    const DF2 L = df2_mul(ggp, inv);
+    const DF2 sinv = df2_mul(s, inv);  // 1/(g g')
+    DF2 M = df2_add(df2_sqr(L), sinv);
+    M = DF2{add2(M.h, M.h), add2(M.l, M.l)};
+    const DF2 nAi = df2_add(df2_mul(df2_dup(r.nq), r2), df2_dup(r.np));
+    const DF2 nAj = df2_neg(df2_add(df2_mul(df2_rec(c.v[R_Q]), r2), df2_rec(c.v[R_P])));
+    const DF2 rp = df2_mul(r2, inv);
     if (kind == 0) {
-        const DF LGi = df_add(L, df_mul(gp, sinv)), LGj = df_add(L, df_mul(g, sinv));
-        DF br = df_add(DF{1.0f, 0.0f}, df_mul(nAi, LGi));
-        br = df_add(br, df_mul(nAj, LGj));
-        br = df_add(br, df_mul(df_mul(nAi, nAj), M));
-        ta = df_mul(inv, br);                                   // T1c
-        tb = df_mul(rp, df_add(df_mul(nAi, M), LGj));           // T2c
+        const DF2 LGi = df2_add(L, df2_mul(gp, sinv)), LGj = df2_add(L, df2_mul(g, sinv));
+        DF2 br = df2_add(DF2{f2(1.0f), f2(0.0f)}, df2_mul(nAi, LGi));
+        br = df2_add(br, df2_mul(nAj, LGj));
+        br = df2_add(br, df2_mul(df2_mul(nAi, nAj), M));
+        ta = df2_mul(inv, br);                                   // T1c
+        tb = df2_mul(rp, df2_add(df2_mul(nAi, M), LGj));         // T2c
     } else {
-        const DF LGi = df_add(L, df_mul(gp, sinv));
-        ta = df_mul(rp, df_add(df_mul(nAj, M), LGi));           // T3c
-        tb = df_mul(df_mul(rp, r2), M);                         // T4c
+        const DF2 LGi = df2_add(L, df2_mul(gp, sinv));
+        ta = df2_mul(rp, df2_add(df2_mul(nAj, M), LGi));         // T3c
+        tb = df2_mul(df2_mul(rp, r2), M);                        // T4c
     }
 }
 
@@ -349,8 +409,8 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
                                (s == P.k.s0 ? O64_FIRST : 0) | (s == P.k.s1 - 1 ? O64_LAST : 0), 0};
         constexpr uint32_t rec_bytes = kO64Kj * kO64RecBytes, civ_bytes = kO64Ppad * 4u;
         mbar_expect_tx(&b_full[P.slot], L.slot_bytes + rec_bytes + civ_bytes);
-        bulk_g2s(smem + L.rec_off + P.slot * rec_bytes, args.rec + static_cast<int64_t>(kO64Kj) * s,
-                 rec_bytes, &b_full[P.slot]);
+        bulk_g2s(smem + L.rec_off + P.slot * rec_bytes, args.rec + static_cast<int64_t>(kO64Kj / 2) * s,
+                 rec_bytes, &b_full[P.slot]);  // the stage's kO64Kj / 2 pair records
         bulk_g2s(smem + L.civ_off + P.slot * civ_bytes, args.civ + static_cast<int64_t>(kO64Ppad) * s,
                  civ_bytes, &b_full[P.slot]);
         uint8_t* base = smem + P.slot * L.slot_bytes;
@@ -451,25 +511,38 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
         if (m.flags & O64_FIRST) {
             kind0 = m.kind;
             i = static_cast<int64_t>(m.row_tile) * 128 + quad * 32 + lane;
-            const O64Rec R = args.rec[i < args.nk ? i : args.nk_pad - 1];  // a padding record
-            rc.xh = R.a.x; rc.xl = R.a.y; rc.yh = R.a.z; rc.yl = R.a.w;
-            rc.zh = R.b.x; rc.zl = R.b.y;
-            rc.om = DF{R.b.z, R.b.w};
-            rc.ka = DF{R.c.x, R.c.y};
-            rc.np = DF{-R.c.z, -R.c.w};
-            rc.nq = DF{-R.d.x, -R.d.y};
+            const int64_t ir = i < args.nk ? i : args.nk_pad - 1;  // a padding record
+            const O64Rec& R = args.rec[ir >> 1];
+            const bool odd = (ir & 1) != 0;
+            auto hl = [&](int q) {
+                const float4 v = R.v[q];
+                return DF{odd ? v.y : v.x, odd ? v.w : v.z};
+            };
+            const DF x = hl(R_X), y = hl(R_Y), z = hl(R_Z);
+            rc.xh = x.h; rc.xl = x.l; rc.yh = y.h; rc.yl = y.l; rc.zh = z.h; rc.zl = z.l;
+            rc.om = hl(R_OM);
+            rc.ka = hl(R_KA);
+            const DF p = hl(R_P), q = hl(R_Q);
+            rc.np = DF{-p.h, -p.l};
+            rc.nq = DF{-q.h, -q.l};
             until_flush = args.flush;
         }
-        // tiles of this warp's 4 j (records 4 part .. 4 part + 3)
+        // tiles of this warp's 4 j (pair records 2 part, 2 part + 1), two j per packed lane pair
         const O64Rec* rs = reinterpret_cast<const O64Rec*>(smem + L.rec_off + slot * kO64Kj * kO64RecBytes);
         DF ta[4], tb[4];
         float mx = 0.0f;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            o64_tiles(kind0, rc, rs[4 * part + h], ta[h], tb[h]);
-            tb[h] = df_scale(tb[h], inv_cy);  // the tile that multiplies y carries 1/c_y
-            mx = fmaxf(mx, fmaxf(fabsf(ta[h].h), fabsf(tb[h].h)));
+        for (int hp = 0; hp < 2; ++hp) {
+            DF2 a2, b2;
+            o64_tiles2(kind0, rc, rs[2 * part + hp], a2, b2);
+            b2 = DF2{mul2(b2.h, f2(inv_cy)), mul2(b2.l, f2(inv_cy))};  // the tile that multiplies y carries 1/c_y
+            ta[2 * hp] = DF{a2.h.x, a2.l.x};
+            ta[2 * hp + 1] = DF{a2.h.y, a2.l.y};
+            tb[2 * hp] = DF{b2.h.x, b2.l.x};
+            tb[2 * hp + 1] = DF{b2.h.y, b2.l.y};
         }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) mx = fmaxf(mx, fmaxf(fabsf(ta[h].h), fabsf(tb[h].h)));
         // the row's largest |T| over the stage: the quad's 4 parts
         const int xs = static_cast<int>(gs & 1u);
         float* xrow = xm + (static_cast<size_t>(xs * 4 + quad) * 32 + lane) * 4;
@@ -590,21 +663,26 @@ __device__ __forceinline__ float2 o64_split(double v) {
     return make_float2(h, __double2float_rn(v - static_cast<double>(h)));
 }
 
-// Column records of the kept points (padding points keep the prepared padding values).
+// Pair records of the kept points (padding points keep the prepared padding values): point j
+// writes lane j & 1 of pair record j / 2.
 __global__ void __launch_bounds__(256)
 k_o64_records(const double4* __restrict__ r64a, const double4* __restrict__ r64b, int64_t nk_pad,
               O64Rec* __restrict__ rec) {
     const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= nk_pad) return;
     const double4 a = r64a[j], b = r64b[j];
-    const float2 x = o64_split(a.x), y = o64_split(a.y), z = o64_split(a.z);
-    const float2 om = o64_split(b.x), ka = o64_split(b.y), p = o64_split(b.z), q = o64_split(b.w);
-    O64Rec R;
-    R.a = make_float4(x.x, x.y, y.x, y.y);
-    R.b = make_float4(z.x, z.y, om.x, om.y);
-    R.c = make_float4(ka.x, ka.y, p.x, p.y);
-    R.d = make_float4(q.x, q.y, 0.f, 0.f);
-    rec[j] = R;
+    const double vals[7] = {a.x, a.y, a.z, b.x, b.y, b.z, b.w};  // x y z omega kappa p q
+    float* r = reinterpret_cast<float*>(rec + (j >> 1)) + (j & 1);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const float2 v = o64_split(vals[q]);
+        r[4 * q] = v.x;      // hi of this lane
+        r[4 * q + 2] = v.y;  // lo of this lane
+    }
+    if ((j & 1) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[28 + k] = 0.0f;
+    }
 }
 
 // Largest |u'| and |y'| over all trials (u' = -3/2 u, y' = 3/2 y) as FP64 bit patterns
@@ -733,7 +811,7 @@ cudaError_t launch_o64_prep(const PointsDev& p, const double* u, const double* y
     const int ng = (P + pg - 1) / pg;
     const int64_t nb = nk_pad / 256;
     k_o64_records<<<static_cast<unsigned>(nb), 256, 0, st>>>(p.r64a, p.r64b, nk_pad,
-                                                              static_cast<O64Rec*>(rec));
+                                                              static_cast<O64Rec*>(rec));  // nk_pad / 2 pair records
     cudaError_t e = cudaMemsetAsync(colmax, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     // zero factors for the padding columns of every group

@@ -309,6 +309,11 @@ cudaError_t launch_hess_epilogue(const PointsDev& p, int32_t P, const double* ac
                                  const double* A, const double* B, const double* C,
                                  const double* rt_k, const double* gt_k, double* f_rho_t,
                                  double* f_gamma_t, int* err, cudaStream_t st);
+// Hessian-vector product from the contraction (caller order): hv_rho = w f^{rho,t},
+// hv_grad = 2 w (f^{gamma,t} grad rho + f^gamma grad rho^t) at kept points.
+cudaError_t launch_hvp_assemble(const PointsDev& p, int32_t P, const double* W, const double* f_rho_t,
+                                const double* f_gamma_t, const double* grad_rho_t, double* hv_rho,
+                                double* hv_grad, cudaStream_t st);
 // Batched Hessian epilogue: block k of molecule m covers kept points 256 (k mod nb) .. of
 // trial t = k / nb, nb = ceil(nk / 256); outputs at the molecule's trial offset.
 cudaError_t launch_hess_epilogue_batch(const EpiMol* mols, const int64_t* pre, int n_mol, int64_t n_blocks,

@@ -147,6 +147,7 @@ struct vv10_ctx {
     vv10::DevBuf o64_sl;            // FP64-accurate contraction: FP16 trial slice arrays
     vv10::DevBuf o64_small;         // their factors and y balance
     vv10::DevBuf o64_rec;           // and the points' FP32-pair column records
+    vv10::DevBuf hvp_fr, hvp_fg;    // Hessian-vector product: the contraction's outputs
 
     // coordinate scratch
     vv10::DevBuf gk;

@@ -52,7 +52,7 @@ EXPORTS = ("vv10_create", "vv10_destroy", "vv10_status_string", "vv10_last_error
            "vv10_set_options", "vv10_evaluate", "vv10_coord_hessian",
            "vv10_weight_response", "vv10_energy", "vv10_fock_matrix",
            "vv10_orbital_hessian", "vv10_nuclear_gradient", "vv10_fock_derivative",
-           "vv10_nuclear_hessian")
+           "vv10_nuclear_hessian", "vv10_hessian_vector_product")
 VV10_NOALLOC_MAX_POINTS = 32768
 VV10_MAX_TRIALS = 4096  # include/vv10.h: VV10_MAX_TRIALS (also the most weight directions)
 VV10_N_PHASES = 16
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
                                      ctypes.POINTER(I64), P]),
         "vv10_energy_potential": (st, [P, st, ctypes.POINTER(D), P, P, P]),
         "vv10_hessian_contract": (st, [P, st, I32, P, P, P, P, P]),
+        "vv10_hessian_vector_product": (st, [P, st, I32, P, P, P, P, P]),
         "vv10_coord_grad": (st, [P, st, P, P, P, P]),
         "vv10_coord_hessian": (st, [P, st, P, P, P]),
         "vv10_weight_response": (st, [P, st, ctypes.c_int32, P, P, P, P, P]),
@@ -216,6 +217,18 @@ def vv10_hessian_contract(h, prec: int, rho_t, grad_rho_t, f_rho_t, f_gamma_t,
         _dptr(f_rho_t, "f_rho_t", shape=(P, n)), _dptr(f_gamma_t, "f_gamma_t", shape=(P, n)),
         _stream(stream))
     _check(h, st, "vv10_hessian_contract")
+
+
+def vv10_hessian_vector_product(h, prec: int, rho_t, grad_rho_t, hv_rho, hv_grad,
+                                stream=None) -> None:
+    """hv_rho = w f^{rho,t}, hv_grad = 2 w (f^{gamma,t} grad rho + f^gamma grad rho^t)."""
+    P, n = int(rho_t.shape[0]), int(rho_t.shape[1])
+    st = load().vv10_hessian_vector_product(
+        h, int(prec), P, _dptr(rho_t, "rho_t", shape=(P, n)),
+        _dptr(grad_rho_t, "grad_rho_t", shape=(P, n, 3)),
+        _dptr(hv_rho, "hv_rho", shape=(P, n)), _dptr(hv_grad, "hv_grad", shape=(P, n, 3)),
+        _stream(stream))
+    _check(h, st, "vv10_hessian_vector_product")
 
 
 def vv10_coord_grad(h, prec: int, grad_points=None, grad_atoms=None, EUW_Bgr=None,
@@ -509,6 +522,12 @@ class VV10:
         fg = torch.empty_like(rho_t)
         vv10_hessian_contract(self.h, prec, rho_t, grad_rho_t, fr, fg, stream)
         return fr, fg
+
+    def hessian_vector_product(self, rho_t, grad_rho_t, prec=VV10_FP64, stream=None):
+        hr = torch.empty_like(rho_t)
+        hg = torch.empty_like(grad_rho_t)
+        vv10_hessian_vector_product(self.h, prec, rho_t, grad_rho_t, hr, hg, stream)
+        return hr, hg
 
     def coord_grad(self, prec=VV10_FP64, atoms=True, resolved=False, stream=None):
         dev = torch.device("cuda", self.device)

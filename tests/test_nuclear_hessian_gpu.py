@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 FP64 = vv10.VV10_FP64
 MIXED = vv10.VV10_MIXED_TF32X3
 F16 = vv10.VV10_MIXED_F16X3
+F64TC = vv10.VV10_FP64_TC
 
 
 @pytest.fixture(scope="module")
@@ -86,8 +87,8 @@ def water_small():
     return case(synth.water(), 10, 26)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F16, 1e-6)],
-                         ids=["fp64", "tf32x3", "f16x3"])
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F16, 1e-6), (F64TC, 1e-10)],
+                         ids=["fp64", "tf32x3", "f16x3", "fp64tc"])
 def test_water_against_oracle_terms(dev, oracle_mod, water_small, prec, tol):
     ref = oracle_hessian(oracle_mod, water_small)
     got = gpu_hessian(oracle_mod, water_small, prec, dev)

@@ -152,6 +152,32 @@ def test_hessian_mixed_trial_counts(dev, oracle_mod, P, tcp):
     eng.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-6), (F64TC, 1e-10)],
+                         ids=["fp64", "mixed", "fp64tc"])
+def test_hessian_vector_product(dev, oracle_mod, prec, tol):
+    """vv10_hessian_vector_product: w f^{rho,t} and 2 w (f^{gamma,t} grad rho + f^gamma grad
+    rho^t) against the same quantities from the oracle's contraction and potential; dropped
+    points zero."""
+    g = synth.config_water(n_rad=16, n_ang=38)
+    rt, gt = synth.trial_densities(g.molecule, g.coords)
+    args = (g.coords, g.weights, g.rho, g.grad_rho)
+    fr, fg = oracle_mod.hessian_contract(*args, rt, gt)
+    _, _, vg = oracle_mod.potential(*args)
+    w = g.weights
+    ref_r = w[None] * fr
+    ref_g = 2.0 * w[None, :, None] * (fg[..., None] * g.grad_rho[None] + vg[None, :, None] * gt)
+    eng = make_engine(g, dev)
+    eng.energy_potential(prec)
+    hr, hg = eng.hessian_vector_product(T(rt, dev), T(gt, dev), prec)
+    vv10.vv10_sync(eng.h)
+    hr, hg = hr.cpu().numpy(), hg.cpu().numpy()
+    check(hr, ref_r, tol, what="hv_rho")
+    check(hg, ref_g, tol, what="hv_grad")
+    kept = g.rho >= 1e-10
+    assert not hr[:, ~kept].any() and not hg[:, ~kept].any()
+    eng.close()
+
+
 def test_fp64tc_trial_scales(dev, oracle_mod):
     """Trials 20 orders of magnitude apart, one zero trial and one with zero u or y part:
     each column has its own power-of-two factor, so every trial keeps FP64 accuracy relative
