@@ -128,7 +128,8 @@ vv10_status vv10_prepare_points(vv10_handle h, int64_t n, const double* xyz, con
  *   f^gamma_i = rho_i omega_gamma,i W_i,
  * with U_i, W_i the pair sums defined there.  f^rho and f^gamma are per unit weight:
  * dE/d rho_i = w_i f^rho_i and dE/d(grad rho_i) = 2 w_i f^gamma_i grad rho_i.
- *   prec      VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ *   prec      VV10_FP64 (VV10_FP64_TC computes the same here), or a mixed mode (FP32
+ *             pair arithmetic, FP64 sums)
  *   energy    HOST pointer, receives E (may be NULL: then the call does not synchronise)
  *   vrho      n device out, f^rho (may be NULL)
  *   vgamma    n device out, f^gamma (may be NULL)
@@ -140,7 +141,8 @@ vv10_status vv10_energy_potential(vv10_handle h, vv10_precision prec, double* en
 /* The energy alone (Sec. II.A, the quadrature form of E^VV10), from the unordered pairs:
  *   E = beta sum_i c_i + sum_{i<j} c_i c_j Phi_ij + 1/2 sum_i c_i^2 Phi_ii,   c_i = w_i rho_i,
  * the same E as vv10_energy_potential with half the pair evaluations (Phi_ij = Phi_ji).
- *   prec     VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ *   prec     VV10_FP64 (VV10_FP64_TC computes the same here), or a mixed mode (FP32
+ *            pair arithmetic, FP64 sums)
  *   energy   HOST pointer, receives E (required; the call synchronises `stream`)
  * Leaves the row sums cached by vv10_energy_potential as they were.  The sum is formed in a
  * fixed order: repeated calls give identical results.  Errors: INVALID_ARG, OOM, CUDA. */
@@ -204,7 +206,8 @@ vv10_status vv10_coord_grad(vv10_handle h, vv10_precision prec, double* grad_poi
  *   E_grgr     n_atom x n_atom x 3 x 3 device out (may be NULL): block (A, B) row-major
  *   D_points   n x n_atom x 3 x 3 device out (may be NULL): D_i^B in the caller's point
  *              order; zero for B = atom(i) and for points below rho_cut
- *   prec       VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ *   prec       VV10_FP64 (VV10_FP64_TC computes the same here), or a mixed mode (FP32
+ *              pair arithmetic, FP64 sums)
  * Needs atom_of_point at prepare time (else INVALID_ARG) and no earlier call other than
  * vv10_prepare_points.  Holds about 48 n_atom (n / 128 + n_atom) bytes of scratch.  The
  * blocks are summed in a fixed order: repeated calls give identical results.
@@ -223,7 +226,8 @@ vv10_status vv10_coord_hessian(vv10_handle h, vv10_precision prec, double* E_grg
  *   w_t        P x n device in, direction p of point i at w_t[p n + i] (caller order)
  *   E_t, U_t, W_t   P x n device out, same layout (each may be NULL); zero for points
  *              below rho_cut
- *   prec       VV10_FP64, or a mixed mode (FP32 pair arithmetic, FP64 sums)
+ *   prec       VV10_FP64 (VV10_FP64_TC computes the same here), or a mixed mode (FP32
+ *              pair arithmetic, FP64 sums)
  * Needs no earlier call other than vv10_prepare_points.  Holds 8 P n_kept bytes of scratch.
  * Errors: INVALID_ARG, UNSUPPORTED (P too large), OOM, CUDA. */
 vv10_status vv10_weight_response(vv10_handle h, vv10_precision prec, int32_t P,
@@ -400,8 +404,9 @@ vv10_status vv10_energy_potential_noalloc(int64_t n, const double* xyz, const do
  * vv10_batch_hessian_contract: f^{rho,t}, f^{gamma,t} (Eq. frhot) for P[m] trial densities
  * of molecule m (P: HOST int32[n_mol], each in [1, VV10_MAX_TRIALS]).  rho_t, grad_rho_t,
  * f_rho_t, f_gamma_t are the concatenation over molecules of each molecule's [P[m]][n_m]
- * (and [P[m]][n_m][3]) row-major blocks, molecule 0 first.  prec: VV10_FP64 or
- * VV10_MIXED_TF32X3 (VV10_MIXED_BF16X3: UNSUPPORTED).  Needs a preceding
+ * (and [P[m]][n_m][3]) row-major blocks, molecule 0 first.  prec: VV10_FP64,
+ * VV10_MIXED_TF32X3 or VV10_MIXED_F16X3 (VV10_MIXED_BF16X3 and VV10_FP64_TC:
+ * UNSUPPORTED).  Needs a preceding
  * vv10_batch_energy_potential.  Not synchronised.  Errors: INVALID_ARG, UNSUPPORTED, OOM,
  * CUDA.
  *

@@ -21,7 +21,7 @@ from paper_2208_14639_gb300 import synth, vv10
 pytestmark = pytest.mark.gpu
 
 PRECS = [(vv10.VV10_FP64, None, 1e-10), (vv10.VV10_MIXED_TF32X3, 1e-7, 1e-6),
-         (vv10.VV10_MIXED_BF16X3, 1e-7, 1e-6)]
+         (vv10.VV10_MIXED_BF16X3, 1e-7, 1e-6), (vv10.VV10_FP64_TC, None, 1e-10)]
 
 
 def _rel(a, b):
@@ -67,7 +67,7 @@ def _call(g, prec, dev, d=None):
     return float(energy.item()), vrho.cpu().numpy(), vgamma.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec,tol_e,tol_v", PRECS, ids=["fp64", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec,tol_e,tol_v", PRECS, ids=["fp64", "tf32x3", "bf16x3", "fp64tc"])
 def test_noalloc_matches_oracle(dev, systems, prec, tol_e, tol_v):
     for g, e_ref, vr_ref, vg_ref in systems:  # two calls in a row sharing the static scratch
         e, vr, vg = _call(g, prec, dev)
