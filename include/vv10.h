@@ -442,8 +442,10 @@ vv10_status vv10_sync(vv10_handle h, void* stream);
  *         {1, 2, 4} (FP64: {1, 2}), n_split = number of j-splits (0 = from the SM count);
  *   6, 7  batched pair sums, 6 + fp64: rows_per_thread as above, n_split = j tiles (of 256
  *         points) per split (0 = 32);
- *   8     tensor-core contraction: rows_per_thread = the widest trial group, in [32, 192]
- *         (n_split unused).  Groups of at most 64 trials produce both outputs from one tile
+ *   8     tensor-core contraction: rows_per_thread = the widest trial group, in [32, 192];
+ *         n_split = the split-FP16 contraction's j chunk in MB of trial tiles, in [4, 96]
+ *         (0 = 24): the persistent CTAs walk the chunks in order so that a chunk's tiles
+ *         stay in L2.  Groups of at most 64 trials produce both outputs from one tile
  *         generation; wider groups issue fewer MMAs per trial.
  * vv10_set_tiles fixes a shape (rows_per_thread = 0: back to automatic, i.e. the autotuner's
  * choice when tuning is enabled, else the default); the autotuner never replaces a fixed

@@ -1237,12 +1237,17 @@ vv10_status vv10_debug_inject(vv10_handle h, int what, int64_t value) {
 vv10_status vv10_set_tiles(vv10_handle h, int what, int rows_per_thread, int n_split) {
     VV10_CHECK_HANDLE(h);
     if (what < 0 || what > 8 || rows_per_thread < 0 || n_split < 0) return VV10_ERR_INVALID_ARG;
-    if (what == 8) {  // widest trial group of the tensor-core contraction
+    if (what == 8) {  // widest trial group of the tensor-core contraction; j-chunk size
         if (rows_per_thread != 0 && (rows_per_thread < 32 || rows_per_thread > 192)) {
             h->set_error("the trial-group width must be 0 or in [32, 192]");
             return VV10_ERR_INVALID_ARG;
         }
+        if (n_split != 0 && (n_split < 4 || n_split > 96)) {
+            h->set_error("the j-chunk size must be 0 or in [4, 96] MB");
+            return VV10_ERR_INVALID_ARG;
+        }
         h->tc_cap_manual = rows_per_thread;
+        h->tc_chunk_mb = n_split;
         h->batch.tc_classes.clear();  // rebuild the batch layouts with the new width
         h->batch.f16_classes.clear();
         h->batch_drop_graph();
@@ -1272,7 +1277,7 @@ vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n
     if (what < 0 || what > 8 || !rows_per_thread || !n_split) return VV10_ERR_INVALID_ARG;
     if (what == 8) {
         *rows_per_thread = h->tc_cap_manual > 0 ? h->tc_cap_manual : h->tc_cap_last;
-        *n_split = 0;
+        *n_split = h->tc_chunk_mb > 0 ? h->tc_chunk_mb : 24;
     } else if (what >= 6) {
         h->batch_tiles(what == 7, rows_per_thread, n_split);
     } else {

@@ -55,7 +55,7 @@ constexpr int kF16Threads = kF16Warps * 32;
 constexpr int kF16Ring = 4;                     // stages of trial tiles in flight
 constexpr int kF16MaxPpad = 192;
 constexpr uint32_t kF16TmemCols = 512;
-constexpr size_t kF16ChunkBytes = 48u << 20;    // trial-tile bytes of one j chunk (L2-resident)
+constexpr size_t kF16ChunkBytes = 24u << 20;    // trial-tile bytes of one j chunk (L2-resident)
 
 struct F16Layout {
     uint32_t tile_bytes;  // one Ppad x 64-half trial tile (128-byte rows: 16 u, 16 y, 16 u, 16 y)
@@ -462,7 +462,9 @@ k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CU
                     const int64_t tg = static_cast<int64_t>(M.t0) + t;
                     double* o = M.acc + ((static_cast<int64_t>(kind) * M.acc_P + tg) * M.nk_pad + i);
                     const double v = static_cast<double>(acc[k][c]) * M.col_isc[tg];
-                    *o += (kind == 0) ? v : -v;
+                    // streaming loads and stores: the partial output must not evict the
+                    // chunk's trial tiles from L2
+                    __stcs(o, __ldcs(o) + ((kind == 0) ? v : -v));
                 }
                 acc[k][c] = 0.0f;
             }
@@ -931,8 +933,8 @@ int hess_f16_kinds_per_tile(int ppad) { return ppad <= 64 ? 2 : 1; }
 // rows; col_isc and params as written by launch_f16_trial_split.
 cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
                             const void* bh, const void* bl, int64_t rows, const double* col_isc,
-                            const float* params, int n_sm, int flush, double* acc, int* err,
-                            cudaStream_t st) {
+                            const float* params, int n_sm, int flush, size_t chunk_bytes,
+                            double* acc, int* err, cudaStream_t st) {
     if (p.nk == 0) return cudaSuccess;
     const int ppad = hess_tc_ppad(Pn);
     if (ppad > kF16MaxPpad || t0 + ppad > rows) return cudaErrorInvalidValue;
@@ -946,7 +948,7 @@ cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t 
     a.n_units = (nk_t == 2 ? 1 : 2) * ((p.nk + 127) / 128);
     a.n_stage = static_cast<int32_t>(p.nk_pad / kF16Kj);
     const size_t stage_bytes = 2u * static_cast<size_t>(ppad) * 128u + 1024u;
-    int64_t chunk = static_cast<int64_t>(kF16ChunkBytes / stage_bytes);
+    int64_t chunk = static_cast<int64_t>((chunk_bytes > 0 ? chunk_bytes : kF16ChunkBytes) / stage_bytes);
     if (chunk < 64) chunk = 64;
     a.chunk = static_cast<int32_t>(chunk < a.n_stage ? chunk : a.n_stage);
     a.flush = flush > 0 ? flush : 512;

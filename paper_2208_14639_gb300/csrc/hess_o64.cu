@@ -486,7 +486,7 @@ k_hess_o64(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUte
                 const int64_t tg = static_cast<int64_t>(args.t0) + t;
                 double* o = args.acc + ((static_cast<int64_t>(kind) * args.acc_P + tg) * args.nk_pad + i);
                 const double v = static_cast<double>(ahi[c]) + static_cast<double>(alo[c]);
-                *o += (kind == 0) ? v : -v;
+                __stcs(o, __ldcs(o) + ((kind == 0) ? v : -v));  // streaming: keep the tiles in L2
             }
             ahi[c] = alo[c] = 0.0f;
         }

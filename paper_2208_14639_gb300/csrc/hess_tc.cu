@@ -412,7 +412,9 @@ k_hess_tc(const __grid_constant__ CUtensorMap tm_uh, const __grid_constant__ CUt
                     if (i < nk && t < Pn) {
                         double* o = acc_base + ((static_cast<int64_t>(kind) * acc_P + t0 + t) * nk_pad + i);
                         const double v = static_cast<double>(acc[k][c]);
-                        *o += (kind == 0) ? v : -v;  // the gamma accumulator holds -(T3 u + T4 y)
+                        // the gamma accumulator holds -(T3 u + T4 y); streaming loads and
+                        // stores keep the partial output from evicting the trial tiles
+                        __stcs(o, __ldcs(o) + ((kind == 0) ? v : -v));
                     }
                     acc[k][c] = 0.0f;
                 }

@@ -214,7 +214,8 @@ vv10_status vv10_ctx::f16_contract(int32_t Pn, int cap, cudaStream_t st) {
         const int t0 = g * pg;
         const int pn = (Pn - t0 < pg) ? Pn - t0 : pg;
         H_CUDA(launch_hess_f16(P, pn, t0, Pn, tc16_bh.p, tc16_bl.p, rows, col_isc, params, n_sm,
-                               tc_flush, static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
+                               tc_flush, static_cast<size_t>(tc_chunk_mb) << 20,
+                               static_cast<double*>(hacc.p), static_cast<int*>(dev_err.p), st),
                "FP16 tensor-core contraction");
     }
     return VV10_OK;

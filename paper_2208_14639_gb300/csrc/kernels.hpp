@@ -231,7 +231,8 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
                            int64_t rows, int n_sm, int flush, double* acc, int* err,
                            cudaStream_t st);
 
-// Tensor-core split-FP16 contraction (hess_f16.cu).  launch_f16_trial_split turns u, y
+// Tensor-core split-FP16 contraction (hess_f16.cu).  chunk_bytes: trial-tile bytes of one j
+// chunk (0: the default, 24 MB).  launch_f16_trial_split turns u, y
 // (FP64 [P][nk_pad]) into scaled FP16 hi / lo tiles [rows][2 nk_pad] (per stage of 16 j: 16 u
 // then 16 y), the global y balance factor (params[0] = 1/c_y, params[1] = c_y) and per-trial
 // factors (scale[t] = s_t, col_isc[t] = 1/s_t; colmax: 2 P scratch words).  launch_hess_f16
@@ -257,8 +258,8 @@ cudaError_t launch_hess_f16_batch(const void* mols, const void* tasks, int64_t n
                                   int* counter, int n_sm, int flush, int* err, cudaStream_t st);
 cudaError_t launch_hess_f16(const PointsDev& p, int32_t Pn, int32_t t0, int64_t acc_P,
                             const void* bh, const void* bl, int64_t rows, const double* col_isc,
-                            const float* params, int n_sm, int flush, double* acc, int* err,
-                            cudaStream_t st);
+                            const float* params, int n_sm, int flush, size_t chunk_bytes,
+                            double* acc, int* err, cudaStream_t st);
 
 // Tensor-core contraction with FP64 accuracy (hess_o64.cu).  launch_o64_prep writes the
 // kept points' column records (`rec`, 64 B per point, nk_pad of them), cuts u, y (FP64

@@ -172,6 +172,7 @@ struct vv10_ctx {
 
     // stages between FP64 flushes of the tensor-core contraction's register accumulators
     int tc_flush = 512;
+    int tc_chunk_mb = 0;            // j-chunk of the split-FP16 contraction (MB of trial tiles; 0 = 24)
 
     // launch accounting / profiling
     bool prof_on = false;
