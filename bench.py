@@ -76,9 +76,10 @@ O64_ALU_OPS_PER_PAIR = 2 * (33 + 250 + 60 + 80)
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the current kernel on
 # the full-size launch, keyed by (kernel, workload); absent -> traffic null.
 PROFILED_TRAFFIC = {
-    # k_hess_f16 on the 60-atom grid (P = 180, one 192-wide group, 24 MB j chunks): ncu
-    # dram__bytes_read.sum + dram__bytes_write.sum of one launch
-    ("k_hess_f16", "chon60"): 681.98e9 + 194.92e9,
+    # k_hess_f16 on the 60-atom grid (P = 180, one 192-wide group, 24 MB j chunks, evict-last
+    # trial tiles, streaming partial output): ncu dram__bytes_read.sum + dram__bytes_write.sum
+    # of one launch
+    ("k_hess_f16", "chon60"): 630.09e9 + 194.94e9,
 }
 
 

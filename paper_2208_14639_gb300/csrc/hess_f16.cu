@@ -384,8 +384,10 @@ k_hess_f16(const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CU
         uint8_t* rec = smem + L.rec_off + P.slot * 1024;
         mbar_expect_tx(&b_full[P.slot], L.slot_bytes + 1024u);
         bulk_g2s(rec, M.r32p + 2 * kF16Kj * static_cast<int64_t>(s), 1024u, &b_full[P.slot]);
-        tc::tma_load_2d(base, mh, 64 * s, M.t0, &b_full[P.slot]);
-        tc::tma_load_2d(base + L.tile_bytes, ml, 64 * s, M.t0, &b_full[P.slot]);
+        // the chunk's trial tiles are re-read by every unit: keep them in L2 before other lines
+        const uint64_t pol = tc::l2_evict_last();
+        tc::tma_load_2d_hint(base, mh, 64 * s, M.t0, &b_full[P.slot], pol);
+        tc::tma_load_2d_hint(base + L.tile_bytes, ml, 64 * s, M.t0, &b_full[P.slot], pol);
         ++P.issued;
         if (++P.slot == kF16Ring) {
             P.slot = 0;
