@@ -1066,7 +1066,7 @@ def gpu_batch_arm(args):
     dev = torch.device("cuda", local)
     from paper_2208_14639_gb300 import vv10 as vv
     vv.load(build_if_missing=True)
-    result = batch_record(args, dev, world, rank, args.steps, args.warmup, args.precision,
+    result = batch_record(args, dev, world, rank, args.steps, args.warmup, args.batch_precision,
                           with_fp64=not args.no_fp64_arm, with_cpu=not args.no_cpu_baseline)
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -1184,8 +1184,9 @@ def main(argv=None):
     ap.add_argument("--no-batch", dest="with_batch", action="store_false",
                     help="leave out the 64-molecule batch record of the single-system runs")
     ap.add_argument("--batch-precision", choices=("f16x3", "mixed", "tf32x3", "fp64"), default="tf32x3",
-                    help="the batch record's precision (split TF32: its trial groups are at most "
-                         "96 wide, where the split-FP16 kernel is not the faster one)")
+                    help="the batch's precision, as a record of the single-system run and with "
+                         "--workload batch (split TF32: its trial groups are at most 96 wide, "
+                         "where the split-FP16 kernel is not the faster one)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args(argv)
