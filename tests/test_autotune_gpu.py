@@ -178,3 +178,33 @@ def test_tuned_batch_matches_untuned(dev):
         vv10.vv10_destroy(h)
     for a, b in zip(*outs):
         assert rel(a, b) <= 1e-12
+
+
+def test_contraction_j_chunks(dev):
+    """The split-FP16 contraction's j chunk (MB of trial tiles kept in L2): 4, 24 and 96 MB
+    walk the same sums in different chunks (and so flush the FP32 register sums at different
+    stages), agreeing to the mixed tolerance; sizes outside [4, 96] are refused."""
+    g = synth.make_system(synth.random_chon(np.random.default_rng(11), 4), 40, 110)
+    rng = np.random.default_rng(180)
+    P = 180  # one 192-wide group: 50 KB per 32-j stage, so 4 MB chunks are 82 stages
+    rt = torch.from_numpy(rng.normal(size=(P, g.n)) * g.rho).to(dev)
+    gt = torch.from_numpy(rng.normal(size=(P, g.n, 3)) * np.abs(g.grad_rho)[None]).to(dev)
+    eng = engine(g, dev)
+    eng.energy_potential(vv10.VV10_MIXED_F16X3)
+    out = {}
+    for mb in (4, 24, 96):
+        vv10.vv10_set_tiles(eng.h, vv10.TILES_CONTRACTION, 0, mb)
+        assert vv10.vv10_get_tiles(eng.h, vv10.TILES_CONTRACTION)[1] == mb
+        fr, fg = eng.hessian_contract(rt, gt, vv10.VV10_MIXED_F16X3)
+        vv10.vv10_sync(eng.h)
+        out[mb] = (fr.cpu().numpy(), fg.cpu().numpy())
+    for mb in (4, 96):
+        for k in range(2):
+            ref = out[24][k]
+            assert np.linalg.norm(out[mb][k] - ref) <= 1e-6 * np.linalg.norm(ref)
+    for bad in (2, 100):
+        with pytest.raises(vv10.VV10Error):
+            vv10.vv10_set_tiles(eng.h, vv10.TILES_CONTRACTION, 0, bad)
+    vv10.vv10_set_tiles(eng.h, vv10.TILES_CONTRACTION, 0, 0)
+    assert vv10.vv10_get_tiles(eng.h, vv10.TILES_CONTRACTION)[1] == 24
+    eng.close()
