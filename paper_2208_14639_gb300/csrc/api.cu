@@ -1277,7 +1277,8 @@ vv10_status vv10_get_tiles(vv10_handle h, int what, int* rows_per_thread, int* n
     if (what < 0 || what > 8 || !rows_per_thread || !n_split) return VV10_ERR_INVALID_ARG;
     if (what == 8) {
         *rows_per_thread = h->tc_cap_manual > 0 ? h->tc_cap_manual : h->tc_cap_last;
-        *n_split = h->tc_chunk_mb > 0 ? h->tc_chunk_mb : 24;
+        *n_split = h->tc_chunk_mb > 0 ? h->tc_chunk_mb
+                                      : static_cast<int>(hess_f16_default_chunk_bytes() >> 20);
     } else if (what >= 6) {
         h->batch_tiles(what == 7, rows_per_thread, n_split);
     } else {

@@ -930,6 +930,7 @@ static cudaError_t launch_f16_dispatch(int ppad, const CUtensorMap* maps, const 
 }
 
 int hess_f16_kinds_per_tile(int ppad) { return ppad <= 64 ? 2 : 1; }
+size_t hess_f16_default_chunk_bytes() { return kF16ChunkBytes; }
 
 // Contract the trials [t0, t0 + Pn) (Pn <= 192) of one system; the split arrays have `rows`
 // rows; col_isc and params as written by launch_f16_trial_split.

@@ -232,7 +232,7 @@ cudaError_t launch_hess_tc(const PointsDev& p, int32_t Pn, int32_t t0, int64_t a
                            cudaStream_t st);
 
 // Tensor-core split-FP16 contraction (hess_f16.cu).  chunk_bytes: trial-tile bytes of one j
-// chunk (0: the default, 24 MB).  launch_f16_trial_split turns u, y
+// chunk (0: the default, hess_f16_default_chunk_bytes(), 24 MB).  launch_f16_trial_split turns u, y
 // (FP64 [P][nk_pad]) into scaled FP16 hi / lo tiles [rows][2 nk_pad] (per stage of 16 j: 16 u
 // then 16 y), the global y balance factor (params[0] = 1/c_y, params[1] = c_y) and per-trial
 // factors (scale[t] = s_t, col_isc[t] = 1/s_t; colmax: 2 P scratch words).  launch_hess_f16
@@ -243,6 +243,7 @@ cudaError_t launch_f16_trial_split(const double* u, const double* y, int32_t P, 
                                    float* scale, double* col_isc, void* bh, void* bl,
                                    cudaStream_t st);
 int hess_f16_kinds_per_tile(int ppad);
+size_t hess_f16_default_chunk_bytes();
 // Batched split-FP16 contraction over a task table (one launch per padded width): tasks
 // (molecule, 128-row tile, kind) largest molecules first, taken from an atomic counter.
 size_t hess_f16_mol_bytes();
